@@ -1,0 +1,209 @@
+"""Template meshes and convex hulls for the synthetic workloads.
+
+A geometry carries the two representations the method attaches to every
+surface (Sec. IV-A): a mesh (vertices and edges) and the parameters of a
+smooth SDF primitive (Sec. IV-B).  For the four analytic primitives the mesh
+is a *unit template*: each vertex row is ``(u_x, u_y, u_z, s)`` and the
+library / oracle map it to a surface point from the primitive's dimensions
+(box and ellipsoid scale each axis, cylinder and capsule scale the radius and
+half-length).  For a convex hull the rows are the vertices themselves
+(``s = 0``) and the SDF parameters are the outward face planes
+``(n_x, n_y, n_z, o)``, with plane value ``n . y - o``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID, KIND_HULL = 0, 1, 2, 3, 4
+KIND_NAMES = {KIND_BOX: "box", KIND_CAPSULE: "capsule", KIND_CYLINDER: "cylinder",
+              KIND_ELLIPSOID: "ellipsoid", KIND_HULL: "hull"}
+
+
+@dataclasses.dataclass
+class Geometry:
+    kind: int
+    dims: np.ndarray          # (3,) float32, default dimensions
+    verts: np.ndarray         # (V, 4) float32 template rows
+    edges: np.ndarray         # (E, 2) int32 vertex indices
+    planes: np.ndarray        # (F, 4) float32, hull only (else shape (0, 4))
+
+    @property
+    def n_verts(self):
+        return int(self.verts.shape[0])
+
+    @property
+    def n_edges(self):
+        return int(self.edges.shape[0])
+
+    @property
+    def n_planes(self):
+        return int(self.planes.shape[0])
+
+
+def _edges_from_faces(faces):
+    es = set()
+    for f in faces:
+        m = len(f)
+        for i in range(m):
+            a, b = int(f[i]), int(f[(i + 1) % m])
+            es.add((min(a, b), max(a, b)))
+    return np.array(sorted(es), dtype=np.int32)
+
+
+def box_template():
+    """8 corners of the cube [-1, 1]^3 and its 12 edges."""
+    v = np.array([[x, y, z, 0.0] for x in (-1, 1) for y in (-1, 1) for z in (-1, 1)],
+                 dtype=np.float32)
+    e = []
+    for i in range(8):
+        for j in range(i + 1, 8):
+            if np.abs(v[i, :3] - v[j, :3]).sum() == 2.0:
+                e.append((i, j))
+    return v, np.array(e, dtype=np.int32)
+
+
+def cylinder_template(n=16):
+    """Two rings of ``n`` points on the unit cylinder rims (z = -1, +1)."""
+    th = 2 * np.pi * np.arange(n) / n
+    v = []
+    for z in (-1.0, 1.0):
+        for t in th:
+            v.append((np.cos(t), np.sin(t), z, 0.0))
+    e = []
+    for r in range(2):
+        for i in range(n):
+            e.append((r * n + i, r * n + (i + 1) % n))
+    for i in range(n):
+        e.append((i, n + i))
+    return np.array(v, dtype=np.float32), np.array(e, dtype=np.int32)
+
+
+def capsule_template(n=16, lats=(0.0, np.pi / 4)):
+    """Two hemispherical caps: rings at the given latitudes plus the poles.
+
+    Row ``(u, s)`` maps to ``r * u + s * h * z_hat`` (s = +-1 picks the cap).
+    """
+    th = 2 * np.pi * np.arange(n) / n
+    v, ring_ids = [], {}
+    for s in (-1.0, 1.0):
+        for li, lat in enumerate(lats):
+            ids = []
+            for t in th:
+                ids.append(len(v))
+                v.append((np.cos(lat) * np.cos(t), np.cos(lat) * np.sin(t), s * np.sin(lat), s))
+            ring_ids[(s, li)] = ids
+    poles = {}
+    for s in (-1.0, 1.0):
+        poles[s] = len(v)
+        v.append((0.0, 0.0, s, s))
+    e = []
+    for key, ids in ring_ids.items():
+        for i in range(n):
+            e.append((ids[i], ids[(i + 1) % n]))
+    for s in (-1.0, 1.0):
+        for li in range(len(lats) - 1):
+            a, b = ring_ids[(s, li)], ring_ids[(s, li + 1)]
+            for i in range(n):
+                e.append((a[i], b[i]))
+        top = ring_ids[(s, len(lats) - 1)]
+        for i in range(n):
+            e.append((top[i], poles[s]))
+    lo, hi = ring_ids[(-1.0, 0)], ring_ids[(1.0, 0)]
+    for i in range(n):
+        e.append((lo[i], hi[i]))
+    e = np.array([(min(a, b), max(a, b)) for a, b in e], dtype=np.int32)
+    return np.array(v, dtype=np.float32), e
+
+
+def icosphere_template(level=1):
+    """Subdivided icosahedron on the unit sphere (level 1: 42 vertices, 120 edges)."""
+    t = (1.0 + 5 ** 0.5) / 2.0
+    p = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t),
+         (0, -1, -t), (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    pts = [np.array(q, dtype=np.float64) / np.linalg.norm(q) for q in p]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+             (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+             (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        cache, nf = {}, []
+
+        def mid(a, b):
+            k = (min(a, b), max(a, b))
+            if k not in cache:
+                m = pts[a] + pts[b]
+                pts.append(m / np.linalg.norm(m))
+                cache[k] = len(pts) - 1
+            return cache[k]
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    v = np.zeros((len(pts), 4), dtype=np.float32)
+    v[:, :3] = np.array(pts)
+    return v, _edges_from_faces(faces)
+
+
+def hull_from_points(points):
+    """Convex hull of a point set: compact vertex list, unique edges, face planes.
+
+    Uses qhull (scipy).  Faces are the triangles qhull reports; each plane row
+    is ``(n, o)`` with unit outward normal ``n`` and offset ``o = n . p``.
+    """
+    from scipy.spatial import ConvexHull
+    pts = np.asarray(points, dtype=np.float64)
+    h = ConvexHull(pts)
+    vid = np.array(sorted(h.vertices))
+    remap = -np.ones(len(pts), dtype=np.int64)
+    remap[vid] = np.arange(len(vid))
+    faces = remap[h.simplices]
+    verts = np.zeros((len(vid), 4), dtype=np.float32)
+    verts[:, :3] = pts[vid]
+    edges = _edges_from_faces(faces)
+    eq = h.equations                       # n . x + off <= 0 inside
+    planes = np.zeros((len(eq), 4), dtype=np.float32)
+    planes[:, :3] = eq[:, :3]
+    planes[:, 3] = -eq[:, 3]
+    return Geometry(KIND_HULL, np.ones(3, dtype=np.float32), verts, edges, planes)
+
+
+_TEMPLATES = {}
+
+
+def primitive_geometry(kind, dims=(1.0, 1.0, 1.0)):
+    """Template geometry of an analytic primitive with default ``dims``."""
+    if kind not in _TEMPLATES:
+        if kind == KIND_BOX:
+            _TEMPLATES[kind] = box_template()
+        elif kind == KIND_CYLINDER:
+            _TEMPLATES[kind] = cylinder_template()
+        elif kind == KIND_CAPSULE:
+            _TEMPLATES[kind] = capsule_template()
+        elif kind == KIND_ELLIPSOID:
+            _TEMPLATES[kind] = icosphere_template(1)
+        else:
+            raise ValueError(kind)
+    v, e = _TEMPLATES[kind]
+    return Geometry(kind, np.asarray(dims, dtype=np.float32), v.copy(), e.copy(),
+                    np.zeros((0, 4), dtype=np.float32))
+
+
+def support(geom: Geometry, dims, u):
+    """Support function max_{x in S} u . x of the exact (unsmoothed) shape.
+
+    ``u``: (..., 3) directions in the shape's local frame.  Used only to place
+    bodies at a chosen projected overlap; it is not part of the method.
+    """
+    u = np.asarray(u, dtype=np.float64)
+    d = np.asarray(dims, dtype=np.float64)
+    if geom.kind == KIND_BOX:
+        return np.abs(u) @ d
+    if geom.kind == KIND_HULL:
+        return (u @ geom.verts[:, :3].astype(np.float64).T).max(-1)
+    if geom.kind == KIND_CAPSULE:
+        return d[1] * np.abs(u[..., 2]) + d[0] * np.linalg.norm(u, axis=-1)
+    if geom.kind == KIND_CYLINDER:
+        return d[1] * np.abs(u[..., 2]) + d[0] * np.hypot(u[..., 0], u[..., 1])
+    if geom.kind == KIND_ELLIPSOID:
+        return np.linalg.norm(u * d, axis=-1)
+    raise ValueError(geom.kind)

@@ -1,0 +1,186 @@
+"""Seeded workload generators with the shapes of the paper's benchmark settings.
+
+Every workload is a batch of independent body pairs (A, B).  Pair ``i`` names
+two geometries, carries both rigid poses as ``(qw, qx, qy, qz, tx, ty, tz)``
+per body, the per-body primitive dimensions and the smoothing ``tau``.
+
+Placement: A's orientation and B's are uniform random (Shoemake), ``t_A`` is
+uniform in ``[-1, 1]^3``; a random unit direction ``u`` is drawn and B is put
+along ``u`` so that the two shapes' projections on ``u`` overlap by ``delta``
+(exact support functions).  The true penetration depth is then in
+``[0, delta]``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+from .geometry import (KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID,
+                       Geometry, hull_from_points, primitive_geometry, support)
+
+SEED_BASE = 20261203
+PRIMITIVE_KINDS = (KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    geoms: list                 # list[Geometry]
+    pair_geoms: np.ndarray      # (n, 2) int32
+    poses: np.ndarray           # (n, 14) float32
+    dims: np.ndarray            # (n, 6) float32
+    tau: np.ndarray             # (n,) float32
+    K: int = 8
+
+    @property
+    def n_pairs(self):
+        return int(self.pair_geoms.shape[0])
+
+    def subset(self, idx):
+        idx = np.asarray(idx)
+        return Workload(self.name + "[sub]", self.geoms, self.pair_geoms[idx].copy(),
+                        self.poses[idx].copy(), self.dims[idx].copy(), self.tau[idx].copy(), self.K)
+
+    def pair_counts(self):
+        """(V_A, V_B, E_A, E_B) per pair."""
+        nv = np.array([g.n_verts for g in self.geoms])
+        ne = np.array([g.n_edges for g in self.geoms])
+        a, b = self.pair_geoms[:, 0], self.pair_geoms[:, 1]
+        return nv[a], nv[b], ne[a], ne[b]
+
+
+def random_quaternions(rng, n):
+    """Uniform random unit quaternions (Shoemake), layout (w, x, y, z)."""
+    u1, u2, u3 = rng.random(n), rng.random(n), rng.random(n)
+    a, b = np.sqrt(1 - u1), np.sqrt(u1)
+    q = np.stack([b * np.cos(2 * np.pi * u3), a * np.sin(2 * np.pi * u2),
+                  a * np.cos(2 * np.pi * u2), b * np.sin(2 * np.pi * u3)], axis=1)
+    return q
+
+
+def _rotmat(q):
+    w, x, y, z = (q / np.linalg.norm(q, axis=-1, keepdims=True)).T
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], -2)
+
+
+def _unit_vectors(rng, n):
+    g = rng.normal(size=(n, 3))
+    return g / np.linalg.norm(g, axis=1, keepdims=True)
+
+
+def _ball_points(rng, n):
+    return _unit_vectors(rng, n) * rng.random(n)[:, None] ** (1.0 / 3.0)
+
+
+def _place(rng, geoms, pair_geoms, dims, delta):
+    n = pair_geoms.shape[0]
+    qa, qb = random_quaternions(rng, n), random_quaternions(rng, n)
+    ta = rng.uniform(-1.0, 1.0, size=(n, 3))
+    u = _unit_vectors(rng, n)
+    Ra, Rb = _rotmat(qa), _rotmat(qb)
+    tb = np.empty_like(ta)
+    for i in range(n):
+        ga, gb = geoms[pair_geoms[i, 0]], geoms[pair_geoms[i, 1]]
+        ha = support(ga, dims[i, :3], Ra[i].T @ u[i])
+        hb = support(gb, dims[i, 3:], Rb[i].T @ (-u[i]))
+        tb[i] = ta[i] + (ha + hb - delta[i]) * u[i]
+    poses = np.concatenate([qa, ta, qb, tb], axis=1).astype(np.float32)
+    return poses
+
+
+def config_box_box(n=1024, seed=SEED_BASE + 1, tau=1e-2, half=0.5):
+    """Two cubes of half-extent 0.5 at ``n`` seeded relative poses."""
+    rng = np.random.default_rng(seed)
+    geoms = [primitive_geometry(KIND_BOX, (half, half, half))]
+    pg = np.zeros((n, 2), dtype=np.int32)
+    dims = np.full((n, 6), half, dtype=np.float32)
+    delta = rng.uniform(0.0, 0.1, n)
+    poses = _place(rng, geoms, pg, dims, delta)
+    return Workload("box-box", geoms, pg, poses, dims, np.full(n, tau, np.float32))
+
+
+def _primitive_dims(rng, kind):
+    d = rng.uniform(0.2, 1.0, 3)
+    if kind in (KIND_CAPSULE, KIND_CYLINDER):
+        d[2] = 0.0
+    return d
+
+
+def config_hull_vs_primitive(n=4096, seed=SEED_BASE + 2, n_points=(8, 64), log_uniform=False,
+                             taus=(1e-2,), name="hull-vs-primitive"):
+    """Hull of N points uniform in the unit ball (A) against a random primitive (B)."""
+    rng = np.random.default_rng(seed)
+    prims = {k: primitive_geometry(k) for k in PRIMITIVE_KINDS}
+    geoms = [prims[k] for k in PRIMITIVE_KINDS]
+    pg = np.zeros((n, 2), dtype=np.int32)
+    dims = np.zeros((n, 6), dtype=np.float32)
+    lo, hi = n_points
+    for i in range(n):
+        if log_uniform:
+            m = int(np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1)))))
+            m = min(max(m, lo), hi)
+        else:
+            m = int(rng.integers(lo, hi + 1))
+        g = hull_from_points(_ball_points(rng, m))
+        geoms.append(g)
+        k = PRIMITIVE_KINDS[int(rng.integers(0, 4))]
+        pg[i] = (len(geoms) - 1, PRIMITIVE_KINDS.index(k))
+        dims[i, :3] = 1.0
+        dims[i, 3:] = _primitive_dims(rng, k)
+    delta = rng.uniform(0.0, 0.1, n)
+    poses = _place(rng, geoms, pg, dims, delta)
+    tau = np.asarray(taus, dtype=np.float32)[rng.integers(0, len(taus), n)]
+    return Workload(name, geoms, pg, poses, dims, tau.astype(np.float32))
+
+
+def config_box_vs_sphere_hull(n=1024, seed=SEED_BASE + 3, n_sphere=32, tau=1e-2):
+    """Box (dims U[0.2, 1]) against the hull of 32 points uniform on the unit sphere."""
+    rng = np.random.default_rng(seed)
+    geoms = [primitive_geometry(KIND_BOX)]
+    pg = np.zeros((n, 2), dtype=np.int32)
+    dims = np.ones((n, 6), dtype=np.float32)
+    for i in range(n):
+        geoms.append(hull_from_points(_unit_vectors(rng, n_sphere)))
+        pg[i] = (0, len(geoms) - 1)
+        dims[i, :3] = rng.uniform(0.2, 1.0, 3)
+    delta = rng.uniform(0.0, 0.1, n)
+    poses = _place(rng, geoms, pg, dims, delta)
+    return Workload("box-vs-hull32", geoms, pg, poses, dims, np.full(n, tau, np.float32))
+
+
+def config_mixed(n=65536, seed=SEED_BASE + 4):
+    """Hulls of 8..256 points (log-uniform) against mixed primitives, tau in {1e-3, 1e-2, 1e-1}."""
+    return config_hull_vs_primitive(n=n, seed=seed, n_points=(8, 256), log_uniform=True,
+                                    taus=(1e-3, 1e-2, 1e-1), name="mixed-uneven")
+
+
+def serving_trace(seed=SEED_BASE + 5, rate=2000.0, duration=10.0, max_pairs=8192):
+    """Poisson arrivals; request sizes log-uniform in [1, max_pairs]; fwd or fwd+bwd 50/50.
+
+    Returns a list of ``(arrival_s, n_pairs, with_backward)``.
+    """
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        m = int(np.floor(np.exp(rng.uniform(0.0, np.log(max_pairs + 1)))))
+        out.append((t, max(1, min(m, max_pairs)), bool(rng.integers(0, 2))))
+    return out
+
+
+def make_config(idx, n=None):
+    """Workload of one of the benchmark settings by index (1..4), optionally resized."""
+    if idx == 1:
+        return config_box_box(n or 1024)
+    if idx == 2:
+        return config_hull_vs_primitive(n or 4096)
+    if idx == 3:
+        return config_box_vs_sphere_hull(n or 1024)
+    if idx == 4:
+        return config_mixed(n or 65536)
+    raise ValueError(idx)
