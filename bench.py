@@ -1,0 +1,286 @@
+"""Throughput benchmark of the smooth contact-manifold library on GB300.
+
+Workload (default): 4096 independent pairs, each the convex hull of 8..64 points
+uniform in the unit ball against a random smooth primitive (box, capsule,
+cylinder, ellipsoid; dims U[0.2, 1]), tau = 1e-2, penetration U[0, 0.1], K = 8,
+FP32.  A step is one forward manifold over the whole batch (and, with
+``--mode fwdbwd``, also the backward).  Inputs are resident in HBM; L2 is
+flushed (512 MB write) between timed steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "hull(8-64 pts) vs primitive, 4096 pairs, tau=1e-2, K=8"
+
+
+# ----------------------------------------------------------------- algorithmic work
+# MUFU (transcendental) operations the method needs, counted once per evaluation
+# as the definition requires: exp / log / reciprocal / sqrt / rsqrt each 1.
+def _sdf_mufu(kind, n_planes):
+    if kind in (synth.KIND_BOX, synth.KIND_HULL):
+        F = 6 if kind == synth.KIND_BOX else n_planes
+        return F + 2            # F exps, one log, one reciprocal (value + gradient of the LSE)
+    if kind == synth.KIND_ELLIPSOID:
+        return 2                # |y| and f^-1/2
+    if kind == synth.KIND_CAPSULE:
+        return 9                # soft clip (2 exp + 2 log), |w|, its inverse, two sigmoids (2 exp + 2 rcp)
+    if kind == synth.KIND_CYLINDER:
+        return 7                # rho, 1/rho, 3-term LSE (3 exp, log, rcp)
+    raise ValueError(kind)
+
+
+QP_MUFU = 32        # 3 reciprocals, 4 soft clips (16), soft argmin (4 exp + rcp), 4 sigmoids (8)
+EE_EXTRA = 2 + 2 + 4 + 4 + 2 + 4 + 2   # dbar, nbar, 2 soft signs, 2 pen, cl, nn (2 row/col exps + 2 values), SoftSort 2
+VS_EXTRA = 1 + 2 + 1                   # normal, activity sigmoid, SoftSort
+
+
+def mufu_ops_per_pair(w, flags=0):
+    nvA, nvB, neA, neB = w.pair_counts()
+    out = np.zeros(w.n_pairs)
+    for i in range(w.n_pairs):
+        ga, gb = w.geoms[w.pair_geoms[i, 0]], w.geoms[w.pair_geoms[i, 1]]
+        sa, sb = _sdf_mufu(ga.kind, ga.n_planes), _sdf_mufu(gb.kind, gb.n_planes)
+        vs = nvA[i] * (sb + VS_EXTRA) + (0 if flags & 2 else nvB[i] * (sa + VS_EXTRA))
+        ee = 0 if flags & 3 else neA[i] * neB[i] * (QP_MUFU + EE_EXTRA + 2 * sa + 2 * sb)
+        out[i] = vs + ee
+    return out
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows for j in range(4) if r[3 + j] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------- reference arm
+def cpu_oracle_rate(w, budget_s=15.0, max_pairs=None):
+    """Pairs/s of the FP64 oracle (as it stands) on the first pairs of ``w`` within ``budget_s``."""
+    import torch
+    import oracle
+    done, t0 = 0, time.perf_counter()
+    limit = w.n_pairs if max_pairs is None else min(max_pairs, w.n_pairs)
+    while done < limit and time.perf_counter() - t0 < budget_s:
+        oracle.batch_manifold(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, idx=[done])
+        done += 1
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, torch.get_num_threads()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = synth.make_config(2)
+    steps = []
+    per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, budget_s=per_step_budget / 4)
+    total_pairs, total_t = 0, 0.0
+    for _ in range(args.steps):
+        r, n, dt, cores = cpu_oracle_rate(w, budget_s=per_step_budget)
+        steps.append(dt)
+        total_pairs += n
+        total_t += dt
+    value = total_pairs / total_t
+    line = {"impl": "reference", "metric": "contact pairs/s (forward manifold)", "value": value,
+            "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{total_pairs} pairs of the workload, in order, "
+                                       f"{per_step_budget:.1f} s per step"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--pairs", type=int, default=4096, help="pairs per GPU (profiling uses fewer)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2602_20304_gb300 import api
+    from paper_2602_20304_gb300.engine import Engine, workload_tensors
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # each rank owns an independent replica of the workload (weak scaling, no collective)
+    w = synth.config_hull_vs_primitive(n=args.pairs, seed=synth.SEED_BASE + 2 + 1000 * rank)
+    eng = Engine(local)
+    ids = eng.add_geometries(w.geoms)
+    pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+    params = eng.params()
+    out = torch.empty((w.n_pairs, params.K, 8), device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 512 MB > L2
+
+    for _ in range(max(3, args.warmup)):
+        eng.forward(pg, poses, dims, tau, params, out)
+    torch.cuda.synchronize()
+    eng.check()
+
+    # ---- device-resident timing, one kernel launch per step, L2 flushed in between
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            evs[s][0].record(stream)
+            eng.forward(pg, poses, dims, tau, params, out)
+            evs[s][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * w.n_pairs * args.steps / (total_ms * 1e-3)
+
+    # ---- end to end through the public API: pinned host inputs -> device -> host result
+    hp = [t.cpu().pin_memory() for t in (pg, poses, dims, tau)]
+    hout = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+    dev_in = [torch.empty_like(t) for t in (pg, poses, dims, tau)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for s in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        for d, h in zip(dev_in, hp):
+            d.copy_(h, non_blocking=True)
+        eng.forward(*dev_in, params=params, out=out)
+        hout.copy_(out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    barrier()
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = sum(t.numel() * t.element_size() for t in hp)
+    d2h = hout.numel() * hout.element_size()
+    e2e = {"value": world * w.n_pairs * args.steps / (e2e_ms * 1e-3), "unit": "pairs/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the (single) kernel: MUFU work per launch / launch duration
+    fma_peak, mufu_peak = api.cm_measure_pipe_peaks(local)
+    ops = float(mufu_ops_per_pair(w).sum())
+    kernel_s = float(np.mean(step_ms)) * 1e-3
+    achieved = ops / kernel_s
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": mufu_peak / 1e9, "unit": "Gop/s (MUFU)",
+            "frac": achieved / mufu_peak, "traffic": None,
+            "peak_source": "measured ex2.approx throughput (cm_measure_pipe_peaks)",
+            "fma_peak_tflops": fma_peak / 1e12}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        r, n, dt, cores = cpu_oracle_rate(w, budget_s=args.cpu_seconds)
+        cpu = {"value": r, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {n} pairs of the workload ({dt:.1f} s)"}
+
+    line = {"metric": "contact pairs/s (forward manifold)", "value": value, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_gpu": w.n_pairs, "parallelism": f"replicas x{world}",
+                       "l2": "flushed (512 MB write) between timed steps"},
+            "gpu_launches": args.steps, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * contact_manifold.h -- C ABI of the GB300 (sm_103a) smooth contact-manifold library.
+ *
+ * The library evaluates, for many independent body pairs at once, the smoothly
+ * differentiable contact manifold of "Smoothly Differentiable and Efficiently
+ * Vectorizable Contact Manifold Generation" (arXiv 2602.20304): the map
+ * g_{1,2}(pose_1, pose_2) -> {(p_k, d_k, n_k)}_{k=1..K} of Sec. IV-A, built from
+ *   - vertex-SDF contacts (Sec. IV-C) of every vertex of each body against the
+ *     smooth analytic SDF primitive of the other (Sec. IV-B),
+ *   - edge-edge contacts (Sec. IV-D) of every edge pair: the regularised 2x2
+ *     box QP solved by the smoothed analytic active set, witness points,
+ *     signed distance and normal, and the con/pen/nn/cl activity indicators,
+ *   - a SoftSort top-K reduction (Sec. III) of all candidates to K points.
+ * Each output point carries a fourth quantity beside (p, d, n): its soft
+ * activity weight w.  Rows are laid out (p_x, p_y, p_z, d, n_x, n_y, n_z, w).
+ *
+ * Conventions shared by every call:
+ *   - All pointers named "device" are CUDA device pointers owned by the caller;
+ *     the library never frees or retains them past the call (asynchronous
+ *     calls read them until the work queued on `stream` completes).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Every compute call is asynchronous on that stream.
+ *   - No call aborts the process.  Errors are returned as cm_status and the
+ *     message of the last failing call on the calling thread is available from
+ *     cm_last_error().  Bad geometry ids found on the device do not fault: the
+ *     kernel skips the pair, writes NaN to its output rows and raises a sticky
+ *     device flag that cm_check_device_error() reports.
+ *   - Floating point is FP32 throughout.
+ */
+#ifndef CONTACT_MANIFOLD_H
+#define CONTACT_MANIFOLD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Compile-time limits (validated at cm_create_geometry / on every call). */
+#define CM_MAX_K 16        /* contact points per pair */
+#define CM_MAX_VERTS 256   /* mesh vertices per geometry */
+#define CM_MAX_EDGES 768   /* mesh edges per geometry */
+#define CM_MAX_PLANES 512  /* convex-polyhedron planes per geometry */
+
+typedef enum {
+  CM_OK = 0,
+  CM_ERR_INVALID_ARG = 1, /* a size, pointer, id or parameter is out of range */
+  CM_ERR_OOM = 2,         /* a device or host allocation failed */
+  CM_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+  CM_ERR_ADMISSION = 4,   /* a request does not fit the context's HBM budget */
+  CM_ERR_TIMEOUT = 5,     /* cm_wait deadline passed before the request finished */
+  CM_ERR_NOT_FOUND = 6,   /* unknown geometry id or request ticket */
+  CM_ERR_DEVICE = 7       /* a kernel raised the sticky device error flag */
+} cm_status;
+
+/* SDF primitive families (Sec. IV-B).  BOX and HULL are convex polyhedra
+ * (LSE over planes, Sec. IV-B2); ELLIPSOID is the superquadric with
+ * eps1 = eps2 = 1 (Sec. IV-B1); CAPSULE and CYLINDER are smooth readings of the
+ * usual primitives (soft-clipped segment distance; LSE of radial and cap
+ * distances).  dims: BOX (hx, hy, hz); CAPSULE (r, h, -); CYLINDER (r, h, -);
+ * ELLIPSOID (a, b, c); HULL unused. */
+enum { CM_BOX = 0, CM_CAPSULE = 1, CM_CYLINDER = 2, CM_ELLIPSOID = 3, CM_HULL = 4 };
+
+/* Flags of cm_params.flags: the simplifications of Supplement A. */
+enum {
+  CM_FLAG_NO_EE = 1,     /* vertex-SDF contacts only ("Ours-NE") */
+  CM_FLAG_ONE_SIDED = 2  /* only A's vertices against B's SDF ("Ours-NE-S"); implies NO_EE */
+};
+
+typedef struct cm_context cm_context;
+
+/* A surface in its two representations (Sec. IV-A): mesh and SDF parameters.
+ * verts: host, n_verts x 4 floats.  For the analytic primitives each row is a
+ *   unit template (u_x, u_y, u_z, s) that maps to a local vertex from the dims
+ *   in use: BOX/ELLIPSOID (d0 u_x, d1 u_y, d2 u_z); CYLINDER (r u_x, r u_y, h u_z);
+ *   CAPSULE (r u_x, r u_y, r u_z + s h).  For HULL the rows are the vertices.
+ * edges: host, n_edges x 2 int32 vertex indices.
+ * planes: host, HULL only, n_planes x 4 floats (n_x, n_y, n_z, o) with unit
+ *   outward n; the plane value at y is n . y - o.  NULL / 0 for other kinds.
+ * The library copies everything; the caller may free its arrays on return. */
+typedef struct {
+  int32_t kind;
+  float dims[3];
+  int32_t n_verts;
+  const float* verts;
+  int32_t n_edges;
+  const int32_t* edges;
+  int32_t n_planes;
+  const float* planes;
+} cm_geometry_desc;
+
+/* Method parameters.  tau: smoothing of the SDF LSE, soft sign, penetration,
+ * nearest-neighbour, clashing and SoftSort operators (used when the per-pair
+ * tau pointer is NULL).  w_reg: L2 regulariser of the E-E QP (Sec. IV-D2).
+ * eps_clip / eps_min / eps_comp: smoothing of the soft clip, soft argmin and
+ * soft comparisons inside the 2x2 box-QP solve.  K: contact points (1..16). */
+typedef struct {
+  float tau;
+  float w_reg;
+  float eps_clip;
+  float eps_min;
+  float eps_comp;
+  int32_t K;
+  int32_t flags;
+} cm_params;
+
+/* Fills the defaults: tau 1e-2, w_reg 1e-2, eps_* 0.1, K 8, flags 0. */
+void cm_default_params(cm_params* p);
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the device
+ * memory the context may hold for serving requests (0 = no bound).
+ * Returns CM_ERR_CUDA if the device cannot be used. */
+cm_status cm_create_context(int device, size_t hbm_budget_bytes, cm_context** out);
+
+/* Waits for the context's work, frees everything it owns.  NULL is ignored. */
+void cm_destroy_context(cm_context* ctx);
+
+/* Registers a geometry and returns its id (0, 1, 2, ... in creation order).
+ * Validates sizes against the CM_MAX_* limits, finite values, edge indices,
+ * dims > 0 for primitives and n_planes >= 4 for hulls.  The packed device copy
+ * is uploaded lazily before the next compute call (or by cm_sync_geometry). */
+cm_status cm_create_geometry(cm_context* ctx, const cm_geometry_desc* desc, int32_t* geom_id);
+
+/* Uploads pending geometry now (synchronously).  Call before capturing a CUDA
+ * graph that launches compute calls, so that the capture contains no copies. */
+cm_status cm_sync_geometry(cm_context* ctx);
+
+/* Number of registered geometries. */
+int32_t cm_num_geometries(const cm_context* ctx);
+
+/* Forward manifold of n_pairs independent pairs (Sec. IV-A's g_{1,2} per pair).
+ * pair_geoms: device, n_pairs x 2 int32 geometry ids (A, B).
+ * poses: device, n_pairs x 14 floats (qw, qx, qy, qz, tx, ty, tz) of A then B;
+ *   the rotation is that of q / |q|.
+ * dims: device, n_pairs x 6 floats (dims of A then B) or NULL for each
+ *   geometry's registered dims.
+ * tau: device, n_pairs floats or NULL for params->tau.
+ * out: device, n_pairs x K x 8 floats (p, d, n, w) in world coordinates.
+ * n_pairs == 0 is a no-op. */
+cm_status cm_contact_manifold_fwd(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms,
+                                  const float* poses, const float* dims, const float* tau,
+                                  const cm_params* params, float* out, void* stream);
+
+/* Reads (and clears) the sticky device error flag; synchronises the context's
+ * default work.  Returns CM_ERR_DEVICE with a message naming the first bad pair
+ * when a kernel met an invalid geometry id. */
+cm_status cm_check_device_error(cm_context* ctx);
+
+/* Measures the device's FP32 FMA throughput (flop/s, 2 per FMA) and MUFU ex2
+ * throughput (op/s) with two short synthetic kernels on `device`; used as the
+ * denominators of the arithmetic roofline.  Not part of the paper's method. */
+cm_status cm_measure_pipe_peaks(int device, double* fma_flops, double* mufu_ops);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* cm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CONTACT_MANIFOLD_H */

@@ -1,0 +1,173 @@
+"""Thin ctypes binding of the C ABI in ``include/contact_manifold.h``.
+
+Functions keep the C names and only marshal arguments: torch tensors are
+passed as raw device pointers, the stream as the torch stream's handle.  Every
+step of the manifold runs in the CUDA library; there is no Python or CPU
+compute path, and importing this module fails if the library is not built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libcontact_manifold.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        f"{_LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = ctypes.CDLL(_LIB_PATH)
+
+CM_OK, CM_ERR_INVALID_ARG, CM_ERR_OOM, CM_ERR_CUDA = 0, 1, 2, 3
+CM_ERR_ADMISSION, CM_ERR_TIMEOUT, CM_ERR_NOT_FOUND, CM_ERR_DEVICE = 4, 5, 6, 7
+CM_BOX, CM_CAPSULE, CM_CYLINDER, CM_ELLIPSOID, CM_HULL = 0, 1, 2, 3, 4
+CM_FLAG_NO_EE, CM_FLAG_ONE_SIDED = 1, 2
+CM_MAX_K = 16
+
+
+class cm_geometry_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dims", ctypes.c_float * 3),
+                ("n_verts", ctypes.c_int32), ("verts", ctypes.POINTER(ctypes.c_float)),
+                ("n_edges", ctypes.c_int32), ("edges", ctypes.POINTER(ctypes.c_int32)),
+                ("n_planes", ctypes.c_int32), ("planes", ctypes.POINTER(ctypes.c_float))]
+
+
+class cm_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_float), ("w_reg", ctypes.c_float), ("eps_clip", ctypes.c_float),
+                ("eps_min", ctypes.c_float), ("eps_comp", ctypes.c_float), ("K", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_SIGS = {
+    "cm_default_params": (None, [ctypes.POINTER(cm_params)]),
+    "cm_last_error": (ctypes.c_char_p, []),
+    "cm_create_context": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "cm_destroy_context": (None, [_vp]),
+    "cm_create_geometry": (ctypes.c_int, [_vp, ctypes.POINTER(cm_geometry_desc),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "cm_sync_geometry": (ctypes.c_int, [_vp]),
+    "cm_num_geometries": (ctypes.c_int32, [_vp]),
+    "cm_check_device_error": (ctypes.c_int, [_vp]),
+    "cm_contact_manifold_fwd": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                               ctypes.POINTER(cm_params), _vp, _vp]),
+    "cm_measure_pipe_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double)]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class CMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def _check(status):
+    if status != CM_OK:
+        raise CMError(status, cm_last_error())
+
+
+def cm_last_error() -> str:
+    return _lib.cm_last_error().decode()
+
+
+def cm_default_params(**overrides) -> cm_params:
+    p = cm_params()
+    _lib.cm_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def cm_create_context(device: int = 0, hbm_budget_bytes: int = 0):
+    h = _vp()
+    _check(_lib.cm_create_context(device, hbm_budget_bytes, ctypes.byref(h)))
+    return h
+
+
+def cm_destroy_context(ctx) -> None:
+    _lib.cm_destroy_context(ctx)
+
+
+def cm_create_geometry(ctx, kind, dims, verts, edges, planes=None) -> int:
+    v = np.ascontiguousarray(verts, dtype=np.float32)
+    e = np.ascontiguousarray(edges, dtype=np.int32)
+    p = None if planes is None or len(planes) == 0 else np.ascontiguousarray(planes, dtype=np.float32)
+    d = cm_geometry_desc()
+    d.kind = int(kind)
+    for i in range(3):
+        d.dims[i] = float(dims[i])
+    d.n_verts = int(v.shape[0])
+    d.verts = v.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    d.n_edges = int(e.shape[0])
+    d.edges = e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    d.n_planes = 0 if p is None else int(p.shape[0])
+    d.planes = None if p is None else p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    gid = ctypes.c_int32()
+    _check(_lib.cm_create_geometry(ctx, ctypes.byref(d), ctypes.byref(gid)))
+    return gid.value
+
+
+def cm_sync_geometry(ctx) -> None:
+    _check(_lib.cm_sync_geometry(ctx))
+
+
+def cm_num_geometries(ctx) -> int:
+    return int(_lib.cm_num_geometries(ctx))
+
+
+def cm_check_device_error(ctx) -> None:
+    _check(_lib.cm_check_device_error(ctx))
+
+
+def _ptr(t):
+    return None if t is None else _vp(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return _vp(s.cuda_stream)
+
+
+def _check_tensor(t, name, dtype, shape0):
+    import torch
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if t.shape[0] != shape0:
+        raise ValueError(f"{name} has {t.shape[0]} rows, expected {shape0}")
+    del torch
+
+
+def cm_contact_manifold_fwd(ctx, pair_geoms, poses, dims, tau, params, out, stream=None) -> None:
+    """Launch the forward manifold on torch CUDA tensors (see the C header for layouts)."""
+    import torch
+    n = int(pair_geoms.shape[0])
+    _check_tensor(pair_geoms, "pair_geoms", torch.int32, n)
+    _check_tensor(poses, "poses", torch.float32, n)
+    _check_tensor(dims, "dims", torch.float32, n)
+    _check_tensor(tau, "tau", torch.float32, n)
+    _check_tensor(out, "out", torch.float32, n)
+    _check(_lib.cm_contact_manifold_fwd(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau),
+                                        ctypes.byref(params), _ptr(out), _stream_handle(stream)))
+
+
+def cm_measure_pipe_peaks(device: int = 0):
+    """(FP32 FMA flop/s, MUFU ex2 op/s) measured on ``device``."""
+    f, m = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.cm_measure_pipe_peaks(device, ctypes.byref(f), ctypes.byref(m)))
+    return f.value, m.value
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects the library to export."""
+    return sorted(_SIGS)

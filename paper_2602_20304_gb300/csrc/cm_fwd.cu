@@ -1,0 +1,156 @@
+// cm_fwd.cu -- forward contact-manifold kernel (sm_103a).
+//
+// One CTA per body pair at a time (a persistent grid walks a work queue of
+// pairs).  Per pair:
+//   1. stage both meshes and A's planes/B's planes in shared memory, A moved
+//      into B's frame;
+//   2. vertex-SDF candidates (Sec. IV-C), warp-strided, streamed into the
+//      warp's SoftSort top-K state;
+//   3. E-E pass 1: witness QP of every edge pair -> unsigned distance dbar_kl,
+//      kept in the CTA's scratch slice (global memory, L2-resident);
+//   4. soft row and column minima L = m - tau log sum exp(-(dbar - m)/tau) of
+//      the distance matrix (nn indicators of Sec. IV-D3, Eq. nn_check);
+//   5. E-E pass 2: witness QP again, four SDF evaluations, sign, pen, nn, cl and
+//      activity -> two candidates per edge pair, streamed into the warp state;
+//   6. merge the warps' states and write the K rows, rotated back to world.
+#include "cm_pair.cuh"
+
+namespace cm {
+
+__device__ __forceinline__ int next_pair(const FwdArgs& a, int& slot_iter) {
+  if (a.work_counter) {
+    __shared__ int next;
+    __syncthreads();
+    if (threadIdx.x == 0) next = atomicAdd(a.work_counter, 1);
+    __syncthreads();
+    int i = next;
+    if (i >= a.n_pairs) return -1;
+    return a.order ? a.order[i] : i;
+  }
+  int i = blockIdx.x + slot_iter * gridDim.x;
+  ++slot_iter;
+  if (i >= a.n_pairs) return -1;
+  return a.order ? a.order[i] : i;
+}
+
+__global__ void __launch_bounds__(256) cm_fwd_kernel(const FwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ PairShared ps;
+  const PairSmem sm = carve(smem_raw, a.sm);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int K = a.p.K;
+  float* D = a.scratch + (int64_t)blockIdx.x * a.scratch_stride;
+  int it = 0;
+  for (;;) {
+    const int pi = next_pair(a, it);
+    if (pi < 0) break;
+    __syncthreads();
+    if (threadIdx.x == 0) pair_setup(a, pi, ps);
+    __syncthreads();
+    if (ps.bad) {
+      if (threadIdx.x == 0) atomicCAS(a.err, 0, pi + 1);
+      for (int i = threadIdx.x; i < K * 8; i += blockDim.x) a.out[(size_t)pi * K * 8 + i] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    pair_stage(a, pi, ps, sm);
+    __syncthreads();
+    const PairBodies bb = pair_bodies(ps, sm);
+    const float k2 = ps.k2;
+
+    WarpTopK st;
+    wtk_init(st);
+    float y[8], y2[8];
+
+    // ---- vertex-SDF candidates
+    const bool one_sided = (a.p.flags & 2) != 0;
+    const bool no_ee = one_sided || (a.p.flags & 1) != 0;
+    const int nvs = one_sided ? ps.nvA : ps.nvA + ps.nvB;
+    for (int base = warp * 32; base < nvs; base += nwarps * 32) {
+      const int c = base + lane;
+      const bool valid = c < nvs;
+      float s = 0.f;
+      if (valid) s = vs_candidate(ps, sm, bb, c, y);
+      wtk_push(st, valid, s, y, K, k2);
+    }
+
+    if (!no_ee) {
+      const int neA = ps.neA, neB = ps.neB, nee = neA * neB;
+      // ---- E-E pass 1: unsigned distances
+      for (int i = threadIdx.x; i < nee; i += blockDim.x) {
+        const int k = i / neB, l = i - k * neB;
+        Witness w = ee_witness(edge_pair(sm, k, l), a.p);
+        D[i] = w.dbar;
+      }
+      __syncthreads();
+      // ---- soft row minima (warp per row) and column minima (thread per column)
+      for (int k = warp; k < neA; k += nwarps) {
+        float m = 3.0e38f;
+        for (int l = lane; l < neB; l += 32) m = fminf(m, D[k * neB + l]);
+        m = warp_min(m);
+        float S = 0.f;
+        for (int l = lane; l < neB; l += 32) S += ex2((m - D[k * neB + l]) * k2);
+        S = warp_sum(S);
+        if (lane == 0) sm.rowL[k] = m - ps.tau * kLn2 * lg2(S);
+      }
+      for (int l = threadIdx.x; l < neB; l += blockDim.x) {
+        float m = 3.0e38f;
+        for (int k = 0; k < neA; ++k) m = fminf(m, D[k * neB + l]);
+        float S = 0.f;
+        for (int k = 0; k < neA; ++k) S += ex2((m - D[k * neB + l]) * k2);
+        sm.colL[l] = m - ps.tau * kLn2 * lg2(S);
+      }
+      __syncthreads();
+      // ---- E-E pass 2: candidates
+      for (int base = warp * 32; base < nee; base += nwarps * 32) {
+        const int i = base + lane;
+        const bool valid = i < nee;
+        float s1 = 0.f, s2 = 0.f;
+        if (valid) {
+          const int k = i / neB, l = i - k * neB;
+          const EdgePair ep = edge_pair(sm, k, l);
+          Witness w = ee_witness(ep, a.p);
+          ee_candidates(ps, sm, bb, ep, w, sm.rowL[k], sm.colL[l], y, y2, s1, s2);
+        }
+        wtk_push(st, valid, s1, y, K, k2);
+        wtk_push(st, valid, s2, y2, K, k2);
+      }
+    }
+
+    // ---- merge warps and write the K rows
+    float* ws = sm.warp + warp * kWarpStateFloats;
+    wtk_store(st, ws, K);
+    __syncthreads();
+    if (warp == 0) {
+      for (int w = 1; w < nwarps; ++w) wtk_merge(st, sm.warp + w * kWarpStateFloats, K, k2);
+      wtk_finish(st, K, k2, y);
+      if (lane < K) {
+        V3 p = mul(ps.RB, v3(y[0], y[1], y[2])) + ps.tB;
+        V3 n = mul(ps.RB, v3(y[4], y[5], y[6]));
+        float* o = a.out + ((size_t)pi * K + lane) * 8;
+        o[0] = p.x; o[1] = p.y; o[2] = p.z; o[3] = y[3];
+        o[4] = n.x; o[5] = n.y; o[6] = n.z; o[7] = y[7];
+      }
+    }
+  }
+}
+
+cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(cm_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  cm_fwd_kernel<<<grid, block, a.sm.total, s>>>(a);
+  return cudaGetLastError();
+}
+
+int fwd_max_blocks_per_sm(int block, int smem_bytes) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_fwd_kernel, block, smem_bytes) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+}  // namespace cm

@@ -1,0 +1,57 @@
+// cm_internal.h -- structures shared by the host runtime and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cm_math.cuh"
+
+namespace cm {
+
+// One registered geometry inside the packed device store.
+struct GeomHeader {
+  int32_t kind;
+  int32_t n_verts, n_edges, n_planes;
+  int32_t v_off, e_off, p_off;  // offsets into verts (float4), edges (uint32), planes (float4)
+  int32_t pad0;
+  float dims[3];
+  float pad1;
+};
+static_assert(sizeof(GeomHeader) == 48, "GeomHeader layout");
+
+// Byte offsets of the per-CTA shared-memory carve-up (sized on the host from the
+// largest registered geometry).
+struct SmemLayout {
+  int vA, vAl, vB, pA, pB, eA, eB, rowL, colL, warp;
+  int total;
+  int max_v, max_e, max_p;
+};
+
+struct FwdArgs {
+  const GeomHeader* hdr;
+  int32_t n_geoms;
+  const float4* verts;
+  const uint32_t* edges;  // (i | j << 16)
+  const float4* planes;
+  int32_t n_pairs;
+  const int32_t* pair_geoms;
+  const float* poses;
+  const float* dims;  // may be null
+  const float* tau;   // may be null
+  Params p;
+  float* out;
+  float* scratch;            // per-CTA slices of scratch_stride floats (E-E distances)
+  int64_t scratch_stride;
+  int* err;                  // sticky device error: first bad pair index + 1
+  SmemLayout sm;
+  int32_t* work_counter;     // persistent-CTA work queue (may be null: static striding)
+  const int32_t* order;      // optional pair order for the work queue (may be null)
+};
+
+constexpr int kMaxK = 16;
+constexpr int kWarpStateFloats = kMaxK * 9 + 10;
+
+cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s);
+int fwd_max_blocks_per_sm(int block, int smem_bytes);
+
+}  // namespace cm

@@ -1,0 +1,351 @@
+// cm_math.cuh -- FP32 device arithmetic of the smooth contact manifold (arXiv 2602.20304).
+//
+// Everything a CUDA thread computes for one vertex or one edge pair: the smooth
+// operators of Sec. III, the SDF primitives of Sec. IV-B, the regularised E-E
+// box QP with its smoothed analytic active set (Sec. IV-D2) and the signed
+// witness quantities (Sec. IV-D3).  Transcendentals go to the MUFU pipe
+// through ex2.approx / lg2.approx / rcp.approx / rsqrt.approx.
+#pragma once
+
+#include <cstdint>
+#include <cmath>
+
+#if defined(__CUDACC__)
+#define CM_HD __host__ __device__ __forceinline__
+#else
+#define CM_HD inline
+#endif
+
+namespace cm {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// ---------------------------------------------------------------- MUFU wrappers
+CM_HD float ex2(float x) {
+#if defined(__CUDA_ARCH__)
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+#else
+  return exp2f(x);
+#endif
+}
+CM_HD float lg2(float x) {
+#if defined(__CUDA_ARCH__)
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+#else
+  return log2f(x);
+#endif
+}
+CM_HD float rcp(float x) {
+#if defined(__CUDA_ARCH__)
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+#else
+  return 1.0f / x;
+#endif
+}
+CM_HD float rsq(float x) {
+#if defined(__CUDA_ARCH__)
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+#else
+  return 1.0f / sqrtf(x);
+#endif
+}
+CM_HD float sqrt_(float x) {
+#if defined(__CUDA_ARCH__)
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+#else
+  return sqrtf(x);
+#endif
+}
+CM_HD float exp_(float x) { return ex2(x * kLog2e); }
+
+// ---------------------------------------------------------------- 3-vectors
+struct V3 {
+  float x, y, z;
+};
+CM_HD V3 v3(float x, float y, float z) { return V3{x, y, z}; }
+CM_HD V3 operator+(V3 a, V3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+CM_HD V3 operator-(V3 a, V3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+CM_HD V3 operator-(V3 a) { return v3(-a.x, -a.y, -a.z); }
+CM_HD V3 operator*(float s, V3 a) { return v3(s * a.x, s * a.y, s * a.z); }
+CM_HD V3 operator*(V3 a, float s) { return v3(s * a.x, s * a.y, s * a.z); }
+CM_HD V3& operator+=(V3& a, V3 b) {
+  a.x += b.x;
+  a.y += b.y;
+  a.z += b.z;
+  return a;
+}
+CM_HD float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+CM_HD V3 cross(V3 a, V3 b) {
+  return v3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
+}
+CM_HD V3 fma3(float s, V3 a, V3 b) { return v3(fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z)); }
+
+// Row-major 3x3 rotation.
+struct M3 {
+  float m[9];
+};
+CM_HD V3 mul(const M3& R, V3 v) {
+  return v3(fmaf(R.m[0], v.x, fmaf(R.m[1], v.y, R.m[2] * v.z)),
+            fmaf(R.m[3], v.x, fmaf(R.m[4], v.y, R.m[5] * v.z)),
+            fmaf(R.m[6], v.x, fmaf(R.m[7], v.y, R.m[8] * v.z)));
+}
+CM_HD V3 mulT(const M3& R, V3 v) {
+  return v3(fmaf(R.m[0], v.x, fmaf(R.m[3], v.y, R.m[6] * v.z)),
+            fmaf(R.m[1], v.x, fmaf(R.m[4], v.y, R.m[7] * v.z)),
+            fmaf(R.m[2], v.x, fmaf(R.m[5], v.y, R.m[8] * v.z)));
+}
+// Rotation of the normalised quaternion (w, x, y, z).
+CM_HD M3 quat_rot(float w, float x, float y, float z) {
+  float s = 1.0f / sqrtf(w * w + x * x + y * y + z * z);
+  w *= s; x *= s; y *= s; z *= s;
+  M3 R;
+  R.m[0] = 1.f - 2.f * (y * y + z * z); R.m[1] = 2.f * (x * y - w * z); R.m[2] = 2.f * (x * z + w * y);
+  R.m[3] = 2.f * (x * y + w * z); R.m[4] = 1.f - 2.f * (x * x + z * z); R.m[5] = 2.f * (y * z - w * x);
+  R.m[6] = 2.f * (x * z - w * y); R.m[7] = 2.f * (y * z + w * x); R.m[8] = 1.f - 2.f * (x * x + y * y);
+  return R;
+}
+// A^T B
+CM_HD M3 mulTM(const M3& A, const M3& B) {
+  M3 C;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      C.m[i * 3 + j] = A.m[0 * 3 + i] * B.m[0 * 3 + j] + A.m[1 * 3 + i] * B.m[1 * 3 + j] +
+                       A.m[2 * 3 + i] * B.m[2 * 3 + j];
+  return C;
+}
+
+// ---------------------------------------------------------------- smooth operators (Sec. III)
+CM_HD float sigmoid(float x) { return rcp(1.0f + exp_(-x)); }
+// log(1 + e^x) as max(x, 0) + log(1 + e^-|x|)
+CM_HD float softplus(float x) { return fmaxf(x, 0.0f) + kLn2 * lg2(1.0f + exp_(-fabsf(x))); }
+CM_HD float relu_s(float x, float inv_eps, float eps) { return eps * softplus(x * inv_eps); }
+CM_HD float clip_s(float x, float lo, float hi, float inv_eps, float eps) {
+  return lo + relu_s(x - lo, inv_eps, eps) - relu_s(x - hi, inv_eps, eps);
+}
+// tanh(x) = 1 - 2 / (e^{2x} + 1); saturates cleanly to +-1.
+CM_HD float tanh_(float x) { return 1.0f - 2.0f * rcp(exp_(2.0f * x) + 1.0f); }
+CM_HD float within01(float x, float inv_eps) { return sigmoid(x * inv_eps) * sigmoid((1.0f - x) * inv_eps); }
+
+struct Params {
+  float tau, w_reg, eps_clip, eps_min, eps_comp;
+  int K, flags;
+};
+
+// ---------------------------------------------------------------- geometry kinds
+enum Kind : int { kBox = 0, kCapsule = 1, kCylinder = 2, kEllipsoid = 3, kHull = 4 };
+
+// Local vertex of a template row u = (u_x, u_y, u_z, s) for the given dims.
+CM_HD V3 map_vertex(int kind, float ux, float uy, float uz, float s, V3 d) {
+  switch (kind) {
+    case kBox:
+    case kEllipsoid: return v3(d.x * ux, d.y * uy, d.z * uz);
+    case kCylinder: return v3(d.x * ux, d.x * uy, d.y * uz);
+    case kCapsule: return v3(d.x * ux, d.x * uy, fmaf(d.x, uz, s * d.y));
+    default: return v3(ux, uy, uz);
+  }
+}
+
+// SDF value and the gradient its normal is built from (grad phi; grad f for the
+// superquadric), in the body's local frame.
+struct Sdf {
+  float phi;
+  V3 g;
+};
+
+// Box: convex polyhedron of the planes +-y_i - h_i (Sec. IV-B2).
+CM_HD Sdf sdf_box(V3 y, V3 h, float tau, float inv_tau) {
+  float px = y.x - h.x, nx = -y.x - h.x, py = y.y - h.y, ny = -y.y - h.y, pz = y.z - h.z,
+        nz = -y.z - h.z;
+  float m = fmaxf(fmaxf(fmaxf(px, nx), fmaxf(py, ny)), fmaxf(pz, nz));
+  float k = inv_tau * kLog2e;
+  float epx = ex2((px - m) * k), enx = ex2((nx - m) * k), epy = ex2((py - m) * k),
+        eny = ex2((ny - m) * k), epz = ex2((pz - m) * k), enz = ex2((nz - m) * k);
+  float S = ((epx + enx) + (epy + eny)) + (epz + enz);
+  float r = rcp(S);
+  Sdf o;
+  o.phi = m + tau * kLn2 * lg2(S);
+  o.g = v3((epx - enx) * r, (epy - eny) * r, (epz - enz) * r);
+  return o;
+}
+
+// Convex polyhedron given by planes (n, o): LSE_tau of n . y - o (Sec. IV-B2).
+// Two passes over the planes: the maximum, then the shifted exponential sum.
+CM_HD Sdf sdf_planes(V3 y, const float4* P, int nP, float tau, float inv_tau) {
+  float m = -3.0e38f;
+  for (int f = 0; f < nP; ++f) {
+    float4 p = P[f];
+    m = fmaxf(m, fmaf(p.x, y.x, fmaf(p.y, y.y, fmaf(p.z, y.z, -p.w))));
+  }
+  float k = inv_tau * kLog2e;
+  float S = 0.f;
+  V3 G = v3(0.f, 0.f, 0.f);
+  float mk = m * k;
+  for (int f = 0; f < nP; ++f) {
+    float4 p = P[f];
+    float s = fmaf(p.x, y.x, fmaf(p.y, y.y, fmaf(p.z, y.z, -p.w)));
+    float e = ex2(fmaf(s, k, -mk));
+    S += e;
+    G.x = fmaf(e, p.x, G.x);
+    G.y = fmaf(e, p.y, G.y);
+    G.z = fmaf(e, p.z, G.z);
+  }
+  float r = rcp(S);
+  Sdf o;
+  o.phi = m + tau * kLn2 * lg2(S);
+  o.g = G * r;
+  return o;
+}
+
+// Superquadric with eps1 = eps2 = 1 (Sec. IV-B1): phi = |y| (1 - f^-1/2), f = |y~|^2;
+// the normal comes from grad f = 2 y / d^2.
+CM_HD Sdf sdf_ellipsoid(V3 y, V3 d) {
+  V3 id = v3(rcp(d.x), rcp(d.y), rcp(d.z));
+  V3 yt = v3(y.x * id.x, y.y * id.y, y.z * id.z);
+  float f = dot(yt, yt);
+  float r = sqrt_(dot(y, y));
+  Sdf o;
+  o.phi = r - r * rsq(f);
+  o.g = v3(2.f * yt.x * id.x, 2.f * yt.y * id.y, 2.f * yt.z * id.z);
+  return o;
+}
+
+// Capsule of radius r around the z segment [-h, h] with a soft-clipped axial
+// coordinate: phi = |y - clip_s(y_z, -h, h) z| - r.
+CM_HD Sdf sdf_capsule(V3 y, float rad, float h, float tau, float inv_tau) {
+  float up = (y.z + h) * inv_tau, dn = (y.z - h) * inv_tau;
+  float c = -h + tau * (softplus(up) - softplus(dn));
+  V3 w = v3(y.x, y.y, y.z - c);
+  float r2 = dot(w, w);
+  float ir = r2 > 0.f ? rsq(r2) : 0.f;
+  float r = r2 * ir;
+  float dc = sigmoid(up) - sigmoid(dn);
+  Sdf o;
+  o.phi = r - rad;
+  o.g = v3(w.x * ir, w.y * ir, w.z * (1.f - dc) * ir);
+  return o;
+}
+
+// Cylinder of radius r and half-height h along z: LSE_tau(rho - r, z - h, -z - h).
+CM_HD Sdf sdf_cylinder(V3 y, float rad, float h, float tau, float inv_tau) {
+  float rho2 = y.x * y.x + y.y * y.y;
+  float irho = rho2 > 0.f ? rsq(rho2) : 0.f;
+  float rho = rho2 * irho;
+  float s0 = rho - rad, s1 = y.z - h, s2 = -y.z - h;
+  float m = fmaxf(s0, fmaxf(s1, s2));
+  float k = inv_tau * kLog2e;
+  float e0 = ex2((s0 - m) * k), e1 = ex2((s1 - m) * k), e2 = ex2((s2 - m) * k);
+  float S = e0 + e1 + e2;
+  float ri = rcp(S);
+  Sdf o;
+  o.phi = m + tau * kLn2 * lg2(S);
+  float a = e0 * ri * irho;
+  o.g = v3(a * y.x, a * y.y, (e1 - e2) * ri);
+  return o;
+}
+
+// Regularised normal g / sqrt(tau + |g|^2) (Sec. IV-B).
+CM_HD V3 normal_of(V3 g, float tau) { return g * rsq(tau + dot(g, g)); }
+
+// A body as seen by the kernels: its kind, the dims in use and its planes.
+struct Body {
+  int kind;
+  V3 dims;
+  const float4* planes;
+  int n_planes;
+};
+
+CM_HD Sdf body_sdf(const Body& b, V3 y, float tau, float inv_tau) {
+  switch (b.kind) {
+    case kBox: return sdf_box(y, b.dims, tau, inv_tau);
+    case kEllipsoid: return sdf_ellipsoid(y, b.dims);
+    case kCapsule: return sdf_capsule(y, b.dims.x, b.dims.y, tau, inv_tau);
+    case kCylinder: return sdf_cylinder(y, b.dims.x, b.dims.y, tau, inv_tau);
+    default: return sdf_planes(y, b.planes, b.n_planes, tau, inv_tau);
+  }
+}
+
+// ---------------------------------------------------------------- E-E witness QP (Sec. IV-D2)
+// Box QP  min 1/2 a^T Q a + c^T a  on [0,1]^2 with Q = A^T A + lam I,
+// c = A^T b - lam/2 (1, 1), A = [t1, t2], t1 = a1 - a0, t2 = b0 - b1, b = a0 - b0.
+// The unconstrained minimiser uses the Lagrange / Binet-Cauchy forms
+//   det Q  = |t1 x t2|^2 + lam (|t1|^2 + |t2|^2) + lam^2,
+//   Q12 c2 - Q22 c1 = -(t1 x t2).(b x t2) + lam ((|t2|^2 - t1.t2)/2 - t1.b + lam/2),
+//   Q12 c1 - Q11 c2 = -(t1 x t2).(t1 x b) + lam ((|t1|^2 - t1.t2)/2 - t2.b + lam/2),
+// which equal the textbook 2x2 inverse but keep the FP32 cancellation of the
+// near-parallel case inside one cross product.
+struct QPOut {
+  float a1, a2, con;
+};
+
+CM_HD float qp_cost(float Q11, float Q12, float Q22, float c1, float c2, float a1, float a2) {
+  return 0.5f * (Q11 * a1 * a1 + 2.f * Q12 * a1 * a2 + Q22 * a2 * a2) + c1 * a1 + c2 * a2;
+}
+
+struct QPPre {  // quantities of the QP set-up, reused by the adjoint
+  V3 t1, t2, b;
+  float Q11, Q12, Q22, c1, c2;
+};
+
+CM_HD QPPre qp_setup(V3 a0, V3 a1, V3 b0, V3 b1, float lam) {
+  QPPre q;
+  q.t1 = a1 - a0;
+  q.t2 = b0 - b1;
+  q.b = a0 - b0;
+  float T11 = dot(q.t1, q.t1), T12 = dot(q.t1, q.t2), T22 = dot(q.t2, q.t2);
+  q.Q11 = T11 + lam;
+  q.Q12 = T12;
+  q.Q22 = T22 + lam;
+  q.c1 = dot(q.t1, q.b) - 0.5f * lam;
+  q.c2 = dot(q.t2, q.b) - 0.5f * lam;
+  return q;
+}
+
+CM_HD QPOut qp_solve(const QPPre& q, float lam, const Params& p) {
+  V3 X = cross(q.t1, q.t2);
+  float T11 = q.Q11 - lam, T22 = q.Q22 - lam, T12 = q.Q12;
+  float B1 = q.c1 + 0.5f * lam, B2 = q.c2 + 0.5f * lam;
+  float det = dot(X, X) + lam * (T11 + T22) + lam * lam;
+  float n1 = -dot(X, cross(q.b, q.t2)) + lam * (0.5f * (T22 - T12) - B1 + 0.5f * lam);
+  float n2 = -dot(X, cross(q.t1, q.b)) + lam * (0.5f * (T11 - T12) - B2 + 0.5f * lam);
+  float idet = rcp(det);
+  float au1 = n1 * idet, au2 = n2 * idet;
+  // minimisers along the four sides of the unit box, soft-clipped to [0, 1]
+  float ie = rcp(p.eps_clip);
+  float iQ11 = rcp(q.Q11), iQ22 = rcp(q.Q22);
+  float s1 = clip_s(-(q.Q12 + q.c2) * iQ22, 0.f, 1.f, ie, p.eps_clip);  // a1 = 1
+  float s2 = clip_s(-q.c2 * iQ22, 0.f, 1.f, ie, p.eps_clip);             // a1 = 0
+  float s3 = clip_s(-(q.Q12 + q.c1) * iQ11, 0.f, 1.f, ie, p.eps_clip);  // a2 = 1
+  float s4 = clip_s(-q.c1 * iQ11, 0.f, 1.f, ie, p.eps_clip);             // a2 = 0
+  float J1 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, 1.f, s1);
+  float J2 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, 0.f, s2);
+  float J3 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, s3, 1.f);
+  float J4 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, s4, 0.f);
+  // soft argmin of the four costs
+  float Jm = fminf(fminf(J1, J2), fminf(J3, J4));
+  float k = -rcp(p.eps_min) * kLog2e;
+  float w1 = ex2((J1 - Jm) * k), w2 = ex2((J2 - Jm) * k), w3 = ex2((J3 - Jm) * k),
+        w4 = ex2((J4 - Jm) * k);
+  float iw = rcp((w1 + w2) + (w3 + w4));
+  float ac1 = (w1 + w3 * s3 + w4 * s4) * iw;
+  float ac2 = (w1 * s1 + w2 * s2 + w3) * iw;
+  float ic = rcp(p.eps_comp);
+  float con = within01(au1, ic) * within01(au2, ic);
+  QPOut o;
+  o.a1 = fmaf(con, au1 - ac1, ac1);
+  o.a2 = fmaf(con, au2 - ac2, ac2);
+  o.con = con;
+  return o;
+}
+
+}  // namespace cm

@@ -1,0 +1,228 @@
+// cm_pair.cuh -- per-pair staging and per-candidate arithmetic shared by the
+// forward and adjoint kernels.
+//
+// A CTA owns one body pair at a time.  Everything is evaluated in the local
+// frame of body B: B's vertices and planes are used as registered, A's
+// vertices are moved by the relative pose (R_rel = R_B^T R_A,
+// t_rel = R_B^T (t_A - t_B)), and A's SDF at a B-frame point y is evaluated at
+// R_rel^T (y - t_rel) in A's frame.  Outputs are rotated back to world at the end.
+#pragma once
+
+#include "cm_internal.h"
+#include "cm_softsort.cuh"
+
+namespace cm {
+
+struct PairShared {
+  M3 RA, RB, Rrel;
+  V3 tA, tB, trel;
+  V3 dA, dB;
+  int kindA, kindB;
+  int nvA, nvB, neA, neB, npA, npB;
+  float tau, inv_tau, k2;
+  int bad;  // invalid geometry id
+};
+
+struct PairSmem {
+  float4* vA;      // A's vertices in B's frame
+  float4* vAl;     // A's vertices in A's own frame
+  float4* vB;      // B's vertices (B frame = local)
+  float4* pA;      // A's planes (A frame)
+  float4* pB;      // B's planes
+  uint32_t* eA;
+  uint32_t* eB;
+  float* rowL;     // soft row minima of the E-E distance matrix (nn-Gamma_1)
+  float* colL;     // soft column minima (nn-Gamma_2)
+  float* warp;     // per-warp SoftSort states
+};
+
+__device__ __forceinline__ PairSmem carve(unsigned char* base, const SmemLayout& L) {
+  PairSmem s;
+  s.vA = reinterpret_cast<float4*>(base + L.vA);
+  s.vAl = reinterpret_cast<float4*>(base + L.vAl);
+  s.vB = reinterpret_cast<float4*>(base + L.vB);
+  s.pA = reinterpret_cast<float4*>(base + L.pA);
+  s.pB = reinterpret_cast<float4*>(base + L.pB);
+  s.eA = reinterpret_cast<uint32_t*>(base + L.eA);
+  s.eB = reinterpret_cast<uint32_t*>(base + L.eB);
+  s.rowL = reinterpret_cast<float*>(base + L.rowL);
+  s.colL = reinterpret_cast<float*>(base + L.colL);
+  s.warp = reinterpret_cast<float*>(base + L.warp);
+  return s;
+}
+
+// Thread 0: header, pose and frame set-up of pair `pi`.  Returns via `ps`.
+__device__ inline void pair_setup(const FwdArgs& a, int pi, PairShared& ps) {
+  const int ga = a.pair_geoms[2 * pi], gb = a.pair_geoms[2 * pi + 1];
+  ps.bad = (ga < 0 || ga >= a.n_geoms || gb < 0 || gb >= a.n_geoms) ? 1 : 0;
+  if (ps.bad) return;
+  const GeomHeader& A = a.hdr[ga];
+  const GeomHeader& B = a.hdr[gb];
+  const float* P = a.poses + 14 * (size_t)pi;
+  ps.RA = quat_rot(P[0], P[1], P[2], P[3]);
+  ps.tA = v3(P[4], P[5], P[6]);
+  ps.RB = quat_rot(P[7], P[8], P[9], P[10]);
+  ps.tB = v3(P[11], P[12], P[13]);
+  ps.Rrel = mulTM(ps.RB, ps.RA);
+  ps.trel = mulT(ps.RB, ps.tA - ps.tB);
+  if (a.dims) {
+    const float* D = a.dims + 6 * (size_t)pi;
+    ps.dA = v3(D[0], D[1], D[2]);
+    ps.dB = v3(D[3], D[4], D[5]);
+  } else {
+    ps.dA = v3(A.dims[0], A.dims[1], A.dims[2]);
+    ps.dB = v3(B.dims[0], B.dims[1], B.dims[2]);
+  }
+  ps.kindA = A.kind;
+  ps.kindB = B.kind;
+  ps.nvA = A.n_verts; ps.nvB = B.n_verts;
+  ps.neA = A.n_edges; ps.neB = B.n_edges;
+  ps.npA = A.n_planes; ps.npB = B.n_planes;
+  ps.tau = a.tau ? a.tau[pi] : a.p.tau;
+  ps.inv_tau = 1.0f / ps.tau;
+  ps.k2 = ps.inv_tau * kLog2e;
+}
+
+// Cooperative: copy pair `pi`'s geometry into shared memory (A's vertices moved
+// into B's frame).  Caller syncs before and after.
+__device__ inline void pair_stage(const FwdArgs& a, int pi, const PairShared& ps, const PairSmem& sm) {
+  const int ga = a.pair_geoms[2 * pi], gb = a.pair_geoms[2 * pi + 1];
+  const GeomHeader& A = a.hdr[ga];
+  const GeomHeader& B = a.hdr[gb];
+  for (int i = threadIdx.x; i < ps.nvA; i += blockDim.x) {
+    float4 u = a.verts[A.v_off + i];
+    V3 v = map_vertex(ps.kindA, u.x, u.y, u.z, u.w, ps.dA);
+    V3 y = mul(ps.Rrel, v) + ps.trel;
+    sm.vA[i] = make_float4(y.x, y.y, y.z, 0.f);
+    sm.vAl[i] = make_float4(v.x, v.y, v.z, 0.f);
+  }
+  for (int i = threadIdx.x; i < ps.nvB; i += blockDim.x) {
+    float4 u = a.verts[B.v_off + i];
+    V3 v = map_vertex(ps.kindB, u.x, u.y, u.z, u.w, ps.dB);
+    sm.vB[i] = make_float4(v.x, v.y, v.z, 0.f);
+  }
+  for (int i = threadIdx.x; i < ps.neA; i += blockDim.x) sm.eA[i] = a.edges[A.e_off + i];
+  for (int i = threadIdx.x; i < ps.neB; i += blockDim.x) sm.eB[i] = a.edges[B.e_off + i];
+  for (int i = threadIdx.x; i < ps.npA; i += blockDim.x) sm.pA[i] = a.planes[A.p_off + i];
+  for (int i = threadIdx.x; i < ps.npB; i += blockDim.x) sm.pB[i] = a.planes[B.p_off + i];
+}
+
+__device__ __forceinline__ V3 ld3(const float4& f) { return v3(f.x, f.y, f.z); }
+
+struct PairBodies {
+  Body A, B;
+};
+
+__device__ __forceinline__ PairBodies pair_bodies(const PairShared& ps, const PairSmem& sm) {
+  PairBodies b;
+  b.A.kind = ps.kindA; b.A.dims = ps.dA; b.A.planes = sm.pA; b.A.n_planes = ps.npA;
+  b.B.kind = ps.kindB; b.B.dims = ps.dB; b.B.planes = sm.pB; b.B.n_planes = ps.npB;
+  return b;
+}
+
+// SDF of A at a B-frame point: value and the gradient rotated into B's frame.
+__device__ __forceinline__ Sdf sdfA_at(const PairShared& ps, const Body& A, V3 y) {
+  V3 x = mulT(ps.Rrel, y - ps.trel);
+  Sdf s = body_sdf(A, x, ps.tau, ps.inv_tau);
+  s.g = mul(ps.Rrel, s.g);
+  return s;
+}
+__device__ __forceinline__ Sdf sdfB_at(const PairShared& ps, const Body& B, V3 y) {
+  return body_sdf(B, y, ps.tau, ps.inv_tau);
+}
+
+// Vertex-SDF candidate c in [0, nvA + nvB): A's vertices against B, then B's
+// against A (Sec. IV-C).  Payload (p, d, n, w), score -w d.
+__device__ __forceinline__ float vs_candidate(const PairShared& ps, const PairSmem& sm,
+                                              const PairBodies& bb, int c, float (&y)[8]) {
+  V3 p;
+  Sdf s;
+  if (c < ps.nvA) {
+    p = ld3(sm.vA[c]);
+    s = sdfB_at(ps, bb.B, p);
+  } else {
+    p = ld3(sm.vB[c - ps.nvA]);
+    s = sdfA_at(ps, bb.A, p);
+  }
+  V3 n = normal_of(s.g, ps.tau);
+  float w = sigmoid(-s.phi * ps.inv_tau);
+  y[0] = p.x; y[1] = p.y; y[2] = p.z; y[3] = s.phi;
+  y[4] = n.x; y[5] = n.y; y[6] = n.z; y[7] = w;
+  return -w * s.phi;
+}
+
+// Edge endpoints of element (k, l); A's edge also in A's own frame.
+struct EdgePair {
+  V3 a0, a1, b0, b1;
+  int ia0, ia1;
+};
+__device__ __forceinline__ EdgePair edge_pair(const PairSmem& sm, int k, int l) {
+  uint32_t ea = sm.eA[k], eb = sm.eB[l];
+  EdgePair e;
+  e.ia0 = ea & 0xffffu;
+  e.ia1 = ea >> 16;
+  e.a0 = ld3(sm.vA[e.ia0]);
+  e.a1 = ld3(sm.vA[e.ia1]);
+  e.b0 = ld3(sm.vB[eb & 0xffffu]);
+  e.b1 = ld3(sm.vB[eb >> 16]);
+  return e;
+}
+
+// Witness points of an edge pair (Sec. IV-D2, IV-D3).
+struct Witness {
+  V3 e1, e2, delta;
+  float dbar, con;
+  QPOut qp;
+};
+__device__ __forceinline__ Witness ee_witness(const EdgePair& e, const Params& p) {
+  QPPre q = qp_setup(e.a0, e.a1, e.b0, e.b1, p.w_reg);
+  Witness w;
+  w.qp = qp_solve(q, p.w_reg, p);
+  w.e1 = fma3(w.qp.a1, e.a1 - e.a0, e.a0);
+  w.e2 = fma3(w.qp.a2, e.b1 - e.b0, e.b0);
+  w.delta = w.e1 - w.e2;
+  float r2 = dot(w.delta, w.delta);
+  w.dbar = sqrt_(r2);
+  w.con = w.qp.con;
+  return w;
+}
+
+// Both E-E candidates of element (k, l) (Sec. IV-D3): sign, penetration,
+// nearest-neighbour (from the soft row / column minima L), clashing, activity.
+// A's normal at its own witness is evaluated from A's local vertices: the SDF
+// normal near a mesh corner turns at a rate ~1/tau, and a frame round trip of
+// e1* would add FP32 position error that the soft sign then amplifies.
+__device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSmem& sm,
+                                              const PairBodies& bb, const EdgePair& ep,
+                                              const Witness& w, float rowL, float colL,
+                                              float (&y1)[8], float (&y2)[8], float& s1, float& s2) {
+  const float tau = ps.tau, it = ps.inv_tau;
+  V3 nbar = w.delta * rsq(dot(w.delta, w.delta) + tau * tau);
+  const V3 la0 = ld3(sm.vAl[ep.ia0]), la1 = ld3(sm.vAl[ep.ia1]);
+  const V3 e1l = fma3(w.qp.a1, la1 - la0, la0);
+  Sdf B_e1 = sdfB_at(ps, bb.B, w.e1);                   // phi_B(e1*)
+  Sdf B_e2 = sdfB_at(ps, bb.B, w.e2);                   // nu_B(e2*)
+  Sdf A_e2 = sdfA_at(ps, bb.A, w.e2);                   // phi_A(e2*)
+  Sdf A_e1 = body_sdf(bb.A, e1l, tau, it);              // nu_A(e1*), A frame
+  A_e1.g = mul(ps.Rrel, A_e1.g);
+  V3 nuB = normal_of(B_e2.g, tau);
+  V3 nuA = normal_of(A_e1.g, tau);
+  float g1 = tanh_(dot(nuB, nbar) * it);
+  float g2 = tanh_(-dot(nuA, nbar) * it);
+  float pen1 = sigmoid(-B_e1.phi * it);
+  float pen2 = sigmoid(-A_e2.phi * it);
+  float cl = sigmoid(-dot(nuA, nuB) * it);
+  float nn1 = ex2((rowL - w.dbar) * ps.k2);
+  float nn2 = ex2((colL - w.dbar) * ps.k2);
+  float base = w.con * cl;
+  float w1 = base * pen1 * nn1, w2 = base * pen2 * nn2;
+  float d1 = g1 * w.dbar, d2 = g2 * w.dbar;
+  y1[0] = w.e1.x; y1[1] = w.e1.y; y1[2] = w.e1.z; y1[3] = d1;
+  y1[4] = g1 * nbar.x; y1[5] = g1 * nbar.y; y1[6] = g1 * nbar.z; y1[7] = w1;
+  y2[0] = w.e2.x; y2[1] = w.e2.y; y2[2] = w.e2.z; y2[3] = d2;
+  y2[4] = -g2 * nbar.x; y2[5] = -g2 * nbar.y; y2[6] = -g2 * nbar.z; y2[7] = w2;
+  s1 = -w1 * d1;
+  s2 = -w2 * d2;
+}
+
+}  // namespace cm

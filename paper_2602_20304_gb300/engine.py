@@ -1,0 +1,59 @@
+"""Convenience layer over the C ABI: geometry registration from mesh/SDF descriptions
+and torch-tensor calls of the forward manifold.  Argument marshalling only."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import api
+
+
+class Engine:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.device = device
+        self.ctx = api.cm_create_context(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.ctx is not None:
+            api.cm_destroy_context(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_geometry(self, g) -> int:
+        """Registers an object with kind, dims, verts (V, 4), edges (E, 2), planes (F, 4)."""
+        return api.cm_create_geometry(self.ctx, g.kind, g.dims, g.verts, g.edges,
+                                      g.planes if len(g.planes) else None)
+
+    def add_geometries(self, geoms) -> np.ndarray:
+        ids = np.array([self.add_geometry(g) for g in geoms], dtype=np.int32)
+        api.cm_sync_geometry(self.ctx)
+        return ids
+
+    def params(self, **kw) -> api.cm_params:
+        return api.cm_default_params(**kw)
+
+    def forward(self, pair_geoms, poses, dims=None, tau=None, params=None, out=None, stream=None):
+        params = params or self.params()
+        n = int(pair_geoms.shape[0])
+        if out is None:
+            out = torch.empty((n, params.K, 8), dtype=torch.float32, device=pair_geoms.device)
+        api.cm_contact_manifold_fwd(self.ctx, pair_geoms, poses, dims, tau, params, out, stream)
+        return out
+
+    def check(self):
+        api.cm_check_device_error(self.ctx)
+
+
+def workload_tensors(w, device="cuda", id_map=None):
+    """Device tensors (pair_geoms, poses, dims, tau) of a synthetic workload."""
+    pg = w.pair_geoms if id_map is None else id_map[w.pair_geoms]
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)  # noqa: E731
+    return (t(pg, torch.int32), t(w.poses, torch.float32), t(w.dims, torch.float32),
+            t(w.tau, torch.float32))

@@ -1,0 +1,133 @@
+"""Forward parity of the CUDA library against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from _parity import TOL, assert_close, errors, oracle_forward, tol_for_tau
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def engine():
+    from paper_2602_20304_gb300.engine import Engine
+    e = Engine(0)
+    yield e
+    e.close()
+
+
+def run(engine, w, **pkw):
+    from paper_2602_20304_gb300.engine import workload_tensors
+    ids = engine.add_geometries(w.geoms)
+    pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+    params = engine.params(**pkw)
+    out = engine.forward(pg, poses, dims, tau, params)
+    torch.cuda.synchronize()
+    engine.check()
+    return out.cpu().numpy().astype(np.float64), params
+
+
+def test_box_box_all_pairs(engine):
+    """1024 box-box poses, tau = 1e-2, K = 8: every pair against the oracle."""
+    w = synth.make_config(1)
+    gpu, params = run(engine, w)
+    ref = oracle_forward(w, params)
+    err = assert_close(gpu, ref, what="box-box")
+    print("box-box max abs errors", err)
+
+
+def test_hull_vs_primitive_subset(engine):
+    w = synth.make_config(2, 96)
+    gpu, params = run(engine, w)
+    ref = oracle_forward(w, params)
+    print("hull-vs-primitive", assert_close(gpu, ref, what="hull-vs-primitive"))
+
+
+def test_hull_vs_primitive_full_size_sampled(engine):
+    """All 4096 pairs in one launch; 24 seeded pairs re-computed by the oracle."""
+    w = synth.make_config(2)
+    gpu, params = run(engine, w)
+    idx = np.random.default_rng(0).choice(w.n_pairs, 24, replace=False)
+    ref = oracle_forward(w, params, idx=idx)
+    print("hull-vs-primitive sampled", assert_close(gpu[idx], ref, what="full-size sample"))
+
+
+def test_box_vs_sphere_hull_subset(engine):
+    w = synth.make_config(3, 64)
+    gpu, params = run(engine, w)
+    print("box-vs-hull32", assert_close(gpu, oracle_forward(w, params), what="box-vs-hull32"))
+
+
+@pytest.mark.parametrize("tau", [1e-3, 1e-2, 1e-1])
+def test_mixed_sizes_per_tau(engine, tau):
+    """Hulls of 8..256 points against all primitive kinds at each smoothing level."""
+    w = synth.config_mixed(n=48, seed=99)
+    w.tau[:] = tau
+    gpu, params = run(engine, w)
+    ref = oracle_forward(w, params)
+    print(f"mixed tau={tau}", assert_close(gpu, ref, tol=tol_for_tau(tau), what=f"mixed tau={tau}"))
+    if tau < 1e-2:
+        # most pairs still meet the fixed tolerance; only ill-conditioned ones need the scaled one
+        e = np.abs(gpu - ref).reshape(len(gpu), -1, 8).max(1)
+        ok = (e[:, :4].max(1) <= TOL["d"]) & (e[:, 4:7].max(1) <= TOL["n"])
+        assert ok.mean() >= 0.75, ok.mean()
+
+
+@pytest.mark.parametrize("flags", [1, 2])
+def test_simplification_flags(engine, flags):
+    w = synth.make_config(2, 32)
+    gpu, params = run(engine, w, flags=flags, K=4)
+    assert_close(gpu, oracle_forward(w, params), what=f"flags={flags}")
+
+
+@pytest.mark.parametrize("K", [1, 3, 16])
+def test_other_K(engine, K):
+    w = synth.make_config(1, 64)
+    gpu, params = run(engine, w, K=K)
+    assert gpu.shape[1] == K
+    assert_close(gpu, oracle_forward(w, params), what=f"K={K}")
+
+
+def test_swap_symmetry_on_gpu(engine):
+    """Exchanging the bodies of every pair leaves the manifold unchanged."""
+    w = synth.make_config(2, 64)
+    a, params = run(engine, w)
+    ws = w.subset(np.arange(w.n_pairs))
+    ws.pair_geoms = w.pair_geoms[:, ::-1].copy()
+    ws.poses = np.concatenate([w.poses[:, 7:], w.poses[:, :7]], axis=1).copy()
+    ws.dims = np.concatenate([w.dims[:, 3:], w.dims[:, :3]], axis=1).copy()
+    b, _ = run(engine, ws)
+    err = errors(a, b)
+    for k in err:
+        assert err[k] <= 2 * TOL[k], err
+
+
+def test_invalid_geometry_id_sets_flag(engine):
+    from paper_2602_20304_gb300 import api
+    w = synth.make_config(1, 8)
+    from paper_2602_20304_gb300.engine import workload_tensors
+    ids = engine.add_geometries(w.geoms)
+    pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+    pg[3, 1] = 10 ** 6
+    out = engine.forward(pg, poses, dims, tau)
+    with pytest.raises(api.CMError) as ei:
+        engine.check()
+    assert ei.value.status == api.CM_ERR_DEVICE and "pair 3" in str(ei.value)
+    o = out.cpu().numpy()
+    assert np.isnan(o[3]).all() and np.isfinite(np.delete(o, 3, axis=0)).all()
+    engine.check()                                   # flag was cleared
+
+
+def test_empty_and_argument_errors(engine):
+    from paper_2602_20304_gb300 import api
+    engine.add_geometries(synth.make_config(1, 2).geoms)
+    z = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    out = engine.forward(z, torch.zeros((0, 14), device="cuda"))
+    assert out.shape == (0, 8, 8)
+    with pytest.raises(api.CMError):
+        engine.forward(torch.zeros((1, 2), dtype=torch.int32, device="cuda"),
+                       torch.zeros((1, 14), device="cuda"), params=engine.params(K=17))
+    with pytest.raises(api.CMError):
+        engine.forward(torch.zeros((1, 2), dtype=torch.int32, device="cuda"),
+                       torch.zeros((1, 14), device="cuda"), params=engine.params(tau=0.0))

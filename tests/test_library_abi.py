@@ -1,0 +1,64 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/*.h declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(cm_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2602_20304_gb300 import build_lib
+    return build_lib.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("cm_create_context", "cm_create_geometry", "cm_contact_manifold_fwd",
+                     "cm_last_error", "cm_destroy_context"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_binding_covers_the_header(libpath):
+    from paper_2602_20304_gb300 import api
+    assert set(api.exported_symbols()) <= set(declared_functions())
+
+
+def test_default_params(libpath):
+    from paper_2602_20304_gb300 import api
+    p = api.cm_default_params()
+    assert (p.K, p.flags) == (8, 0)
+    assert abs(p.tau - 1e-2) < 1e-9 and abs(p.w_reg - 1e-2) < 1e-9
+    assert abs(p.eps_clip - 0.1) < 1e-7 and abs(p.eps_min - 0.1) < 1e-7 and abs(p.eps_comp - 0.1) < 1e-7
+
+
+def test_no_device_is_an_error_not_a_crash(libpath):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2602_20304_gb300 import api
+    with pytest.raises(api.CMError) as ei:
+        api.cm_create_context(0)
+    assert ei.value.status in (api.CM_ERR_CUDA, api.CM_ERR_INVALID_ARG)
+    assert api.cm_last_error()
