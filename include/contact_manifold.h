@@ -142,6 +142,27 @@ cm_status cm_contact_manifold_fwd(cm_context* ctx, int32_t n_pairs, const int32_
                                   const float* poses, const float* dims, const float* tau,
                                   const cm_params* params, float* out, void* stream);
 
+/* Same computation and arguments as cm_contact_manifold_fwd, but the call
+ * allocates no memory (no cudaMalloc, no library allocation).  The paper has no
+ * counterpart: this exists for callers that cannot allocate while they run the
+ * manifold -- a simulator step inside a CUDA stream capture, a real-time loop
+ * with a fixed memory footprint, a host that owns all device memory through its
+ * own pool.  Its E-E distance scratch is one fixed 64 MiB device array (16 Mi
+ * floats) in the library, present on every GPU that loads it until exit.
+ *   - Limit: the largest registered geometry may have at most
+ *     floor(sqrt(16 Mi / number_of_SMs)) edges (332 on a 152-SM GB300);
+ *     otherwise CM_ERR_INVALID_ARG with a message stating the limit.
+ *   - Geometry must already be uploaded (cm_sync_geometry); a pending upload is
+ *     an error here instead of an allocation.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call, from any context, shares the one array per device: calls whose
+ *     kernels overlap on the GPU (other streams, other threads) race on it and
+ *     must be serialised by the caller.  Nothing in it needs to start at zero. */
+cm_status cm_contact_manifold_fwd_noalloc(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms,
+                                          const float* poses, const float* dims, const float* tau,
+                                          const cm_params* params, float* out, void* stream);
+
 /* Reads (and clears) the sticky device error flag; synchronises the context's
  * default work.  Returns CM_ERR_DEVICE with a message naming the first bad pair
  * when a kernel met an invalid geometry id. */

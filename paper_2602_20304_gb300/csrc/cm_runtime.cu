@@ -316,3 +316,104 @@ cm_status cm_contact_manifold_fwd(cm_context* c, int32_t n_pairs, const int32_t*
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free forward entry point.
+//
+// Some callers must not allocate device memory while they run the manifold:
+// a simulator stepping inside a CUDA stream capture (cudaMalloc is not allowed
+// there), a real-time control loop that was promised a fixed memory footprint,
+// or a host application that owns every device allocation through its own
+// pool.  cm_contact_manifold_fwd may grow its scratch on a call, so those
+// callers use this variant instead: its E-E distance scratch is the fixed
+// file-scope device array below, sized once for the whole process.
+// ---------------------------------------------------------------------------
+#define CM_NOALLOC_SCRATCH_FLOATS (16u * 1024u * 1024u)  // 64 MiB of FP32 per GPU
+
+static __device__ __align__(256) float g_noalloc_scratch[CM_NOALLOC_SCRATCH_FLOATS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current).
+// The host-side symbol is only a stand-in, so the address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+cm_status noalloc_scratch(int device, float** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(CM_ERR_INVALID_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+    g_noalloc_ptr[device] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return CM_OK;
+}
+}  // namespace
+
+extern "C" cm_status cm_contact_manifold_fwd_noalloc(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms,
+                                                      const float* poses, const float* dims, const float* tau,
+                                                      const cm_params* params, float* out, void* stream) {
+  if (!c) return fail(CM_ERR_INVALID_ARG, "NULL context");
+  cm_status st = check_params(params);
+  if (st != CM_OK) return st;
+  if (n_pairs < 0) return fail(CM_ERR_INVALID_ARG, "n_pairs < 0");
+  if (n_pairs == 0) return CM_OK;
+  if (!pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "pair_geoms, poses and out are required");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
+  if (c->dirty)
+    return fail(CM_ERR_INVALID_ARG, "geometry not uploaded: call cm_sync_geometry before the no-alloc entry point");
+  if (params->flags & (CM_FLAG_NO_EE | CM_FLAG_ONE_SIDED)) {
+    const int min_cands = (params->flags & CM_FLAG_ONE_SIDED) ? c->min_v : 2 * c->min_v;
+    if (params->K > min_cands)
+      return fail(CM_ERR_INVALID_ARG, "K exceeds the vertex-contact count of the smallest registered geometry");
+  } else if (c->min_e < 3) {
+    return fail(CM_ERR_INVALID_ARG, "E-E contacts need every registered geometry to have >= 3 edges");
+  }
+  // one scratch slice of max_e^2 floats per CTA; the fixed array must hold a
+  // slice for every SM so that the launch still fills the GPU
+  const int64_t stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
+  const int64_t slices = (int64_t)CM_NOALLOC_SCRATCH_FLOATS / stride;
+  if (slices < c->num_sms) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf,
+                  "no-alloc scratch too small: the largest registered geometry has %d edges; at most %d edges fit "
+                  "(%u floats of scratch, one %d x %d slice per SM)",
+                  c->max_e, (int)std::sqrt((double)CM_NOALLOC_SCRATCH_FLOATS / c->num_sms),
+                  CM_NOALLOC_SCRATCH_FLOATS, c->max_e, c->max_e);
+    return fail(CM_ERR_INVALID_ARG, buf);
+  }
+  cudaSetDevice(c->device);
+  float* scratch = nullptr;
+  if ((st = noalloc_scratch(c->device, &scratch)) != CM_OK) return st;
+
+  const int block = 256;
+  FwdArgs a{};
+  a.sm = make_layout(c, block / 32);
+  const int per_sm = fwd_max_blocks_per_sm(block, a.sm.total);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)n_pairs, (int64_t)c->num_sms * per_sm, slices}));
+  a.hdr = c->d_hdr;
+  a.n_geoms = (int32_t)c->hdr.size();
+  a.verts = c->d_verts;
+  a.edges = c->d_edges;
+  a.planes = c->d_planes;
+  a.n_pairs = n_pairs;
+  a.pair_geoms = pair_geoms;
+  a.poses = poses;
+  a.dims = dims;
+  a.tau = tau;
+  a.p = Params{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K, params->flags};
+  a.out = out;
+  a.scratch = scratch;  // written before it is read: no clearing needed
+  a.scratch_stride = stride;
+  a.err = c->d_err;
+  a.work_counter = nullptr;
+  a.order = nullptr;
+  cudaError_t e = launch_fwd(a, grid, block, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "no-alloc forward launch");
+  return CM_OK;
+}
