@@ -142,6 +142,22 @@ cm_status cm_contact_manifold_fwd(cm_context* ctx, int32_t n_pairs, const int32_
                                   const float* poses, const float* dims, const float* tau,
                                   const cm_params* params, float* out, void* stream);
 
+/* Adjoint of cm_contact_manifold_fwd (the whole manifold: SDF primitives,
+ * QP active set with its soft clips and soft argmin, sign / penetration /
+ * nearest-neighbour / clashing indicators, SoftSort).  Same pair arguments as
+ * the forward, plus
+ * grad_out: device, n_pairs x K x 8, dL/d out in the forward's layout;
+ * grad_poses: device, n_pairs x 14, receives dL/d poses (for the raw
+ *   quaternion components, i.e. tangent to the unit sphere, and translations);
+ * grad_dims: device, n_pairs x 6 or NULL, receives dL/d dims of A then B (the
+ *   dims in use; zero for hulls).
+ * The forward is recomputed per pair inside the call; nothing is kept between
+ * the forward and backward calls. */
+cm_status cm_contact_manifold_bwd(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms,
+                                  const float* poses, const float* dims, const float* tau,
+                                  const cm_params* params, const float* grad_out, float* grad_poses,
+                                  float* grad_dims, void* stream);
+
 /* Same computation and arguments as cm_contact_manifold_fwd, but the call
  * allocates no memory (no cudaMalloc, no library allocation).  The paper has no
  * counterpart: this exists for callers that cannot allocate while they run the

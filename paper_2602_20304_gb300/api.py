@@ -54,6 +54,8 @@ _SIGS = {
     "cm_check_device_error": (ctypes.c_int, [_vp]),
     "cm_contact_manifold_fwd": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
                                                ctypes.POINTER(cm_params), _vp, _vp]),
+    "cm_contact_manifold_bwd": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                               ctypes.POINTER(cm_params), _vp, _vp, _vp, _vp]),
     "cm_contact_manifold_fwd_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
                                                        ctypes.POINTER(cm_params), _vp, _vp]),
     "cm_measure_pipe_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -161,6 +163,23 @@ def cm_contact_manifold_fwd(ctx, pair_geoms, poses, dims, tau, params, out, stre
     _check_tensor(out, "out", torch.float32, n)
     _check(_lib.cm_contact_manifold_fwd(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau),
                                         ctypes.byref(params), _ptr(out), _stream_handle(stream)))
+
+
+def cm_contact_manifold_bwd(ctx, pair_geoms, poses, dims, tau, params, grad_out, grad_poses, grad_dims,
+                            stream=None) -> None:
+    """Launch the adjoint on torch CUDA tensors (see the C header for layouts)."""
+    import torch
+    n = int(pair_geoms.shape[0])
+    _check_tensor(pair_geoms, "pair_geoms", torch.int32, n)
+    _check_tensor(poses, "poses", torch.float32, n)
+    _check_tensor(dims, "dims", torch.float32, n)
+    _check_tensor(tau, "tau", torch.float32, n)
+    _check_tensor(grad_out, "grad_out", torch.float32, n)
+    _check_tensor(grad_poses, "grad_poses", torch.float32, n)
+    _check_tensor(grad_dims, "grad_dims", torch.float32, n)
+    _check(_lib.cm_contact_manifold_bwd(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau),
+                                        ctypes.byref(params), _ptr(grad_out), _ptr(grad_poses),
+                                        _ptr(grad_dims), _stream_handle(stream)))
 
 
 def cm_contact_manifold_fwd_noalloc(ctx, pair_geoms, poses, dims, tau, params, out, stream=None) -> None:

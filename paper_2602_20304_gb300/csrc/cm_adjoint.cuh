@@ -1,0 +1,529 @@
+// cm_adjoint.cuh -- hand-written reverse-mode adjoints of the per-candidate
+// arithmetic in cm_math.cuh / cm_pair.cuh.
+//
+// Every function recomputes the forward quantities it needs (nothing of the
+// forward is stored per candidate) and accumulates parameter adjoints into an
+// Adj record: the relative pose (R_rel, t_rel) of A in B's frame and the dims
+// of both bodies.  The per-pair epilogue chains these to the quaternions and
+// translations of both bodies.
+#pragma once
+
+#include "cm_math.cuh"
+
+namespace cm {
+
+struct Adj {
+  float R[9];  // d L / d R_rel
+  V3 t;        // d L / d t_rel
+  V3 dA, dB;   // d L / d dims of A and B
+};
+
+CM_HD void adj_zero(Adj& a) {
+  for (int i = 0; i < 9; ++i) a.R[i] = 0.f;
+  a.t = a.dA = a.dB = v3(0.f, 0.f, 0.f);
+}
+// R += u v^T
+CM_HD void add_outer(float* R, V3 u, V3 v) {
+  R[0] = fmaf(u.x, v.x, R[0]); R[1] = fmaf(u.x, v.y, R[1]); R[2] = fmaf(u.x, v.z, R[2]);
+  R[3] = fmaf(u.y, v.x, R[3]); R[4] = fmaf(u.y, v.y, R[4]); R[5] = fmaf(u.y, v.z, R[5]);
+  R[6] = fmaf(u.z, v.x, R[6]); R[7] = fmaf(u.z, v.y, R[7]); R[8] = fmaf(u.z, v.z, R[8]);
+}
+
+// ---------------------------------------------------------------- smooth operators
+CM_HD float sigmoid_grad_from(float s) { return s * (1.f - s); }            // d sigmoid / dx
+CM_HD float clip_s_grad(float x, float lo, float hi, float inv_eps) {       // d clip_s / dx
+  return sigmoid((x - lo) * inv_eps) - sigmoid((x - hi) * inv_eps);
+}
+// d within01 / dx = within * (sigma((1-x)/eps) - sigma(x/eps)) / eps
+CM_HD float within01_grad(float x, float inv_eps) {
+  float a = sigmoid(x * inv_eps), b = sigmoid((1.f - x) * inv_eps);
+  return a * b * (b - a) * inv_eps;
+}
+
+// ---------------------------------------------------------------- normal
+// nu = g / sqrt(tau + |g|^2)  ->  gbar
+CM_HD V3 normal_bwd(V3 g, float tau, V3 nubar) {
+  float r = rsq(tau + dot(g, g));
+  float gn = dot(g, nubar);
+  return nubar * r - g * (gn * r * r * r);
+}
+
+// ---------------------------------------------------------------- SDF primitives
+// Each takes the forward (phi, g) at y and the adjoints (phibar, gbar) and
+// accumulates ybar and (where the primitive depends on them) dbar.
+
+// Box: planes +-e_i . y - h_i; pi_f = exp((s_f - phi)/tau); sbar_f = pi_f (phibar + gbar.(n_f - g)/tau).
+CM_HD void sdf_box_bwd(V3 y, V3 h, const Sdf& f, float inv_tau, float phibar, V3 gbar, V3& ybar, V3& hbar) {
+  const float k = inv_tau * kLog2e;
+  const float yy[3] = {y.x, y.y, y.z}, hh[3] = {h.x, h.y, h.z}, gg[3] = {f.g.x, f.g.y, f.g.z},
+              gb[3] = {gbar.x, gbar.y, gbar.z};
+  const float gdotg = dot(gbar, f.g);
+  float yb[3], hb[3];
+  for (int i = 0; i < 3; ++i) {
+    // plane +e_i: value y_i - h_i, normal e_i;  plane -e_i: value -y_i - h_i, normal -e_i
+    float pp = ex2((yy[i] - hh[i] - f.phi) * k), pn = ex2((-yy[i] - hh[i] - f.phi) * k);
+    float sp = pp * (phibar + (gb[i] - gdotg) * inv_tau);
+    float sn = pn * (phibar + (-gb[i] - gdotg) * inv_tau);
+    yb[i] = sp - sn;
+    hb[i] = -(sp + sn);
+    (void)gg;
+  }
+  ybar += v3(yb[0], yb[1], yb[2]);
+  hbar += v3(hb[0], hb[1], hb[2]);
+}
+
+CM_HD void sdf_planes_bwd(V3 y, const float4* P, int nP, const Sdf& f, float inv_tau, float phibar, V3 gbar,
+                          V3& ybar) {
+  const float k = inv_tau * kLog2e;
+  const float base = phibar - dot(gbar, f.g) * inv_tau;
+  const float mk = f.phi * k;
+  V3 acc = v3(0.f, 0.f, 0.f);
+  for (int i = 0; i < nP; ++i) {
+    float4 p = P[i];
+    float s = fmaf(p.x, y.x, fmaf(p.y, y.y, fmaf(p.z, y.z, -p.w)));
+    float pi = ex2(fmaf(s, k, -mk));
+    float sb = pi * (base + (gbar.x * p.x + gbar.y * p.y + gbar.z * p.z) * inv_tau);
+    acc.x = fmaf(sb, p.x, acc.x);
+    acc.y = fmaf(sb, p.y, acc.y);
+    acc.z = fmaf(sb, p.z, acc.z);
+  }
+  ybar += acc;
+}
+
+// Ellipsoid: phi = r - r f^-1/2, r = |y|, f = sum y_i^2/d_i^2; g = 2 y / d^2.
+CM_HD void sdf_ellipsoid_bwd(V3 y, V3 d, float phibar, V3 gbar, V3& ybar, V3& dbar) {
+  V3 id = v3(rcp(d.x), rcp(d.y), rcp(d.z));
+  V3 yt = v3(y.x * id.x, y.y * id.y, y.z * id.z);
+  float f = dot(yt, yt);
+  float r2 = dot(y, y);
+  float ir = r2 > 0.f ? rsq(r2) : 0.f;
+  float r = r2 * ir;
+  float fm12 = rsq(f);
+  float fm32 = fm12 * fm12 * fm12;
+  // d phi / d y = (1 - f^-1/2) y / r + r f^-3/2 y / d^2
+  float a = (1.f - fm12) * ir, b = r * fm32;
+  V3 dpdy = v3(y.x * (a + b * id.x * id.x), y.y * (a + b * id.y * id.y), y.z * (a + b * id.z * id.z));
+  // d phi / d d_i = -r f^-3/2 y_i^2 / d_i^3
+  V3 dpdd = v3(-b * yt.x * yt.x * id.x, -b * yt.y * yt.y * id.y, -b * yt.z * yt.z * id.z);
+  // g_i = 2 y_i / d_i^2: dg_i/dy_i = 2 / d_i^2, dg_i/dd_i = -4 y_i / d_i^3
+  ybar += v3(phibar * dpdy.x + 2.f * gbar.x * id.x * id.x, phibar * dpdy.y + 2.f * gbar.y * id.y * id.y,
+             phibar * dpdy.z + 2.f * gbar.z * id.z * id.z);
+  dbar += v3(phibar * dpdd.x - 4.f * gbar.x * yt.x * id.x * id.x, phibar * dpdd.y - 4.f * gbar.y * yt.y * id.y * id.y,
+             phibar * dpdd.z - 4.f * gbar.z * yt.z * id.z * id.z);
+}
+
+// Capsule (rad, h): c = clip_s(z, -h, h); w = (x, y, z - c); rho = |w|; phi = rho - rad;
+// g = (u_x, u_y, u_z (1 - c')) with u = w / rho, c' = sig+ - sig-.
+CM_HD void sdf_capsule_bwd(V3 y, float rad, float h, float tau, float inv_tau, float phibar, V3 gbar, V3& ybar,
+                           V3& dbar) {
+  float up = (y.z + h) * inv_tau, dn = (y.z - h) * inv_tau;
+  float c = -h + tau * (softplus(up) - softplus(dn));
+  float sp = sigmoid(up), sn = sigmoid(dn);
+  float cp = sp - sn;
+  V3 w = v3(y.x, y.y, y.z - c);
+  float r2 = dot(w, w);
+  float ir = r2 > 0.f ? rsq(r2) : 0.f;
+  V3 u = w * ir;
+  // g = (u_x, u_y, u_z (1 - c'))
+  V3 ub = v3(gbar.x, gbar.y, gbar.z * (1.f - cp));
+  float cpb = -gbar.z * u.z;
+  // w adjoint: phi = |w| and u = w / |w|
+  float uu = dot(u, ub);
+  V3 wb = u * phibar + (ub - u * uu) * ir;
+  // w = (x, y, z - c)
+  float cb = -wb.z;
+  float dcdz = cp, dcdh = -1.f + sp + sn;
+  float gp = sigmoid_grad_from(sp), gn = sigmoid_grad_from(sn);
+  float dcpdz = (gp - gn) * inv_tau, dcpdh = (gp + gn) * inv_tau;
+  ybar += v3(wb.x, wb.y, wb.z + cb * dcdz + cpb * dcpdz);
+  dbar += v3(-phibar, cb * dcdh + cpb * dcpdh, 0.f);
+}
+
+// Cylinder (rad, h): s = (rho - rad, z - h, -z - h), phi = LSE_tau(s), pi = softmax(s / tau),
+// g = (pi0 x / rho, pi0 y / rho, pi1 - pi2).
+CM_HD void sdf_cylinder_bwd(V3 y, float rad, float h, const Sdf& f, float inv_tau, float phibar, V3 gbar,
+                            V3& ybar, V3& dbar) {
+  float rho2 = y.x * y.x + y.y * y.y;
+  float irho = rho2 > 0.f ? rsq(rho2) : 0.f;
+  float rho = rho2 * irho;
+  float k = inv_tau * kLog2e;
+  float s0 = rho - rad, s1 = y.z - h, s2 = -y.z - h;
+  float p0 = ex2((s0 - f.phi) * k), p1 = ex2((s1 - f.phi) * k), p2 = ex2((s2 - f.phi) * k);
+  float ex = y.x * irho, ey = y.y * irho;
+  float pb0 = gbar.x * ex + gbar.y * ey, pb1 = gbar.z, pb2 = -gbar.z;
+  float m = pb0 * p0 + pb1 * p1 + pb2 * p2;
+  float sb0 = phibar * p0 + p0 * (pb0 - m) * inv_tau;
+  float sb1 = phibar * p1 + p1 * (pb1 - m) * inv_tau;
+  float sb2 = phibar * p2 + p2 * (pb2 - m) * inv_tau;
+  // radial unit e = (x, y) / rho: ebar = pi0 (gbar_x, gbar_y)
+  float ebx = p0 * gbar.x, eby = p0 * gbar.y;
+  float ee = ex * ebx + ey * eby;
+  float xb = (ebx - ex * ee) * irho + sb0 * ex;
+  float yb = (eby - ey * ee) * irho + sb0 * ey;
+  ybar += v3(xb, yb, sb1 - sb2);
+  dbar += v3(-sb0, -sb1 - sb2, 0.f);
+}
+
+CM_HD void body_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_tau, float phibar, V3 gbar,
+                        V3& ybar, V3& dbar) {
+  switch (b.kind) {
+    case kBox: sdf_box_bwd(y, b.dims, f, inv_tau, phibar, gbar, ybar, dbar); break;
+    case kEllipsoid: sdf_ellipsoid_bwd(y, b.dims, phibar, gbar, ybar, dbar); break;
+    case kCapsule: sdf_capsule_bwd(y, b.dims.x, b.dims.y, tau, inv_tau, phibar, gbar, ybar, dbar); break;
+    case kCylinder: sdf_cylinder_bwd(y, b.dims.x, b.dims.y, f, inv_tau, phibar, gbar, ybar, dbar); break;
+    default: sdf_planes_bwd(y, b.planes, b.n_planes, f, inv_tau, phibar, gbar, ybar); break;
+  }
+}
+
+// ---------------------------------------------------------------- vertex templates
+// v = map(kind, u, dims) -> dims adjoint from the mapped vertex v and its cap sign s.
+CM_HD void map_vertex_bwd(int kind, V3 v, float s, V3 d, V3 vbar, V3& dbar) {
+  switch (kind) {
+    case kBox:
+    case kEllipsoid:
+      dbar += v3(vbar.x * v.x * rcp(d.x), vbar.y * v.y * rcp(d.y), vbar.z * v.z * rcp(d.z));
+      break;
+    case kCylinder:
+      dbar += v3((vbar.x * v.x + vbar.y * v.y) * rcp(d.x), vbar.z * v.z * rcp(d.y), 0.f);
+      break;
+    case kCapsule: {
+      float ir = rcp(d.x);
+      V3 u = v3(v.x * ir, v.y * ir, (v.z - s * d.y) * ir);
+      dbar += v3(dot(vbar, u), vbar.z * s, 0.f);
+      break;
+    }
+    default: break;
+  }
+}
+
+// ---------------------------------------------------------------- E-E box QP
+// Reverse of qp_setup + qp_solve: (abar1, abar2, conbar) -> adjoints of a0, a1, b0, b1.
+CM_HD void qp_bwd(const QPPre& q, float lam, const Params& p, float ab1, float ab2, float conb, V3& a0b, V3& a1b,
+                  V3& b0b, V3& b1b) {
+  // ---- forward recompute
+  V3 X = cross(q.t1, q.t2);
+  float T11 = q.Q11 - lam, T22 = q.Q22 - lam, T12 = q.Q12;
+  float B1 = q.c1 + 0.5f * lam, B2 = q.c2 + 0.5f * lam;
+  float det = dot(X, X) + lam * (T11 + T22) + lam * lam;
+  float n1 = -dot(X, cross(q.b, q.t2)) + lam * (0.5f * (T22 - T12) - B1 + 0.5f * lam);
+  float n2 = -dot(X, cross(q.t1, q.b)) + lam * (0.5f * (T11 - T12) - B2 + 0.5f * lam);
+  float idet = rcp(det);
+  float au1 = n1 * idet, au2 = n2 * idet;
+  float ie = rcp(p.eps_clip);
+  float iQ11 = rcp(q.Q11), iQ22 = rcp(q.Q22);
+  float z1 = -(q.Q12 + q.c2) * iQ22, z2 = -q.c2 * iQ22, z3 = -(q.Q12 + q.c1) * iQ11, z4 = -q.c1 * iQ11;
+  float s1 = clip_s(z1, 0.f, 1.f, ie, p.eps_clip), s2 = clip_s(z2, 0.f, 1.f, ie, p.eps_clip);
+  float s3 = clip_s(z3, 0.f, 1.f, ie, p.eps_clip), s4 = clip_s(z4, 0.f, 1.f, ie, p.eps_clip);
+  float J1 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, 1.f, s1);
+  float J2 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, 0.f, s2);
+  float J3 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, s3, 1.f);
+  float J4 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, s4, 0.f);
+  float Jm = fminf(fminf(J1, J2), fminf(J3, J4));
+  float iem = rcp(p.eps_min);
+  float k = -iem * kLog2e;
+  float w1 = ex2((J1 - Jm) * k), w2 = ex2((J2 - Jm) * k), w3 = ex2((J3 - Jm) * k), w4 = ex2((J4 - Jm) * k);
+  float iw = rcp((w1 + w2) + (w3 + w4));
+  float pr1 = w1 * iw, pr2 = w2 * iw, pr3 = w3 * iw, pr4 = w4 * iw;
+  float ac1 = pr1 + pr3 * s3 + pr4 * s4;
+  float ac2 = pr1 * s1 + pr2 * s2 + pr3;
+  float ic = rcp(p.eps_comp);
+  float wi1 = within01(au1, ic), wi2 = within01(au2, ic);
+  float con = wi1 * wi2;
+
+  // ---- reverse of alpha = con au + (1 - con) ac
+  float aub1 = con * ab1, aub2 = con * ab2;
+  float acb1 = (1.f - con) * ab1, acb2 = (1.f - con) * ab2;
+  float cb = conb + ab1 * (au1 - ac1) + ab2 * (au2 - ac2);
+  aub1 += cb * wi2 * within01_grad(au1, ic);
+  aub2 += cb * wi1 * within01_grad(au2, ic);
+
+  // ---- soft argmin: ac = sum_j pr_j a_j, candidates (1, s1), (0, s2), (s3, 1), (s4, 0)
+  float pb1 = acb1 + acb2 * s1, pb2 = acb2 * s2, pb3 = acb1 * s3 + acb2, pb4 = acb1 * s4;
+  float sbar1 = pr1 * acb2, sbar2 = pr2 * acb2, sbar3 = pr3 * acb1, sbar4 = pr4 * acb1;
+  float pm = pr1 * pb1 + pr2 * pb2 + pr3 * pb3 + pr4 * pb4;
+  float Jb1 = -iem * pr1 * (pb1 - pm), Jb2 = -iem * pr2 * (pb2 - pm), Jb3 = -iem * pr3 * (pb3 - pm),
+        Jb4 = -iem * pr4 * (pb4 - pm);
+
+  // ---- costs J(a) = 1/2 a^T Q a + c^T a
+  float Qb11 = 0.f, Qb12 = 0.f, Qb22 = 0.f, cb1 = 0.f, cb2 = 0.f;
+  auto cost_bwd = [&](float Jb, float x1, float x2, float& x1b, float& x2b) {
+    Qb11 += Jb * 0.5f * x1 * x1;
+    Qb12 += Jb * x1 * x2;
+    Qb22 += Jb * 0.5f * x2 * x2;
+    cb1 += Jb * x1;
+    cb2 += Jb * x2;
+    x1b += Jb * (q.Q11 * x1 + q.Q12 * x2 + q.c1);
+    x2b += Jb * (q.Q12 * x1 + q.Q22 * x2 + q.c2);
+  };
+  float dummy = 0.f;
+  cost_bwd(Jb1, 1.f, s1, dummy, sbar1);
+  cost_bwd(Jb2, 0.f, s2, dummy, sbar2);
+  cost_bwd(Jb3, s3, 1.f, sbar3, dummy);
+  cost_bwd(Jb4, s4, 0.f, sbar4, dummy);
+
+  // ---- side minimisers z_j through the soft clip
+  float zb1 = sbar1 * clip_s_grad(z1, 0.f, 1.f, ie), zb2 = sbar2 * clip_s_grad(z2, 0.f, 1.f, ie);
+  float zb3 = sbar3 * clip_s_grad(z3, 0.f, 1.f, ie), zb4 = sbar4 * clip_s_grad(z4, 0.f, 1.f, ie);
+  // z1 = -(Q12 + c2)/Q22, z2 = -c2/Q22, z3 = -(Q12 + c1)/Q11, z4 = -c1/Q11
+  Qb12 += -zb1 * iQ22 - zb3 * iQ11;
+  cb2 += -(zb1 + zb2) * iQ22;
+  cb1 += -(zb3 + zb4) * iQ11;
+  Qb22 += -(zb1 * z1 + zb2 * z2) * iQ22;
+  Qb11 += -(zb3 * z3 + zb4 * z4) * iQ11;
+
+  // ---- unconstrained minimiser au = -Q^-1 c:  cbar = -v, Qbar = -v au^T with v = Q^-1 aubar
+  float v1 = (q.Q22 * aub1 - q.Q12 * aub2) * idet;
+  float v2 = (-q.Q12 * aub1 + q.Q11 * aub2) * idet;
+  cb1 -= v1;
+  cb2 -= v2;
+  Qb11 -= v1 * au1;
+  Qb22 -= v2 * au2;
+  Qb12 -= v1 * au2 + v2 * au1;
+
+  // ---- Q = A^T A + lam I, c = A^T b - lam/2 with A = [t1, t2]
+  V3 t1b = q.t1 * (2.f * Qb11) + q.t2 * Qb12 + q.b * cb1;
+  V3 t2b = q.t2 * (2.f * Qb22) + q.t1 * Qb12 + q.b * cb2;
+  V3 bb = q.t1 * cb1 + q.t2 * cb2;
+  // t1 = a1 - a0, t2 = b0 - b1, b = a0 - b0
+  a1b += t1b;
+  a0b += bb - t1b;
+  b0b += t2b - bb;
+  b1b += -t2b;
+}
+
+// ---------------------------------------------------------------- frame of a pair
+// Everything is evaluated in B's frame; A-local x maps to R_rel x + t_rel.
+struct Frame {
+  M3 R;
+  V3 t;
+  float tau, inv_tau, k2;
+};
+
+// A-local point x with adjoint xbar at B-frame point y = R x + t  (x = R^T (y - t)).
+CM_HD V3 pull_point_bwd(const Frame& F, V3 y, V3 xbar, Adj& adj) {
+  V3 Rx = mul(F.R, xbar);
+  adj.t += -Rx;
+  add_outer(adj.R, y - F.t, xbar);
+  return Rx;  // ybar contribution
+}
+// B-frame point y = R v + t of an A-local vertex v: ybar -> (adj.R, adj.t), returns vbar (local).
+CM_HD V3 push_point_bwd(const Frame& F, V3 v, V3 ybar, Adj& adj) {
+  add_outer(adj.R, ybar, v);
+  adj.t += ybar;
+  return mulT(F.R, ybar);
+}
+
+// ---------------------------------------------------------------- vertex-SDF candidate
+// Candidate of A's vertex (vL local, vB in B's frame) against B, or of B's
+// vertex (vB) against A.  Upstream: yb[8] for (p, d, n, w) in B's frame, sb for
+// the score s = -w d.
+template <bool kOfA>
+CM_HD void vs_bwd(const Frame& F, const Body& A, const Body& B, float4 vL, V3 vB, const float (&yb)[8], float sb,
+                  Adj& adj) {
+  const float tau = F.tau, it = F.inv_tau;
+  if (kOfA) {
+    Sdf f = body_sdf(B, vB, tau, it);
+    float w = sigmoid(-f.phi * it);
+    float wb = yb[7] - sb * f.phi;
+    float phib = yb[3] - sb * w - wb * sigmoid_grad_from(w) * it;
+    V3 gb = normal_bwd(f.g, tau, v3(yb[4], yb[5], yb[6]));
+    V3 pb = v3(yb[0], yb[1], yb[2]);
+    body_sdf_bwd(B, vB, f, tau, it, phib, gb, pb, adj.dB);
+    V3 vl = v3(vL.x, vL.y, vL.z);
+    V3 vbar = push_point_bwd(F, vl, pb, adj);
+    map_vertex_bwd(A.kind, vl, vL.w, A.dims, vbar, adj.dA);
+  } else {
+    V3 x = mulT(F.R, vB - F.t);
+    Sdf f = body_sdf(A, x, tau, it);
+    float w = sigmoid(-f.phi * it);
+    float wb = yb[7] - sb * f.phi;
+    float phib = yb[3] - sb * w - wb * sigmoid_grad_from(w) * it;
+    V3 nub = v3(yb[4], yb[5], yb[6]);            // n = R nu_local
+    V3 nuL = normal_of(f.g, tau);
+    add_outer(adj.R, nub, nuL);
+    V3 gb = normal_bwd(f.g, tau, mulT(F.R, nub));
+    V3 xb = v3(0.f, 0.f, 0.f);
+    body_sdf_bwd(A, x, f, tau, it, phib, gb, xb, adj.dA);
+    V3 pb = v3(yb[0], yb[1], yb[2]) + pull_point_bwd(F, vB, xb, adj);
+    map_vertex_bwd(B.kind, vB, vL.w, B.dims, pb, adj.dB);
+  }
+}
+
+// ---------------------------------------------------------------- witness + QP reverse
+struct EEGeom {
+  float4 a0, a1;    // A's edge in B's frame (w unused)
+  float4 a0L, a1L;  // A's edge in A's frame (w = capsule cap sign)
+  float4 b0, b1;    // B's edge (w = capsule cap sign)
+};
+CM_HD V3 xyz(float4 f) { return v3(f.x, f.y, f.z); }
+
+// e1 = a0 + al1 (a1 - a0) (B frame), e1L likewise in A's frame, e2 = b0 + al2 (b1 - b0).
+// Backpropagates e1bar, e1Lbar, e2bar and extra alpha / con adjoints through the
+// witness interpolation and the QP into the parameters.
+CM_HD void witness_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g,
+                       const QPPre& q, const QPOut& o, V3 e1b, V3 e1Lb, V3 e2b, float conb, Adj& adj) {
+  V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
+  V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L);
+  float ab1 = dot(e1b, a1 - a0) + dot(e1Lb, a1L - a0L);
+  float ab2 = dot(e2b, b1 - b0);
+  V3 a0b = e1b * (1.f - o.a1), a1b = e1b * o.a1;
+  V3 b0b = e2b * (1.f - o.a2), b1b = e2b * o.a2;
+  qp_bwd(q, p.w_reg, p, ab1, ab2, conb, a0b, a1b, b0b, b1b);
+  // A's endpoints: B-frame adjoint pulled to A's frame, plus the A-frame adjoint
+  V3 l0 = push_point_bwd(F, a0L, a0b, adj) + e1Lb * (1.f - o.a1);
+  V3 l1 = push_point_bwd(F, a1L, a1b, adj) + e1Lb * o.a1;
+  map_vertex_bwd(A.kind, a0L, g.a0L.w, A.dims, l0, adj.dA);
+  map_vertex_bwd(A.kind, a1L, g.a1L.w, A.dims, l1, adj.dA);
+  map_vertex_bwd(B.kind, b0, g.b0.w, B.dims, b0b, adj.dB);
+  map_vertex_bwd(B.kind, b1, g.b1.w, B.dims, b1b, adj.dB);
+}
+
+// ---------------------------------------------------------------- E-E element
+// Recomputes both candidates of an edge pair, asks `up` for their upstream
+// adjoints, and backpropagates everything except the nearest-neighbour
+// softmax's dependence on the distance matrix, which is returned as
+// t_b = nnbar_b * nn_b for the separate distance-adjoint pass.
+struct EECand {
+  float y1[8], y2[8];
+  float s1, s2;
+};
+
+template <class Upstream>
+CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float rowL,
+                  float colL, Upstream&& up, float& t1, float& t2, Adj& adj) {
+  const float tau = F.tau, it = F.inv_tau;
+  V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
+  V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L);
+  // ---- forward recompute
+  QPPre q = qp_setup(a0, a1, b0, b1, p.w_reg);
+  QPOut o = qp_solve(q, p.w_reg, p);
+  V3 e1 = fma3(o.a1, a1 - a0, a0), e2 = fma3(o.a2, b1 - b0, b0);
+  V3 e1L = fma3(o.a1, a1L - a0L, a0L);
+  V3 D = e1 - e2;
+  float r2 = dot(D, D);
+  float dbar = sqrt_(r2);
+  float qn = rsq(r2 + tau * tau);
+  V3 nbar = D * qn;
+  Sdf SB1 = body_sdf(B, e1, tau, it);
+  Sdf SB2 = body_sdf(B, e2, tau, it);
+  V3 x2 = mulT(F.R, e2 - F.t);
+  Sdf SA2 = body_sdf(A, x2, tau, it);
+  Sdf SA1 = body_sdf(A, e1L, tau, it);
+  V3 nuB = normal_of(SB2.g, tau);
+  V3 nuAL = normal_of(SA1.g, tau);
+  V3 nuA = mul(F.R, nuAL);
+  float g1 = tanh_(dot(nuB, nbar) * it), g2 = tanh_(-dot(nuA, nbar) * it);
+  float pen1 = sigmoid(-SB1.phi * it), pen2 = sigmoid(-SA2.phi * it);
+  float cl = sigmoid(-dot(nuA, nuB) * it);
+  float nn1 = ex2((rowL - dbar) * F.k2), nn2 = ex2((colL - dbar) * F.k2);
+  float con = o.con;
+  float w1 = con * cl * pen1 * nn1, w2 = con * cl * pen2 * nn2;
+  EECand c;
+  c.y1[0] = e1.x; c.y1[1] = e1.y; c.y1[2] = e1.z; c.y1[3] = g1 * dbar;
+  c.y1[4] = g1 * nbar.x; c.y1[5] = g1 * nbar.y; c.y1[6] = g1 * nbar.z; c.y1[7] = w1;
+  c.y2[0] = e2.x; c.y2[1] = e2.y; c.y2[2] = e2.z; c.y2[3] = g2 * dbar;
+  c.y2[4] = -g2 * nbar.x; c.y2[5] = -g2 * nbar.y; c.y2[6] = -g2 * nbar.z; c.y2[7] = w2;
+  c.s1 = -w1 * c.y1[3];
+  c.s2 = -w2 * c.y2[3];
+  float yb1[8], yb2[8], sb1, sb2;
+  up(c, yb1, sb1, yb2, sb2);
+  // ---- reverse
+  float wb1 = yb1[7] - sb1 * c.y1[3], wb2 = yb2[7] - sb2 * c.y2[3];
+  float db1 = yb1[3] - sb1 * w1, db2 = yb2[3] - sb2 * w2;
+  V3 nb1 = v3(yb1[4], yb1[5], yb1[6]), nb2 = v3(yb2[4], yb2[5], yb2[6]);
+  float gb1 = db1 * dbar + dot(nb1, nbar);
+  float gb2 = db2 * dbar - dot(nb2, nbar);
+  float dbarb = db1 * g1 + db2 * g2;
+  V3 nbarb = nb1 * g1 - nb2 * g2;
+  float conb = wb1 * cl * pen1 * nn1 + wb2 * cl * pen2 * nn2;
+  float clb = wb1 * con * pen1 * nn1 + wb2 * con * pen2 * nn2;
+  float penb1 = wb1 * con * cl * nn1, penb2 = wb2 * con * cl * nn2;
+  t1 = wb1 * con * cl * pen1 * nn1;
+  t2 = wb2 * con * cl * pen2 * nn2;
+  float phibB1 = -penb1 * sigmoid_grad_from(pen1) * it;
+  float phibA2 = -penb2 * sigmoid_grad_from(pen2) * it;
+  float cclb = -clb * sigmoid_grad_from(cl) * it;
+  V3 nuAb = nuB * cclb, nuBb = nuA * cclb;
+  float xb1 = gb1 * (1.f - g1 * g1) * it;
+  float xb2 = gb2 * (1.f - g2 * g2) * it;
+  nuBb += nbar * xb1;
+  nbarb += nuB * xb1;
+  nuAb += nbar * (-xb2);
+  nbarb += nuA * (-xb2);
+  V3 Db = nbarb * qn - D * (dot(D, nbarb) * qn * qn * qn);
+  if (dbar > 0.f) Db += D * (dbarb * rcp(dbar));
+  V3 e1b = Db + v3(yb1[0], yb1[1], yb1[2]);
+  V3 e2b = -Db + v3(yb2[0], yb2[1], yb2[2]);
+  // SDF reverses
+  body_sdf_bwd(B, e1, SB1, tau, it, phibB1, v3(0.f, 0.f, 0.f), e1b, adj.dB);
+  body_sdf_bwd(B, e2, SB2, tau, it, 0.f, normal_bwd(SB2.g, tau, nuBb), e2b, adj.dB);
+  V3 x2b = v3(0.f, 0.f, 0.f);
+  body_sdf_bwd(A, x2, SA2, tau, it, phibA2, v3(0.f, 0.f, 0.f), x2b, adj.dA);
+  e2b += pull_point_bwd(F, e2, x2b, adj);
+  add_outer(adj.R, nuAb, nuAL);
+  V3 e1Lb = v3(0.f, 0.f, 0.f);
+  body_sdf_bwd(A, e1L, SA1, tau, it, 0.f, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), e1Lb, adj.dA);
+  witness_bwd(F, A, B, p, g, q, o, e1b, e1Lb, e2b, conb, adj);
+}
+
+// Distance-matrix adjoint of one element: Dbar flows through dbar = |e1* - e2*|.
+CM_HD void ee_dbar_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float Dbar,
+                       Adj& adj) {
+  V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
+  QPPre q = qp_setup(a0, a1, b0, b1, p.w_reg);
+  QPOut o = qp_solve(q, p.w_reg, p);
+  V3 e1 = fma3(o.a1, a1 - a0, a0), e2 = fma3(o.a2, b1 - b0, b0);
+  V3 D = e1 - e2;
+  float r2 = dot(D, D);
+  if (!(r2 > 0.f)) return;
+  V3 Db = D * (Dbar * rsq(r2));
+  witness_bwd(F, A, B, p, g, q, o, Db, v3(0.f, 0.f, 0.f), -Db, 0.f, adj);
+}
+
+// ---------------------------------------------------------------- pose epilogue
+// R(q / |q|) reverse: Rbar (row-major) -> qbar for the raw quaternion (w, x, y, z).
+CM_HD void quat_rot_bwd(const float* q4, const float* Rb, float* qb) {
+  float n = sqrtf(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
+  float in = 1.f / n;
+  float w = q4[0] * in, x = q4[1] * in, y = q4[2] * in, z = q4[3] * in;
+  const float* R = Rb;
+  float gw = 2.f * (-z * R[1] + y * R[2] + z * R[3] - x * R[5] - y * R[6] + x * R[7]);
+  float gx = 2.f * (y * R[1] + z * R[2] + y * R[3] - 2.f * x * R[4] - w * R[5] + z * R[6] + w * R[7] - 2.f * x * R[8]);
+  float gy = 2.f * (-2.f * y * R[0] + x * R[1] + w * R[2] + x * R[3] + z * R[5] - w * R[6] + z * R[7] - 2.f * y * R[8]);
+  float gz = 2.f * (-2.f * z * R[0] - w * R[1] + x * R[2] + w * R[3] - 2.f * z * R[4] + y * R[5] + x * R[6] + y * R[7]);
+  float dp = gw * w + gx * x + gy * y + gz * z;
+  qb[0] = (gw - w * dp) * in;
+  qb[1] = (gx - x * dp) * in;
+  qb[2] = (gy - y * dp) * in;
+  qb[3] = (gz - z * dp) * in;
+}
+
+// Pair epilogue: adjoints of (R_rel, t_rel) plus the output-transform adjoints
+// (Rb_out for R_B, tb_out for t_B) -> gradients of both poses (14 floats).
+// R_rel = R_B^T R_A, t_rel = R_B^T (t_A - t_B).
+CM_HD void pose_epilogue(const float* P, const M3& RA, const M3& RB, const Adj& adj, const float* Rb_out,
+                         V3 tb_out, float* gpose) {
+  float RAb[9], RBb[9];
+  for (int i = 0; i < 9; ++i) RBb[i] = Rb_out[i];
+  // R_rel = R_B^T R_A: RAb = R_B adj.R; RBb += R_A adj.R^T
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      float a = 0.f, b = 0.f;
+      for (int k = 0; k < 3; ++k) {
+        a += RB.m[i * 3 + k] * adj.R[k * 3 + j];
+        b += RA.m[i * 3 + k] * adj.R[j * 3 + k];
+      }
+      RAb[i * 3 + j] = a;
+      RBb[i * 3 + j] += b;
+    }
+  // t_rel = R_B^T (t_A - t_B)
+  V3 d = v3(P[4] - P[11], P[5] - P[12], P[6] - P[13]);
+  V3 tA_b = mul(RB, adj.t);
+  add_outer(RBb, d, adj.t);
+  quat_rot_bwd(P, RAb, gpose);
+  gpose[4] = tA_b.x; gpose[5] = tA_b.y; gpose[6] = tA_b.z;
+  quat_rot_bwd(P + 7, RBb, gpose + 7);
+  gpose[11] = tb_out.x - tA_b.x; gpose[12] = tb_out.y - tA_b.y; gpose[13] = tb_out.z - tA_b.z;
+}
+
+}  // namespace cm

@@ -1,0 +1,327 @@
+// cm_bwd.cu -- adjoint kernel of the contact manifold (sm_103a).
+//
+// Given dL/d out (K x 8 per pair) it returns dL/d poses (14 per pair) and
+// dL/d dims (6 per pair).  Nothing of the forward is stored between the calls:
+// each CTA recomputes its pair's forward (candidates, distance matrix,
+// nearest-neighbour statistics, the SoftSort top-K list and normalisers) and
+// then runs the reverse sweep:
+//   1. SoftSort reverse per candidate (K exponentials) -> dL/d(p, d, n, w) and
+//      dL/d score, while accumulating dL/d s^_k of the K largest scores;
+//      vertex-SDF candidates are backpropagated to the parameters right away;
+//   2. each edge pair's reverse (indicators, sign, SDF normals through their
+//      Hessian-vector products, witnesses, 2x2 QP) except the nearest-neighbour
+//      softmax's coupling across its row and column, which is kept as
+//      t_b = dL/d nn_b * nn_b in the CTA's scratch, summed per row / column;
+//   3. the K top candidates receive dL/d s^_k through their own score;
+//   4. the distance-matrix adjoint dL/d D_kl = (nn1 R_k - t1 + nn2 C_l - t2) / tau
+//      flows through |e1* - e2*| and the QP;
+//   5. CTA reduction of the relative-pose and dims adjoints and the chain to
+//      both quaternions and translations.
+#include "cm_adjoint.cuh"
+#include "cm_pair.cuh"
+
+namespace cm {
+
+struct BwdShared {
+  float G[kMaxK][8];  // upstream of row k in B's frame
+  float Gout[kMaxK];  // G_k . out_k
+  float invZ[kMaxK];  // 1 / sum_i exp(-|s^_k - s_i| / tau)
+  float shat[kMaxK];
+  int sid[kMaxK];
+  float shatbar[kMaxK];
+  float Rout[9];      // adjoint of R_B from the output rotation
+  float tout[3];
+  float adj[18];      // CTA-reduced Adj: R (9), t (3), dA (3), dB (3)
+};
+
+__device__ __forceinline__ EEGeom ee_geom(const PairSmem& sm, int k, int l) {
+  uint32_t ea = sm.eA[k], eb = sm.eB[l];
+  EEGeom g;
+  g.a0 = sm.vA[ea & 0xffffu];
+  g.a1 = sm.vA[ea >> 16];
+  g.a0L = sm.vAl[ea & 0xffffu];
+  g.a1L = sm.vAl[ea >> 16];
+  g.b0 = sm.vB[eb & 0xffffu];
+  g.b1 = sm.vB[eb >> 16];
+  return g;
+}
+
+// SoftSort reverse of one candidate (y, s): ybar, sbar and the per-thread
+// partial dL/d s^_k (the K rows' dependence on the selected scores).
+__device__ __forceinline__ void ss_bwd(const BwdShared& bs, int K, float it, float k2, const float (&y)[8], float s,
+                                       float (&yb)[8], float& sb, float (&shb)[kMaxK]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) yb[c] = 0.f;
+  sb = 0.f;
+#pragma unroll
+  for (int k = 0; k < kMaxK; ++k) {
+    if (k < K) {
+      const float d = bs.shat[k] - s;
+      const float gam = ex2(-fabsf(d) * k2) * bs.invZ[k];
+      float a = -bs.Gout[k];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        yb[c] = fmaf(bs.G[k][c], gam, yb[c]);
+        a = fmaf(bs.G[k][c], y[c], a);
+      }
+      const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+      const float term = gam * a * sg * it;
+      sb += term;
+      shb[k] -= term;
+    }
+  }
+}
+
+__device__ __forceinline__ void adj_reduce(const Adj& a, float* dst) {
+  float v[18];
+  for (int i = 0; i < 9; ++i) v[i] = a.R[i];
+  v[9] = a.t.x; v[10] = a.t.y; v[11] = a.t.z;
+  v[12] = a.dA.x; v[13] = a.dA.y; v[14] = a.dA.z;
+  v[15] = a.dB.x; v[16] = a.dB.y; v[17] = a.dB.z;
+#pragma unroll
+  for (int i = 0; i < 18; ++i) {
+    float s = warp_sum(v[i]);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&dst[i], s);
+  }
+}
+
+__global__ void __launch_bounds__(256, 1) cm_bwd_kernel(const FwdArgs a, const float* grad_out, float* grad_poses,
+                                                        float* grad_dims) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ PairShared ps;
+  __shared__ BwdShared bs;
+  const PairSmem sm = carve(smem_raw, a.sm);
+  float* rowR = sm.rowL + a.sm.max_e;  // second half of the statistics buffers
+  float* colC = sm.colL + a.sm.max_e;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int K = a.p.K;
+  float* Dm = a.scratch + (int64_t)blockIdx.x * a.scratch_stride * 3;
+  float* T1 = Dm + a.scratch_stride;
+  float* T2 = T1 + a.scratch_stride;
+  for (int pi = blockIdx.x; pi < a.n_pairs; pi += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) pair_setup(a, pi, ps);
+    __syncthreads();
+    if (ps.bad) {
+      if (threadIdx.x == 0) atomicCAS(a.err, 0, pi + 1);
+      for (int i = threadIdx.x; i < 14; i += blockDim.x) grad_poses[(size_t)pi * 14 + i] = __int_as_float(0x7fc00000);
+      if (grad_dims)
+        for (int i = threadIdx.x; i < 6; i += blockDim.x) grad_dims[(size_t)pi * 6 + i] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    pair_stage(a, pi, ps, sm);
+    __syncthreads();
+    const PairBodies bb = pair_bodies(ps, sm);
+    const float k2 = ps.k2, it = ps.inv_tau;
+    Frame F;
+    F.R = ps.Rrel;
+    F.t = ps.trel;
+    F.tau = ps.tau;
+    F.inv_tau = it;
+    F.k2 = k2;
+    const bool one_sided = (a.p.flags & 2) != 0;
+    const bool no_ee = one_sided || (a.p.flags & 1) != 0;
+    const int nvs = one_sided ? ps.nvA : ps.nvA + ps.nvB;
+    const int neA = ps.neA, neB = ps.neB, nee = no_ee ? 0 : neA * neB;
+
+    // ================= forward recompute
+    WarpTopK st;
+    wtk_init(st);
+    float y[8], y2[8];
+    for (int base = warp * 32; base < nvs; base += nwarps * 32) {
+      const int c = base + lane;
+      const bool valid = c < nvs;
+      float s = 0.f;
+      if (valid) s = vs_candidate(ps, sm, bb, c, y);
+      wtk_push(st, valid, s, y, K, k2, c);
+    }
+    if (nee) {
+      for (int i = threadIdx.x; i < nee; i += blockDim.x) {
+        const int k = i / neB, l = i - k * neB;
+        Dm[i] = ee_witness(edge_pair(sm, k, l), a.p).dbar;
+      }
+      __syncthreads();
+      for (int k = warp; k < neA; k += nwarps) {
+        float m = 3.0e38f;
+        for (int l = lane; l < neB; l += 32) m = fminf(m, Dm[k * neB + l]);
+        m = warp_min(m);
+        float S = 0.f;
+        for (int l = lane; l < neB; l += 32) S += ex2((m - Dm[k * neB + l]) * k2);
+        S = warp_sum(S);
+        if (lane == 0) {
+          sm.rowL[k] = m - ps.tau * kLn2 * lg2(S);
+          rowR[k] = 0.f;
+        }
+      }
+      for (int l = threadIdx.x; l < neB; l += blockDim.x) {
+        float m = 3.0e38f;
+        for (int k = 0; k < neA; ++k) m = fminf(m, Dm[k * neB + l]);
+        float S = 0.f;
+        for (int k = 0; k < neA; ++k) S += ex2((m - Dm[k * neB + l]) * k2);
+        sm.colL[l] = m - ps.tau * kLn2 * lg2(S);
+        colC[l] = 0.f;
+      }
+      __syncthreads();
+      for (int base = warp * 32; base < nee; base += nwarps * 32) {
+        const int i = base + lane;
+        const bool valid = i < nee;
+        float s1 = 0.f, s2 = 0.f;
+        if (valid) {
+          const int k = i / neB, l = i - k * neB;
+          const EdgePair ep = edge_pair(sm, k, l);
+          Witness w = ee_witness(ep, a.p);
+          ee_candidates(ps, sm, bb, ep, w, sm.rowL[k], sm.colL[l], y, y2, s1, s2);
+        }
+        wtk_push(st, valid, s1, y, K, k2, nvs + 2 * i);
+        wtk_push(st, valid, s2, y2, K, k2, nvs + 2 * i + 1);
+      }
+    }
+    wtk_store(st, sm.warp + warp * kWarpStateFloats, K);
+    __syncthreads();
+    if (warp == 0) {
+      for (int w = 1; w < nwarps; ++w) wtk_merge(st, sm.warp + w * kWarpStateFloats, K, k2);
+      float Z = 1.f;
+      wtk_finish(st, K, k2, y, &Z);
+      // upstream of row k in B's frame and the output-rotation adjoints
+      float Rl[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      V3 tl = v3(0.f, 0.f, 0.f);
+      if (lane < K) {
+        const float* g = grad_out + ((size_t)pi * K + lane) * 8;
+        V3 gp = v3(g[0], g[1], g[2]), gn = v3(g[4], g[5], g[6]);
+        V3 gpb = mulT(ps.RB, gp), gnb = mulT(ps.RB, gn);
+        float G[8] = {gpb.x, gpb.y, gpb.z, g[3], gnb.x, gnb.y, gnb.z, g[7]};
+        float go = 0.f;
+        for (int c = 0; c < 8; ++c) {
+          bs.G[lane][c] = G[c];
+          go = fmaf(G[c], y[c], go);
+        }
+        bs.Gout[lane] = go;
+        bs.invZ[lane] = 1.0f / Z;
+        bs.shat[lane] = st.ls;
+        bs.sid[lane] = st.lid;
+        bs.shatbar[lane] = 0.f;
+        add_outer(Rl, gp, v3(y[0], y[1], y[2]));
+        add_outer(Rl, gn, v3(y[4], y[5], y[6]));
+        tl = gp;
+      }
+      for (int i = 0; i < 9; ++i) Rl[i] = warp_sum(Rl[i]);
+      tl = v3(warp_sum(tl.x), warp_sum(tl.y), warp_sum(tl.z));
+      if (lane == 0) {
+        for (int i = 0; i < 9; ++i) bs.Rout[i] = Rl[i];
+        bs.tout[0] = tl.x; bs.tout[1] = tl.y; bs.tout[2] = tl.z;
+      }
+    }
+    for (int i = threadIdx.x; i < 18; i += blockDim.x) bs.adj[i] = 0.f;
+    __syncthreads();
+
+    // ================= reverse sweep
+    Adj adj;
+    adj_zero(adj);
+    float shb[kMaxK];
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) shb[k] = 0.f;
+    for (int c = threadIdx.x; c < nvs; c += blockDim.x) {
+      float s = vs_candidate(ps, sm, bb, c, y);
+      float yb[8], sb;
+      ss_bwd(bs, K, it, k2, y, s, yb, sb, shb);
+      if (c < ps.nvA) vs_bwd<true>(F, bb.A, bb.B, sm.vAl[c], ld3(sm.vA[c]), yb, sb, adj);
+      else vs_bwd<false>(F, bb.A, bb.B, sm.vB[c - ps.nvA], ld3(sm.vB[c - ps.nvA]), yb, sb, adj);
+    }
+    for (int i = threadIdx.x; i < nee; i += blockDim.x) {
+      const int k = i / neB, l = i - k * neB;
+      float t1, t2;
+      ee_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, k, l), sm.rowL[k], sm.colL[l],
+             [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
+               ss_bwd(bs, K, it, k2, cc.y1, cc.s1, yb1, sb1, shb);
+               ss_bwd(bs, K, it, k2, cc.y2, cc.s2, yb2, sb2, shb);
+             },
+             t1, t2, adj);
+      T1[i] = t1;
+      T2[i] = t2;
+      atomicAdd(&rowR[k], t1);
+      atomicAdd(&colC[l], t2);
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) {
+      if (k < K) {
+        float v = warp_sum(shb[k]);
+        if (lane == 0) atomicAdd(&bs.shatbar[k], v);
+      }
+    }
+    __syncthreads();
+    // the K selected scores: their own candidates receive dL/d s^_k
+    if (threadIdx.x < K) {
+      const int k = threadIdx.x;
+      const int id = bs.sid[k];
+      const float sx = bs.shatbar[k];
+      const float zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (id >= 0 && id < nvs) {
+        if (id < ps.nvA) vs_bwd<true>(F, bb.A, bb.B, sm.vAl[id], ld3(sm.vA[id]), zero, sx, adj);
+        else vs_bwd<false>(F, bb.A, bb.B, sm.vB[id - ps.nvA], ld3(sm.vB[id - ps.nvA]), zero, sx, adj);
+      } else if (id >= nvs) {
+        const int e = id - nvs, i = e >> 1, b = e & 1, kk = i / neB, ll = i - kk * neB;
+        float t1, t2;
+        ee_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, kk, ll), sm.rowL[kk], sm.colL[ll],
+               [&](const EECand&, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
+                 for (int c = 0; c < 8; ++c) {
+                   yb1[c] = 0.f;
+                   yb2[c] = 0.f;
+                 }
+                 sb1 = b == 0 ? sx : 0.f;
+                 sb2 = b == 1 ? sx : 0.f;
+               },
+               t1, t2, adj);
+        atomicAdd(&T1[i], t1);
+        atomicAdd(&T2[i], t2);
+        atomicAdd(&rowR[kk], t1);
+        atomicAdd(&colC[ll], t2);
+      }
+    }
+    __syncthreads();
+    // distance-matrix adjoint through the nearest-neighbour softmaxes
+    for (int i = threadIdx.x; i < nee; i += blockDim.x) {
+      const int k = i / neB, l = i - k * neB;
+      const float D = Dm[i];
+      const float nn1 = ex2((sm.rowL[k] - D) * k2), nn2 = ex2((sm.colL[l] - D) * k2);
+      const float Db = (nn1 * rowR[k] - T1[i] + nn2 * colC[l] - T2[i]) * it;
+      if (Db != 0.f) ee_dbar_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, k, l), Db, adj);
+    }
+    adj_reduce(adj, bs.adj);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Adj r;
+      for (int i = 0; i < 9; ++i) r.R[i] = bs.adj[i];
+      r.t = v3(bs.adj[9], bs.adj[10], bs.adj[11]);
+      r.dA = v3(bs.adj[12], bs.adj[13], bs.adj[14]);
+      r.dB = v3(bs.adj[15], bs.adj[16], bs.adj[17]);
+      float gp[14];
+      pose_epilogue(a.poses + 14 * (size_t)pi, ps.RA, ps.RB, r, bs.Rout, v3(bs.tout[0], bs.tout[1], bs.tout[2]), gp);
+      for (int i = 0; i < 14; ++i) grad_poses[(size_t)pi * 14 + i] = gp[i];
+      if (grad_dims) {
+        float* gd = grad_dims + (size_t)pi * 6;
+        gd[0] = r.dA.x; gd[1] = r.dA.y; gd[2] = r.dA.z;
+        gd[3] = r.dB.x; gd[4] = r.dB.y; gd[5] = r.dB.z;
+      }
+    }
+  }
+}
+
+cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,
+                       int block, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(cm_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  cm_bwd_kernel<<<grid, block, a.sm.total, s>>>(a, grad_out, grad_poses, grad_dims);
+  return cudaGetLastError();
+}
+
+int bwd_max_blocks_per_sm(int block, int smem_bytes) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel, block, smem_bytes) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+}  // namespace cm

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) cm_fwd_kernel(const FwdArgs a) {
       const bool valid = c < nvs;
       float s = 0.f;
       if (valid) s = vs_candidate(ps, sm, bb, c, y);
-      wtk_push(st, valid, s, y, K, k2);
+      wtk_push(st, valid, s, y, K, k2, c);
     }
 
     if (!no_ee) {
@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(256) cm_fwd_kernel(const FwdArgs a) {
           Witness w = ee_witness(ep, a.p);
           ee_candidates(ps, sm, bb, ep, w, sm.rowL[k], sm.colL[l], y, y2, s1, s2);
         }
-        wtk_push(st, valid, s1, y, K, k2);
-        wtk_push(st, valid, s2, y2, K, k2);
+        wtk_push(st, valid, s1, y, K, k2, nvs + 2 * i);
+        wtk_push(st, valid, s2, y2, K, k2, nvs + 2 * i + 1);
       }
     }
 

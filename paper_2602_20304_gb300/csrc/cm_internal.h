@@ -49,9 +49,12 @@ struct FwdArgs {
 };
 
 constexpr int kMaxK = 16;
-constexpr int kWarpStateFloats = kMaxK * 9 + 10;
+constexpr int kWarpStateFloats = kMaxK * 9 + 10 + kMaxK;  // list, C, threshold, ids
 
 cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s);
 int fwd_max_blocks_per_sm(int block, int smem_bytes);
+cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,
+                       int block, cudaStream_t s);
+int bwd_max_blocks_per_sm(int block, int smem_bytes);
 
 }  // namespace cm

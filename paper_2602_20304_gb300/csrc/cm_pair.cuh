@@ -94,12 +94,12 @@ __device__ inline void pair_stage(const FwdArgs& a, int pi, const PairShared& ps
     V3 v = map_vertex(ps.kindA, u.x, u.y, u.z, u.w, ps.dA);
     V3 y = mul(ps.Rrel, v) + ps.trel;
     sm.vA[i] = make_float4(y.x, y.y, y.z, 0.f);
-    sm.vAl[i] = make_float4(v.x, v.y, v.z, 0.f);
+    sm.vAl[i] = make_float4(v.x, v.y, v.z, u.w);  // w: template cap sign (capsules)
   }
   for (int i = threadIdx.x; i < ps.nvB; i += blockDim.x) {
     float4 u = a.verts[B.v_off + i];
     V3 v = map_vertex(ps.kindB, u.x, u.y, u.z, u.w, ps.dB);
-    sm.vB[i] = make_float4(v.x, v.y, v.z, 0.f);
+    sm.vB[i] = make_float4(v.x, v.y, v.z, u.w);
   }
   for (int i = threadIdx.x; i < ps.neA; i += blockDim.x) sm.eA[i] = a.edges[A.e_off + i];
   for (int i = threadIdx.x; i < ps.neB; i += blockDim.x) sm.eB[i] = a.edges[B.e_off + i];

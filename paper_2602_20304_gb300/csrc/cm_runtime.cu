@@ -108,8 +108,8 @@ SmemLayout make_layout(const cm_context* c, int nwarps) {
   L.pB = o; o = align16(o + 16 * c->max_p);
   L.eA = o; o = align16(o + 4 * c->max_e);
   L.eB = o; o = align16(o + 4 * c->max_e);
-  L.rowL = o; o = align16(o + 4 * c->max_e);
-  L.colL = o; o = align16(o + 4 * c->max_e);
+  L.rowL = o; o = align16(o + 8 * c->max_e);   // soft minima (+ row adjoint sums in the backward)
+  L.colL = o; o = align16(o + 8 * c->max_e);
   L.warp = o; o = align16(o + 4 * kWarpStateFloats * nwarps);
   L.total = o;
   return L;
@@ -316,6 +316,55 @@ cm_status cm_contact_manifold_fwd(cm_context* c, int32_t n_pairs, const int32_t*
 }
 
 }  // extern "C"
+
+extern "C" cm_status cm_contact_manifold_bwd(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms,
+                                              const float* poses, const float* dims, const float* tau,
+                                              const cm_params* params, const float* grad_out, float* grad_poses,
+                                              float* grad_dims, void* stream) {
+  if (!c) return fail(CM_ERR_INVALID_ARG, "NULL context");
+  cm_status st = check_params(params);
+  if (st != CM_OK) return st;
+  if (n_pairs < 0) return fail(CM_ERR_INVALID_ARG, "n_pairs < 0");
+  if (n_pairs == 0) return CM_OK;
+  if (!pair_geoms || !poses || !grad_out || !grad_poses)
+    return fail(CM_ERR_INVALID_ARG, "pair_geoms, poses, grad_out and grad_poses are required");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
+  if (params->flags & (CM_FLAG_NO_EE | CM_FLAG_ONE_SIDED)) {
+    const int min_cands = (params->flags & CM_FLAG_ONE_SIDED) ? c->min_v : 2 * c->min_v;
+    if (params->K > min_cands)
+      return fail(CM_ERR_INVALID_ARG, "K exceeds the vertex-contact count of the smallest registered geometry");
+  } else if (c->min_e < 3) {
+    return fail(CM_ERR_INVALID_ARG, "E-E contacts need every registered geometry to have >= 3 edges");
+  }
+  cudaSetDevice(c->device);
+  if ((st = sync_geometry_locked(c)) != CM_OK) return st;
+  const int block = 256;
+  FwdArgs a{};
+  a.sm = make_layout(c, block / 32);
+  const int per_sm = bwd_max_blocks_per_sm(block, a.sm.total);
+  const int grid = std::max(1, std::min<int>(n_pairs, c->num_sms * per_sm));
+  const int64_t stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
+  if ((st = ensure_scratch(c, (size_t)grid * stride * 3)) != CM_OK) return st;
+  a.hdr = c->d_hdr;
+  a.n_geoms = (int32_t)c->hdr.size();
+  a.verts = c->d_verts;
+  a.edges = c->d_edges;
+  a.planes = c->d_planes;
+  a.n_pairs = n_pairs;
+  a.pair_geoms = pair_geoms;
+  a.poses = poses;
+  a.dims = dims;
+  a.tau = tau;
+  a.p = Params{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K, params->flags};
+  a.out = nullptr;
+  a.scratch = c->d_scratch;
+  a.scratch_stride = stride;
+  a.err = c->d_err;
+  cudaError_t e = launch_bwd(a, grad_out, grad_poses, grad_dims, grid, block, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return CM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free forward entry point.

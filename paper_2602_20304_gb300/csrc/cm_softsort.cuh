@@ -24,12 +24,14 @@ constexpr float kNegInf = -INFINITY;
 struct WarpTopK {
   float ls;      // score of the list entry held by this lane (lanes < K), -inf if empty
   float ly[8];   // its payload (p, d, n, w)
+  int lid;       // its candidate id
   float C[9];    // this lane's share of the below-threshold accumulator (weight, payload)
   float thr;     // warp-uniform K-th largest score so far (-inf until K entries)
 };
 
 __device__ __forceinline__ void wtk_init(WarpTopK& st) {
   st.ls = kNegInf;
+  st.lid = -1;
 #pragma unroll
   for (int c = 0; c < 8; ++c) st.ly[c] = 0.f;
 #pragma unroll
@@ -40,12 +42,13 @@ __device__ __forceinline__ void wtk_init(WarpTopK& st) {
 // Offers one candidate per lane (valid lanes only).  All 32 lanes must call.
 // k2 = log2(e) / tau.
 __device__ __forceinline__ void wtk_push(WarpTopK& st, bool valid, float s, const float (&y)[8],
-                                         int K, float k2) {
+                                         int K, float k2, int id = -1) {
   const int lane = threadIdx.x & 31;
   unsigned m = __ballot_sync(kFull, valid && s > st.thr);
   while (m) {
     const int src = __ffs(m) - 1;
     const float sn = __shfl_sync(kFull, s, src);
+    const int idn = __shfl_sync(kFull, id, src);
     float yn[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) yn[c] = __shfl_sync(kFull, y[c], src);
@@ -55,16 +58,19 @@ __device__ __forceinline__ void wtk_push(WarpTopK& st, bool valid, float s, cons
 #pragma unroll
     for (int c = 0; c < 8; ++c) old_y[c] = st.ly[c];
     const float up_s = __shfl_up_sync(kFull, st.ls, 1);
+    const int up_id = __shfl_up_sync(kFull, st.lid, 1);
     float up_y[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) up_y[c] = __shfl_up_sync(kFull, st.ly[c], 1);
     if (lane < K) {
       if (lane > pos) {
         st.ls = up_s;
+        st.lid = up_id;
 #pragma unroll
         for (int c = 0; c < 8; ++c) st.ly[c] = up_y[c];
       } else if (lane == pos) {
         st.ls = sn;
+        st.lid = idn;
 #pragma unroll
         for (int c = 0; c < 8; ++c) st.ly[c] = yn[c];
       }
@@ -126,6 +132,7 @@ __device__ __forceinline__ void wtk_store(const WarpTopK& st, float* dst, int K)
     for (int c = 0; c < 9; ++c) dst[16 * 9 + c] = Cs[c];
     dst[16 * 9 + 9] = st.thr;
   }
+  if (lane < K) dst[16 * 9 + 10 + lane] = __int_as_float(st.lid);
 }
 
 // Folds a stored warp state into this warp's state.
@@ -134,16 +141,18 @@ __device__ __forceinline__ void wtk_merge(WarpTopK& st, const float* src, int K,
   float y[8];
   float s = kNegInf;
   bool valid = false;
+  int id = -1;
   if (lane < K) {
     s = src[lane * 9];
     valid = s != kNegInf;
+    id = __float_as_int(src[16 * 9 + 10 + lane]);
 #pragma unroll
     for (int c = 0; c < 8; ++c) y[c] = src[lane * 9 + 1 + c];
   } else {
 #pragma unroll
     for (int c = 0; c < 8; ++c) y[c] = 0.f;
   }
-  wtk_push(st, valid, s, y, K, k2);
+  wtk_push(st, valid, s, y, K, k2, id);
   const float thr_w = src[16 * 9 + 9];
   if (lane == 0 && thr_w != kNegInf) {
     // thr_w <= st.thr once the other warp's K entries have been offered
@@ -153,8 +162,9 @@ __device__ __forceinline__ void wtk_merge(WarpTopK& st, const float* src, int K,
   }
 }
 
-// Final rows: lane k < K returns out_k in y (weights normalised).  All lanes call.
-__device__ __forceinline__ void wtk_finish(const WarpTopK& st, int K, float k2, float (&y)[8]) {
+// Final rows: lane k < K returns out_k in y (weights normalised) and, in Z, the
+// row's normaliser sum_i exp(-|s^_k - s_i| / tau).  All lanes call.
+__device__ __forceinline__ void wtk_finish(const WarpTopK& st, int K, float k2, float (&y)[8], float* Z = nullptr) {
   const int lane = threadIdx.x & 31;
   float Ct[9];
 #pragma unroll
@@ -174,6 +184,7 @@ __device__ __forceinline__ void wtk_finish(const WarpTopK& st, int K, float k2, 
   const float inv = 1.0f / num[0];
 #pragma unroll
   for (int c = 0; c < 8; ++c) y[c] = num[1 + c] * inv;
+  if (Z) *Z = num[0];
 }
 
 }  // namespace cm

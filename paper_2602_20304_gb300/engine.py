@@ -47,8 +47,45 @@ class Engine:
         api.cm_contact_manifold_fwd(self.ctx, pair_geoms, poses, dims, tau, params, out, stream)
         return out
 
+    def backward(self, pair_geoms, poses, dims, tau, grad_out, params=None, stream=None):
+        """(dL/d poses, dL/d dims or None) for upstream ``grad_out`` (n, K, 8)."""
+        params = params or self.params()
+        gp = torch.empty_like(poses)
+        gd = None if dims is None else torch.empty_like(dims)
+        api.cm_contact_manifold_bwd(self.ctx, pair_geoms, poses, dims, tau, params,
+                                    grad_out.contiguous(), gp, gd, stream)
+        return gp, gd
+
     def check(self):
         api.cm_check_device_error(self.ctx)
+
+
+class ContactManifold(torch.autograd.Function):
+    """out = manifold(poses, dims); differentiable in poses and dims through the
+    library's adjoint kernel (the backward recomputes the forward per pair)."""
+
+    @staticmethod
+    def forward(ctx, poses, dims, engine, pair_geoms, tau, params):
+        out = engine.forward(pair_geoms, poses.detach().contiguous(),
+                             None if dims is None else dims.detach().contiguous(), tau, params)
+        ctx.engine, ctx.params = engine, params
+        ctx.has_dims = dims is not None
+        ctx.save_for_backward(poses.detach(), dims.detach() if dims is not None else poses.new_empty(0),
+                              pair_geoms, tau if tau is not None else poses.new_empty(0))
+        ctx.has_tau = tau is not None
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        poses, dims, pg, tau = ctx.saved_tensors
+        gp, gd = ctx.engine.backward(pg, poses.contiguous(), dims.contiguous() if ctx.has_dims else None,
+                                     tau if ctx.has_tau else None, grad_out, ctx.params)
+        return gp, (gd if ctx.has_dims else None), None, None, None, None
+
+
+def contact_manifold(engine, pair_geoms, poses, dims=None, tau=None, params=None):
+    """Differentiable manifold (n, K, 8) of the pairs; see ``ContactManifold``."""
+    return ContactManifold.apply(poses, dims, engine, pair_geoms, tau, params or engine.params())
 
 
 def workload_tensors(w, device="cuda", id_map=None):
