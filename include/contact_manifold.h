@@ -158,6 +158,37 @@ cm_status cm_contact_manifold_bwd(cm_context* ctx, int32_t n_pairs, const int32_
                                   const cm_params* params, const float* grad_out, float* grad_poses,
                                   float* grad_dims, void* stream);
 
+/* Batching layer (not part of the paper's method).
+ *
+ * cm_autotune times a few launch shapes (threads per CTA, CTAs per SM, with or
+ * without the size-ordered work list) of the forward -- and of the adjoint
+ * when grad_out is given -- on this batch, and keeps the fastest for later
+ * calls with the same direction, batch-size bucket (power of two), largest
+ * edge count (bucket of 32) and flags.  It runs the kernels several times,
+ * overwrites out / grad_poses / grad_dims, and synchronises `stream`.
+ * cm_get_launch_shape reports the shape a call would use. */
+cm_status cm_autotune(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
+                      const float* dims, const float* tau, const cm_params* params, float* out,
+                      const float* grad_out, float* grad_poses, float* grad_dims, void* stream);
+cm_status cm_get_launch_shape(const cm_context* ctx, int32_t n_pairs, int32_t backward, int32_t flags,
+                              int32_t* block, int32_t* ctas_per_sm, int32_t* ordered);
+
+/* A plan is the steady-state step of one fixed batch -- work ordering, forward
+ * and (when grad_out != NULL) adjoint -- captured once into a CUDA graph with
+ * its own scratch, then replayed by cm_plan_launch with a single graph launch.
+ * The plan keeps the device pointers it was made with: the caller updates the
+ * contents of poses / dims / tau / grad_out in place between launches and
+ * reads out / grad_poses / grad_dims after the launch completes on `stream`.
+ * Registering new geometry invalidates plans (cm_plan_launch then returns
+ * CM_ERR_INVALID_ARG).  Plans of one context may run concurrently on
+ * different streams; each owns its scratch.  cm_plan_create synchronises. */
+typedef struct cm_plan cm_plan;
+cm_status cm_plan_create(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
+                         const float* dims, const float* tau, const cm_params* params, float* out,
+                         const float* grad_out, float* grad_poses, float* grad_dims, cm_plan** plan);
+cm_status cm_plan_launch(cm_plan* plan, void* stream);
+void cm_plan_destroy(cm_plan* plan);
+
 /* Same computation and arguments as cm_contact_manifold_fwd, but the call
  * allocates no memory (no cudaMalloc, no library allocation).  The paper has no
  * counterpart: this exists for callers that cannot allocate while they run the

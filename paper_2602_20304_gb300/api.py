@@ -58,6 +58,15 @@ _SIGS = {
                                                ctypes.POINTER(cm_params), _vp, _vp, _vp, _vp]),
     "cm_contact_manifold_fwd_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
                                                        ctypes.POINTER(cm_params), _vp, _vp]),
+    "cm_autotune": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.POINTER(cm_params),
+                                   _vp, _vp, _vp, _vp, _vp]),
+    "cm_get_launch_shape": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    "cm_plan_create": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.POINTER(cm_params),
+                                      _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "cm_plan_launch": (ctypes.c_int, [_vp, _vp]),
+    "cm_plan_destroy": (None, [_vp]),
     "cm_measure_pipe_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double)]),
 }
@@ -193,6 +202,39 @@ def cm_contact_manifold_fwd_noalloc(ctx, pair_geoms, poses, dims, tau, params, o
     _check_tensor(out, "out", torch.float32, n)
     _check(_lib.cm_contact_manifold_fwd_noalloc(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau),
                                                 ctypes.byref(params), _ptr(out), _stream_handle(stream)))
+
+
+def cm_autotune(ctx, pair_geoms, poses, dims, tau, params, out, grad_out=None, grad_poses=None,
+                grad_dims=None, stream=None) -> None:
+    """Pick and remember the fastest launch shape for this batch (see the C header)."""
+    n = int(pair_geoms.shape[0])
+    _check(_lib.cm_autotune(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau), ctypes.byref(params),
+                            _ptr(out), _ptr(grad_out), _ptr(grad_poses), _ptr(grad_dims), _stream_handle(stream)))
+
+
+def cm_get_launch_shape(ctx, n_pairs, backward=False, flags=0):
+    b, p, o = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.cm_get_launch_shape(ctx, n_pairs, int(backward), flags, ctypes.byref(b), ctypes.byref(p),
+                                    ctypes.byref(o)))
+    return b.value, p.value, o.value
+
+
+def cm_plan_create(ctx, pair_geoms, poses, dims, tau, params, out, grad_out=None, grad_poses=None,
+                   grad_dims=None):
+    """Capture the step of this batch in a CUDA graph; returns the plan handle."""
+    h = _vp()
+    n = int(pair_geoms.shape[0])
+    _check(_lib.cm_plan_create(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau), ctypes.byref(params),
+                               _ptr(out), _ptr(grad_out), _ptr(grad_poses), _ptr(grad_dims), ctypes.byref(h)))
+    return h
+
+
+def cm_plan_launch(plan, stream=None) -> None:
+    _check(_lib.cm_plan_launch(plan, _stream_handle(stream)))
+
+
+def cm_plan_destroy(plan) -> None:
+    _lib.cm_plan_destroy(plan)
 
 
 def cm_measure_pipe_peaks(device: int = 0):

@@ -98,7 +98,10 @@ __global__ void __launch_bounds__(256, 1) cm_bwd_kernel(const FwdArgs a, const f
   float* Dm = a.scratch + (int64_t)blockIdx.x * a.scratch_stride * 3;
   float* T1 = Dm + a.scratch_stride;
   float* T2 = T1 + a.scratch_stride;
-  for (int pi = blockIdx.x; pi < a.n_pairs; pi += gridDim.x) {
+  int iter = 0;
+  for (;;) {
+    const int pi = next_pair(a, iter);
+    if (pi < 0) break;
     __syncthreads();
     if (threadIdx.x == 0) pair_setup(a, pi, ps);
     __syncthreads();

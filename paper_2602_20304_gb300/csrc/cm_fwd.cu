@@ -17,23 +17,7 @@
 
 namespace cm {
 
-__device__ __forceinline__ int next_pair(const FwdArgs& a, int& slot_iter) {
-  if (a.work_counter) {
-    __shared__ int next;
-    __syncthreads();
-    if (threadIdx.x == 0) next = atomicAdd(a.work_counter, 1);
-    __syncthreads();
-    int i = next;
-    if (i >= a.n_pairs) return -1;
-    return a.order ? a.order[i] : i;
-  }
-  int i = blockIdx.x + slot_iter * gridDim.x;
-  ++slot_iter;
-  if (i >= a.n_pairs) return -1;
-  return a.order ? a.order[i] : i;
-}
-
-__global__ void __launch_bounds__(256) cm_fwd_kernel(const FwdArgs a) {
+__global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PairShared ps;
   const PairSmem sm = carve(smem_raw, a.sm);

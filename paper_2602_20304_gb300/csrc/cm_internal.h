@@ -48,6 +48,14 @@ struct FwdArgs {
   const int32_t* order;      // optional pair order for the work queue (may be null)
 };
 
+// Launch shape of a manifold kernel: threads per CTA, CTAs per SM (0 = as many
+// as fit) and whether pairs are pulled from the size-ordered work list.
+struct LaunchCfg {
+  int block;
+  int per_sm;
+  int ordered;
+};
+
 constexpr int kMaxK = 16;
 constexpr int kWarpStateFloats = kMaxK * 9 + 10 + kMaxK;  // list, C, threshold, ids
 
@@ -56,5 +64,7 @@ int fwd_max_blocks_per_sm(int block, int smem_bytes);
 cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,
                        int block, cudaStream_t s);
 int bwd_max_blocks_per_sm(int block, int smem_bytes);
+cudaError_t launch_order(const int32_t* pair_geoms, const GeomHeader* hdr, int n_geoms, int n, int32_t* order,
+                         int32_t* counter, cudaStream_t s);
 
 }  // namespace cm

@@ -107,6 +107,25 @@ __device__ inline void pair_stage(const FwdArgs& a, int pi, const PairShared& ps
   for (int i = threadIdx.x; i < ps.npB; i += blockDim.x) sm.pB[i] = a.planes[B.p_off + i];
 }
 
+// Next pair of this CTA: from the size-ordered work queue when one is given
+// (largest pairs first, an atomic counter shared by all CTAs), else a static
+// grid stride.  Called by every thread of the CTA.
+__device__ __forceinline__ int next_pair(const FwdArgs& a, int& slot_iter) {
+  if (a.work_counter) {
+    __shared__ int next;
+    __syncthreads();
+    if (threadIdx.x == 0) next = atomicAdd(a.work_counter, 1);
+    __syncthreads();
+    int i = next;
+    if (i >= a.n_pairs) return -1;
+    return a.order ? a.order[i] : i;
+  }
+  int i = blockIdx.x + slot_iter * gridDim.x;
+  ++slot_iter;
+  if (i >= a.n_pairs) return -1;
+  return a.order ? a.order[i] : i;
+}
+
 __device__ __forceinline__ V3 ld3(const float4& f) { return v3(f.x, f.y, f.z); }
 
 struct PairBodies {

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -49,6 +50,12 @@ struct cm_context {
   float* d_scratch = nullptr;
   size_t scratch_floats = 0;
   int* d_err = nullptr;
+  // size-ordered work list of the last batch and its atomic counter
+  int32_t* d_order = nullptr;
+  size_t cap_order = 0;
+  int32_t* d_counter = nullptr;
+  uint64_t geom_gen = 0;                 // bumped by every geometry upload
+  std::map<uint64_t, cm::LaunchCfg> tuned;  // autotuned launch shapes
 };
 
 namespace {
@@ -79,6 +86,7 @@ cm_status sync_geometry_locked(cm_context* c) {
   if ((e = grow_upload(c->d_edges, c->cap_edges, c->edges)) != cudaSuccess) return cuda_fail(e, "geometry upload");
   if ((e = grow_upload(c->d_planes, c->cap_planes, c->planes)) != cudaSuccess) return cuda_fail(e, "geometry upload");
   c->dirty = false;
+  ++c->geom_gen;
   return CM_OK;
 }
 
@@ -126,6 +134,123 @@ cm_status ensure_scratch(cm_context* c, size_t floats) {
   return CM_OK;
 }
 
+
+cm_status ensure_order(cm_context* c, size_t n) {
+  if (!c->d_counter) {
+    cudaError_t e = cudaMalloc(&c->d_counter, sizeof(int32_t));
+    if (e != cudaSuccess) return fail(CM_ERR_OOM, std::string("work counter allocation: ") + cudaGetErrorString(e));
+  }
+  if (n <= c->cap_order) return CM_OK;
+  if (c->d_order) cudaFree(c->d_order);
+  c->d_order = nullptr;
+  c->cap_order = 0;
+  cudaError_t e = cudaMalloc(&c->d_order, n * sizeof(int32_t));
+  if (e != cudaSuccess) return fail(CM_ERR_OOM, std::string("work list allocation: ") + cudaGetErrorString(e));
+  c->cap_order = n;
+  return CM_OK;
+}
+
+cm_status check_k(const cm_context* c, const cm_params* params) {
+  if (params->flags & (CM_FLAG_NO_EE | CM_FLAG_ONE_SIDED)) {
+    const int min_cands = (params->flags & CM_FLAG_ONE_SIDED) ? c->min_v : 2 * c->min_v;
+    if (params->K > min_cands)
+      return fail(CM_ERR_INVALID_ARG, "K exceeds the vertex-contact count of the smallest registered geometry");
+  } else if (c->min_e < 3) {
+    return fail(CM_ERR_INVALID_ARG, "E-E contacts need every registered geometry to have >= 3 edges");
+  }
+  return CM_OK;
+}
+
+// Autotune cache key: direction, batch size (power-of-two bucket), largest edge
+// count (bucket of 32) and the flags that change the work.
+uint64_t tune_key(int bwd, int n_pairs, int max_e, int flags) {
+  int nb = 0;
+  while ((1 << nb) < n_pairs && nb < 31) ++nb;
+  return ((uint64_t)bwd << 40) | ((uint64_t)nb << 32) | ((uint64_t)(max_e / 32) << 8) | (uint64_t)(flags & 3);
+}
+
+LaunchCfg default_cfg(const cm_context* c, int bwd, int n_pairs) {
+  LaunchCfg g;
+  g.block = 256;
+  g.per_sm = 0;
+  g.ordered = n_pairs >= 2 * c->num_sms ? 1 : 0;
+  (void)bwd;
+  return g;
+}
+
+LaunchCfg pick_cfg(const cm_context* c, int bwd, int n_pairs, int flags) {
+  auto it = c->tuned.find(tune_key(bwd, n_pairs, c->max_e, flags));
+  return it != c->tuned.end() ? it->second : default_cfg(c, bwd, n_pairs);
+}
+
+Params to_params(const cm_params* p) {
+  return Params{p->tau, p->w_reg, p->eps_clip, p->eps_min, p->eps_comp, p->K, p->flags};
+}
+
+// Grid and shared-memory layout of one launch shape.
+void shape(const cm_context* c, int bwd, const LaunchCfg& cfg, int n_pairs, SmemLayout& L, int& grid) {
+  L = make_layout(c, cfg.block / 32);
+  int per_sm = bwd ? bwd_max_blocks_per_sm(cfg.block, L.total) : fwd_max_blocks_per_sm(cfg.block, L.total);
+  if (cfg.per_sm > 0) per_sm = std::min(per_sm, cfg.per_sm);
+  grid = std::max(1, std::min<int>(n_pairs, c->num_sms * per_sm));
+}
+
+size_t scratch_need(const cm_context* c, int bwd, int grid) {
+  const int64_t stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
+  return (size_t)grid * stride * (bwd ? 3 : 1);
+}
+
+// Queues one manifold step (work ordering + forward or adjoint kernel) on `s`
+// with the given buffers; allocates nothing.
+cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs, const int32_t* pg,
+                       const float* poses, const float* dims, const float* tau, const cm_params* params, float* out,
+                       const float* grad_out, float* grad_poses, float* grad_dims, float* scratch,
+                       int32_t* order, int32_t* counter, cudaStream_t s) {
+  FwdArgs a{};
+  int grid = 1;
+  shape(c, bwd, cfg, n_pairs, a.sm, grid);
+  a.hdr = c->d_hdr;
+  a.n_geoms = (int32_t)c->hdr.size();
+  a.verts = c->d_verts;
+  a.edges = c->d_edges;
+  a.planes = c->d_planes;
+  a.n_pairs = n_pairs;
+  a.pair_geoms = pg;
+  a.poses = poses;
+  a.dims = dims;
+  a.tau = tau;
+  a.p = to_params(params);
+  a.out = out;
+  a.scratch = scratch;
+  a.scratch_stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
+  a.err = c->d_err;
+  a.work_counter = nullptr;
+  a.order = nullptr;
+  cudaError_t e;
+  if (cfg.ordered) {
+    if ((e = launch_order(pg, c->d_hdr, a.n_geoms, n_pairs, order, counter, s)) != cudaSuccess)
+      return cuda_fail(e, "work-order launch");
+    a.order = order;
+    a.work_counter = counter;
+  }
+  e = bwd ? launch_bwd(a, grad_out, grad_poses, grad_dims, grid, cfg.block, s) : launch_fwd(a, grid, cfg.block, s);
+  if (e != cudaSuccess) return cuda_fail(e, bwd ? "backward launch" : "forward launch");
+  return CM_OK;
+}
+
+// Context-owned buffers for one call with the chosen shape, then the step.
+cm_status run_step(cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs, const int32_t* pg,
+                   const float* poses, const float* dims, const float* tau, const cm_params* params, float* out,
+                   const float* grad_out, float* grad_poses, float* grad_dims, cudaStream_t s) {
+  SmemLayout L;
+  int grid = 1;
+  shape(c, bwd, cfg, n_pairs, L, grid);
+  cm_status st = ensure_scratch(c, scratch_need(c, bwd, grid));
+  if (st != CM_OK) return st;
+  if ((st = ensure_order(c, (size_t)n_pairs)) != CM_OK) return st;
+  return enqueue_step(c, bwd, cfg, n_pairs, pg, poses, dims, tau, params, out, grad_out, grad_poses, grad_dims,
+                      c->d_scratch, c->d_order, c->d_counter, s);
+}
 }  // namespace
 
 extern "C" {
@@ -175,6 +300,8 @@ void cm_destroy_context(cm_context* c) {
   cudaFree(c->d_planes);
   cudaFree(c->d_scratch);
   cudaFree(c->d_err);
+  cudaFree(c->d_order);
+  cudaFree(c->d_counter);
   delete c;
 }
 
@@ -272,47 +399,11 @@ cm_status cm_contact_manifold_fwd(cm_context* c, int32_t n_pairs, const int32_t*
   if (!pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "pair_geoms, poses and out are required");
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
-  // every pair must offer at least K candidates: with E-E contacts any two
-  // geometries of >= 3 edges give 2 * 3 * 3 = 18 > CM_MAX_K; without them the
-  // vertex count of the smallest registered geometry bounds it
-  if (params->flags & (CM_FLAG_NO_EE | CM_FLAG_ONE_SIDED)) {
-    const int min_cands = (params->flags & CM_FLAG_ONE_SIDED) ? c->min_v : 2 * c->min_v;
-    if (params->K > min_cands)
-      return fail(CM_ERR_INVALID_ARG, "K exceeds the vertex-contact count of the smallest registered geometry");
-  } else if (c->min_e < 3) {
-    return fail(CM_ERR_INVALID_ARG, "E-E contacts need every registered geometry to have >= 3 edges");
-  }
+  if ((st = check_k(c, params)) != CM_OK) return st;
   cudaSetDevice(c->device);
   if ((st = sync_geometry_locked(c)) != CM_OK) return st;
-
-  const int block = 256;
-  FwdArgs a{};
-  a.sm = make_layout(c, block / 32);
-  const int per_sm = fwd_max_blocks_per_sm(block, a.sm.total);
-  const int grid = std::max(1, std::min<int>(n_pairs, c->num_sms * per_sm));
-  const int64_t stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
-  if ((st = ensure_scratch(c, (size_t)grid * stride)) != CM_OK) return st;
-
-  a.hdr = c->d_hdr;
-  a.n_geoms = (int32_t)c->hdr.size();
-  a.verts = c->d_verts;
-  a.edges = c->d_edges;
-  a.planes = c->d_planes;
-  a.n_pairs = n_pairs;
-  a.pair_geoms = pair_geoms;
-  a.poses = poses;
-  a.dims = dims;
-  a.tau = tau;
-  a.p = Params{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K, params->flags};
-  a.out = out;
-  a.scratch = c->d_scratch;
-  a.scratch_stride = stride;
-  a.err = c->d_err;
-  a.work_counter = nullptr;
-  a.order = nullptr;
-  cudaError_t e = launch_fwd(a, grid, block, (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, "forward launch");
-  return CM_OK;
+  return run_step(c, 0, pick_cfg(c, 0, n_pairs, params->flags), n_pairs, pair_geoms, poses, dims, tau, params, out,
+                  nullptr, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -330,40 +421,11 @@ extern "C" cm_status cm_contact_manifold_bwd(cm_context* c, int32_t n_pairs, con
     return fail(CM_ERR_INVALID_ARG, "pair_geoms, poses, grad_out and grad_poses are required");
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
-  if (params->flags & (CM_FLAG_NO_EE | CM_FLAG_ONE_SIDED)) {
-    const int min_cands = (params->flags & CM_FLAG_ONE_SIDED) ? c->min_v : 2 * c->min_v;
-    if (params->K > min_cands)
-      return fail(CM_ERR_INVALID_ARG, "K exceeds the vertex-contact count of the smallest registered geometry");
-  } else if (c->min_e < 3) {
-    return fail(CM_ERR_INVALID_ARG, "E-E contacts need every registered geometry to have >= 3 edges");
-  }
+  if ((st = check_k(c, params)) != CM_OK) return st;
   cudaSetDevice(c->device);
   if ((st = sync_geometry_locked(c)) != CM_OK) return st;
-  const int block = 256;
-  FwdArgs a{};
-  a.sm = make_layout(c, block / 32);
-  const int per_sm = bwd_max_blocks_per_sm(block, a.sm.total);
-  const int grid = std::max(1, std::min<int>(n_pairs, c->num_sms * per_sm));
-  const int64_t stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
-  if ((st = ensure_scratch(c, (size_t)grid * stride * 3)) != CM_OK) return st;
-  a.hdr = c->d_hdr;
-  a.n_geoms = (int32_t)c->hdr.size();
-  a.verts = c->d_verts;
-  a.edges = c->d_edges;
-  a.planes = c->d_planes;
-  a.n_pairs = n_pairs;
-  a.pair_geoms = pair_geoms;
-  a.poses = poses;
-  a.dims = dims;
-  a.tau = tau;
-  a.p = Params{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K, params->flags};
-  a.out = nullptr;
-  a.scratch = c->d_scratch;
-  a.scratch_stride = stride;
-  a.err = c->d_err;
-  cudaError_t e = launch_bwd(a, grad_out, grad_poses, grad_dims, grid, block, (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
-  return CM_OK;
+  return run_step(c, 1, pick_cfg(c, 1, n_pairs, params->flags), n_pairs, pair_geoms, poses, dims, tau, params,
+                  nullptr, grad_out, grad_poses, grad_dims, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -464,5 +526,184 @@ extern "C" cm_status cm_contact_manifold_fwd_noalloc(cm_context* c, int32_t n_pa
   a.order = nullptr;
   cudaError_t e = launch_fwd(a, grid, block, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "no-alloc forward launch");
+  return CM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times a small set of launch shapes on the caller's batch and
+// keeps the fastest per (direction, batch-size bucket, largest edge count,
+// flags) for the context's later calls and plans.
+// ---------------------------------------------------------------------------
+extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
+                                 const float* dims, const float* tau, const cm_params* params, float* out,
+                                 const float* grad_out, float* grad_poses, float* grad_dims, void* stream) {
+  if (!c) return fail(CM_ERR_INVALID_ARG, "NULL context");
+  cm_status st = check_params(params);
+  if (st != CM_OK) return st;
+  if (n_pairs <= 0 || !pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "a non-empty batch is required");
+  if (grad_out && !grad_poses) return fail(CM_ERR_INVALID_ARG, "grad_poses is required with grad_out");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
+  if ((st = check_k(c, params)) != CM_OK) return st;
+  cudaSetDevice(c->device);
+  if ((st = sync_geometry_locked(c)) != CM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int bwd = 0; bwd < (grad_out ? 2 : 1); ++bwd) {
+    const int blocks[3] = {128, 256, 512};
+    const int per_sms[3] = {1, 2, 0};
+    LaunchCfg best = default_cfg(c, bwd, n_pairs);
+    float best_ms = 3.0e38f;
+    for (int bi = 0; bi < 3; ++bi) {
+      if (bwd && blocks[bi] > 256) continue;  // the adjoint kernel is built for <= 256 threads
+      for (int pi = 0; pi < 3; ++pi)
+        for (int ord = 0; ord < 2; ++ord) {
+          LaunchCfg g{blocks[bi], per_sms[pi], ord};
+          float ms_sum = 0.f;
+          for (int rep = 0; rep < 3; ++rep) {
+            if (rep > 0) cudaEventRecord(e0, s);
+            st = run_step(c, bwd, g, n_pairs, pair_geoms, poses, dims, tau, params, out, grad_out, grad_poses,
+                          grad_dims, s);
+            if (st != CM_OK) break;
+            if (rep > 0) {
+              cudaEventRecord(e1, s);
+              cudaEventSynchronize(e1);
+              float ms = 0.f;
+              cudaEventElapsedTime(&ms, e0, e1);
+              ms_sum += ms;
+            }
+          }
+          if (st != CM_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+          }
+          if (ms_sum < best_ms) {
+            best_ms = ms_sum;
+            best = g;
+          }
+        }
+    }
+    c->tuned[tune_key(bwd, n_pairs, c->max_e, params->flags)] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  return CM_OK;
+}
+
+extern "C" cm_status cm_get_launch_shape(const cm_context* c, int32_t n_pairs, int32_t backward, int32_t flags,
+                                         int32_t* block, int32_t* ctas_per_sm, int32_t* ordered) {
+  if (!c || !block || !ctas_per_sm || !ordered) return fail(CM_ERR_INVALID_ARG, "NULL argument");
+  LaunchCfg g = pick_cfg(c, backward ? 1 : 0, n_pairs, flags);
+  *block = g.block;
+  *ctas_per_sm = g.per_sm;
+  *ordered = g.ordered;
+  return CM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plans: the steady-state step of a fixed batch (work ordering + forward, and
+// optionally + adjoint) captured once into a CUDA graph with its own scratch,
+// then replayed with one graph launch per step.  The caller rewrites the
+// input buffers (poses, dims, tau, grad_out) in place between replays.
+// ---------------------------------------------------------------------------
+struct cm_plan {
+  cm_context* ctx = nullptr;
+  uint64_t geom_gen = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  float* scratch = nullptr;
+  int32_t* order = nullptr;
+  int32_t* counter = nullptr;
+};
+
+extern "C" void cm_plan_destroy(cm_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  cudaFree(p->scratch);
+  cudaFree(p->order);
+  cudaFree(p->counter);
+  delete p;
+}
+
+extern "C" cm_status cm_plan_create(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
+                                    const float* dims, const float* tau, const cm_params* params, float* out,
+                                    const float* grad_out, float* grad_poses, float* grad_dims, cm_plan** plan) {
+  if (!c || !plan) return fail(CM_ERR_INVALID_ARG, "NULL argument");
+  *plan = nullptr;
+  cm_status st = check_params(params);
+  if (st != CM_OK) return st;
+  if (n_pairs <= 0 || !pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "a non-empty batch is required");
+  if (grad_out && !grad_poses) return fail(CM_ERR_INVALID_ARG, "grad_poses is required with grad_out");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
+  if ((st = check_k(c, params)) != CM_OK) return st;
+  cudaSetDevice(c->device);
+  if ((st = sync_geometry_locked(c)) != CM_OK) return st;
+  cm_plan* p = new (std::nothrow) cm_plan();
+  if (!p) return fail(CM_ERR_OOM, "plan allocation");
+  p->ctx = c;
+  p->geom_gen = c->geom_gen;
+  const LaunchCfg gf = pick_cfg(c, 0, n_pairs, params->flags);
+  const LaunchCfg gb = pick_cfg(c, 1, n_pairs, params->flags);
+  SmemLayout L;
+  int grid_f = 1, grid_b = 1;
+  shape(c, 0, gf, n_pairs, L, grid_f);
+  shape(c, 1, gb, n_pairs, L, grid_b);
+  size_t need = scratch_need(c, 0, grid_f);
+  if (grad_out) need = std::max(need, scratch_need(c, 1, grid_b));
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->scratch, need * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&p->order, (size_t)n_pairs * sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&p->counter, sizeof(int32_t))) != cudaSuccess) {
+    cm_plan_destroy(p);
+    return fail(CM_ERR_OOM, std::string("plan buffers: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+    cm_plan_destroy(p);
+    return cuda_fail(e, "plan stream");
+  }
+  // first launches outside the capture set the kernels' attributes
+  st = enqueue_step(c, 0, gf, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, nullptr, nullptr,
+                    p->scratch, p->order, p->counter, p->cap);
+  if (st == CM_OK && grad_out)
+    st = enqueue_step(c, 1, gb, n_pairs, pair_geoms, poses, dims, tau, params, nullptr, grad_out, grad_poses,
+                      grad_dims, p->scratch, p->order, p->counter, p->cap);
+  if (st == CM_OK && (e = cudaStreamSynchronize(p->cap)) != cudaSuccess) st = cuda_fail(e, "plan warm-up");
+  if (st == CM_OK && (e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    st = cuda_fail(e, "begin capture");
+  if (st == CM_OK) {
+    cm_status s1 = enqueue_step(c, 0, gf, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, nullptr,
+                                nullptr, p->scratch, p->order, p->counter, p->cap);
+    if (s1 == CM_OK && grad_out)
+      s1 = enqueue_step(c, 1, gb, n_pairs, pair_geoms, poses, dims, tau, params, nullptr, grad_out, grad_poses,
+                        grad_dims, p->scratch, p->order, p->counter, p->cap);
+    e = cudaStreamEndCapture(p->cap, &p->graph);
+    if (s1 != CM_OK) st = s1;
+    else if (e != cudaSuccess) st = cuda_fail(e, "end capture");
+  }
+  if (st == CM_OK && (e = cudaGraphInstantiate(&p->exec, p->graph, 0)) != cudaSuccess)
+    st = cuda_fail(e, "graph instantiate");
+  if (st != CM_OK) {
+    cm_plan_destroy(p);
+    return st;
+  }
+  *plan = p;
+  return CM_OK;
+}
+
+extern "C" cm_status cm_plan_launch(cm_plan* p, void* stream) {
+  if (!p) return fail(CM_ERR_INVALID_ARG, "NULL plan");
+  if (p->ctx->geom_gen != p->geom_gen)
+    return fail(CM_ERR_INVALID_ARG, "geometry changed since the plan was made: create the plan again");
+  cudaError_t e = cudaGraphLaunch(p->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
   return CM_OK;
 }
