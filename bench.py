@@ -152,6 +152,84 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- serving
+def serve_benchmark(eng, api, seconds, seed=synth.SEED_BASE + 5):
+    """Poisson trace of requests (2000/s, 1..8192 pairs log-uniform, forward or forward+backward
+    50/50) over a pool of mixed pairs, once through the continuous-batching server and once
+    through the plain path (one forward [+ adjoint] launch per request, in arrival order)."""
+    import torch
+    pool = synth.config_mixed(n=1024, seed=seed)
+    ids = eng.add_geometries(pool.geoms)
+    trace = synth.serving_trace(seed=seed, duration=seconds)
+    rng = np.random.default_rng(seed)
+    sizes = np.array([n for _, n, _ in trace])
+    total = int(sizes.sum())
+    idx = rng.integers(0, pool.n_pairs, total)
+    P = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()  # noqa: E731
+    pg_all, poses_all = P(ids[pool.pair_geoms[idx]], torch.int32), P(pool.poses[idx])
+    dims_all, tau_all = P(pool.dims[idx]), P(pool.tau[idx])
+    gout_all = P(rng.normal(size=(total, 8, 8)).astype(np.float32))
+    out_all = torch.empty((total, 8, 8)).pin_memory()
+    gp_all, gd_all = torch.empty((total, 14)).pin_memory(), torch.empty((total, 6)).pin_memory()
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    params = eng.params()
+
+    def req(i):
+        a, b = int(offs[i]), int(offs[i + 1])
+        bwd = trace[i][2]
+        return (pg_all[a:b], poses_all[a:b], out_all[a:b], dims_all[a:b], tau_all[a:b],
+                gout_all[a:b] if bwd else None, gp_all[a:b] if bwd else None, gd_all[a:b] if bwd else None)
+
+    # warm both paths (kernels, pools) on a few requests
+    api.cm_server_start(eng.ctx, params, max_batch_pairs=65536, n_streams=4)
+    for i in range(4):
+        api.cm_wait(eng.ctx, api.cm_submit(eng.ctx, *req(i)), -1)
+    t0 = time.perf_counter()
+    tickets = []
+    for i, (ta, n, bwd) in enumerate(trace):
+        d = t0 + ta - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tickets.append(api.cm_submit(eng.ctx, *req(i)))
+    for t in tickets:
+        api.cm_wait(eng.ctx, t, -1)
+    t_end = time.perf_counter()
+    lat = np.array([api.cm_request_latency(eng.ctx, t) for t in tickets])
+    api.cm_server_stop(eng.ctx)
+    served = {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+              "pairs_per_s": total / (t_end - t0), "requests": len(trace), "pairs": total,
+              "trace_seconds": seconds}
+
+    # plain path: one launch (two with the adjoint) per request, sequential
+    dev = [torch.empty(t.shape, dtype=t.dtype, device="cuda") for t in (pg_all, poses_all, dims_all, tau_all)]
+    dgo = torch.empty(gout_all.shape, device="cuda")
+    lat_p = []
+    t0 = time.perf_counter()
+    for i, (ta, n, bwd) in enumerate(trace):
+        d = t0 + ta - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        a, b = int(offs[i]), int(offs[i + 1])
+        pg, poses, dims, tau = (x[a:b] for x in dev)
+        for x, h in zip((pg, poses, dims, tau), (pg_all, poses_all, dims_all, tau_all)):
+            x.copy_(h[a:b], non_blocking=True)
+        out = eng.forward(pg, poses, dims, tau, params)
+        out_all[a:b].copy_(out, non_blocking=True)
+        if bwd:
+            dgo[a:b].copy_(gout_all[a:b], non_blocking=True)
+            gp, gd = eng.backward(pg, poses, dims, tau, dgo[a:b], params)
+            gp_all[a:b].copy_(gp, non_blocking=True)
+            gd_all[a:b].copy_(gd, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        lat_p.append(time.perf_counter() - (t0 + ta))
+    t_end = time.perf_counter()
+    lat_p = np.array(lat_p)
+    plain = {"p50_ms": 1e3 * float(np.percentile(lat_p, 50)), "p99_ms": 1e3 * float(np.percentile(lat_p, 99)),
+             "pairs_per_s": total / (t_end - t0)}
+    return {"workload": "Poisson 2000 req/s, 1..8192 pairs log-uniform of hull(8-256) vs primitive, "
+                        "tau in {1e-3,1e-2,1e-1}, fwd or fwd+bwd 50/50", "served": served, "plain": plain}
+
+
 # ----------------------------------------------------------------- our arm
 def main():
     ap = argparse.ArgumentParser()
@@ -162,6 +240,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--pairs", type=int, default=4096, help="pairs per GPU (profiling uses fewer)")
+    ap.add_argument("--serve-seconds", type=float, default=0.5,
+                    help="length of the Poisson serving trace (0 skips the serving comparison)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -282,6 +362,10 @@ def main():
             "peak_source": "measured ex2.approx throughput (cm_measure_pipe_peaks)",
             "fma_peak_tflops": fma_peak / 1e12}
 
+    serving = None
+    if args.serve_seconds > 0 and world == 1:
+        serving = serve_benchmark(Engine(local, hbm_budget_bytes=40 << 30), api, args.serve_seconds)
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         r, n, dt, cores = cpu_oracle_rate(w, budget_s=args.cpu_seconds)
@@ -296,7 +380,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "pairs_per_gpu": w.n_pairs, "parallelism": f"replicas x{world}",
                        "l2": "flushed (512 MB write) between timed steps"},
-            "gpu_launches": launches_f * args.steps, "e2e": e2e,
+            "gpu_launches": launches_f * args.steps, "e2e": e2e, "serving": serving,
             "launch_shape": {"fwd": {"block": shape_f[0], "ctas_per_sm": shape_f[1], "ordered": shape_f[2]},
                              "bwd": {"block": shape_b[0], "ctas_per_sm": shape_b[1], "ordered": shape_b[2]},
                              "cuda_graph": True}, "roofline": roof, "cpu_baseline": cpu,

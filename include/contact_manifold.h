@@ -189,6 +189,47 @@ cm_status cm_plan_create(cm_context* ctx, int32_t n_pairs, const int32_t* pair_g
 cm_status cm_plan_launch(cm_plan* plan, void* stream);
 void cm_plan_destroy(cm_plan* plan);
 
+/* Serving (not part of the paper's method): a scheduler thread per context
+ * continuously batches requests from many clients.  Requests are admitted in
+ * arrival order as the context's HBM budget (cm_create_context) and the batch
+ * pair limit allow; each admitted group becomes one batch (forward over all
+ * its pairs, adjoint over the pairs of forward+backward requests) issued on
+ * one of n_streams streams, so batches formed while others run overlap on the
+ * GPU.  Geometry stays resident; pair data is copied in and results copied out
+ * per request.  All requests of one server agree on whether they give dims
+ * and tau.  Host buffers of a request (pinned memory recommended) must stay
+ * valid until the request is done. */
+typedef struct {
+  int32_t n_pairs;        /* 1..max_batch_pairs */
+  int32_t with_backward;  /* 0: forward only; 1: forward + adjoint */
+  const int32_t* pair_geoms; /* host, n x 2 */
+  const float* poses;        /* host, n x 14 */
+  const float* dims;         /* host, n x 6, or NULL (registered dims) */
+  const float* tau;          /* host, n, or NULL (the server's params.tau) */
+  const float* grad_out;     /* host, n x K x 8 (with_backward) */
+  float* out;                /* host, n x K x 8, written on completion */
+  float* grad_poses;         /* host, n x 14 (with_backward) */
+  float* grad_dims;          /* host, n x 6 or NULL */
+} cm_request_desc;
+
+/* Starts the serving loop of `ctx` with fixed method params.  Returns
+ * CM_ERR_ADMISSION if the budget cannot hold one batch's scratch. */
+cm_status cm_server_start(cm_context* ctx, const cm_params* params, int32_t max_batch_pairs, int32_t n_streams);
+/* Queues a request; CM_ERR_ADMISSION if it cannot fit the budget even alone. */
+cm_status cm_submit(cm_context* ctx, const cm_request_desc* req, uint64_t* ticket);
+/* Non-blocking: *done = 1 once the request's results are in its host buffers. */
+cm_status cm_poll(cm_context* ctx, uint64_t ticket, int32_t* done);
+/* Blocks up to timeout_ms; CM_ERR_TIMEOUT if the request is still running. */
+cm_status cm_wait(cm_context* ctx, uint64_t ticket, int32_t timeout_ms);
+/* Submission-to-completion time of a finished request, in seconds. */
+cm_status cm_request_latency(cm_context* ctx, uint64_t ticket, double* seconds);
+/* Forgets a finished request (its ticket becomes unknown). */
+cm_status cm_release(cm_context* ctx, uint64_t ticket);
+/* Pairs and batches completed so far and device bytes currently admitted. */
+cm_status cm_server_stats(cm_context* ctx, uint64_t* pairs_done, uint64_t* batches_done, uint64_t* bytes_in_use);
+/* Drains queued and running requests, then stops the loop. */
+cm_status cm_server_stop(cm_context* ctx);
+
 /* Same computation and arguments as cm_contact_manifold_fwd, but the call
  * allocates no memory (no cudaMalloc, no library allocation).  The paper has no
  * counterpart: this exists for callers that cannot allocate while they run the

@@ -41,7 +41,15 @@ class cm_params(ctypes.Structure):
                 ("flags", ctypes.c_int32)]
 
 
+class cm_request_desc(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int32), ("with_backward", ctypes.c_int32),
+                ("pair_geoms", ctypes.c_void_p), ("poses", ctypes.c_void_p), ("dims", ctypes.c_void_p),
+                ("tau", ctypes.c_void_p), ("grad_out", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("grad_poses", ctypes.c_void_p), ("grad_dims", ctypes.c_void_p)]
+
+
 _vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
 _SIGS = {
     "cm_default_params": (None, [ctypes.POINTER(cm_params)]),
     "cm_last_error": (ctypes.c_char_p, []),
@@ -67,6 +75,14 @@ _SIGS = {
                                       _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "cm_plan_launch": (ctypes.c_int, [_vp, _vp]),
     "cm_plan_destroy": (None, [_vp]),
+    "cm_server_start": (ctypes.c_int, [_vp, ctypes.POINTER(cm_params), ctypes.c_int32, ctypes.c_int32]),
+    "cm_submit": (ctypes.c_int, [_vp, ctypes.POINTER(cm_request_desc), ctypes.POINTER(_u64)]),
+    "cm_poll": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_int32)]),
+    "cm_wait": (ctypes.c_int, [_vp, _u64, ctypes.c_int32]),
+    "cm_request_latency": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_double)]),
+    "cm_release": (ctypes.c_int, [_vp, _u64]),
+    "cm_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "cm_server_stop": (ctypes.c_int, [_vp]),
     "cm_measure_pipe_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double)]),
 }
@@ -235,6 +251,82 @@ def cm_plan_launch(plan, stream=None) -> None:
 
 def cm_plan_destroy(plan) -> None:
     _lib.cm_plan_destroy(plan)
+
+
+_KEEPALIVE = {}
+
+
+def _host_ptr(a):
+    """Address of a host buffer: a CPU torch tensor or a numpy array (kept alive by the caller)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("request buffers must be contiguous host tensors")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("request buffers must be C-contiguous")
+    return a.ctypes.data
+
+
+def cm_server_start(ctx, params, max_batch_pairs=65536, n_streams=4) -> None:
+    _check(_lib.cm_server_start(ctx, ctypes.byref(params), max_batch_pairs, n_streams))
+
+
+def cm_submit(ctx, pair_geoms, poses, out, dims=None, tau=None, grad_out=None, grad_poses=None,
+              grad_dims=None) -> int:
+    """Queue a request on host buffers; returns its ticket.  The buffers are kept alive
+    by this module until cm_release."""
+    d = cm_request_desc()
+    d.n_pairs = int(pair_geoms.shape[0])
+    d.with_backward = 1 if grad_out is not None else 0
+    d.pair_geoms, d.poses, d.dims, d.tau = (_host_ptr(pair_geoms), _host_ptr(poses), _host_ptr(dims),
+                                            _host_ptr(tau))
+    d.grad_out, d.out, d.grad_poses, d.grad_dims = (_host_ptr(grad_out), _host_ptr(out), _host_ptr(grad_poses),
+                                                    _host_ptr(grad_dims))
+    t = _u64()
+    _check(_lib.cm_submit(ctx, ctypes.byref(d), ctypes.byref(t)))
+    _KEEPALIVE[(ctx.value, t.value)] = (pair_geoms, poses, out, dims, tau, grad_out, grad_poses, grad_dims)
+    return t.value
+
+
+def cm_poll(ctx, ticket) -> bool:
+    done = ctypes.c_int32()
+    _check(_lib.cm_poll(ctx, ticket, ctypes.byref(done)))
+    return bool(done.value)
+
+
+def cm_wait(ctx, ticket, timeout_ms=-1) -> None:
+    """Block until the request is done; timeout_ms < 0 waits for ever."""
+    while True:
+        st = _lib.cm_wait(ctx, ticket, 1000 if timeout_ms < 0 else timeout_ms)
+        if st == CM_ERR_TIMEOUT and timeout_ms < 0:
+            continue
+        _check(st)
+        return
+
+
+def cm_request_latency(ctx, ticket) -> float:
+    v = ctypes.c_double()
+    _check(_lib.cm_request_latency(ctx, ticket, ctypes.byref(v)))
+    return v.value
+
+
+def cm_release(ctx, ticket) -> None:
+    _check(_lib.cm_release(ctx, ticket))
+    _KEEPALIVE.pop((ctx.value, ticket), None)
+
+
+def cm_server_stats(ctx):
+    a, b, c = _u64(), _u64(), _u64()
+    _check(_lib.cm_server_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def cm_server_stop(ctx) -> None:
+    _check(_lib.cm_server_stop(ctx))
+    for k in [k for k in _KEEPALIVE if k[0] == ctx.value]:
+        _KEEPALIVE.pop(k)
 
 
 def cm_measure_pipe_peaks(device: int = 0):

@@ -11,11 +11,12 @@
 #include <vector>
 
 #include "contact_manifold.h"
-#include "cm_internal.h"
+#include "cm_context.h"
 
 using namespace cm;
 
-namespace {
+namespace cm {
+namespace rt {
 thread_local std::string g_last_error;
 
 cm_status fail(cm_status s, const std::string& msg) {
@@ -25,40 +26,18 @@ cm_status fail(cm_status s, const std::string& msg) {
 cm_status cuda_fail(cudaError_t e, const char* what) {
   return fail(CM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+namespace {
 int align16(int x) { return (x + 15) & ~15; }
 }  // namespace
+}  // namespace rt
+}  // namespace cm
 
-struct cm_context {
-  int device = 0;
-  size_t budget = 0;
-  int num_sms = 0;
-  std::mutex mu;
-  // host copy of the packed geometry store
-  std::vector<GeomHeader> hdr;
-  std::vector<float4> verts;
-  std::vector<uint32_t> edges;
-  std::vector<float4> planes;
-  int max_v = 0, max_e = 0, max_p = 0, min_v = 1 << 30, min_e = 1 << 30;
-  bool dirty = false;
-  // device copy
-  GeomHeader* d_hdr = nullptr;
-  float4* d_verts = nullptr;
-  uint32_t* d_edges = nullptr;
-  float4* d_planes = nullptr;
-  size_t cap_hdr = 0, cap_verts = 0, cap_edges = 0, cap_planes = 0;
-  // scratch for the E-E distance matrix (per CTA slice) and the error flag
-  float* d_scratch = nullptr;
-  size_t scratch_floats = 0;
-  int* d_err = nullptr;
-  // size-ordered work list of the last batch and its atomic counter
-  int32_t* d_order = nullptr;
-  size_t cap_order = 0;
-  int32_t* d_counter = nullptr;
-  uint64_t geom_gen = 0;                 // bumped by every geometry upload
-  std::map<uint64_t, cm::LaunchCfg> tuned;  // autotuned launch shapes
-};
+using namespace cm::rt;
 
-namespace {
+
+
+namespace cm {
+namespace rt {
 
 template <class T>
 cudaError_t grow_upload(T*& dptr, size_t& cap, const std::vector<T>& host) {
@@ -251,7 +230,8 @@ cm_status run_step(cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs
   return enqueue_step(c, bwd, cfg, n_pairs, pg, poses, dims, tau, params, out, grad_out, grad_poses, grad_dims,
                       c->d_scratch, c->d_order, c->d_counter, s);
 }
-}  // namespace
+}  // namespace rt
+}  // namespace cm
 
 extern "C" {
 
@@ -292,6 +272,7 @@ cm_status cm_create_context(int device, size_t hbm_budget_bytes, cm_context** ou
 
 void cm_destroy_context(cm_context* c) {
   if (!c) return;
+  server_shutdown(c);  // drain and stop the serving loop before freeing what it uses
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   cudaFree(c->d_hdr);
