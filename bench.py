@@ -240,6 +240,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--pairs", type=int, default=4096, help="pairs per GPU (profiling uses fewer)")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (profiling)")
     ap.add_argument("--serve-seconds", type=float, default=0.5,
                     help="length of the Poisson serving trace (0 skips the serving comparison)")
     args = ap.parse_args()
@@ -277,7 +278,8 @@ def main():
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 512 MB > L2
 
     # batching layer: autotuned launch shapes, then one CUDA-graph replay per step
-    api.cm_autotune(eng.ctx, pg, poses, dims, tau, params, out, grad_out, gp, gd)
+    if not args.no_autotune:
+        api.cm_autotune(eng.ctx, pg, poses, dims, tau, params, out, grad_out, gp, gd)
     shape_f = api.cm_get_launch_shape(eng.ctx, w.n_pairs, False)
     shape_b = api.cm_get_launch_shape(eng.ctx, w.n_pairs, True)
     plan_f = api.cm_plan_create(eng.ctx, pg, poses, dims, tau, params, out)

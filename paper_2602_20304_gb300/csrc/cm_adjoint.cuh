@@ -72,22 +72,25 @@ CM_HD void sdf_box_bwd(V3 y, V3 h, const Sdf& f, float inv_tau, float phibar, V3
   hbar += v3(hb[0], hb[1], hb[2]);
 }
 
+// Planes arrive pre-scaled by k = log2(e) / tau (see sdf_planes): the scaled
+// plane value is the base-2 exponent and the unit normal is (k n) / k.
 CM_HD void sdf_planes_bwd(V3 y, const float4* P, int nP, const Sdf& f, float inv_tau, float phibar, V3 gbar,
                           V3& ybar) {
-  const float k = inv_tau * kLog2e;
+  const float k = inv_tau * kLog2e, ik = rcp(k);
   const float base = phibar - dot(gbar, f.g) * inv_tau;
   const float mk = f.phi * k;
+  const float gk = inv_tau * ik;  // gbar . n_f / tau with n_f = (k n_f) / k
   V3 acc = v3(0.f, 0.f, 0.f);
   for (int i = 0; i < nP; ++i) {
     float4 p = P[i];
     float s = fmaf(p.x, y.x, fmaf(p.y, y.y, fmaf(p.z, y.z, -p.w)));
-    float pi = ex2(fmaf(s, k, -mk));
-    float sb = pi * (base + (gbar.x * p.x + gbar.y * p.y + gbar.z * p.z) * inv_tau);
+    float pi = ex2(s - mk);
+    float sb = pi * (base + (gbar.x * p.x + gbar.y * p.y + gbar.z * p.z) * gk);
     acc.x = fmaf(sb, p.x, acc.x);
     acc.y = fmaf(sb, p.y, acc.y);
     acc.z = fmaf(sb, p.z, acc.z);
   }
-  ybar += acc;
+  ybar += acc * ik;
 }
 
 // Ellipsoid: phi = r - r f^-1/2, r = |y|, f = sum y_i^2/d_i^2; g = 2 y / d^2.

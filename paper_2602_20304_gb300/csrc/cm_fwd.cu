@@ -23,7 +23,11 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
   const PairSmem sm = carve(smem_raw, a.sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int K = a.p.K;
-  float* D = a.scratch + (int64_t)blockIdx.x * a.scratch_stride;
+  const int64_t ss = a.scratch_stride;
+  float* D = a.scratch + (int64_t)blockIdx.x * ss * (a.store_alpha ? 4 : 1);
+  float* A1 = D + ss;   // alpha1, alpha2, con of pass 1 (store_alpha only)
+  float* A2 = A1 + ss;
+  float* CN = A2 + ss;
   int it = 0;
   for (;;) {
     const int pi = next_pair(a, it);
@@ -64,6 +68,11 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
         const int k = i / neB, l = i - k * neB;
         Witness w = ee_witness(edge_pair(sm, k, l), a.p);
         D[i] = w.dbar;
+        if (a.store_alpha) {
+          A1[i] = w.qp.a1;
+          A2[i] = w.qp.a2;
+          CN[i] = w.qp.con;
+        }
       }
       __syncthreads();
       // ---- soft row minima (warp per row) and column minima (thread per column)
@@ -92,7 +101,16 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
         if (valid) {
           const int k = i / neB, l = i - k * neB;
           const EdgePair ep = edge_pair(sm, k, l);
-          Witness w = ee_witness(ep, a.p);
+          Witness w;
+          if (a.store_alpha) {
+            QPOut q;
+            q.a1 = A1[i];
+            q.a2 = A2[i];
+            q.con = CN[i];
+            w = ee_witness_from(ep, q);
+          } else {
+            w = ee_witness(ep, a.p);
+          }
           ee_candidates(ps, sm, bb, ep, w, sm.rowL[k], sm.colL[l], y, y2, s1, s2);
         }
         wtk_push(st, valid, s1, y, K, k2, nvs + 2 * i);

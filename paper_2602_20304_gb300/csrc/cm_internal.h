@@ -22,7 +22,7 @@ static_assert(sizeof(GeomHeader) == 48, "GeomHeader layout");
 // Byte offsets of the per-CTA shared-memory carve-up (sized on the host from the
 // largest registered geometry).
 struct SmemLayout {
-  int vA, vAl, vB, pA, pB, eA, eB, rowL, colL, warp;
+  int vA, vAl, vB, pA, pB, eA, eB, rowL, colL, warp, eA6, eAl6, eB6;
   int total;
   int max_v, max_e, max_p;
 };
@@ -45,6 +45,7 @@ struct FwdArgs {
   int* err;                  // sticky device error: first bad pair index + 1
   SmemLayout sm;
   int32_t* work_counter;     // persistent-CTA work queue (may be null: static striding)
+  int32_t store_alpha;       // pass 1 keeps (alpha1, alpha2, con) beside dbar: 4 scratch floats per edge pair
   const int32_t* order;      // optional pair order for the work queue (may be null)
 };
 

@@ -179,32 +179,105 @@ CM_HD Sdf sdf_box(V3 y, V3 h, float tau, float inv_tau) {
   return o;
 }
 
-// Convex polyhedron given by planes (n, o): LSE_tau of n . y - o (Sec. IV-B2).
-// Two passes over the planes: the maximum, then the shifted exponential sum.
-CM_HD Sdf sdf_planes(V3 y, const float4* P, int nP, float tau, float inv_tau) {
-  float m = -3.0e38f;
-  for (int f = 0; f < nP; ++f) {
-    float4 p = P[f];
-    m = fmaxf(m, fmaf(p.x, y.x, fmaf(p.y, y.y, fmaf(p.z, y.z, -p.w))));
-  }
-  float k = inv_tau * kLog2e;
-  float S = 0.f;
+// ---------------------------------------------------------------- packed FP32x2
+CM_HD float2 ffma2(float2 a, float2 b, float2 c) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+  return __ffma2_rn(a, b, c);
+#else
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+CM_HD float2 fadd2(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+  return __fadd2_rn(a, b);
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+CM_HD float2 dup2(float a) { return make_float2(a, a); }
+
+// Convex polyhedron given by planes (n, o): phi = LSE_tau of n . y - o (Sec. IV-B2).
+// The planes arrive pre-scaled by k = log2(e) / tau, (k n, k o), so a plane value
+// is already the exponent in base 2; phi = tau ln2 (m + log2 S) and the gradient
+// sum_f pi_f n_f is rescaled by 1/k = tau ln2.  Single pass over the planes in
+// chunks of 4 with an online maximum (a rescale only when the maximum grows).
+CM_HD Sdf sdf_planes(V3 y, const float4* P, int nP, float tau, float /*inv_tau*/) {
+  float m = -3.0e38f, S = 0.f;
   V3 G = v3(0.f, 0.f, 0.f);
-  float mk = m * k;
-  for (int f = 0; f < nP; ++f) {
-    float4 p = P[f];
-    float s = fmaf(p.x, y.x, fmaf(p.y, y.y, fmaf(p.z, y.z, -p.w)));
-    float e = ex2(fmaf(s, k, -mk));
-    S += e;
-    G.x = fmaf(e, p.x, G.x);
-    G.y = fmaf(e, p.y, G.y);
-    G.z = fmaf(e, p.z, G.z);
+  for (int f0 = 0; f0 < nP; f0 += 4) {
+    float z[4];
+    float4 q[4];
+    float cm = m;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int f = f0 + j;
+      q[j] = f < nP ? P[f] : make_float4(0.f, 0.f, 0.f, 3.0e38f);
+      z[j] = fmaf(q[j].x, y.x, fmaf(q[j].y, y.y, fmaf(q[j].z, y.z, -q[j].w)));
+      cm = fmaxf(cm, z[j]);
+    }
+    if (cm > m) {
+      const float r = ex2(m - cm);
+      S *= r;
+      G = G * r;
+      m = cm;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float e = ex2(z[j] - m);
+      S += e;
+      G.x = fmaf(e, q[j].x, G.x);
+      G.y = fmaf(e, q[j].y, G.y);
+      G.z = fmaf(e, q[j].z, G.z);
+    }
   }
-  float r = rcp(S);
+  const float t = tau * kLn2;
   Sdf o;
-  o.phi = m + tau * kLn2 * lg2(S);
-  o.g = G * r;
+  o.phi = t * (m + lg2(S));
+  o.g = G * (t * rcp(S));
   return o;
+}
+
+// The same LSE at two points at once: the value at y1 and the gradient at y2
+// (the two uses an edge pair makes of one body's SDF).  Each plane is loaded
+// once and both plane values come from packed FP32x2 FMAs.
+CM_HD void sdf_planes2(V3 y1, V3 y2, const float4* P, int nP, float tau, Sdf& o1, Sdf& o2) {
+  const float2 X = make_float2(y1.x, y2.x), Y = make_float2(y1.y, y2.y), Z = make_float2(y1.z, y2.z);
+  float2 m = dup2(-3.0e38f), S = dup2(0.f);
+  V3 G = v3(0.f, 0.f, 0.f);
+  for (int f0 = 0; f0 < nP; f0 += 4) {
+    float2 z[4];
+    float4 q[4];
+    float2 cm = m;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int f = f0 + j;
+      q[j] = f < nP ? P[f] : make_float4(0.f, 0.f, 0.f, 3.0e38f);
+      z[j] = ffma2(dup2(q[j].x), X, ffma2(dup2(q[j].y), Y, ffma2(dup2(q[j].z), Z, dup2(-q[j].w))));
+      cm.x = fmaxf(cm.x, z[j].x);
+      cm.y = fmaxf(cm.y, z[j].y);
+    }
+    if (cm.x > m.x || cm.y > m.y) {
+      const float r1 = ex2(m.x - cm.x), r2 = ex2(m.y - cm.y);
+      S = make_float2(S.x * r1, S.y * r2);
+      G = G * r2;
+      m = cm;
+    }
+    const float2 nm = make_float2(-m.x, -m.y);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 d = fadd2(z[j], nm);
+      const float2 e = make_float2(ex2(d.x), ex2(d.y));
+      S = fadd2(S, e);
+      G.x = fmaf(e.y, q[j].x, G.x);
+      G.y = fmaf(e.y, q[j].y, G.y);
+      G.z = fmaf(e.y, q[j].z, G.z);
+    }
+  }
+  const float t = tau * kLn2;
+  o1.phi = t * (m.x + lg2(S.x));
+  o1.g = v3(0.f, 0.f, 0.f);
+  o2.phi = t * (m.y + lg2(S.y));
+  o2.g = G * (t * rcp(S.y));
 }
 
 // Superquadric with eps1 = eps2 = 1 (Sec. IV-B1): phi = |y| (1 - f^-1/2), f = |y~|^2;
@@ -257,7 +330,8 @@ CM_HD Sdf sdf_cylinder(V3 y, float rad, float h, float tau, float inv_tau) {
 // Regularised normal g / sqrt(tau + |g|^2) (Sec. IV-B).
 CM_HD V3 normal_of(V3 g, float tau) { return g * rsq(tau + dot(g, g)); }
 
-// A body as seen by the kernels: its kind, the dims in use and its planes.
+// A body as seen by the kernels: its kind, the dims in use and its planes
+// (hull planes pre-scaled by log2(e) / tau, see sdf_planes).
 struct Body {
   int kind;
   V3 dims;
@@ -272,6 +346,16 @@ CM_HD Sdf body_sdf(const Body& b, V3 y, float tau, float inv_tau) {
     case kCapsule: return sdf_capsule(y, b.dims.x, b.dims.y, tau, inv_tau);
     case kCylinder: return sdf_cylinder(y, b.dims.x, b.dims.y, tau, inv_tau);
     default: return sdf_planes(y, b.planes, b.n_planes, tau, inv_tau);
+  }
+}
+
+// A body's SDF at two points: o1 for its value at y1, o2 for its gradient at y2.
+CM_HD void body_sdf2(const Body& b, V3 y1, V3 y2, float tau, float inv_tau, Sdf& o1, Sdf& o2) {
+  if (b.kind == kHull) {
+    sdf_planes2(y1, y2, b.planes, b.n_planes, tau, o1, o2);
+  } else {
+    o1 = body_sdf(b, y1, tau, inv_tau);
+    o2 = body_sdf(b, y2, tau, inv_tau);
   }
 }
 

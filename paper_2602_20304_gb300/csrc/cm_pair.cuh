@@ -31,6 +31,10 @@ struct PairSmem {
   float4* pB;      // B's planes
   uint32_t* eA;
   uint32_t* eB;
+  float* eA6;      // A's edge endpoints in B's frame, SoA: [c * max_e + k], c = a0x, a0y, a0z, a1x, a1y, a1z
+  float* eAl6;     // A's edge endpoints in A's frame, same layout
+  float* eB6;      // B's edge endpoints, same layout
+  int es;          // SoA stride (largest edge count)
   float* rowL;     // soft row minima of the E-E distance matrix (nn-Gamma_1)
   float* colL;     // soft column minima (nn-Gamma_2)
   float* warp;     // per-warp SoftSort states
@@ -48,6 +52,10 @@ __device__ __forceinline__ PairSmem carve(unsigned char* base, const SmemLayout&
   s.rowL = reinterpret_cast<float*>(base + L.rowL);
   s.colL = reinterpret_cast<float*>(base + L.colL);
   s.warp = reinterpret_cast<float*>(base + L.warp);
+  s.eA6 = reinterpret_cast<float*>(base + L.eA6);
+  s.eAl6 = reinterpret_cast<float*>(base + L.eAl6);
+  s.eB6 = reinterpret_cast<float*>(base + L.eB6);
+  s.es = L.max_e;
   return s;
 }
 
@@ -101,10 +109,39 @@ __device__ inline void pair_stage(const FwdArgs& a, int pi, const PairShared& ps
     V3 v = map_vertex(ps.kindB, u.x, u.y, u.z, u.w, ps.dB);
     sm.vB[i] = make_float4(v.x, v.y, v.z, u.w);
   }
-  for (int i = threadIdx.x; i < ps.neA; i += blockDim.x) sm.eA[i] = a.edges[A.e_off + i];
-  for (int i = threadIdx.x; i < ps.neB; i += blockDim.x) sm.eB[i] = a.edges[B.e_off + i];
-  for (int i = threadIdx.x; i < ps.npA; i += blockDim.x) sm.pA[i] = a.planes[A.p_off + i];
-  for (int i = threadIdx.x; i < ps.npB; i += blockDim.x) sm.pB[i] = a.planes[B.p_off + i];
+  for (int i = threadIdx.x; i < ps.neA; i += blockDim.x) {
+    const uint32_t e = a.edges[A.e_off + i];
+    sm.eA[i] = e;
+    const float4 u0 = a.verts[A.v_off + (e & 0xffffu)], u1 = a.verts[A.v_off + (e >> 16)];
+    const V3 l0 = map_vertex(ps.kindA, u0.x, u0.y, u0.z, u0.w, ps.dA);
+    const V3 l1 = map_vertex(ps.kindA, u1.x, u1.y, u1.z, u1.w, ps.dA);
+    const V3 w0 = mul(ps.Rrel, l0) + ps.trel, w1 = mul(ps.Rrel, l1) + ps.trel;
+    const int es = sm.es;
+    sm.eA6[i] = w0.x; sm.eA6[es + i] = w0.y; sm.eA6[2 * es + i] = w0.z;
+    sm.eA6[3 * es + i] = w1.x; sm.eA6[4 * es + i] = w1.y; sm.eA6[5 * es + i] = w1.z;
+    sm.eAl6[i] = l0.x; sm.eAl6[es + i] = l0.y; sm.eAl6[2 * es + i] = l0.z;
+    sm.eAl6[3 * es + i] = l1.x; sm.eAl6[4 * es + i] = l1.y; sm.eAl6[5 * es + i] = l1.z;
+  }
+  for (int i = threadIdx.x; i < ps.neB; i += blockDim.x) {
+    const uint32_t e = a.edges[B.e_off + i];
+    sm.eB[i] = e;
+    const float4 u0 = a.verts[B.v_off + (e & 0xffffu)], u1 = a.verts[B.v_off + (e >> 16)];
+    const V3 l0 = map_vertex(ps.kindB, u0.x, u0.y, u0.z, u0.w, ps.dB);
+    const V3 l1 = map_vertex(ps.kindB, u1.x, u1.y, u1.z, u1.w, ps.dB);
+    const int es = sm.es;
+    sm.eB6[i] = l0.x; sm.eB6[es + i] = l0.y; sm.eB6[2 * es + i] = l0.z;
+    sm.eB6[3 * es + i] = l1.x; sm.eB6[4 * es + i] = l1.y; sm.eB6[5 * es + i] = l1.z;
+  }
+  // hull planes pre-scaled by k = log2(e) / tau (see sdf_planes)
+  const float k = ps.k2;
+  for (int i = threadIdx.x; i < ps.npA; i += blockDim.x) {
+    const float4 q = a.planes[A.p_off + i];
+    sm.pA[i] = make_float4(q.x * k, q.y * k, q.z * k, q.w * k);
+  }
+  for (int i = threadIdx.x; i < ps.npB; i += blockDim.x) {
+    const float4 q = a.planes[B.p_off + i];
+    sm.pB[i] = make_float4(q.x * k, q.y * k, q.z * k, q.w * k);
+  }
 }
 
 // Next pair of this CTA: from the size-ordered work queue when one is given
@@ -170,20 +207,20 @@ __device__ __forceinline__ float vs_candidate(const PairShared& ps, const PairSm
   return -w * s.phi;
 }
 
-// Edge endpoints of element (k, l); A's edge also in A's own frame.
+// Edge endpoints of element (k, l) from the SoA endpoint arrays (lanes of a
+// warp take consecutive l, so B's reads are conflict-free and A's broadcast).
 struct EdgePair {
   V3 a0, a1, b0, b1;
-  int ia0, ia1;
+  int k;
 };
 __device__ __forceinline__ EdgePair edge_pair(const PairSmem& sm, int k, int l) {
-  uint32_t ea = sm.eA[k], eb = sm.eB[l];
+  const int es = sm.es;
   EdgePair e;
-  e.ia0 = ea & 0xffffu;
-  e.ia1 = ea >> 16;
-  e.a0 = ld3(sm.vA[e.ia0]);
-  e.a1 = ld3(sm.vA[e.ia1]);
-  e.b0 = ld3(sm.vB[eb & 0xffffu]);
-  e.b1 = ld3(sm.vB[eb >> 16]);
+  e.k = k;
+  e.a0 = v3(sm.eA6[k], sm.eA6[es + k], sm.eA6[2 * es + k]);
+  e.a1 = v3(sm.eA6[3 * es + k], sm.eA6[4 * es + k], sm.eA6[5 * es + k]);
+  e.b0 = v3(sm.eB6[l], sm.eB6[es + l], sm.eB6[2 * es + l]);
+  e.b1 = v3(sm.eB6[3 * es + l], sm.eB6[4 * es + l], sm.eB6[5 * es + l]);
   return e;
 }
 
@@ -193,10 +230,9 @@ struct Witness {
   float dbar, con;
   QPOut qp;
 };
-__device__ __forceinline__ Witness ee_witness(const EdgePair& e, const Params& p) {
-  QPPre q = qp_setup(e.a0, e.a1, e.b0, e.b1, p.w_reg);
+__device__ __forceinline__ Witness ee_witness_from(const EdgePair& e, const QPOut& qp) {
   Witness w;
-  w.qp = qp_solve(q, p.w_reg, p);
+  w.qp = qp;
   w.e1 = fma3(w.qp.a1, e.a1 - e.a0, e.a0);
   w.e2 = fma3(w.qp.a2, e.b1 - e.b0, e.b0);
   w.delta = w.e1 - w.e2;
@@ -204,6 +240,10 @@ __device__ __forceinline__ Witness ee_witness(const EdgePair& e, const Params& p
   w.dbar = sqrt_(r2);
   w.con = w.qp.con;
   return w;
+}
+__device__ __forceinline__ Witness ee_witness(const EdgePair& e, const Params& p) {
+  QPPre q = qp_setup(e.a0, e.a1, e.b0, e.b1, p.w_reg);
+  return ee_witness_from(e, qp_solve(q, p.w_reg, p));
 }
 
 // Both E-E candidates of element (k, l) (Sec. IV-D3): sign, penetration,
@@ -217,12 +257,14 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
                                               float (&y1)[8], float (&y2)[8], float& s1, float& s2) {
   const float tau = ps.tau, it = ps.inv_tau;
   V3 nbar = w.delta * rsq(dot(w.delta, w.delta) + tau * tau);
-  const V3 la0 = ld3(sm.vAl[ep.ia0]), la1 = ld3(sm.vAl[ep.ia1]);
+  const int es = sm.es, k = ep.k;
+  const V3 la0 = v3(sm.eAl6[k], sm.eAl6[es + k], sm.eAl6[2 * es + k]);
+  const V3 la1 = v3(sm.eAl6[3 * es + k], sm.eAl6[4 * es + k], sm.eAl6[5 * es + k]);
   const V3 e1l = fma3(w.qp.a1, la1 - la0, la0);
-  Sdf B_e1 = sdfB_at(ps, bb.B, w.e1);                   // phi_B(e1*)
-  Sdf B_e2 = sdfB_at(ps, bb.B, w.e2);                   // nu_B(e2*)
-  Sdf A_e2 = sdfA_at(ps, bb.A, w.e2);                   // phi_A(e2*)
-  Sdf A_e1 = body_sdf(bb.A, e1l, tau, it);              // nu_A(e1*), A frame
+  Sdf B_e1, B_e2, A_e2, A_e1;
+  body_sdf2(bb.B, w.e1, w.e2, tau, it, B_e1, B_e2);     // phi_B(e1*), nu_B(e2*)
+  const V3 x2 = mulT(ps.Rrel, w.e2 - ps.trel);
+  body_sdf2(bb.A, x2, e1l, tau, it, A_e2, A_e1);        // phi_A(e2*), nu_A(e1*) in A's frame
   A_e1.g = mul(ps.Rrel, A_e1.g);
   V3 nuB = normal_of(B_e2.g, tau);
   V3 nuA = normal_of(A_e1.g, tau);

@@ -98,6 +98,9 @@ SmemLayout make_layout(const cm_context* c, int nwarps) {
   L.rowL = o; o = align16(o + 8 * c->max_e);   // soft minima (+ row adjoint sums in the backward)
   L.colL = o; o = align16(o + 8 * c->max_e);
   L.warp = o; o = align16(o + 4 * kWarpStateFloats * nwarps);
+  L.eA6 = o; o = align16(o + 24 * c->max_e);
+  L.eAl6 = o; o = align16(o + 24 * c->max_e);
+  L.eB6 = o; o = align16(o + 24 * c->max_e);
   L.total = o;
   return L;
 }
@@ -174,9 +177,10 @@ void shape(const cm_context* c, int bwd, const LaunchCfg& cfg, int n_pairs, Smem
   grid = std::max(1, std::min<int>(n_pairs, c->num_sms * per_sm));
 }
 
+// Forward: dbar, alpha1, alpha2, con per edge pair; adjoint: dbar, t1, t2.
 size_t scratch_need(const cm_context* c, int bwd, int grid) {
   const int64_t stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
-  return (size_t)grid * stride * (bwd ? 3 : 1);
+  return (size_t)grid * stride * (bwd ? 3 : 4);
 }
 
 // Queues one manifold step (work ordering + forward or adjoint kernel) on `s`
@@ -205,6 +209,7 @@ cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32
   a.err = c->d_err;
   a.work_counter = nullptr;
   a.order = nullptr;
+  a.store_alpha = bwd ? 0 : 1;
   cudaError_t e;
   if (cfg.ordered) {
     if ((e = launch_order(pg, c->d_hdr, a.n_geoms, n_pairs, order, counter, s)) != cudaSuccess)
