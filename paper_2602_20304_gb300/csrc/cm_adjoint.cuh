@@ -178,6 +178,41 @@ CM_HD void body_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_
   }
 }
 
+// Reverse of sdf_planes2: the value at y1 (adjoint phibar1) and the gradient
+// at y2 (adjoint gbar2) in one pass over the (pre-scaled) planes.
+CM_HD void sdf_planes2_bwd(V3 y1, V3 y2, const float4* P, int nP, const Sdf& f1, const Sdf& f2, float inv_tau,
+                           float phibar1, V3 gbar2, V3& ybar1, V3& ybar2) {
+  const float k = inv_tau * kLog2e, ik = rcp(k);
+  const float2 X = make_float2(y1.x, y2.x), Y = make_float2(y1.y, y2.y), Z = make_float2(y1.z, y2.z);
+  const float2 mk = make_float2(-f1.phi * k, -f2.phi * k);
+  const float base2 = -dot(gbar2, f2.g) * inv_tau;
+  const float gk = inv_tau * ik;
+  float2 ax = dup2(0.f), ay = dup2(0.f), az = dup2(0.f);
+  for (int i = 0; i < nP; ++i) {
+    const float4 q = P[i];
+    const float2 z = ffma2(dup2(q.x), X, ffma2(dup2(q.y), Y, ffma2(dup2(q.z), Z, dup2(-q.w))));
+    const float2 d = fadd2(z, mk);
+    const float p1 = ex2(d.x), p2 = ex2(d.y);
+    const float2 sb = make_float2(p1 * phibar1, p2 * (base2 + (gbar2.x * q.x + gbar2.y * q.y + gbar2.z * q.z) * gk));
+    ax = ffma2(sb, dup2(q.x), ax);
+    ay = ffma2(sb, dup2(q.y), ay);
+    az = ffma2(sb, dup2(q.z), az);
+  }
+  ybar1 += v3(ax.x, ay.x, az.x) * ik;
+  ybar2 += v3(ax.y, ay.y, az.y) * ik;
+}
+
+// Reverse of body_sdf2 (value at y1, gradient at y2).
+CM_HD void body_sdf2_bwd(const Body& b, V3 y1, V3 y2, const Sdf& f1, const Sdf& f2, float tau, float inv_tau,
+                         float phibar1, V3 gbar2, V3& ybar1, V3& ybar2, V3& dbar) {
+  if (b.kind == kHull) {
+    sdf_planes2_bwd(y1, y2, b.planes, b.n_planes, f1, f2, inv_tau, phibar1, gbar2, ybar1, ybar2);
+  } else {
+    body_sdf_bwd(b, y1, f1, tau, inv_tau, phibar1, v3(0.f, 0.f, 0.f), ybar1, dbar);
+    body_sdf_bwd(b, y2, f2, tau, inv_tau, 0.f, gbar2, ybar2, dbar);
+  }
+}
+
 // ---------------------------------------------------------------- vertex templates
 // v = map(kind, u, dims) -> dims adjoint from the mapped vertex v and its cap sign s.
 CM_HD void map_vertex_bwd(int kind, V3 v, float s, V3 d, V3 vbar, V3& dbar) {
@@ -393,13 +428,13 @@ struct EECand {
 
 template <class Upstream>
 CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float rowL,
-                  float colL, Upstream&& up, float& t1, float& t2, Adj& adj) {
+                  float colL, const QPOut* stored, Upstream&& up, float& t1, float& t2, Adj& adj) {
   const float tau = F.tau, it = F.inv_tau;
   V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
   V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L);
-  // ---- forward recompute
+  // ---- forward recompute (the QP result may come from the pass that built the distances)
   QPPre q = qp_setup(a0, a1, b0, b1, p.w_reg);
-  QPOut o = qp_solve(q, p.w_reg, p);
+  QPOut o = stored ? *stored : qp_solve(q, p.w_reg, p);
   V3 e1 = fma3(o.a1, a1 - a0, a0), e2 = fma3(o.a2, b1 - b0, b0);
   V3 e1L = fma3(o.a1, a1L - a0L, a0L);
   V3 D = e1 - e2;
@@ -407,11 +442,10 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
   float dbar = sqrt_(r2);
   float qn = rsq(r2 + tau * tau);
   V3 nbar = D * qn;
-  Sdf SB1 = body_sdf(B, e1, tau, it);
-  Sdf SB2 = body_sdf(B, e2, tau, it);
+  Sdf SB1, SB2, SA2, SA1;
+  body_sdf2(B, e1, e2, tau, it, SB1, SB2);
   V3 x2 = mulT(F.R, e2 - F.t);
-  Sdf SA2 = body_sdf(A, x2, tau, it);
-  Sdf SA1 = body_sdf(A, e1L, tau, it);
+  body_sdf2(A, x2, e1L, tau, it, SA2, SA1);
   V3 nuB = normal_of(SB2.g, tau);
   V3 nuAL = normal_of(SA1.g, tau);
   V3 nuA = mul(F.R, nuAL);
@@ -457,24 +491,22 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
   if (dbar > 0.f) Db += D * (dbarb * rcp(dbar));
   V3 e1b = Db + v3(yb1[0], yb1[1], yb1[2]);
   V3 e2b = -Db + v3(yb2[0], yb2[1], yb2[2]);
-  // SDF reverses
-  body_sdf_bwd(B, e1, SB1, tau, it, phibB1, v3(0.f, 0.f, 0.f), e1b, adj.dB);
-  body_sdf_bwd(B, e2, SB2, tau, it, 0.f, normal_bwd(SB2.g, tau, nuBb), e2b, adj.dB);
-  V3 x2b = v3(0.f, 0.f, 0.f);
-  body_sdf_bwd(A, x2, SA2, tau, it, phibA2, v3(0.f, 0.f, 0.f), x2b, adj.dA);
-  e2b += pull_point_bwd(F, e2, x2b, adj);
+  // SDF reverses (one pass per body for its two points)
+  body_sdf2_bwd(B, e1, e2, SB1, SB2, tau, it, phibB1, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
+  V3 x2b = v3(0.f, 0.f, 0.f), e1Lb = v3(0.f, 0.f, 0.f);
   add_outer(adj.R, nuAb, nuAL);
-  V3 e1Lb = v3(0.f, 0.f, 0.f);
-  body_sdf_bwd(A, e1L, SA1, tau, it, 0.f, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), e1Lb, adj.dA);
+  body_sdf2_bwd(A, x2, e1L, SA2, SA1, tau, it, phibA2, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b, e1Lb,
+                adj.dA);
+  e2b += pull_point_bwd(F, e2, x2b, adj);
   witness_bwd(F, A, B, p, g, q, o, e1b, e1Lb, e2b, conb, adj);
 }
 
 // Distance-matrix adjoint of one element: Dbar flows through dbar = |e1* - e2*|.
 CM_HD void ee_dbar_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float Dbar,
-                       Adj& adj) {
+                       const QPOut* stored, Adj& adj) {
   V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
   QPPre q = qp_setup(a0, a1, b0, b1, p.w_reg);
-  QPOut o = qp_solve(q, p.w_reg, p);
+  QPOut o = stored ? *stored : qp_solve(q, p.w_reg, p);
   V3 e1 = fma3(o.a1, a1 - a0, a0), e2 = fma3(o.a2, b1 - b0, b0);
   V3 D = e1 - e2;
   float r2 = dot(D, D);

@@ -23,7 +23,7 @@
 namespace cm {
 
 struct BwdShared {
-  float G[kMaxK][8];  // upstream of row k in B's frame
+  __align__(16) float G[kMaxK][8];  // upstream of row k in B's frame
   float Gout[kMaxK];  // G_k . out_k
   float invZ[kMaxK];  // 1 / sum_i exp(-|s^_k - s_i| / tau)
   float shat[kMaxK];
@@ -50,25 +50,33 @@ __device__ __forceinline__ EEGeom ee_geom(const PairSmem& sm, int k, int l) {
 // partial dL/d s^_k (the K rows' dependence on the selected scores).
 __device__ __forceinline__ void ss_bwd(const BwdShared& bs, int K, float it, float k2, const float (&y)[8], float s,
                                        float (&yb)[8], float& sb, float (&shb)[kMaxK]) {
-#pragma unroll
-  for (int c = 0; c < 8; ++c) yb[c] = 0.f;
+  float2 yb2[4] = {dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f)};
+  const float2 yv[4] = {make_float2(y[0], y[1]), make_float2(y[2], y[3]), make_float2(y[4], y[5]),
+                        make_float2(y[6], y[7])};
   sb = 0.f;
 #pragma unroll
   for (int k = 0; k < kMaxK; ++k) {
     if (k < K) {
       const float d = bs.shat[k] - s;
       const float gam = ex2(-fabsf(d) * k2) * bs.invZ[k];
-      float a = -bs.Gout[k];
+      const float2* G = reinterpret_cast<const float2*>(bs.G[k]);
+      float2 a2 = make_float2(-bs.Gout[k], 0.f);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        yb[c] = fmaf(bs.G[k][c], gam, yb[c]);
-        a = fmaf(bs.G[k][c], y[c], a);
+      for (int c = 0; c < 4; ++c) {
+        const float2 g = G[c];
+        yb2[c] = ffma2(g, dup2(gam), yb2[c]);
+        a2 = ffma2(g, yv[c], a2);
       }
       const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-      const float term = gam * a * sg * it;
+      const float term = gam * (a2.x + a2.y) * sg * it;
       sb += term;
       shb[k] -= term;
     }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    yb[2 * c] = yb2[c].x;
+    yb[2 * c + 1] = yb2[c].y;
   }
 }
 
@@ -85,8 +93,9 @@ __device__ __forceinline__ void adj_reduce(const Adj& a, float* dst) {
   }
 }
 
-__global__ void __launch_bounds__(256, 1) cm_bwd_kernel(const FwdArgs a, const float* grad_out, float* grad_poses,
-                                                        float* grad_dims) {
+template <int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a, const float* grad_out,
+                                                                 float* grad_poses, float* grad_dims) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PairShared ps;
   __shared__ BwdShared bs;
@@ -95,9 +104,12 @@ __global__ void __launch_bounds__(256, 1) cm_bwd_kernel(const FwdArgs a, const f
   float* colC = sm.colL + a.sm.max_e;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int K = a.p.K;
-  float* Dm = a.scratch + (int64_t)blockIdx.x * a.scratch_stride * 3;
+  float* Dm = a.scratch + (int64_t)blockIdx.x * a.scratch_stride * 6;
   float* T1 = Dm + a.scratch_stride;
   float* T2 = T1 + a.scratch_stride;
+  float* QA1 = T2 + a.scratch_stride;  // alpha1, alpha2, con of every edge pair
+  float* QA2 = QA1 + a.scratch_stride;
+  float* QCN = QA2 + a.scratch_stride;
   int iter = 0;
   for (;;) {
     const int pi = next_pair(a, iter);
@@ -141,7 +153,11 @@ __global__ void __launch_bounds__(256, 1) cm_bwd_kernel(const FwdArgs a, const f
     if (nee) {
       for (int i = threadIdx.x; i < nee; i += blockDim.x) {
         const int k = i / neB, l = i - k * neB;
-        Dm[i] = ee_witness(edge_pair(sm, k, l), a.p).dbar;
+        const Witness w = ee_witness(edge_pair(sm, k, l), a.p);
+        Dm[i] = w.dbar;
+        QA1[i] = w.qp.a1;
+        QA2[i] = w.qp.a2;
+        QCN[i] = w.qp.con;
       }
       __syncthreads();
       for (int k = warp; k < neA; k += nwarps) {
@@ -172,7 +188,7 @@ __global__ void __launch_bounds__(256, 1) cm_bwd_kernel(const FwdArgs a, const f
         if (valid) {
           const int k = i / neB, l = i - k * neB;
           const EdgePair ep = edge_pair(sm, k, l);
-          Witness w = ee_witness(ep, a.p);
+          const Witness w = ee_witness_from(ep, QPOut{QA1[i], QA2[i], QCN[i]});
           ee_candidates(ps, sm, bb, ep, w, sm.rowL[k], sm.colL[l], y, y2, s1, s2);
         }
         wtk_push(st, valid, s1, y, K, k2, nvs + 2 * i);
@@ -233,7 +249,8 @@ __global__ void __launch_bounds__(256, 1) cm_bwd_kernel(const FwdArgs a, const f
     for (int i = threadIdx.x; i < nee; i += blockDim.x) {
       const int k = i / neB, l = i - k * neB;
       float t1, t2;
-      ee_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, k, l), sm.rowL[k], sm.colL[l],
+      const QPOut qs{QA1[i], QA2[i], QCN[i]};
+      ee_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, k, l), sm.rowL[k], sm.colL[l], &qs,
              [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
                ss_bwd(bs, K, it, k2, cc.y1, cc.s1, yb1, sb1, shb);
                ss_bwd(bs, K, it, k2, cc.y2, cc.s2, yb2, sb2, shb);
@@ -264,7 +281,8 @@ __global__ void __launch_bounds__(256, 1) cm_bwd_kernel(const FwdArgs a, const f
       } else if (id >= nvs) {
         const int e = id - nvs, i = e >> 1, b = e & 1, kk = i / neB, ll = i - kk * neB;
         float t1, t2;
-        ee_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, kk, ll), sm.rowL[kk], sm.colL[ll],
+        const QPOut qs{QA1[i], QA2[i], QCN[i]};
+        ee_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, kk, ll), sm.rowL[kk], sm.colL[ll], &qs,
                [&](const EECand&, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
                  for (int c = 0; c < 8; ++c) {
                    yb1[c] = 0.f;
@@ -287,7 +305,10 @@ __global__ void __launch_bounds__(256, 1) cm_bwd_kernel(const FwdArgs a, const f
       const float D = Dm[i];
       const float nn1 = ex2((sm.rowL[k] - D) * k2), nn2 = ex2((sm.colL[l] - D) * k2);
       const float Db = (nn1 * rowR[k] - T1[i] + nn2 * colC[l] - T2[i]) * it;
-      if (Db != 0.f) ee_dbar_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, k, l), Db, adj);
+      if (Db != 0.f) {
+        const QPOut qs{QA1[i], QA2[i], QCN[i]};
+        ee_dbar_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, k, l), Db, &qs, adj);
+      }
     }
     adj_reduce(adj, bs.adj);
     __syncthreads();
@@ -309,21 +330,32 @@ __global__ void __launch_bounds__(256, 1) cm_bwd_kernel(const FwdArgs a, const f
   }
 }
 
+// Two builds of the adjoint kernel: one CTA per SM with up to 255 registers,
+// or two CTAs per SM within 128 registers (spilling to L1); the launch shape's
+// CTAs-per-SM picks one (1 -> the first, otherwise the second).
 cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,
-                       int block, cudaStream_t s) {
+                       int block, int per_sm, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(cm_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(cm_bwd_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(cm_bwd_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  cm_bwd_kernel<<<grid, block, a.sm.total, s>>>(a, grad_out, grad_poses, grad_dims);
+  if (per_sm == 1)
+    cm_bwd_kernel<1><<<grid, block, a.sm.total, s>>>(a, grad_out, grad_poses, grad_dims);
+  else
+    cm_bwd_kernel<2><<<grid, block, a.sm.total, s>>>(a, grad_out, grad_poses, grad_dims);
   return cudaGetLastError();
 }
 
-int bwd_max_blocks_per_sm(int block, int smem_bytes) {
+int bwd_max_blocks_per_sm(int block, int smem_bytes, int per_sm) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel, block, smem_bytes) != cudaSuccess) return 1;
+  cudaError_t e = per_sm == 1
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel<1>, block, smem_bytes)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel<2>, block, smem_bytes);
+  if (e != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
 

@@ -63,8 +63,8 @@ constexpr int kWarpStateFloats = kMaxK * 9 + 10 + kMaxK;  // list, C, threshold,
 cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s);
 int fwd_max_blocks_per_sm(int block, int smem_bytes);
 cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,
-                       int block, cudaStream_t s);
-int bwd_max_blocks_per_sm(int block, int smem_bytes);
+                       int block, int per_sm, cudaStream_t s);
+int bwd_max_blocks_per_sm(int block, int smem_bytes, int per_sm);
 cudaError_t launch_order(const int32_t* pair_geoms, const GeomHeader* hdr, int n_geoms, int n, int32_t* order,
                          int32_t* counter, cudaStream_t s);
 

@@ -172,15 +172,15 @@ Params to_params(const cm_params* p) {
 // Grid and shared-memory layout of one launch shape.
 void shape(const cm_context* c, int bwd, const LaunchCfg& cfg, int n_pairs, SmemLayout& L, int& grid) {
   L = make_layout(c, cfg.block / 32);
-  int per_sm = bwd ? bwd_max_blocks_per_sm(cfg.block, L.total) : fwd_max_blocks_per_sm(cfg.block, L.total);
+  int per_sm = bwd ? bwd_max_blocks_per_sm(cfg.block, L.total, cfg.per_sm) : fwd_max_blocks_per_sm(cfg.block, L.total);
   if (cfg.per_sm > 0) per_sm = std::min(per_sm, cfg.per_sm);
   grid = std::max(1, std::min<int>(n_pairs, c->num_sms * per_sm));
 }
 
-// Forward: dbar, alpha1, alpha2, con per edge pair; adjoint: dbar, t1, t2.
+// Forward: dbar, alpha1, alpha2, con per edge pair; adjoint: dbar, t1, t2, alpha1, alpha2, con.
 size_t scratch_need(const cm_context* c, int bwd, int grid) {
   const int64_t stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
-  return (size_t)grid * stride * (bwd ? 3 : 4);
+  return (size_t)grid * stride * (bwd ? 6 : 4);
 }
 
 // Queues one manifold step (work ordering + forward or adjoint kernel) on `s`
@@ -217,7 +217,8 @@ cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32
     a.order = order;
     a.work_counter = counter;
   }
-  e = bwd ? launch_bwd(a, grad_out, grad_poses, grad_dims, grid, cfg.block, s) : launch_fwd(a, grid, cfg.block, s);
+  e = bwd ? launch_bwd(a, grad_out, grad_poses, grad_dims, grid, cfg.block, cfg.per_sm, s)
+          : launch_fwd(a, grid, cfg.block, s);
   if (e != cudaSuccess) return cuda_fail(e, bwd ? "backward launch" : "forward launch");
   return CM_OK;
 }

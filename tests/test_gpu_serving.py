@@ -97,7 +97,7 @@ def test_admission_and_timeouts(pool):
     from paper_2602_20304_gb300 import api
     from paper_2602_20304_gb300.engine import Engine
     w = pool
-    eng = Engine(0, hbm_budget_bytes=512 << 20)
+    eng = Engine(0, hbm_budget_bytes=2 << 30)
     try:
         ids = eng.add_geometries(w.geoms)
         params = eng.params()
