@@ -63,6 +63,18 @@ def mufu_ops_per_pair(w, flags=0):
     return out
 
 
+# ----------------------------------------------------------------- multi-rank helpers
+def rank_seed(rank):
+    """Seed of rank ``rank``'s replica: every rank owns an independent batch (weak scaling)."""
+    return synth.SEED_BASE + 2 + 1000 * rank
+
+
+def aggregate(total_ms, pairs_per_rank, steps, world, all_reduce_max):
+    """Whole-job pairs/s: all ranks' pairs over the slowest rank's time."""
+    ms = all_reduce_max(total_ms) if world > 1 else total_ms
+    return world * pairs_per_rank * steps / (ms * 1e-3), ms
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -266,7 +278,7 @@ def main():
             dist.barrier()
 
     # each rank owns an independent replica of the workload (weak scaling, no collective)
-    w = synth.config_hull_vs_primitive(n=args.pairs, seed=synth.SEED_BASE + 2 + 1000 * rank)
+    w = synth.config_hull_vs_primitive(n=args.pairs, seed=rank_seed(rank))
     eng = Engine(local)
     ids = eng.add_geometries(w.geoms)
     pg, poses, dims, tau = workload_tensors(w, id_map=ids)
@@ -306,18 +318,18 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms = np.array([a.elapsed_time(b) for a, b in evs])
-        tot = float(ms.sum())
-        if world > 1:
-            t = torch.tensor([tot], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        return tot, ms
+        return float(ms.sum()), ms
+
+    def max_over_ranks(v):
+        t = torch.tensor([v], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
     with ClockSampler(local) as clk:
         total_ms, step_ms = timed(plan_f)
         total_fb_ms, _ = timed(plan_fb)
-    value = world * w.n_pairs * args.steps / (total_ms * 1e-3)
-    value_fb = world * w.n_pairs * args.steps / (total_fb_ms * 1e-3)
+    value, total_ms = aggregate(total_ms, w.n_pairs, args.steps, world, max_over_ranks)
+    value_fb, total_fb_ms = aggregate(total_fb_ms, w.n_pairs, args.steps, world, max_over_ranks)
 
     # ---- end to end through the public API: pinned host inputs -> plan buffers -> host result
     hp = [t.cpu().pin_memory() for t in (pg, poses, dims, tau)]
@@ -337,13 +349,10 @@ def main():
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
     barrier()
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_value, e2e_ms = aggregate(e2e_ms, w.n_pairs, args.steps, world, max_over_ranks)
     h2d = sum(t.numel() * t.element_size() for t in hp)
     d2h = hout.numel() * hout.element_size()
-    e2e = {"value": world * w.n_pairs * args.steps / (e2e_ms * 1e-3), "unit": "pairs/s",
+    e2e = {"value": e2e_value, "unit": "pairs/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     api.cm_plan_destroy(plan_f)
     api.cm_plan_destroy(plan_fb)

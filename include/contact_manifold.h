@@ -110,7 +110,9 @@ void cm_default_params(cm_params* p);
 
 /* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the device
  * memory the context may hold for serving requests (0 = no bound).
- * Returns CM_ERR_CUDA if the device cannot be used. */
+ * Returns CM_ERR_CUDA if the device cannot be used.  device = -1 makes a
+ * host-only context: geometry can be registered and validated, every call
+ * that would touch a device returns CM_ERR_INVALID_ARG. */
 cm_status cm_create_context(int device, size_t hbm_budget_bytes, cm_context** out);
 
 /* Waits for the context's work, frees everything it owns.  NULL is ignored. */

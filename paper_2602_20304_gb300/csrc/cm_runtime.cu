@@ -58,6 +58,7 @@ cudaError_t grow_upload(T*& dptr, size_t& cap, const std::vector<T>& host) {
 }
 
 cm_status sync_geometry_locked(cm_context* c) {
+  if (c->device < 0) return fail(CM_ERR_INVALID_ARG, "host-only context: no device work");
   if (!c->dirty) return CM_OK;
   cudaError_t e;
   if ((e = grow_upload(c->d_hdr, c->cap_hdr, c->hdr)) != cudaSuccess) return cuda_fail(e, "geometry upload");
@@ -257,6 +258,14 @@ const char* cm_last_error(void) { return g_last_error.c_str(); }
 cm_status cm_create_context(int device, size_t hbm_budget_bytes, cm_context** out) {
   if (!out) return fail(CM_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
+  if (device == -1) {  // host-only: geometry registration and validation, no device work
+    cm_context* c = new (std::nothrow) cm_context();
+    if (!c) return fail(CM_ERR_OOM, "context allocation");
+    c->device = -1;
+    c->budget = hbm_budget_bytes;
+    *out = c;
+    return CM_OK;
+  }
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -278,6 +287,10 @@ cm_status cm_create_context(int device, size_t hbm_budget_bytes, cm_context** ou
 
 void cm_destroy_context(cm_context* c) {
   if (!c) return;
+  if (c->device < 0) {
+    delete c;
+    return;
+  }
   server_shutdown(c);  // drain and stop the serving loop before freeing what it uses
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
@@ -360,6 +373,7 @@ int32_t cm_num_geometries(const cm_context* c) { return c ? (int32_t)c->hdr.size
 
 cm_status cm_check_device_error(cm_context* c) {
   if (!c) return fail(CM_ERR_INVALID_ARG, "NULL context");
+  if (c->device < 0) return CM_OK;
   cudaSetDevice(c->device);
   int v = 0;
   cudaError_t e = cudaDeviceSynchronize();
@@ -463,6 +477,7 @@ extern "C" cm_status cm_contact_manifold_fwd_noalloc(cm_context* c, int32_t n_pa
   if (!pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "pair_geoms, poses and out are required");
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
+  if (c->device < 0) return fail(CM_ERR_INVALID_ARG, "host-only context: no device work");
   if (c->dirty)
     return fail(CM_ERR_INVALID_ARG, "geometry not uploaded: call cm_sync_geometry before the no-alloc entry point");
   if (params->flags & (CM_FLAG_NO_EE | CM_FLAG_ONE_SIDED)) {

@@ -1,0 +1,102 @@
+"""Host-side logic of the C ABI on a host-only context (no GPU needed): geometry
+validation, argument errors and the refusal of device work."""
+import numpy as np
+import pytest
+
+import synth
+
+
+@pytest.fixture()
+def api():
+    from paper_2602_20304_gb300 import build_lib
+    build_lib.build()
+    from paper_2602_20304_gb300 import api
+    return api
+
+
+@pytest.fixture()
+def ctx(api):
+    c = api.cm_create_context(-1)
+    yield c
+    api.cm_destroy_context(c)
+
+
+def add(api, ctx, g, **over):
+    d = dict(kind=g.kind, dims=g.dims, verts=g.verts, edges=g.edges, planes=g.planes if len(g.planes) else None)
+    d.update(over)
+    return api.cm_create_geometry(ctx, d["kind"], d["dims"], d["verts"], d["edges"], d["planes"])
+
+
+def test_valid_geometries_get_consecutive_ids(api, ctx):
+    w = synth.make_config(2, 4)
+    ids = [add(api, ctx, g) for g in w.geoms]
+    assert ids == list(range(len(w.geoms)))
+    assert api.cm_num_geometries(ctx) == len(w.geoms)
+
+
+@pytest.mark.parametrize("case", ["kind", "edge_index", "degenerate_edge", "nan_vertex", "dims", "planes_on_box",
+                                  "hull_without_planes", "non_unit_plane", "too_many_verts", "too_many_edges"])
+def test_invalid_geometry_is_rejected(api, ctx, case):
+    box = synth.primitive_geometry(synth.KIND_BOX, (0.5, 0.5, 0.5))
+    hull = synth.hull_from_points(np.random.default_rng(0).normal(size=(20, 3)))
+    over, g = {}, box
+    if case == "kind":
+        over = dict(kind=7)
+    elif case == "edge_index":
+        e = box.edges.copy()
+        e[0, 1] = 8
+        over = dict(edges=e)
+    elif case == "degenerate_edge":
+        e = box.edges.copy()
+        e[0, 1] = e[0, 0]
+        over = dict(edges=e)
+    elif case == "nan_vertex":
+        v = box.verts.copy()
+        v[3, 1] = np.nan
+        over = dict(verts=v)
+    elif case == "dims":
+        over = dict(dims=(0.5, -1.0, 0.5))
+    elif case == "planes_on_box":
+        over = dict(planes=hull.planes)
+    elif case == "hull_without_planes":
+        g, over = hull, dict(planes=None)
+    elif case == "non_unit_plane":
+        p = hull.planes.copy()
+        p[0, :3] *= 2
+        g, over = hull, dict(planes=p)
+    elif case == "too_many_verts":
+        g, over = hull, dict(verts=np.zeros((257, 4), np.float32))
+    elif case == "too_many_edges":
+        g, over = hull, dict(edges=np.zeros((769, 2), np.int32) + np.array([0, 1], np.int32))
+    with pytest.raises(api.CMError) as ei:
+        add(api, ctx, g, **over)
+    assert ei.value.status == api.CM_ERR_INVALID_ARG and api.cm_last_error()
+    assert api.cm_num_geometries(ctx) == 0
+
+
+def test_host_only_context_refuses_device_work(api, ctx):
+    add(api, ctx, synth.primitive_geometry(synth.KIND_BOX, (0.5, 0.5, 0.5)))
+    with pytest.raises(api.CMError) as ei:
+        api.cm_sync_geometry(ctx)
+    assert ei.value.status == api.CM_ERR_INVALID_ARG and "host-only" in str(ei.value)
+    with pytest.raises(api.CMError):
+        api.cm_server_start(ctx, api.cm_default_params(), 1024, 2)
+    api.cm_check_device_error(ctx)                  # nothing ran, nothing to report
+
+
+def test_bad_params_are_rejected_before_any_work(api, ctx):
+    import ctypes
+    lib = api._lib
+    add(api, ctx, synth.primitive_geometry(synth.KIND_BOX, (0.5, 0.5, 0.5)))
+    for over in (dict(tau=0.0), dict(tau=float("nan")), dict(w_reg=0.0), dict(K=0), dict(K=17), dict(flags=8),
+                 dict(eps_min=-1.0)):
+        p = api.cm_default_params(**over)
+        st = lib.cm_contact_manifold_fwd(ctx, 1, ctypes.c_void_p(8), ctypes.c_void_p(8), None, None,
+                                         ctypes.byref(p), ctypes.c_void_p(8), None)
+        assert st == api.CM_ERR_INVALID_ARG, over
+    p = api.cm_default_params()
+    assert lib.cm_contact_manifold_fwd(ctx, -1, None, None, None, None, ctypes.byref(p), None, None) == \
+        api.CM_ERR_INVALID_ARG
+    assert lib.cm_contact_manifold_fwd(ctx, 0, None, None, None, None, ctypes.byref(p), None, None) == api.CM_OK
+    assert lib.cm_contact_manifold_fwd(ctx, 3, None, None, None, None, ctypes.byref(p), None, None) == \
+        api.CM_ERR_INVALID_ARG
