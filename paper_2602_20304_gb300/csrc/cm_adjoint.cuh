@@ -426,9 +426,16 @@ struct EECand {
   float s1, s2;
 };
 
+// The four SDF evaluations of an edge pair (values at e1*, e2* of B and at
+// e2*, e1* of A; gradients at e2* of B and at e1* of A, the latter in A's frame).
+struct SdfQuad {
+  Sdf B1, B2, A2, A1;
+};
+
 template <class Upstream>
 CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float rowL,
-                  float colL, const QPOut* stored, Upstream&& up, float& t1, float& t2, Adj& adj) {
+                  float colL, const QPOut* stored, Upstream&& up, float& t1, float& t2, Adj& adj,
+                  const SdfQuad* sdf = nullptr) {
   const float tau = F.tau, it = F.inv_tau;
   V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
   V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L);
@@ -443,9 +450,16 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
   float qn = rsq(r2 + tau * tau);
   V3 nbar = D * qn;
   Sdf SB1, SB2, SA2, SA1;
-  body_sdf2(B, e1, e2, tau, it, SB1, SB2);
   V3 x2 = mulT(F.R, e2 - F.t);
-  body_sdf2(A, x2, e1L, tau, it, SA2, SA1);
+  if (sdf) {
+    SB1 = sdf->B1;
+    SB2 = sdf->B2;
+    SA2 = sdf->A2;
+    SA1 = sdf->A1;
+  } else {
+    body_sdf2(B, e1, e2, tau, it, SB1, SB2);
+    body_sdf2(A, x2, e1L, tau, it, SA2, SA1);
+  }
   V3 nuB = normal_of(SB2.g, tau);
   V3 nuAL = normal_of(SA1.g, tau);
   V3 nuA = mul(F.R, nuAL);

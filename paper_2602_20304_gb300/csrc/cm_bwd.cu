@@ -48,14 +48,15 @@ __device__ __forceinline__ EEGeom ee_geom(const PairSmem& sm, int k, int l) {
 
 // SoftSort reverse of one candidate (y, s): ybar, sbar and the per-thread
 // partial dL/d s^_k (the K rows' dependence on the selected scores).
+template <int KMAX>
 __device__ __forceinline__ void ss_bwd(const BwdShared& bs, int K, float it, float k2, const float (&y)[8], float s,
-                                       float (&yb)[8], float& sb, float (&shb)[kMaxK]) {
+                                       float (&yb)[8], float& sb, float (&shb)[KMAX]) {
   float2 yb2[4] = {dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f)};
   const float2 yv[4] = {make_float2(y[0], y[1]), make_float2(y[2], y[3]), make_float2(y[4], y[5]),
                         make_float2(y[6], y[7])};
   sb = 0.f;
 #pragma unroll
-  for (int k = 0; k < kMaxK; ++k) {
+  for (int k = 0; k < KMAX; ++k) {
     if (k < K) {
       const float d = bs.shat[k] - s;
       const float gam = ex2(-fabsf(d) * k2) * bs.invZ[k];
@@ -93,7 +94,108 @@ __device__ __forceinline__ void adj_reduce(const Adj& a, float* dst) {
   }
 }
 
-template <int kMinBlocks>
+
+// Everything the reverse phases of one pair read.
+struct BwdPair {
+  const FwdArgs* a;
+  const PairShared* ps;
+  PairSmem sm;
+  BwdShared* bs;
+  Frame F;
+  PairBodies bb;
+  float *Dm, *T1, *T2, *QA1, *QA2, *QCN, *rowR, *colC;
+  int nvs, neB, nee, K;
+};
+
+template <int KMAX>
+__device__ __forceinline__ void shb_reduce(const float (&shb)[KMAX], int K, BwdShared& bs) {
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    if (k < K) {
+      const float v = warp_sum(shb[k]);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&bs.shatbar[k], v);
+    }
+  }
+}
+
+// Vertex-SDF reverse of this thread's candidates.
+template <int KMAX>
+__device__ __forceinline__ void vs_reverse_phase(const BwdPair P) {
+  const PairShared& ps = *P.ps;
+  Adj adj;
+  adj_zero(adj);
+  float shb[KMAX];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) shb[k] = 0.f;
+  float y[8];
+  for (int c = threadIdx.x; c < P.nvs; c += blockDim.x) {
+    const float s = vs_candidate(ps, P.sm, P.bb, c, y);
+    float yb[8], sb;
+    ss_bwd<KMAX>(*P.bs, P.K, P.F.inv_tau, P.F.k2, y, s, yb, sb, shb);
+    if (c < ps.nvA) vs_bwd<true>(P.F, P.bb.A, P.bb.B, P.sm.vAl[c], ld3(P.sm.vA[c]), yb, sb, adj);
+    else vs_bwd<false>(P.F, P.bb.A, P.bb.B, P.sm.vB[c - ps.nvA], ld3(P.sm.vB[c - ps.nvA]), yb, sb, adj);
+  }
+  shb_reduce<KMAX>(shb, P.K, *P.bs);
+  adj_reduce(adj, P.bs->adj);
+}
+
+// The K selected scores pass dL/d s^_k to their own candidates (threads < K).
+__device__ __forceinline__ void fixup_phase(const BwdPair P) {
+  const PairShared& ps = *P.ps;
+  const int k = threadIdx.x;
+  const int id = P.bs->sid[k];
+  const float sx = P.bs->shatbar[k];
+  const float zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  Adj adj;
+  adj_zero(adj);
+  if (id >= 0 && id < P.nvs) {
+    if (id < ps.nvA) vs_bwd<true>(P.F, P.bb.A, P.bb.B, P.sm.vAl[id], ld3(P.sm.vA[id]), zero, sx, adj);
+    else vs_bwd<false>(P.F, P.bb.A, P.bb.B, P.sm.vB[id - ps.nvA], ld3(P.sm.vB[id - ps.nvA]), zero, sx, adj);
+  } else if (id >= P.nvs) {
+    const int e = id - P.nvs, i = e >> 1, b = e & 1, kk = i / P.neB, ll = i - kk * P.neB;
+    float t1, t2;
+    const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
+    ee_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(P.sm, kk, ll), P.sm.rowL[kk], P.sm.colL[ll], &qs,
+           [&](const EECand&, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
+             for (int c = 0; c < 8; ++c) {
+               yb1[c] = 0.f;
+               yb2[c] = 0.f;
+             }
+             sb1 = b == 0 ? sx : 0.f;
+             sb2 = b == 1 ? sx : 0.f;
+           },
+           t1, t2, adj);
+    atomicAdd(&P.T1[i], t1);
+    atomicAdd(&P.T2[i], t2);
+    atomicAdd(&P.rowR[kk], t1);
+    atomicAdd(&P.colC[ll], t2);
+  }
+  float* dst = P.bs->adj;
+  for (int i = 0; i < 9; ++i) atomicAdd(&dst[i], adj.R[i]);
+  atomicAdd(&dst[9], adj.t.x); atomicAdd(&dst[10], adj.t.y); atomicAdd(&dst[11], adj.t.z);
+  atomicAdd(&dst[12], adj.dA.x); atomicAdd(&dst[13], adj.dA.y); atomicAdd(&dst[14], adj.dA.z);
+  atomicAdd(&dst[15], adj.dB.x); atomicAdd(&dst[16], adj.dB.y); atomicAdd(&dst[17], adj.dB.z);
+}
+
+// Distance-matrix adjoint through the nearest-neighbour softmaxes.
+__device__ __forceinline__ void dbar_phase(const BwdPair P) {
+  Adj adj;
+  adj_zero(adj);
+  const float k2 = P.F.k2, it = P.F.inv_tau;
+  for (int i = threadIdx.x; i < P.nee; i += blockDim.x) {
+    const int k = i / P.neB, l = i - k * P.neB;
+    const float D = P.Dm[i];
+    const float nn1 = ex2((P.sm.rowL[k] - D) * k2), nn2 = ex2((P.sm.colL[l] - D) * k2);
+    const float Db = (nn1 * P.rowR[k] - P.T1[i] + nn2 * P.colC[l] - P.T2[i]) * it;
+    if (Db != 0.f) {
+      const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
+      ee_dbar_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(P.sm, k, l), Db, &qs, adj);
+    }
+  }
+  adj_reduce(adj, P.bs->adj);
+}
+
+template <int kMinBlocks, int KMAX>
 __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a, const float* grad_out,
                                                                  float* grad_poses, float* grad_dims) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -104,12 +206,13 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
   float* colC = sm.colL + a.sm.max_e;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int K = a.p.K;
-  float* Dm = a.scratch + (int64_t)blockIdx.x * a.scratch_stride * 6;
+  float* Dm = a.scratch + (int64_t)blockIdx.x * a.scratch_stride * 16;
   float* T1 = Dm + a.scratch_stride;
   float* T2 = T1 + a.scratch_stride;
   float* QA1 = T2 + a.scratch_stride;  // alpha1, alpha2, con of every edge pair
   float* QA2 = QA1 + a.scratch_stride;
   float* QCN = QA2 + a.scratch_stride;
+  float* SDF = QCN + a.scratch_stride;  // 10 arrays: the element's four SDF evaluations
   int iter = 0;
   for (;;) {
     const int pi = next_pair(a, iter);
@@ -189,7 +292,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
           const int k = i / neB, l = i - k * neB;
           const EdgePair ep = edge_pair(sm, k, l);
           const Witness w = ee_witness_from(ep, QPOut{QA1[i], QA2[i], QCN[i]});
-          ee_candidates(ps, sm, bb, ep, w, sm.rowL[k], sm.colL[l], y, y2, s1, s2);
+          ee_candidates(ps, sm, bb, ep, w, sm.rowL[k], sm.colL[l], y, y2, s1, s2, SDF, a.scratch_stride, i);
         }
         wtk_push(st, valid, s1, y, K, k2, nvs + 2 * i);
         wtk_push(st, valid, s2, y2, K, k2, nvs + 2 * i + 1);
@@ -234,83 +337,55 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     __syncthreads();
 
     // ================= reverse sweep
-    Adj adj;
-    adj_zero(adj);
-    float shb[kMaxK];
+    BwdPair P;
+    P.a = &a;
+    P.ps = &ps;
+    P.sm = sm;
+    P.bs = &bs;
+    P.F = F;
+    P.bb = bb;
+    P.Dm = Dm; P.T1 = T1; P.T2 = T2; P.QA1 = QA1; P.QA2 = QA2; P.QCN = QCN; P.rowR = rowR; P.colC = colC;
+    P.nvs = nvs; P.neB = neB; P.nee = nee; P.K = K;
+    vs_reverse_phase<KMAX>(P);
+    {
+      Adj adj;
+      adj_zero(adj);
+      float shb[KMAX];
 #pragma unroll
-    for (int k = 0; k < kMaxK; ++k) shb[k] = 0.f;
-    for (int c = threadIdx.x; c < nvs; c += blockDim.x) {
-      float s = vs_candidate(ps, sm, bb, c, y);
-      float yb[8], sb;
-      ss_bwd(bs, K, it, k2, y, s, yb, sb, shb);
-      if (c < ps.nvA) vs_bwd<true>(F, bb.A, bb.B, sm.vAl[c], ld3(sm.vA[c]), yb, sb, adj);
-      else vs_bwd<false>(F, bb.A, bb.B, sm.vB[c - ps.nvA], ld3(sm.vB[c - ps.nvA]), yb, sb, adj);
-    }
-    for (int i = threadIdx.x; i < nee; i += blockDim.x) {
-      const int k = i / neB, l = i - k * neB;
-      float t1, t2;
-      const QPOut qs{QA1[i], QA2[i], QCN[i]};
-      ee_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, k, l), sm.rowL[k], sm.colL[l], &qs,
-             [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
-               ss_bwd(bs, K, it, k2, cc.y1, cc.s1, yb1, sb1, shb);
-               ss_bwd(bs, K, it, k2, cc.y2, cc.s2, yb2, sb2, shb);
-             },
-             t1, t2, adj);
-      T1[i] = t1;
-      T2[i] = t2;
-      atomicAdd(&rowR[k], t1);
-      atomicAdd(&colC[l], t2);
-    }
-#pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
-      if (k < K) {
-        float v = warp_sum(shb[k]);
-        if (lane == 0) atomicAdd(&bs.shatbar[k], v);
-      }
-    }
-    __syncthreads();
-    // the K selected scores: their own candidates receive dL/d s^_k
-    if (threadIdx.x < K) {
-      const int k = threadIdx.x;
-      const int id = bs.sid[k];
-      const float sx = bs.shatbar[k];
-      const float zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (id >= 0 && id < nvs) {
-        if (id < ps.nvA) vs_bwd<true>(F, bb.A, bb.B, sm.vAl[id], ld3(sm.vA[id]), zero, sx, adj);
-        else vs_bwd<false>(F, bb.A, bb.B, sm.vB[id - ps.nvA], ld3(sm.vB[id - ps.nvA]), zero, sx, adj);
-      } else if (id >= nvs) {
-        const int e = id - nvs, i = e >> 1, b = e & 1, kk = i / neB, ll = i - kk * neB;
+      for (int k = 0; k < KMAX; ++k) shb[k] = 0.f;
+      for (int i = threadIdx.x; i < nee; i += blockDim.x) {
+        const int k = i / neB, l = i - k * neB;
         float t1, t2;
         const QPOut qs{QA1[i], QA2[i], QCN[i]};
-        ee_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, kk, ll), sm.rowL[kk], sm.colL[ll], &qs,
-               [&](const EECand&, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
-                 for (int c = 0; c < 8; ++c) {
-                   yb1[c] = 0.f;
-                   yb2[c] = 0.f;
-                 }
-                 sb1 = b == 0 ? sx : 0.f;
-                 sb2 = b == 1 ? sx : 0.f;
+        const int64_t st = a.scratch_stride;
+        const float* q = SDF + i;
+        SdfQuad sq;
+        sq.B1.phi = q[0];
+        sq.B1.g = v3(0.f, 0.f, 0.f);
+        sq.B2.phi = q[st];
+        sq.B2.g = v3(q[2 * st], q[3 * st], q[4 * st]);
+        sq.A2.phi = q[5 * st];
+        sq.A2.g = v3(0.f, 0.f, 0.f);
+        sq.A1.phi = q[6 * st];
+        sq.A1.g = v3(q[7 * st], q[8 * st], q[9 * st]);
+        ee_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, k, l), sm.rowL[k], sm.colL[l], &qs,
+               [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
+                 ss_bwd<KMAX>(bs, K, it, k2, cc.y1, cc.s1, yb1, sb1, shb);
+                 ss_bwd<KMAX>(bs, K, it, k2, cc.y2, cc.s2, yb2, sb2, shb);
                },
-               t1, t2, adj);
-        atomicAdd(&T1[i], t1);
-        atomicAdd(&T2[i], t2);
-        atomicAdd(&rowR[kk], t1);
-        atomicAdd(&colC[ll], t2);
+               t1, t2, adj, &sq);
+        T1[i] = t1;
+        T2[i] = t2;
+        atomicAdd(&rowR[k], t1);
+        atomicAdd(&colC[l], t2);
       }
+      shb_reduce<KMAX>(shb, K, bs);
+      adj_reduce(adj, bs.adj);
     }
     __syncthreads();
-    // distance-matrix adjoint through the nearest-neighbour softmaxes
-    for (int i = threadIdx.x; i < nee; i += blockDim.x) {
-      const int k = i / neB, l = i - k * neB;
-      const float D = Dm[i];
-      const float nn1 = ex2((sm.rowL[k] - D) * k2), nn2 = ex2((sm.colL[l] - D) * k2);
-      const float Db = (nn1 * rowR[k] - T1[i] + nn2 * colC[l] - T2[i]) * it;
-      if (Db != 0.f) {
-        const QPOut qs{QA1[i], QA2[i], QCN[i]};
-        ee_dbar_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, k, l), Db, &qs, adj);
-      }
-    }
-    adj_reduce(adj, bs.adj);
+    if (threadIdx.x < K) fixup_phase(P);
+    __syncthreads();
+    dbar_phase(P);
     __syncthreads();
     if (threadIdx.x == 0) {
       Adj r;
@@ -333,28 +408,38 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
 // Two builds of the adjoint kernel: one CTA per SM with up to 255 registers,
 // or two CTAs per SM within 128 registers (spilling to L1); the launch shape's
 // CTAs-per-SM picks one (1 -> the first, otherwise the second).
-cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,
-                       int block, int per_sm, cudaStream_t s) {
+// Builds of the adjoint kernel: one CTA per SM with up to 255 registers, or two
+// CTAs per SM within 128 registers (the launch shape's CTAs per SM picks: 1 ->
+// the first); each for K <= 8 and K <= 16 (the SoftSort reverse unrolls to it).
+template <int MB, int KM>
+static cudaError_t launch_bwd_t(const FwdArgs& a, const float* g, float* gp, float* gd, int grid, int block,
+                                cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(cm_bwd_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(cm_bwd_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(cm_bwd_kernel<MB, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         MB == 1 ? 180 * 1024 : 110 * 1024);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  if (per_sm == 1)
-    cm_bwd_kernel<1><<<grid, block, a.sm.total, s>>>(a, grad_out, grad_poses, grad_dims);
-  else
-    cm_bwd_kernel<2><<<grid, block, a.sm.total, s>>>(a, grad_out, grad_poses, grad_dims);
+  cm_bwd_kernel<MB, KM><<<grid, block, a.sm.total, s>>>(a, g, gp, gd);
   return cudaGetLastError();
+}
+
+cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,
+                       int block, int per_sm, cudaStream_t s) {
+  const bool k8 = a.p.K <= 8;
+  if (per_sm == 1)
+    return k8 ? launch_bwd_t<1, 8>(a, grad_out, grad_poses, grad_dims, grid, block, s)
+              : launch_bwd_t<1, 16>(a, grad_out, grad_poses, grad_dims, grid, block, s);
+  return k8 ? launch_bwd_t<2, 8>(a, grad_out, grad_poses, grad_dims, grid, block, s)
+            : launch_bwd_t<2, 16>(a, grad_out, grad_poses, grad_dims, grid, block, s);
 }
 
 int bwd_max_blocks_per_sm(int block, int smem_bytes, int per_sm) {
   int n = 0;
   cudaError_t e = per_sm == 1
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel<1>, block, smem_bytes)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel<2>, block, smem_bytes);
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel<1, 16>, block, smem_bytes)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel<2, 16>, block, smem_bytes);
   if (e != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }

@@ -59,11 +59,11 @@ cm_status check_params(const cm_params* p);
 cm_status check_k(const cm_context* c, const cm_params* params);
 LaunchCfg pick_cfg(const cm_context* c, int bwd, int n_pairs, int flags);
 void shape(const cm_context* c, int bwd, const LaunchCfg& cfg, int n_pairs, SmemLayout& L, int& grid);
-size_t scratch_need(const cm_context* c, int bwd, int grid);
+size_t scratch_need(const cm_context* c, int bwd, int grid, int64_t stride);  // stride <= 0: max_e^2
 cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs, const int32_t* pg,
                        const float* poses, const float* dims, const float* tau, const cm_params* params, float* out,
                        const float* grad_out, float* grad_poses, float* grad_dims, float* scratch,
-                       int32_t* order, int32_t* counter, cudaStream_t s);
+                       int32_t* order, int32_t* counter, cudaStream_t s, int64_t stride);  // stride <= 0: max_e^2
 void server_shutdown(cm_context* c);  // cm_serve.cu
 }  // namespace rt
 }  // namespace cm

@@ -251,10 +251,14 @@ __device__ __forceinline__ Witness ee_witness(const EdgePair& e, const Params& p
 // A's normal at its own witness is evaluated from A's local vertices: the SDF
 // normal near a mesh corner turns at a rate ~1/tau, and a frame round trip of
 // e1* would add FP32 position error that the soft sign then amplifies.
+// sdf_out (optional): the four SDF evaluations of the element, kept for the
+// adjoint as 10 arrays of stride sdf_stride at index idx: phi_B(e1*), phi_B(e2*),
+// grad_B(e2*) (3), phi_A(e2*), phi_A(e1*), grad_A(e1*) in A's frame (3).
 __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSmem& sm,
                                               const PairBodies& bb, const EdgePair& ep,
                                               const Witness& w, float rowL, float colL,
-                                              float (&y1)[8], float (&y2)[8], float& s1, float& s2) {
+                                              float (&y1)[8], float (&y2)[8], float& s1, float& s2,
+                                              float* sdf_out = nullptr, int64_t sdf_stride = 0, int idx = 0) {
   const float tau = ps.tau, it = ps.inv_tau;
   V3 nbar = w.delta * rsq(dot(w.delta, w.delta) + tau * tau);
   const int es = sm.es, k = ep.k;
@@ -265,6 +269,12 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
   body_sdf2(bb.B, w.e1, w.e2, tau, it, B_e1, B_e2);     // phi_B(e1*), nu_B(e2*)
   const V3 x2 = mulT(ps.Rrel, w.e2 - ps.trel);
   body_sdf2(bb.A, x2, e1l, tau, it, A_e2, A_e1);        // phi_A(e2*), nu_A(e1*) in A's frame
+  if (sdf_out) {
+    float* o = sdf_out + idx;
+    const int64_t st = sdf_stride;
+    o[0] = B_e1.phi; o[st] = B_e2.phi; o[2 * st] = B_e2.g.x; o[3 * st] = B_e2.g.y; o[4 * st] = B_e2.g.z;
+    o[5 * st] = A_e2.phi; o[6 * st] = A_e1.phi; o[7 * st] = A_e1.g.x; o[8 * st] = A_e1.g.y; o[9 * st] = A_e1.g.z;
+  }
   A_e1.g = mul(ps.Rrel, A_e1.g);
   V3 nuB = normal_of(B_e2.g, tau);
   V3 nuA = normal_of(A_e1.g, tau);

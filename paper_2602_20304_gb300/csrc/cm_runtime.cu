@@ -178,10 +178,11 @@ void shape(const cm_context* c, int bwd, const LaunchCfg& cfg, int n_pairs, Smem
   grid = std::max(1, std::min<int>(n_pairs, c->num_sms * per_sm));
 }
 
-// Forward: dbar, alpha1, alpha2, con per edge pair; adjoint: dbar, t1, t2, alpha1, alpha2, con.
-size_t scratch_need(const cm_context* c, int bwd, int grid) {
-  const int64_t stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
-  return (size_t)grid * stride * (bwd ? 6 : 4);
+// Forward: dbar, alpha1, alpha2, con per edge pair; adjoint: dbar, t1, t2,
+// alpha1, alpha2, con and the ten floats of the element's four SDF evaluations.
+size_t scratch_need(const cm_context* c, int bwd, int grid, int64_t stride) {
+  if (stride <= 0) stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
+  return (size_t)grid * stride * (bwd ? 16 : 4);
 }
 
 // Queues one manifold step (work ordering + forward or adjoint kernel) on `s`
@@ -189,7 +190,7 @@ size_t scratch_need(const cm_context* c, int bwd, int grid) {
 cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs, const int32_t* pg,
                        const float* poses, const float* dims, const float* tau, const cm_params* params, float* out,
                        const float* grad_out, float* grad_poses, float* grad_dims, float* scratch,
-                       int32_t* order, int32_t* counter, cudaStream_t s) {
+                       int32_t* order, int32_t* counter, cudaStream_t s, int64_t stride) {
   FwdArgs a{};
   int grid = 1;
   shape(c, bwd, cfg, n_pairs, a.sm, grid);
@@ -206,7 +207,7 @@ cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32
   a.p = to_params(params);
   a.out = out;
   a.scratch = scratch;
-  a.scratch_stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
+  a.scratch_stride = stride > 0 ? stride : std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
   a.err = c->d_err;
   a.work_counter = nullptr;
   a.order = nullptr;
@@ -231,11 +232,11 @@ cm_status run_step(cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs
   SmemLayout L;
   int grid = 1;
   shape(c, bwd, cfg, n_pairs, L, grid);
-  cm_status st = ensure_scratch(c, scratch_need(c, bwd, grid));
+  cm_status st = ensure_scratch(c, scratch_need(c, bwd, grid, 0));
   if (st != CM_OK) return st;
   if ((st = ensure_order(c, (size_t)n_pairs)) != CM_OK) return st;
   return enqueue_step(c, bwd, cfg, n_pairs, pg, poses, dims, tau, params, out, grad_out, grad_poses, grad_dims,
-                      c->d_scratch, c->d_order, c->d_counter, s);
+                      c->d_scratch, c->d_order, c->d_counter, s, 0);
 }
 }  // namespace rt
 }  // namespace cm
@@ -659,8 +660,8 @@ extern "C" cm_status cm_plan_create(cm_context* c, int32_t n_pairs, const int32_
   int grid_f = 1, grid_b = 1;
   shape(c, 0, gf, n_pairs, L, grid_f);
   shape(c, 1, gb, n_pairs, L, grid_b);
-  size_t need = scratch_need(c, 0, grid_f);
-  if (grad_out) need = std::max(need, scratch_need(c, 1, grid_b));
+  size_t need = scratch_need(c, 0, grid_f, 0);
+  if (grad_out) need = std::max(need, scratch_need(c, 1, grid_b, 0));
   cudaError_t e;
   if ((e = cudaMalloc(&p->scratch, need * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&p->order, (size_t)n_pairs * sizeof(int32_t))) != cudaSuccess ||
@@ -674,19 +675,19 @@ extern "C" cm_status cm_plan_create(cm_context* c, int32_t n_pairs, const int32_
   }
   // first launches outside the capture set the kernels' attributes
   st = enqueue_step(c, 0, gf, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, nullptr, nullptr,
-                    p->scratch, p->order, p->counter, p->cap);
+                    p->scratch, p->order, p->counter, p->cap, 0);
   if (st == CM_OK && grad_out)
     st = enqueue_step(c, 1, gb, n_pairs, pair_geoms, poses, dims, tau, params, nullptr, grad_out, grad_poses,
-                      grad_dims, p->scratch, p->order, p->counter, p->cap);
+                      grad_dims, p->scratch, p->order, p->counter, p->cap, 0);
   if (st == CM_OK && (e = cudaStreamSynchronize(p->cap)) != cudaSuccess) st = cuda_fail(e, "plan warm-up");
   if (st == CM_OK && (e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     st = cuda_fail(e, "begin capture");
   if (st == CM_OK) {
     cm_status s1 = enqueue_step(c, 0, gf, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, nullptr,
-                                nullptr, p->scratch, p->order, p->counter, p->cap);
+                                nullptr, p->scratch, p->order, p->counter, p->cap, 0);
     if (s1 == CM_OK && grad_out)
       s1 = enqueue_step(c, 1, gb, n_pairs, pair_geoms, poses, dims, tau, params, nullptr, grad_out, grad_poses,
-                        grad_dims, p->scratch, p->order, p->counter, p->cap);
+                        grad_dims, p->scratch, p->order, p->counter, p->cap, 0);
     e = cudaStreamEndCapture(p->cap, &p->graph);
     if (s1 != CM_OK) st = s1;
     else if (e != cudaSuccess) st = cuda_fail(e, "end capture");

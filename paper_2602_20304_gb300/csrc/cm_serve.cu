@@ -32,6 +32,7 @@ struct Request {
   uint64_t ticket = 0;
   cm_request_desc d{};
   size_t bytes = 0;          // device bytes of its share of a batch (inputs + outputs)
+  int64_t max_ee = 1;        // largest E_A x E_B among its pairs (scratch slice size)
   Clock::time_point t_submit, t_done;
   int state = 0;             // 0 queued, 1 running, 2 done, 3 failed
   cm_status status = CM_OK;
@@ -39,6 +40,7 @@ struct Request {
 
 struct Batch {
   std::vector<Request*> reqs;
+  int64_t max_ee = 1;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   void* mem = nullptr;       // one device block for every buffer of the batch
@@ -68,7 +70,7 @@ struct Server {
   std::vector<std::unique_ptr<Batch>> running;
   uint64_t next_ticket = 1;
   size_t bytes_in_use = 0;
-  size_t scratch_bytes = 0;  // per-batch scratch reserve
+  int grid_max = 1;          // most CTAs any launch shape of a batch uses
   bool stop = false;
   std::thread thread;
   uint64_t pairs_done = 0, batches_done = 0;
@@ -90,6 +92,13 @@ struct Server {
   }
 
   size_t budget() const { return ctx->budget ? ctx->budget : (size_t)1 << 62; }
+
+  // Scratch of a batch: one slice of max_ee edge pairs per CTA, 16 floats per
+  // edge pair with an adjoint in the batch, else 4; plus the work list.
+  size_t scratch_bytes(int64_t max_ee, bool bwd, int pairs) const {
+    const size_t grid = (size_t)std::min(grid_max, std::max(pairs, 1));  // a launch never has more CTAs than pairs
+    return round256(grid * (size_t)max_ee * (bwd ? 16 : 4) * sizeof(float)) + round256((size_t)pairs * 4 + 4);
+  }
 
   // Runs in the scheduler thread with `mu` held on entry and exit.
   void retire_finished(std::unique_lock<std::mutex>&) {
@@ -129,14 +138,23 @@ struct Server {
       }
     if (s < 0) return nullptr;
     auto b = std::make_unique<Batch>();
-    size_t bytes = scratch_bytes;
+    size_t io = 0;
     int pairs = 0;
+    int64_t mee = 1;
+    bool bwd = false;
+    size_t bytes = 0;
     while (!queue.empty()) {
       Request* r = queue.front();
       if (!b->reqs.empty() && pairs + r->d.n_pairs > max_batch_pairs) break;
-      if (bytes_in_use + bytes + r->bytes > budget()) break;
-      bytes += r->bytes;
+      const int64_t m2 = std::max(mee, r->max_ee);
+      const bool b2 = bwd || r->d.with_backward;
+      const size_t total = io + r->bytes + scratch_bytes(m2, b2, pairs + r->d.n_pairs);
+      if (bytes_in_use + total > budget()) break;
+      io += r->bytes;
       pairs += r->d.n_pairs;
+      mee = m2;
+      bwd = b2;
+      bytes = total;
       b->reqs.push_back(r);
       queue.pop_front();
     }
@@ -144,6 +162,7 @@ struct Server {
     b->stream = streams[s];
     stream_busy[s] = 1;
     b->bytes = bytes;
+    b->max_ee = mee;
     bytes_in_use += bytes;
     return b;
   }
@@ -174,9 +193,10 @@ struct Server {
     float* gout = (float*)take(32 * K * std::max<size_t>(nb, 1));
     float* gp = (float*)take(56 * std::max<size_t>(nb, 1));
     float* gd = (float*)take(24 * std::max<size_t>(nb, 1));
+    const size_t grid = (size_t)std::min(grid_max, (int)std::max<size_t>(n, 1));
+    float* scratch = (float*)take(grid * (size_t)b->max_ee * (nb ? 16 : 4) * sizeof(float));
     int32_t* order = (int32_t*)take(4 * n);
     int32_t* counter = (int32_t*)take(4);
-    float* scratch = (float*)p;
     cudaStream_t s = b->stream;
     // inputs
     size_t off = 0, offb = 0;
@@ -205,12 +225,13 @@ struct Server {
       const float* tptr = has_tau ? tau : nullptr;
       LaunchCfg gf = pick_cfg(ctx, 0, (int)n, params.flags);
       st = enqueue_step(ctx, 0, gf, (int)n, pg, poses, dptr, tptr, &params, out, nullptr, nullptr, nullptr, scratch,
-                        order, counter, s);
+                        order, counter, s, b->max_ee);
       if (st == CM_OK && nb) {
         const size_t t0 = n - nb;
         LaunchCfg gb = pick_cfg(ctx, 1, (int)nb, params.flags);
         st = enqueue_step(ctx, 1, gb, (int)nb, pg + 2 * t0, poses + 14 * t0, has_dims ? dims + 6 * t0 : nullptr,
-                          has_tau ? tau + t0 : nullptr, &params, nullptr, gout, gp, gd, scratch, order, counter, s);
+                          has_tau ? tau + t0 : nullptr, &params, nullptr, gout, gp, gd, scratch, order, counter, s,
+                          b->max_ee);
       }
     }
     if (st != CM_OK) return st;
@@ -302,20 +323,23 @@ cm_status cm_server_start(cm_context* c, const cm_params* params, int32_t max_ba
     srv->streams.push_back(s);
     srv->stream_busy.push_back(0);
   }
-  // scratch reserve of one batch: the larger of the forward and adjoint needs at
-  // the most CTAs any launch shape uses
-  size_t need = 0;
+  // the most CTAs any launch shape of a batch may use (scratch slices per batch)
+  int gmax = 1;
   for (int blk : {128, 256, 512}) {
     SmemLayout L;
     int g = 1;
     shape(c, 0, LaunchCfg{blk, 0, 1}, max_batch_pairs, L, g);
-    need = std::max(need, scratch_need(c, 0, g));
+    gmax = std::max(gmax, g);
     if (blk <= 256) {
-      shape(c, 1, LaunchCfg{blk, 0, 1}, max_batch_pairs, L, g);
-      need = std::max(need, scratch_need(c, 1, g));
+      for (int ps : {1, 2}) {
+        shape(c, 1, LaunchCfg{blk, ps, 1}, max_batch_pairs, L, g);
+        gmax = std::max(gmax, g);
+      }
     }
   }
-  srv->scratch_bytes = (need + 64) * sizeof(float) + (size_t)max_batch_pairs * 64;
+  srv->grid_max = gmax;
+  if (c->budget && srv->scratch_bytes(1, true, 1) + request_bytes(cm_request_desc{1, 1}, params->K) > c->budget)
+    return fail(CM_ERR_ADMISSION, "the HBM budget does not even hold a one-pair batch");
   // batch memory comes from the stream-ordered pool: keep freed blocks cached
   // (up to the budget) instead of returning them to the driver
   cudaMemPool_t pool;
@@ -323,8 +347,6 @@ cm_status cm_server_start(cm_context* c, const cm_params* params, int32_t max_ba
     uint64_t keep = c->budget ? (uint64_t)c->budget : UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
-  if (c->budget && srv->scratch_bytes > c->budget)
-    return fail(CM_ERR_ADMISSION, "the HBM budget does not even hold one batch's scratch");
   Server* raw = srv.get();
   c->server = std::move(srv);
   raw->thread = std::thread([raw] { raw->loop(); });
@@ -343,7 +365,18 @@ cm_status cm_submit(cm_context* c, const cm_request_desc* d, uint64_t* ticket) {
   auto r = std::make_unique<Request>();
   r->d = *d;
   r->bytes = request_bytes(*d, s->params.K);
-  if (s->scratch_bytes + r->bytes > s->budget())
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    const int ng = (int)c->hdr.size();
+    int64_t m = 1;
+    for (int i = 0; i < d->n_pairs; ++i) {
+      const int a = d->pair_geoms[2 * i], b = d->pair_geoms[2 * i + 1];
+      if (a >= 0 && a < ng && b >= 0 && b < ng)
+        m = std::max<int64_t>(m, (int64_t)c->hdr[a].n_edges * c->hdr[b].n_edges);
+    }
+    r->max_ee = m;
+  }
+  if (r->bytes + s->scratch_bytes(r->max_ee, d->with_backward != 0, d->n_pairs) > s->budget())
     return fail(CM_ERR_ADMISSION, "request does not fit the HBM budget even alone");
   r->t_submit = Clock::now();
   {

@@ -117,13 +117,20 @@ def test_admission_and_timeouts(pool):
             api.cm_wait(eng.ctx, t, 60000)
         assert np.isfinite(small["out"].numpy()).all()
         api.cm_server_stop(eng.ctx)
-        # a budget smaller than one batch's scratch cannot start a server
+        # with a 1 MiB budget: a request that cannot fit even alone is refused at submission,
+        # a small one is served
         eng2 = Engine(0, hbm_budget_bytes=1 << 20)
         try:
-            eng2.add_geometries(w.geoms)
+            ids2 = eng2.add_geometries(w.geoms)
+            api.cm_server_start(eng2.ctx, params, max_batch_pairs=8192, n_streams=2)
+            huge = make_requests(w, ids2, rng, [8192], [True])[0]
             with pytest.raises(api.CMError) as ei:
-                api.cm_server_start(eng2.ctx, params, max_batch_pairs=65536, n_streams=2)
+                submit(api, eng2.ctx, huge)
             assert ei.value.status == api.CM_ERR_ADMISSION
+            tiny = make_requests(w, ids2, rng, [2], [True])[0]
+            api.cm_wait(eng2.ctx, submit(api, eng2.ctx, tiny), 60000)
+            assert np.isfinite(tiny["gp"].numpy()).all()
+            api.cm_server_stop(eng2.ctx)
         finally:
             eng2.close()
     finally:
