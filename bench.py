@@ -242,6 +242,61 @@ def serve_benchmark(eng, api, seconds, seed=synth.SEED_BASE + 5):
                         "tau in {1e-3,1e-2,1e-1}, fwd or fwd+bwd 50/50", "served": served, "plain": plain}
 
 
+# ----------------------------------------------------------------- extra settings
+def plan_rate(eng, api, w, params, steps, with_bwd, flush, tune=True):
+    """Pairs/s of graph-replayed steps (forward, or forward + adjoint) on workload ``w``."""
+    import torch
+    from paper_2602_20304_gb300.engine import workload_tensors
+    ids = eng.add_geometries(w.geoms)
+    pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+    out = torch.empty((w.n_pairs, params.K, 8), device="cuda")
+    go = torch.randn_like(out) if with_bwd else None
+    gp = torch.empty_like(poses) if with_bwd else None
+    gd = torch.empty_like(dims) if with_bwd else None
+    if tune:
+        api.cm_autotune(eng.ctx, pg, poses, dims, tau, params, out, go, gp, gd)
+    plan = api.cm_plan_create(eng.ctx, pg, poses, dims, tau, params, out, go, gp, gd)
+    api.cm_plan_launch(plan)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        api.cm_plan_launch(plan)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    api.cm_plan_destroy(plan)
+    eng.check()
+    return w.n_pairs * steps / (ms * 1e-3), ms / steps
+
+
+def extra_settings(Engine, api, local, steps, flush):
+    """The uneven 65536-pair batch (forward and forward+backward) and the paper's two
+    simplifications (vertex-SDF contacts only; one-sided) on the default workload."""
+    eng = Engine(local)
+    try:
+        w4 = synth.config_mixed_pooled()
+        params = eng.params()
+        f4, f4_ms = plan_rate(eng, api, w4, params, steps, False, flush)
+        fb4, fb4_ms = plan_rate(eng, api, w4, params, steps, True, flush)
+        w2 = synth.config_hull_vs_primitive(n=4096, seed=rank_seed(0))
+        # K = 4: the smallest hulls have fewer than 8 vertices for the one-sided mode
+        full, _ = plan_rate(eng, api, w2, eng.params(K=4), steps, False, flush)
+        ne, _ = plan_rate(eng, api, w2, eng.params(K=4, flags=1), steps, False, flush)
+        nes, _ = plan_rate(eng, api, w2, eng.params(K=4, flags=2), steps, False, flush)
+    finally:
+        eng.close()
+    return {"uneven_65536": {"workload": "65536 pairs, hull(8-256 pts, pool of 4096) vs mixed primitives, "
+                                         "tau in {1e-3,1e-2,1e-1}, one persistent launch per step, CUDA graph",
+                             "fwd_pairs_per_s": f4, "fwd_ms": f4_ms, "fwd_bwd_pairs_per_s": fb4, "fwd_bwd_ms": fb4_ms},
+            "simplifications": {"workload": WORKLOAD.replace("K=8", "K=4"), "full_fwd_pairs_per_s": full,
+                                "no_ee_fwd_pairs_per_s": ne, "one_sided_fwd_pairs_per_s": nes,
+                                "speedup_no_ee": ne / full, "speedup_one_sided_vs_no_ee": nes / ne}}
+
+
 # ----------------------------------------------------------------- our arm
 def main():
     ap = argparse.ArgumentParser()
@@ -253,6 +308,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--pairs", type=int, default=4096, help="pairs per GPU (profiling uses fewer)")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (profiling)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and simplification lines")
     ap.add_argument("--serve-seconds", type=float, default=0.5,
                     help="length of the Poisson serving trace (0 skips the serving comparison)")
     args = ap.parse_args()
@@ -373,6 +429,10 @@ def main():
             "peak_source": "measured ex2.approx throughput (cm_measure_pipe_peaks)",
             "fma_peak_tflops": fma_peak / 1e12}
 
+    extra = None
+    if not args.no_extra and world == 1:
+        extra = extra_settings(Engine, api, local, max(3, min(args.steps, 5)), flush)
+
     serving = None
     if args.serve_seconds > 0 and world == 1:
         serving = serve_benchmark(Engine(local, hbm_budget_bytes=40 << 30), api, args.serve_seconds)
@@ -391,7 +451,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "pairs_per_gpu": w.n_pairs, "parallelism": f"replicas x{world}",
                        "l2": "flushed (512 MB write) between timed steps"},
-            "gpu_launches": launches_f * args.steps, "e2e": e2e, "serving": serving,
+            "gpu_launches": launches_f * args.steps, "e2e": e2e, "serving": serving, "extra": extra,
             "launch_shape": {"fwd": {"block": shape_f[0], "ctas_per_sm": shape_f[1], "ordered": shape_f[2]},
                              "bwd": {"block": shape_b[0], "ctas_per_sm": shape_b[1], "ordered": shape_b[2]},
                              "cuda_graph": True}, "roofline": roof, "cpu_baseline": cpu,

@@ -157,6 +157,32 @@ def config_mixed(n=65536, seed=SEED_BASE + 4):
                                     taus=(1e-3, 1e-2, 1e-1), name="mixed-uneven")
 
 
+def config_mixed_pooled(n=65536, pool=4096, seed=SEED_BASE + 4):
+    """The uneven mixed batch at full size with hull geometry drawn from a pool:
+    ``pool`` hulls of 8..256 points (log-uniform) are built once and each of the
+    ``n`` pairs picks one of them at random together with its own primitive,
+    dims, tau in {1e-3, 1e-2, 1e-1} and placement (building 65536 distinct
+    hulls would take minutes of qhull time on the host)."""
+    rng = np.random.default_rng(seed)
+    prims = {k: primitive_geometry(k) for k in PRIMITIVE_KINDS}
+    geoms = [prims[k] for k in PRIMITIVE_KINDS]
+    for _ in range(pool):
+        m = int(np.floor(np.exp(rng.uniform(np.log(8), np.log(257)))))
+        geoms.append(hull_from_points(_ball_points(rng, min(max(m, 8), 256))))
+    pg = np.zeros((n, 2), dtype=np.int32)
+    pg[:, 0] = 4 + rng.integers(0, pool, n)
+    kinds = rng.integers(0, 4, n)
+    pg[:, 1] = kinds
+    dims = np.ones((n, 6), dtype=np.float32)
+    d = rng.uniform(0.2, 1.0, size=(n, 3))
+    d[np.isin(kinds, [1, 2]), 2] = 0.0            # capsule / cylinder use (r, h)
+    dims[:, 3:] = d
+    delta = rng.uniform(0.0, 0.1, n)
+    poses = _place(rng, geoms, pg, dims, delta)
+    tau = np.asarray((1e-3, 1e-2, 1e-1), dtype=np.float32)[rng.integers(0, 3, n)]
+    return Workload("mixed-uneven-pooled", geoms, pg, poses, dims, tau)
+
+
 def serving_trace(seed=SEED_BASE + 5, rate=2000.0, duration=10.0, max_pairs=8192):
     """Poisson arrivals; request sizes log-uniform in [1, max_pairs]; fwd or fwd+bwd 50/50.
 
