@@ -63,6 +63,15 @@ def mufu_ops_per_pair(w, flags=0):
     return out
 
 
+def _hbm_peak():
+    """Measured HBM copy bandwidth of this GPU pool (GB/s), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
 # ----------------------------------------------------------------- multi-rank helpers
 def rank_seed(rank):
     """Seed of rank ``rank``'s replica: every rank owns an independent batch (weak scaling)."""
@@ -297,6 +306,31 @@ def extra_settings(Engine, api, local, steps, flush):
                                 "speedup_no_ee": ne / full, "speedup_one_sided_vs_no_ee": nes / ne}}
 
 
+def witness_rates(api, n=10_000_000, steps=5):
+    """Queries/s of the batched E-E and V-F witness routines, queries uniform in the unit
+    cube; the rows (48 B in, 32 / 16 B out) exceed L2, so each launch streams from HBM."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(synth.SEED_BASE + 6)
+    q = torch.rand((n, 12), device="cuda", generator=g)
+    p = api.cm_default_params()
+    res = {}
+    for name, fn, width in (("ee", api.cm_ee_witness_batch, 8), ("vf", api.cm_vf_witness_batch, 4)):
+        out = torch.empty((n, width), device="cuda")
+        for _ in range(3):
+            fn(q, p, out)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(steps):
+            fn(q, p, out)
+        b.record()
+        b.synchronize()
+        s = a.elapsed_time(b) * 1e-3 / steps
+        res[name] = {"queries_per_s": n / s, "ms": s * 1e3, "hbm_gbs": n * (48 + 4 * width) / s / 1e9}
+    res["queries"] = n
+    return res
+
+
 # ----------------------------------------------------------------- our arm
 def main():
     ap = argparse.ArgumentParser()
@@ -432,6 +466,9 @@ def main():
     extra = None
     if not args.no_extra and world == 1:
         extra = extra_settings(Engine, api, local, max(3, min(args.steps, 5)), flush)
+        extra["witness_points"] = witness_rates(api)
+        for k in ("ee", "vf"):
+            extra["witness_points"][k]["hbm_frac_of_measured"] = extra["witness_points"][k]["hbm_gbs"] / _hbm_peak()
 
     serving = None
     if args.serve_seconds > 0 and world == 1:

@@ -258,6 +258,19 @@ cm_status cm_contact_manifold_fwd_noalloc(cm_context* ctx, int32_t n_pairs, cons
  * when a kernel met an invalid geometry id. */
 cm_status cm_check_device_error(cm_context* ctx);
 
+/* Witness-point routines on their own, for independent queries (the paper's
+ * witness-point throughput setting, Sec. V, Fig. 6).  Device buffers, 16-byte
+ * aligned; they run on the current device and need no context.
+ * cm_ee_witness_batch: queries n x 12 floats (a0, a1 of edge 1; b0, b1 of edge 2);
+ *   the regularised 2x2 box QP with the smoothed analytic active set (Sec. IV-D2)
+ *   using params->w_reg and eps_*; out n x 8 floats (e1*, e2*, con, |e1* - e2*|).
+ * cm_vf_witness_batch: queries n x 12 floats (v, t0, t1, t2); the smoothed closest
+ *   point of the triangle to v (Sec. IV-D1: plane projection blended with the
+ *   soft-argmin of the soft-clipped edge projections by the soft barycentric
+ *   inside test); out n x 4 floats (witness, inside indicator). */
+cm_status cm_ee_witness_batch(int32_t n, const float* queries, const cm_params* params, float* out, void* stream);
+cm_status cm_vf_witness_batch(int32_t n, const float* queries, const cm_params* params, float* out, void* stream);
+
 /* Measures the device's FP32 FMA throughput (flop/s, 2 per FMA) and MUFU ex2
  * throughput (op/s) with two short synthetic kernels on `device`; used as the
  * denominators of the arithmetic roofline.  Not part of the paper's method. */

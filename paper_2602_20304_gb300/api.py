@@ -83,6 +83,8 @@ _SIGS = {
     "cm_release": (ctypes.c_int, [_vp, _u64]),
     "cm_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "cm_server_stop": (ctypes.c_int, [_vp]),
+    "cm_ee_witness_batch": (ctypes.c_int, [ctypes.c_int32, _vp, ctypes.POINTER(cm_params), _vp, _vp]),
+    "cm_vf_witness_batch": (ctypes.c_int, [ctypes.c_int32, _vp, ctypes.POINTER(cm_params), _vp, _vp]),
     "cm_measure_pipe_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double)]),
 }
@@ -327,6 +329,18 @@ def cm_server_stop(ctx) -> None:
     _check(_lib.cm_server_stop(ctx))
     for k in [k for k in _KEEPALIVE if k[0] == ctx.value]:
         _KEEPALIVE.pop(k)
+
+
+def cm_ee_witness_batch(queries, params, out, stream=None) -> None:
+    """Edge-edge witness points of n queries (n, 12) -> out (n, 8) on the current device."""
+    _check(_lib.cm_ee_witness_batch(int(queries.shape[0]), _ptr(queries), ctypes.byref(params), _ptr(out),
+                                    _stream_handle(stream)))
+
+
+def cm_vf_witness_batch(queries, params, out, stream=None) -> None:
+    """Vertex-triangle witness points of n queries (n, 12) -> out (n, 4) on the current device."""
+    _check(_lib.cm_vf_witness_batch(int(queries.shape[0]), _ptr(queries), ctypes.byref(params), _ptr(out),
+                                    _stream_handle(stream)))
 
 
 def cm_measure_pipe_peaks(device: int = 0):

@@ -432,4 +432,40 @@ CM_HD QPOut qp_solve(const QPPre& q, float lam, const Params& p) {
   return o;
 }
 
+// ---------------------------------------------------------------- V-F witness (Sec. IV-D1)
+// Smoothed closest point of triangle (t0, t1, t2) to v: plane projection if the
+// soft barycentric test says inside, else the soft-argmin blend of the three
+// edge projections (edge parameter soft-clipped to [0, 1]).  Returns the
+// witness and the inside indicator.
+CM_HD V3 vf_witness(V3 v, V3 t0, V3 t1, V3 t2, const Params& p, float& inside) {
+  const float ie = rcp(p.eps_clip);
+  V3 q[3];
+  float c[3];
+  const V3 A[3] = {t0, t1, t0}, B[3] = {t1, t2, t2};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const V3 e = B[j] - A[j];
+    const float s = clip_s(dot(v - A[j], e) * rcp(dot(e, e)), 0.f, 1.f, ie, p.eps_clip);
+    q[j] = fma3(s, e, A[j]);
+    const V3 d = v - q[j];
+    c[j] = sqrt_(dot(d, d));
+  }
+  const float cm = fminf(c[0], fminf(c[1], c[2]));
+  const float k = -rcp(p.eps_min) * kLog2e;
+  const float w0 = ex2((c[0] - cm) * k), w1 = ex2((c[1] - cm) * k), w2 = ex2((c[2] - cm) * k);
+  const float iw = rcp(w0 + w1 + w2);
+  const V3 pc = (q[0] * w0 + q[1] * w1 + q[2] * w2) * iw;
+  const V3 d10 = t1 - t0, d20 = t2 - t0;
+  const V3 nb = cross(d10, d20);
+  const float ia = rsq(dot(nb, nb));
+  const V3 n = nb * ia;
+  const V3 rel = v - t0;
+  const V3 pr = rel - n * dot(rel, n);
+  const float b2 = dot(cross(d10, pr), n) * ia, b1 = dot(cross(pr, d20), n) * ia, b0 = 1.f - b1 - b2;
+  const float ic = rcp(p.eps_comp);
+  inside = within01(b0, ic) * within01(b1, ic) * within01(b2, ic);
+  const V3 pu = t0 + pr;
+  return pc + (pu - pc) * inside;
+}
+
 }  // namespace cm
