@@ -291,6 +291,8 @@ def extra_settings(Engine, api, local, steps, flush):
         params = eng.params()
         f4, f4_ms = plan_rate(eng, api, w4, params, steps, False, flush)
         fb4, fb4_ms = plan_rate(eng, api, w4, params, steps, True, flush)
+        # the paper's acceleration structure: all vertices, the 16 deepest soft edges per body
+        sel4, sel4_ms = plan_rate(eng, api, w4, eng.params(top_edges=16), steps, False, flush)
         w2 = synth.config_hull_vs_primitive(n=4096, seed=rank_seed(0))
         # K = 4: the smallest hulls have fewer than 8 vertices for the one-sided mode
         full, _ = plan_rate(eng, api, w2, eng.params(K=4), steps, False, flush)
@@ -300,7 +302,8 @@ def extra_settings(Engine, api, local, steps, flush):
         eng.close()
     return {"uneven_65536": {"workload": "65536 pairs, hull(8-256 pts, pool of 4096) vs mixed primitives, "
                                          "tau in {1e-3,1e-2,1e-1}, one persistent launch per step, CUDA graph",
-                             "fwd_pairs_per_s": f4, "fwd_ms": f4_ms, "fwd_bwd_pairs_per_s": fb4, "fwd_bwd_ms": fb4_ms},
+                             "fwd_pairs_per_s": f4, "fwd_ms": f4_ms, "fwd_bwd_pairs_per_s": fb4, "fwd_bwd_ms": fb4_ms,
+                             "preselect_top_edges_16_fwd_pairs_per_s": sel4, "preselect_fwd_ms": sel4_ms},
             "simplifications": {"workload": WORKLOAD.replace("K=8", "K=4"), "full_fwd_pairs_per_s": full,
                                 "no_ee_fwd_pairs_per_s": ne, "one_sided_fwd_pairs_per_s": nes,
                                 "speedup_no_ee": ne / full, "speedup_one_sided_vs_no_ee": nes / ne}}

@@ -103,9 +103,19 @@ typedef struct {
   float eps_comp;
   int32_t K;
   int32_t flags;
+  /* Soft top-K pre-selection (Sec. IV-A, the differentiable acceleration
+   * structure; Supplement B's safeguard included): when > 0, only the
+   * top_verts deepest soft vertices of each body (depth = the other body's SDF)
+   * and the top_edges deepest soft edges (depth = mean of the corner depths)
+   * generate contacts, each a SoftSort average (temperature tau) of the
+   * vertices / edge endpoints; E-E witnesses are then also weighted by the soft
+   * indicator of lying inside their own body.  0 keeps all (no selection).
+   * At most 16 each; forward only (the adjoint rejects them). */
+  int32_t top_verts;
+  int32_t top_edges;
 } cm_params;
 
-/* Fills the defaults: tau 1e-2, w_reg 1e-2, eps_* 0.1, K 8, flags 0. */
+/* Fills the defaults: tau 1e-2, w_reg 1e-2, eps_* 0.1, K 8, flags 0, no pre-selection. */
 void cm_default_params(cm_params* p);
 
 /* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the device

@@ -38,7 +38,7 @@ class cm_geometry_desc(ctypes.Structure):
 class cm_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("w_reg", ctypes.c_float), ("eps_clip", ctypes.c_float),
                 ("eps_min", ctypes.c_float), ("eps_comp", ctypes.c_float), ("K", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("top_verts", ctypes.c_int32), ("top_edges", ctypes.c_int32)]
 
 
 class cm_request_desc(ctypes.Structure):

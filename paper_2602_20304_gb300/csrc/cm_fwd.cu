@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
     pair_stage(a, pi, ps, sm);
     __syncthreads();
     const PairBodies bb = pair_bodies(ps, sm);
+    if (ps.preselect) preselect_pair(a, ps, sm, bb);
     const float k2 = ps.k2;
 
     WarpTopK st;

@@ -22,7 +22,7 @@ static_assert(sizeof(GeomHeader) == 48, "GeomHeader layout");
 // Byte offsets of the per-CTA shared-memory carve-up (sized on the host from the
 // largest registered geometry).
 struct SmemLayout {
-  int vA, vAl, vB, pA, pB, eA, eB, rowL, colL, warp, eA6, eAl6, eB6;
+  int vA, vAl, vB, pA, pB, eA, eB, rowL, colL, warp, eA6, eAl6, eB6, sel;
   int total;
   int max_v, max_e, max_p;
 };
@@ -58,6 +58,9 @@ struct LaunchCfg {
 };
 
 constexpr int kMaxK = 16;
+// Pre-selection staging: vertex depths of both bodies (2 max_v) + the soft
+// selections: per body 16 vertices (B frame 3 + A frame 3) and 16 edges (12).
+constexpr int kSelFloats = 2 * kMaxK * 6 + 2 * kMaxK * 12 + 2 * kMaxK * 6;
 constexpr int kWarpStateFloats = kMaxK * 9 + 10 + kMaxK;  // list, C, threshold, ids
 
 cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s);

@@ -140,6 +140,7 @@ CM_HD float within01(float x, float inv_eps) { return sigmoid(x * inv_eps) * sig
 struct Params {
   float tau, w_reg, eps_clip, eps_min, eps_comp;
   int K, flags;
+  int top_verts, top_edges;  // soft pre-selection counts (0: all)
 };
 
 // ---------------------------------------------------------------- geometry kinds

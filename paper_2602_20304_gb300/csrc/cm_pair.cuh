@@ -21,6 +21,7 @@ struct PairShared {
   int nvA, nvB, neA, neB, npA, npB;
   float tau, inv_tau, k2;
   int bad;  // invalid geometry id
+  int preselect;  // soft pre-selection active for this pair
 };
 
 struct PairSmem {
@@ -34,7 +35,9 @@ struct PairSmem {
   float* eA6;      // A's edge endpoints in B's frame, SoA: [c * max_e + k], c = a0x, a0y, a0z, a1x, a1y, a1z
   float* eAl6;     // A's edge endpoints in A's frame, same layout
   float* eB6;      // B's edge endpoints, same layout
+  float* sel;      // pre-selection: vertex depths of A and B, then the staged soft selections
   int es;          // SoA stride (largest edge count)
+  int vs;          // vertex stride (largest vertex count)
   float* rowL;     // soft row minima of the E-E distance matrix (nn-Gamma_1)
   float* colL;     // soft column minima (nn-Gamma_2)
   float* warp;     // per-warp SoftSort states
@@ -55,7 +58,9 @@ __device__ __forceinline__ PairSmem carve(unsigned char* base, const SmemLayout&
   s.eA6 = reinterpret_cast<float*>(base + L.eA6);
   s.eAl6 = reinterpret_cast<float*>(base + L.eAl6);
   s.eB6 = reinterpret_cast<float*>(base + L.eB6);
+  s.sel = reinterpret_cast<float*>(base + L.sel);
   s.es = L.max_e;
+  s.vs = L.max_v;
   return s;
 }
 
@@ -86,6 +91,7 @@ __device__ inline void pair_setup(const FwdArgs& a, int pi, PairShared& ps) {
   ps.nvA = A.n_verts; ps.nvB = B.n_verts;
   ps.neA = A.n_edges; ps.neB = B.n_edges;
   ps.npA = A.n_planes; ps.npB = B.n_planes;
+  ps.preselect = (a.p.top_verts > 0 || a.p.top_edges > 0) ? 1 : 0;
   ps.tau = a.tau ? a.tau[pi] : a.p.tau;
   ps.inv_tau = 1.0f / ps.tau;
   ps.k2 = ps.inv_tau * kLog2e;
@@ -287,6 +293,10 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
   float nn2 = ex2((colL - w.dbar) * ps.k2);
   float base = w.con * cl;
   float w1 = base * pen1 * nn1, w2 = base * pen2 * nn2;
+  if (ps.preselect) {  // safeguard: each witness inside its own body
+    w1 *= sigmoid(-A_e1.phi * it);
+    w2 *= sigmoid(-B_e2.phi * it);
+  }
   float d1 = g1 * w.dbar, d2 = g2 * w.dbar;
   y1[0] = w.e1.x; y1[1] = w.e1.y; y1[2] = w.e1.z; y1[3] = d1;
   y1[4] = g1 * nbar.x; y1[5] = g1 * nbar.y; y1[6] = g1 * nbar.z; y1[7] = w1;
@@ -294,6 +304,145 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
   y2[4] = -g2 * nbar.x; y2[5] = -g2 * nbar.y; y2[6] = -g2 * nbar.z; y2[7] = w2;
   s1 = -w1 * d1;
   s2 = -w2 * d2;
+}
+
+// ---------------------------------------------------------------- soft pre-selection
+// (Sec. IV-A; Supplement B).  One warp per selection: the K largest depth scores
+// by K arg-max passes in (score desc, index asc) order, then the SoftSort rows
+// exp(-|s^_k - x_i| / tau) / Z_k applied to the items' payloads.
+template <int P>
+__device__ __forceinline__ void warp_soft_select(int n, int K, float k2, const float* score_src, int kind,
+                                                 const PairSmem& sm, float* dst) {
+  const int lane = threadIdx.x & 31;
+  const float* mA = sm.sel;
+  const float* mB = sm.sel + sm.vs;
+  const int es = sm.es;
+  auto score = [&](int i) -> float {
+    switch (kind) {
+      case 0: return -mA[i];
+      case 1: return -mB[i];
+      case 2: { const uint32_t e = sm.eA[i]; return -0.5f * (mA[e & 0xffffu] + mA[e >> 16]); }
+      default: { const uint32_t e = sm.eB[i]; return -0.5f * (mB[e & 0xffffu] + mB[e >> 16]); }
+    }
+  };
+  auto payload = [&](int i, float (&v)[P]) {
+    if (kind == 0) {
+      const float4 a = sm.vA[i], b = sm.vAl[i];
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = b.x; v[4] = b.y; v[5] = b.z;
+    } else if (kind == 1) {
+      const float4 a = sm.vB[i];
+      v[0] = a.x; v[1] = a.y; v[2] = a.z;
+    } else if (kind == 2) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) v[c] = sm.eA6[c * es + i];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) v[6 + c] = sm.eAl6[c * es + i];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) v[c] = sm.eB6[c * es + i];
+    }
+  };
+  (void)score_src;
+  float prev_s = 3.0e38f;
+  int prev_i = -1;
+  for (int k = 0; k < K; ++k) {
+    // the next item in (score desc, index asc) order after (prev_s, prev_i)
+    float bs = -3.0e38f;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < n; i += 32) {
+      const float x = score(i);
+      const bool after = x < prev_s || (x == prev_s && i > prev_i);
+      if (after && (x > bs || (x == bs && i < bi))) {
+        bs = x;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(kFull, bs, o);
+      const int oi = __shfl_xor_sync(kFull, bi, o);
+      if (os > bs || (os == bs && oi < bi)) {
+        bs = os;
+        bi = oi;
+      }
+    }
+    prev_s = bs;
+    prev_i = bi;
+    // SoftSort row k
+    float acc[P + 1];
+#pragma unroll
+    for (int c = 0; c <= P; ++c) acc[c] = 0.f;
+    for (int i = lane; i < n; i += 32) {
+      const float e = ex2(-fabsf(bs - score(i)) * k2);
+      float v[P];
+      payload(i, v);
+      acc[0] += e;
+#pragma unroll
+      for (int c = 0; c < P; ++c) acc[1 + c] = fmaf(e, v[c], acc[1 + c]);
+    }
+#pragma unroll
+    for (int c = 0; c <= P; ++c) acc[c] = warp_sum(acc[c]);
+    if (lane == 0) {
+      const float iz = 1.0f / acc[0];
+#pragma unroll
+      for (int c = 0; c < P; ++c) dst[k * P + c] = acc[1 + c] * iz;
+    }
+  }
+}
+
+// Replaces the pair's staged vertices and edges by their soft selections.
+// Called by every thread between __syncthreads.
+__device__ inline void preselect_pair(const FwdArgs& a, PairShared& ps, const PairSmem& sm, const PairBodies& bb) {
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  float* mA = sm.sel;
+  float* mB = sm.sel + sm.vs;
+  for (int i = threadIdx.x; i < ps.nvA; i += blockDim.x) mA[i] = sdfB_at(ps, bb.B, ld3(sm.vA[i])).phi;
+  for (int i = threadIdx.x; i < ps.nvB; i += blockDim.x) mB[i] = sdfA_at(ps, bb.A, ld3(sm.vB[i])).phi;
+  __syncthreads();
+  float* stA = sm.sel + 2 * sm.vs;          // 16 x 6: A's soft vertices (B frame, A frame)
+  float* stB = stA + kMaxK * 6;             // 16 x 3: B's soft vertices
+  float* seA = stB + kMaxK * 6;             // 16 x 12: A's soft edges (B frame, A frame)
+  float* seB = seA + kMaxK * 12;            // 16 x 6: B's soft edges
+  const int kvA = a.p.top_verts ? min(a.p.top_verts, ps.nvA) : 0;
+  const int kvB = a.p.top_verts ? min(a.p.top_verts, ps.nvB) : 0;
+  const int keA = a.p.top_edges ? min(a.p.top_edges, ps.neA) : 0;
+  const int keB = a.p.top_edges ? min(a.p.top_edges, ps.neB) : 0;
+  for (int job = warp; job < 4; job += nwarps) {
+    if (job == 0 && kvA) warp_soft_select<6>(ps.nvA, kvA, ps.k2, nullptr, 0, sm, stA);
+    if (job == 1 && kvB) warp_soft_select<3>(ps.nvB, kvB, ps.k2, nullptr, 1, sm, stB);
+    if (job == 2 && keA) warp_soft_select<12>(ps.neA, keA, ps.k2, nullptr, 2, sm, seA);
+    if (job == 3 && keB) warp_soft_select<6>(ps.neB, keB, ps.k2, nullptr, 3, sm, seB);
+  }
+  __syncthreads();
+  const int es = sm.es;
+  for (int i = threadIdx.x; i < kvA; i += blockDim.x) {
+    const float* v = stA + 6 * i;
+    sm.vA[i] = make_float4(v[0], v[1], v[2], 0.f);
+    sm.vAl[i] = make_float4(v[3], v[4], v[5], 0.f);
+  }
+  for (int i = threadIdx.x; i < kvB; i += blockDim.x) {
+    const float* v = stB + 3 * i;
+    sm.vB[i] = make_float4(v[0], v[1], v[2], 0.f);
+  }
+  for (int i = threadIdx.x; i < keA; i += blockDim.x) {
+    const float* v = seA + 12 * i;
+    for (int c = 0; c < 6; ++c) {
+      sm.eA6[c * es + i] = v[c];
+      sm.eAl6[c * es + i] = v[6 + c];
+    }
+  }
+  for (int i = threadIdx.x; i < keB; i += blockDim.x) {
+    const float* v = seB + 6 * i;
+    for (int c = 0; c < 6; ++c) sm.eB6[c * es + i] = v[c];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (kvA) ps.nvA = kvA;
+    if (kvB) ps.nvB = kvB;
+    if (keA) ps.neA = keA;
+    if (keB) ps.neB = keB;
+  }
+  __syncthreads();
 }
 
 }  // namespace cm

@@ -80,6 +80,8 @@ cm_status check_params(const cm_params* p) {
     return fail(CM_ERR_INVALID_ARG, "w_reg must be finite and > 0 (the E-E QP needs it to be strictly convex)");
   if (p->K < 1 || p->K > CM_MAX_K) return fail(CM_ERR_INVALID_ARG, "K must be in 1..16");
   if (p->flags & ~3) return fail(CM_ERR_INVALID_ARG, "unknown flag bits");
+  if (p->top_verts < 0 || p->top_verts > CM_MAX_K || p->top_edges < 0 || p->top_edges > CM_MAX_K)
+    return fail(CM_ERR_INVALID_ARG, "top_verts and top_edges must be in 0..16");
   return CM_OK;
 }
 
@@ -102,6 +104,7 @@ SmemLayout make_layout(const cm_context* c, int nwarps) {
   L.eA6 = o; o = align16(o + 24 * c->max_e);
   L.eAl6 = o; o = align16(o + 24 * c->max_e);
   L.eB6 = o; o = align16(o + 24 * c->max_e);
+  L.sel = o; o = align16(o + 4 * (2 * c->max_v + kSelFloats));
   L.total = o;
   return L;
 }
@@ -135,11 +138,17 @@ cm_status ensure_order(cm_context* c, size_t n) {
 
 cm_status check_k(const cm_context* c, const cm_params* params) {
   if (params->flags & (CM_FLAG_NO_EE | CM_FLAG_ONE_SIDED)) {
-    const int min_cands = (params->flags & CM_FLAG_ONE_SIDED) ? c->min_v : 2 * c->min_v;
+    const int nv = params->top_verts ? std::min(params->top_verts, c->min_v) : c->min_v;
+    const int min_cands = (params->flags & CM_FLAG_ONE_SIDED) ? nv : 2 * nv;
     if (params->K > min_cands)
       return fail(CM_ERR_INVALID_ARG, "K exceeds the vertex-contact count of the smallest registered geometry");
   } else if (c->min_e < 3) {
     return fail(CM_ERR_INVALID_ARG, "E-E contacts need every registered geometry to have >= 3 edges");
+  } else if (params->top_edges || params->top_verts) {
+    const int nv = params->top_verts ? std::min(params->top_verts, c->min_v) : c->min_v;
+    const int ne = params->top_edges ? std::min(params->top_edges, c->min_e) : c->min_e;
+    if (params->K > 2 * nv + 2 * ne * ne)
+      return fail(CM_ERR_INVALID_ARG, "K exceeds the candidates left after pre-selection");
   }
   return CM_OK;
 }
@@ -167,7 +176,7 @@ LaunchCfg pick_cfg(const cm_context* c, int bwd, int n_pairs, int flags) {
 }
 
 Params to_params(const cm_params* p) {
-  return Params{p->tau, p->w_reg, p->eps_clip, p->eps_min, p->eps_comp, p->K, p->flags};
+  return Params{p->tau, p->w_reg, p->eps_clip, p->eps_min, p->eps_comp, p->K, p->flags, p->top_verts, p->top_edges};
 }
 
 // Grid and shared-memory layout of one launch shape.
@@ -252,6 +261,8 @@ void cm_default_params(cm_params* p) {
   p->eps_comp = 0.1f;
   p->K = 8;
   p->flags = 0;
+  p->top_verts = 0;
+  p->top_edges = 0;
 }
 
 const char* cm_last_error(void) { return g_last_error.c_str(); }
@@ -421,6 +432,8 @@ extern "C" cm_status cm_contact_manifold_bwd(cm_context* c, int32_t n_pairs, con
   if (n_pairs == 0) return CM_OK;
   if (!pair_geoms || !poses || !grad_out || !grad_poses)
     return fail(CM_ERR_INVALID_ARG, "pair_geoms, poses, grad_out and grad_poses are required");
+  if (params->top_verts || params->top_edges)
+    return fail(CM_ERR_INVALID_ARG, "the adjoint does not support pre-selection (top_verts / top_edges)");
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
@@ -520,7 +533,7 @@ extern "C" cm_status cm_contact_manifold_fwd_noalloc(cm_context* c, int32_t n_pa
   a.poses = poses;
   a.dims = dims;
   a.tau = tau;
-  a.p = Params{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K, params->flags};
+  a.p = Params{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K, params->flags, params->top_verts, params->top_edges};
   a.out = out;
   a.scratch = scratch;  // written before it is read: no clearing needed
   a.scratch_stride = stride;
@@ -545,6 +558,8 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
   if (st != CM_OK) return st;
   if (n_pairs <= 0 || !pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "a non-empty batch is required");
   if (grad_out && !grad_poses) return fail(CM_ERR_INVALID_ARG, "grad_poses is required with grad_out");
+  if (grad_out && (params->top_verts || params->top_edges))
+    return fail(CM_ERR_INVALID_ARG, "the adjoint does not support pre-selection (top_verts / top_edges)");
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
@@ -645,6 +660,8 @@ extern "C" cm_status cm_plan_create(cm_context* c, int32_t n_pairs, const int32_
   if (st != CM_OK) return st;
   if (n_pairs <= 0 || !pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "a non-empty batch is required");
   if (grad_out && !grad_poses) return fail(CM_ERR_INVALID_ARG, "grad_poses is required with grad_out");
+  if (grad_out && (params->top_verts || params->top_edges))
+    return fail(CM_ERR_INVALID_ARG, "the adjoint does not support pre-selection (top_verts / top_edges)");
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;

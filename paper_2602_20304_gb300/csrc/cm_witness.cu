@@ -62,7 +62,7 @@ extern "C" cm_status cm_ee_witness_batch(int32_t n, const float* queries, const 
   cm_status st = check_batch(n, queries, params, out);
   if (st != CM_OK || n == 0) return st;
   const Params p{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K,
-                 params->flags};
+                 params->flags, 0, 0};
   ee_witness_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, reinterpret_cast<const float4*>(queries), p,
                                                                    reinterpret_cast<float4*>(out));
   cudaError_t e = cudaGetLastError();
@@ -74,7 +74,7 @@ extern "C" cm_status cm_vf_witness_batch(int32_t n, const float* queries, const 
   cm_status st = check_batch(n, queries, params, out);
   if (st != CM_OK || n == 0) return st;
   const Params p{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K,
-                 params->flags};
+                 params->flags, 0, 0};
   vf_witness_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, reinterpret_cast<const float4*>(queries), p,
                                                                    reinterpret_cast<float4*>(out));
   cudaError_t e = cudaGetLastError();

@@ -33,8 +33,24 @@ def oracle_params(p):
 
 
 def oracle_forward(w, params, idx=None):
+    if getattr(params, "top_verts", 0) or getattr(params, "top_edges", 0):
+        return oracle_forward_preselect(w, params, idx)
     return oracle.batch_manifold(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau,
                                  oracle_params(params), idx=idx)
+
+
+def oracle_forward_preselect(w, params, idx=None):
+    import torch
+    from oracle.preselect import pair_manifold_preselect
+    ids = range(w.n_pairs) if idx is None else idx
+    t = lambda x: torch.as_tensor(np.asarray(x), dtype=torch.float64)  # noqa: E731
+    out = []
+    with torch.no_grad():
+        for i in ids:
+            ga, gb = w.geoms[int(w.pair_geoms[i, 0])], w.geoms[int(w.pair_geoms[i, 1])]
+            out.append(pair_manifold_preselect(ga, gb, t(w.poses[i]), t(w.dims[i]), float(w.tau[i]),
+                                               oracle_params(params), params.top_verts, params.top_edges).numpy())
+    return np.stack(out)
 
 
 def errors(gpu, ref):
