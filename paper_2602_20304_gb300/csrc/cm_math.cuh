@@ -281,6 +281,37 @@ CM_HD void sdf_planes2(V3 y1, V3 y2, const float4* P, int nP, float tau, Sdf& o1
   o2.g = G * (t * rcp(S.y));
 }
 
+// What an edge pair's candidates take from a polyhedron's SDF (Sec. IV-D3):
+// sigma(-phi(y1)/tau) at the other body's witness y1 and the gradient at the
+// body's own witness y2 (for its normal), plus sigma(-phi(y2)/tau) for the
+// pre-selection safeguard.  With the planes pre-scaled to base-2 exponents z_f,
+// sigma(-phi/tau) = 1 / (1 + sum_f 2^z_f) exactly, so the plain (unshifted) sum
+// serves: where it over- or underflows in FP32, sigma saturates to 0 or 1 the
+// same way.  The gradient is the ratio G / S, whatever the shift.  The caller
+// uses this only while y2 lies within a scaled distance of 60 of its own edge
+// segment: every plane passes no closer than that bound above the segment and
+// the planes through the edge lie no farther below, so S2 stays within
+// 2^-60 .. nP 2^60.  Returns S1 = sum at y1, S2 = sum at y2 and G2 = grad phi(y2).
+CM_HD void sdf_planes_ee(V3 y1, V3 y2, const float4* P, int nP, float tau, float& S1, float& S2,
+                         V3& G2) {
+  const float2 X = make_float2(y1.x, y2.x), Y = make_float2(y1.y, y2.y), Z = make_float2(y1.z, y2.z);
+  float2 S = dup2(0.f);
+  V3 G = v3(0.f, 0.f, 0.f);
+#pragma unroll 4
+  for (int f = 0; f < nP; ++f) {
+    const float4 q = P[f];
+    const float2 z = ffma2(dup2(q.x), X, ffma2(dup2(q.y), Y, ffma2(dup2(q.z), Z, dup2(-q.w))));
+    const float2 e = make_float2(ex2(z.x), ex2(z.y));
+    S = fadd2(S, e);
+    G.x = fmaf(e.y, q.x, G.x);
+    G.y = fmaf(e.y, q.y, G.y);
+    G.z = fmaf(e.y, q.z, G.z);
+  }
+  S1 = S.x;
+  S2 = S.y;
+  G2 = G * (tau * kLn2 * rcp(S.y));
+}
+
 // Superquadric with eps1 = eps2 = 1 (Sec. IV-B1): phi = |y| (1 - f^-1/2), f = |y~|^2;
 // the normal comes from grad f = 2 y / d^2.
 CM_HD Sdf sdf_ellipsoid(V3 y, V3 d) {

@@ -274,7 +274,25 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
   Sdf B_e1, B_e2, A_e2, A_e1;
   body_sdf2(bb.B, w.e1, w.e2, tau, it, B_e1, B_e2);     // phi_B(e1*), nu_B(e2*)
   const V3 x2 = mulT(ps.Rrel, w.e2 - ps.trel);
-  body_sdf2(bb.A, x2, e1l, tau, it, A_e2, A_e1);        // phi_A(e2*), nu_A(e1*) in A's frame
+  // A hull's sums without a shift (sdf_planes_ee) when only the forward's
+  // quantities are wanted and e1* is within a scaled distance of 60 of A's edge.
+  float pen2 = -1.f, safe1 = 1.f;
+  bool fast = false;
+  if (!sdf_out && bb.A.kind == kHull) {
+    const V3 t1 = la1 - la0;
+    const float ex = fmaxf(fmaxf(-w.qp.a1, w.qp.a1 - 1.f), 0.f) * ps.k2;
+    fast = ex * ex * dot(t1, t1) <= 3600.f;
+  }
+  if (fast) {
+    float S1, S2;
+    sdf_planes_ee(x2, e1l, bb.A.planes, bb.A.n_planes, tau, S1, S2, A_e1.g);
+    pen2 = rcp(1.f + S1);
+    safe1 = rcp(1.f + S2);
+  } else {
+    body_sdf2(bb.A, x2, e1l, tau, it, A_e2, A_e1);      // phi_A(e2*), nu_A(e1*) in A's frame
+    pen2 = sigmoid(-A_e2.phi * it);
+    safe1 = sigmoid(-A_e1.phi * it);
+  }
   if (sdf_out) {
     float* o = sdf_out + idx;
     const int64_t st = sdf_stride;
@@ -287,14 +305,13 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
   float g1 = tanh_(dot(nuB, nbar) * it);
   float g2 = tanh_(-dot(nuA, nbar) * it);
   float pen1 = sigmoid(-B_e1.phi * it);
-  float pen2 = sigmoid(-A_e2.phi * it);
   float cl = sigmoid(-dot(nuA, nuB) * it);
   float nn1 = ex2((rowL - w.dbar) * ps.k2);
   float nn2 = ex2((colL - w.dbar) * ps.k2);
   float base = w.con * cl;
   float w1 = base * pen1 * nn1, w2 = base * pen2 * nn2;
   if (ps.preselect) {  // safeguard: each witness inside its own body
-    w1 *= sigmoid(-A_e1.phi * it);
+    w1 *= safe1;
     w2 *= sigmoid(-B_e2.phi * it);
   }
   float d1 = g1 * w.dbar, d2 = g2 * w.dbar;
