@@ -86,8 +86,21 @@ def _norm(v):
     return torch.where(pos, r, torch.zeros_like(r))
 
 
+def trace_to_surface(x, sdf, iters):
+    """Sphere tracing of points x (..., 3) onto the zero set of ``sdf`` (Supplement,
+    mesh-SDF discrepancies): the direction is fixed at the start point, u = grad phi(x_0)
+    / |grad phi(x_0)|, and each of ``iters`` steps moves x <- x - phi(x) u."""
+    phi, nu = sdf(x)
+    u = nu / torch.linalg.vector_norm(nu, dim=-1, keepdim=True)
+    for i in range(iters):
+        if i:
+            phi, _ = sdf(x)
+        x = x - phi[..., None] * u
+    return x
+
+
 def ee_candidates(a0, a1, b0, b1, sdfA, sdfB, tau, w_reg=0.01, eps_clip=0.1, eps_min=0.1,
-                  eps_comp=0.1):
+                  eps_comp=0.1, trace_iters=0):
     """All E-E contact candidates of one body pair (Sec. IV-D3).
 
     a0, a1: (E_A, 3) world endpoints of A's edges; b0, b1: (E_B, 3) of B's.
@@ -102,9 +115,20 @@ def ee_candidates(a0, a1, b0, b1, sdfA, sdfB, tau, w_reg=0.01, eps_clip=0.1, eps
     makes both penetrating witnesses negative and the whole manifold symmetric
     under swapping A and B.)  eps in nbar = Delta / sqrt(|Delta|^2 + eps) is tau^2.
     Soft-sign and nearest-neighbour softmax use temperature tau.
+
+    trace_iters > 0 projects each witness onto its own body's SDF surface first
+    (trace_to_surface, e1* on A and e2* on B) and the signed distances, normals,
+    penetration and clash indicators and the output points use the projected
+    witnesses.  The nearest-neighbour indicators stay on the QP witnesses' own
+    distances (reading: the supplement moves the points used for signed
+    distances and normals; the nn softmax ranks edge pairs).
     """
     e1, e2, al1, al2, con = ee_witness(a0[:, None, :], a1[:, None, :], b0[None, :, :],
                                        b1[None, :, :], w_reg, eps_clip, eps_min, eps_comp)
+    dbar_qp = _norm(e1 - e2)
+    if trace_iters:
+        e1 = trace_to_surface(e1, sdfA, trace_iters)
+        e2 = trace_to_surface(e2, sdfB, trace_iters)
     delta = e1 - e2
     dbar = _norm(delta)
     nbar1 = delta / torch.sqrt((delta * delta).sum(-1, keepdim=True) + tau * tau)
@@ -118,8 +142,8 @@ def ee_candidates(a0, a1, b0, b1, sdfA, sdfB, tau, w_reg=0.01, eps_clip=0.1, eps
     pen1 = sigmoid(-phiB_e1 / tau)
     pen2 = sigmoid(-phiA_e2 / tau)
     cl = sigmoid(-(nuA_e1 * nuB_e2).sum(-1) / tau)
-    nn1 = torch.softmax(-dbar / tau, dim=1)    # row-wise over B's edges
-    nn2 = torch.softmax(-dbar / tau, dim=0)    # column-wise over A's edges
+    nn1 = torch.softmax(-dbar_qp / tau, dim=1)    # row-wise over B's edges
+    nn2 = torch.softmax(-dbar_qp / tau, dim=0)    # column-wise over A's edges
     w1 = con * pen1 * nn1 * cl
     w2 = con * pen2 * nn2 * cl
     return dict(p1=e1, d1=g1 * dbar, n1=g1[..., None] * nbar1, w1=w1,

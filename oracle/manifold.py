@@ -38,6 +38,7 @@ class Params:
     eps_comp: float = 0.1
     no_ee: bool = False        # V-S contacts only
     one_sided: bool = False    # only A's vertices against B's SDF (implies no_ee)
+    trace_iters: int = 0       # sphere-tracing steps for E-E witnesses (0 = off)
 
 
 def _t(x):
@@ -77,7 +78,7 @@ def pair_candidates(geomA, geomB, pose, dims, tau, params=Params()):
         a0, a1 = A.verts[A.edges[:, 0]], A.verts[A.edges[:, 1]]
         b0, b1 = B.verts[B.edges[:, 0]], B.verts[B.edges[:, 1]]
         c = ee_candidates(a0, a1, b0, b1, A.sdf, B.sdf, tau, params.w_reg, params.eps_clip,
-                          params.eps_min, params.eps_comp)
+                          params.eps_min, params.eps_comp, params.trace_iters)
         for j in (1, 2):
             p, d, n, w = c[f"p{j}"], c[f"d{j}"], c[f"n{j}"], c[f"w{j}"]
             rows.append(torch.cat([p.reshape(-1, 3), d.reshape(-1, 1), n.reshape(-1, 3),

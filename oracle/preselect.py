@@ -57,7 +57,7 @@ def pair_candidates_preselect(geomA, geomB, pose, dims, tau, params, top_verts=0
         ends.append((e0, e1))
     (a0, a1), (b0, b1) = ends
     c = ee_candidates(a0, a1, b0, b1, A.sdf, B.sdf, tau, params.w_reg, params.eps_clip, params.eps_min,
-                      params.eps_comp)
+                      params.eps_comp, params.trace_iters)
     w1, w2 = c["w1"], c["w2"]
     if safeguard:
         phiA_e1, _ = A.sdf(c["p1"])

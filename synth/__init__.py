@@ -8,12 +8,14 @@ independently, in ``oracle/`` (FP64 CPU) and in the CUDA library.
 """
 
 from .geometry import (  # noqa: F401
-    KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID, KIND_HULL, KIND_NAMES,
+    KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID, KIND_HULL, KIND_SQ_UNION, KIND_NAMES,
     Geometry, box_template, cylinder_template, capsule_template,
     icosphere_template, hull_from_points, primitive_geometry, support,
+    superellipsoid_surface, sq_union_geometry,
 )
 from .workloads import (  # noqa: F401
     Workload, random_quaternions, config_box_box, config_hull_vs_primitive,
     config_box_vs_sphere_hull, config_mixed, config_mixed_pooled, serving_trace, make_config,
+    SQ_RESOLUTIONS, random_sq_union, config_sq_union,
     SEED_BASE,
 )

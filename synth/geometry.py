@@ -8,7 +8,11 @@ library / oracle map it to a surface point from the primitive's dimensions
 (box and ellipsoid scale each axis, cylinder and capsule scale the radius and
 half-length).  For a convex hull the rows are the vertices themselves
 (``s = 0``) and the SDF parameters are the outward face planes
-``(n_x, n_y, n_z, o)``, with plane value ``n . y - o``.
+``(n_x, n_y, n_z, o)``, with plane value ``n . y - o``.  A union of
+superquadrics (Sec. IV-B, smooth union of SQ primitives) also carries its
+vertices directly; its ``planes`` hold three rows per primitive:
+``(q_w, q_x, q_y, q_z)`` (orientation in the body frame), ``(t_x, t_y, t_z,
+eps1)`` and ``(a, b, c, eps2)`` (axis lengths and the two exponents).
 """
 from __future__ import annotations
 
@@ -16,8 +20,9 @@ import dataclasses
 import numpy as np
 
 KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID, KIND_HULL = 0, 1, 2, 3, 4
+KIND_SQ_UNION = 5
 KIND_NAMES = {KIND_BOX: "box", KIND_CAPSULE: "capsule", KIND_CYLINDER: "cylinder",
-              KIND_ELLIPSOID: "ellipsoid", KIND_HULL: "hull"}
+              KIND_ELLIPSOID: "ellipsoid", KIND_HULL: "hull", KIND_SQ_UNION: "sq_union"}
 
 
 @dataclasses.dataclass
@@ -198,7 +203,7 @@ def support(geom: Geometry, dims, u):
     d = np.asarray(dims, dtype=np.float64)
     if geom.kind == KIND_BOX:
         return np.abs(u) @ d
-    if geom.kind == KIND_HULL:
+    if geom.kind in (KIND_HULL, KIND_SQ_UNION):
         return (u @ geom.verts[:, :3].astype(np.float64).T).max(-1)
     if geom.kind == KIND_CAPSULE:
         return d[1] * np.abs(u[..., 2]) + d[0] * np.linalg.norm(u, axis=-1)
@@ -207,3 +212,73 @@ def support(geom: Geometry, dims, u):
     if geom.kind == KIND_ELLIPSOID:
         return np.linalg.norm(u * d, axis=-1)
     raise ValueError(geom.kind)
+
+
+def superellipsoid_surface(rings, segs, scale, eps1, eps2):
+    """Mesh of one superquadric's surface in its own frame: ``rings`` latitude rings of
+    ``segs`` points plus the two poles, from the standard superellipsoid parametrisation
+    (x, y, z) = (a C(eta)^eps1 C(w)^eps2, b C(eta)^eps1 S(w)^eps2, c S(eta)^eps1) with
+    C(t)^e = sign(cos t)|cos t|^e and S(t)^e = sign(sin t)|sin t|^e.  Every vertex lies on
+    the surface.  Returns (points (V, 3) float64, edges (E, 2)): ring, meridian and pole
+    edges."""
+    def pw(c, e):
+        return np.sign(c) * np.abs(c) ** e
+    a, b, c = scale
+    eta = -np.pi / 2 + np.pi * np.arange(1, rings + 1) / (rings + 1)
+    om = 2 * np.pi * np.arange(segs) / segs
+    E, W = np.meshgrid(eta, om, indexing="ij")
+    pts = np.stack([a * pw(np.cos(E), eps1) * pw(np.cos(W), eps2),
+                    b * pw(np.cos(E), eps1) * pw(np.sin(W), eps2),
+                    c * pw(np.sin(E), eps1) * np.ones_like(W)], -1).reshape(-1, 3)
+    pts = np.concatenate([pts, [[0.0, 0.0, -c], [0.0, 0.0, c]]])
+    south, north = rings * segs, rings * segs + 1
+    edges = []
+    for i in range(rings):
+        for j in range(segs):
+            edges.append((i * segs + j, i * segs + (j + 1) % segs))
+            if i + 1 < rings:
+                edges.append((i * segs + j, (i + 1) * segs + j))
+    for j in range(segs):
+        edges.append((south, j))
+        edges.append(((rings - 1) * segs + j, north))
+    return pts, np.array(edges, dtype=np.int32)
+
+
+def _quat_matrix(q):
+    w, x, y, z = np.asarray(q, np.float64) / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def sq_union_geometry(prims, rings=2, segs=6):
+    """A body made of superquadrics: ``prims`` is a list of (q (4,), t (3,), scale (3,),
+    eps1, eps2).  The mesh is the union of the primitives' surface meshes with every
+    vertex removed that lies inside the convex hull of another primitive's mesh (and the
+    edges at such vertices), so that the remaining vertices sit on the body's surface."""
+    from scipy.spatial import Delaunay
+    pts, edges, owner = [], [], []
+    for i, (q, t, sc, e1, e2) in enumerate(prims):
+        p, e = superellipsoid_surface(rings, segs, sc, e1, e2)
+        p = p @ _quat_matrix(q).T + np.asarray(t, np.float64)
+        edges.append(e + sum(len(x) for x in pts))
+        pts.append(p)
+        owner.append(np.full(len(p), i))
+    P, Ed, own = np.concatenate(pts), np.concatenate(edges), np.concatenate(owner)
+    keep = np.ones(len(P), bool)
+    for i in range(len(prims)):
+        tri = Delaunay(pts[i])
+        inside = tri.find_simplex(P) >= 0
+        keep &= ~(inside & (own != i))
+    remap = -np.ones(len(P), np.int64)
+    remap[keep] = np.arange(keep.sum())
+    Ed = remap[Ed]
+    Ed = Ed[(Ed >= 0).all(1)].astype(np.int32)
+    verts = np.zeros((int(keep.sum()), 4), np.float32)
+    verts[:, :3] = P[keep]
+    planes = np.zeros((3 * len(prims), 4), np.float32)
+    for i, (q, t, sc, e1, e2) in enumerate(prims):
+        planes[3 * i] = np.asarray(q, np.float64) / np.linalg.norm(q)
+        planes[3 * i + 1] = [t[0], t[1], t[2], e1]
+        planes[3 * i + 2] = [sc[0], sc[1], sc[2], e2]
+    return Geometry(KIND_SQ_UNION, np.ones(3, dtype=np.float32), verts, Ed, planes)

@@ -16,7 +16,7 @@ import dataclasses
 import numpy as np
 
 from .geometry import (KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID,
-                       Geometry, hull_from_points, primitive_geometry, support)
+                       Geometry, hull_from_points, primitive_geometry, support, sq_union_geometry)
 
 SEED_BASE = 20261203
 PRIMITIVE_KINDS = (KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID)
@@ -181,6 +181,44 @@ def config_mixed_pooled(n=65536, pool=4096, seed=SEED_BASE + 4):
     poses = _place(rng, geoms, pg, dims, delta)
     tau = np.asarray((1e-3, 1e-2, 1e-1), dtype=np.float32)[rng.integers(0, 3, n)]
     return Workload("mixed-uneven-pooled", geoms, pg, poses, dims, tau)
+
+
+SQ_RESOLUTIONS = ((4, 10), (3, 8), (2, 8), (2, 6), (1, 6), (1, 4))
+
+
+def random_sq_union(rng, n_prims, step=0.22, scale=(0.12, 0.28), eps=(0.3, 1.5), max_verts=256,
+                    max_edges=768):
+    """A blob of ``n_prims`` superquadrics: each centre is a step of length ``step`` from
+    an earlier primitive's centre (a random tree, like limbs on a body), axis lengths and
+    both exponents uniform, orientations uniform; centred on the mean of the centres.
+    The mesh resolution is the finest that stays within the per-geometry limits."""
+    c = np.zeros((n_prims, 3))
+    for i in range(1, n_prims):
+        c[i] = c[rng.integers(0, i)] + step * _unit_vectors(rng, 1)[0]
+    c -= c.mean(0)
+    q = random_quaternions(rng, n_prims)
+    sc = rng.uniform(scale[0], scale[1], size=(n_prims, 3))
+    e = rng.uniform(eps[0], eps[1], size=(n_prims, 2))
+    prims = [(q[i], c[i], sc[i], float(e[i, 0]), float(e[i, 1])) for i in range(n_prims)]
+    # the finest per-primitive mesh whose pruned union fits 256 vertices and 768 edges
+    for rings, segs in SQ_RESOLUTIONS:
+        g = sq_union_geometry(prims, rings, segs)
+        if g.n_verts <= max_verts and g.n_edges <= max_edges:
+            return g
+    raise ValueError("too many primitives for the mesh limits")
+
+
+def config_sq_union(n=1024, n_prims=18, pool=8, seed=SEED_BASE + 6, tau=1e-2):
+    """Pairs of multi-superquadric bodies (the paper's armadillo setting, Sec. V, with
+    synthetic primitive sets): a pool of bodies of ``n_prims`` primitives each, pairs
+    drawn from it at seeded poses with projected overlap U[0, 0.1]."""
+    rng = np.random.default_rng(seed)
+    geoms = [random_sq_union(rng, n_prims) for _ in range(pool)]
+    pg = rng.integers(0, pool, size=(n, 2)).astype(np.int32)
+    dims = np.ones((n, 6), dtype=np.float32)
+    delta = rng.uniform(0.0, 0.1, n)
+    poses = _place(rng, geoms, pg, dims, delta)
+    return Workload(f"sq-union{n_prims}", geoms, pg, poses, dims, np.full(n, tau, np.float32))
 
 
 def serving_trace(seed=SEED_BASE + 5, rate=2000.0, duration=10.0, max_pairs=8192):
