@@ -42,6 +42,9 @@ extern "C" {
 #define CM_MAX_VERTS 256   /* mesh vertices per geometry */
 #define CM_MAX_EDGES 768   /* mesh edges per geometry */
 #define CM_MAX_PLANES 512  /* convex-polyhedron planes per geometry */
+#define CM_MAX_PRIMS 32    /* superquadrics per SQ_UNION geometry */
+#define CM_MAX_SELECT 32   /* soft pre-selected vertices / edges per body */
+#define CM_MAX_TRACE 8     /* sphere-tracing steps per witness */
 
 typedef enum {
   CM_OK = 0,
@@ -58,9 +61,13 @@ typedef enum {
  * (LSE over planes, Sec. IV-B2); ELLIPSOID is the superquadric with
  * eps1 = eps2 = 1 (Sec. IV-B1); CAPSULE and CYLINDER are smooth readings of the
  * usual primitives (soft-clipped segment distance; LSE of radial and cap
- * distances).  dims: BOX (hx, hy, hz); CAPSULE (r, h, -); CYLINDER (r, h, -);
- * ELLIPSOID (a, b, c); HULL unused. */
-enum { CM_BOX = 0, CM_CAPSULE = 1, CM_CYLINDER = 2, CM_ELLIPSOID = 3, CM_HULL = 4 };
+ * distances).  SQ_UNION is a body made of up to CM_MAX_PRIMS general
+ * superquadrics joined by the smooth union phi = -LSE_tau(-phi_1, ..., -phi_L)
+ * (Sec. IV-B; each phi_l the superquadric SDF of Sec. IV-B1 with exponents
+ * eps1, eps2 in [0.1, 1.9]); its normal blends the primitives' grad f with the
+ * union's weights softmax(-phi_l / tau).  dims: BOX (hx, hy, hz); CAPSULE
+ * (r, h, -); CYLINDER (r, h, -); ELLIPSOID (a, b, c); HULL and SQ_UNION unused. */
+enum { CM_BOX = 0, CM_CAPSULE = 1, CM_CYLINDER = 2, CM_ELLIPSOID = 3, CM_HULL = 4, CM_SQ_UNION = 5 };
 
 /* Flags of cm_params.flags: the simplifications of Supplement A. */
 enum {
@@ -74,10 +81,15 @@ typedef struct cm_context cm_context;
  * verts: host, n_verts x 4 floats.  For the analytic primitives each row is a
  *   unit template (u_x, u_y, u_z, s) that maps to a local vertex from the dims
  *   in use: BOX/ELLIPSOID (d0 u_x, d1 u_y, d2 u_z); CYLINDER (r u_x, r u_y, h u_z);
- *   CAPSULE (r u_x, r u_y, r u_z + s h).  For HULL the rows are the vertices.
+ *   CAPSULE (r u_x, r u_y, r u_z + s h).  For HULL and SQ_UNION the rows are
+ *   the vertices.
  * edges: host, n_edges x 2 int32 vertex indices.
- * planes: host, HULL only, n_planes x 4 floats (n_x, n_y, n_z, o) with unit
- *   outward n; the plane value at y is n . y - o.  NULL / 0 for other kinds.
+ * planes: host.  HULL: n_planes x 4 floats (n_x, n_y, n_z, o) with unit
+ *   outward n; the plane value at y is n . y - o.  SQ_UNION: three rows per
+ *   superquadric (n_planes = 3 L, 1 <= L <= CM_MAX_PRIMS): (q_w, q_x, q_y, q_z)
+ *   its orientation in the body frame (normalised by the library), (t_x, t_y,
+ *   t_z, eps1) its centre and first exponent, (a, b, c, eps2) its semi-axes and
+ *   second exponent.  NULL / 0 for the other kinds.
  * The library copies everything; the caller may free its arrays on return. */
 typedef struct {
   int32_t kind;
@@ -110,12 +122,21 @@ typedef struct {
    * generate contacts, each a SoftSort average (temperature tau) of the
    * vertices / edge endpoints; E-E witnesses are then also weighted by the soft
    * indicator of lying inside their own body.  0 keeps all (no selection).
-   * At most 16 each; forward only (the adjoint rejects them). */
+   * At most CM_MAX_SELECT each; forward only (the adjoint rejects them). */
   int32_t top_verts;
   int32_t top_edges;
+  /* Sphere tracing of E-E witness points (Supplement, mesh-SDF
+   * discrepancies): each witness is moved trace_iters steps x <- x - phi(x) u
+   * along the fixed direction u = grad phi / |grad phi| of its own body's SDF at
+   * the QP witness; signed distances, normals, penetration and clashing
+   * indicators and the output points then use the moved witnesses, while the
+   * nearest-neighbour indicators keep the QP witnesses' distances.
+   * 0 (default) .. CM_MAX_TRACE; forward only (the adjoint rejects it). */
+  int32_t trace_iters;
 } cm_params;
 
-/* Fills the defaults: tau 1e-2, w_reg 1e-2, eps_* 0.1, K 8, flags 0, no pre-selection. */
+/* Fills the defaults: tau 1e-2, w_reg 1e-2, eps_* 0.1, K 8, flags 0, no
+ * pre-selection, no sphere tracing. */
 void cm_default_params(cm_params* p);
 
 /* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the device
@@ -164,7 +185,9 @@ cm_status cm_contact_manifold_fwd(cm_context* ctx, int32_t n_pairs, const int32_
  * grad_dims: device, n_pairs x 6 or NULL, receives dL/d dims of A then B (the
  *   dims in use; zero for hulls).
  * The forward is recomputed per pair inside the call; nothing is kept between
- * the forward and backward calls. */
+ * the forward and backward calls.  Not built for SQ_UNION geometry: returns
+ * CM_ERR_INVALID_ARG when the context holds any (as for pre-selection and
+ * sphere tracing in params). */
 cm_status cm_contact_manifold_bwd(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms,
                                   const float* poses, const float* dims, const float* tau,
                                   const cm_params* params, const float* grad_out, float* grad_poses,

@@ -23,7 +23,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 CM_OK, CM_ERR_INVALID_ARG, CM_ERR_OOM, CM_ERR_CUDA = 0, 1, 2, 3
 CM_ERR_ADMISSION, CM_ERR_TIMEOUT, CM_ERR_NOT_FOUND, CM_ERR_DEVICE = 4, 5, 6, 7
-CM_BOX, CM_CAPSULE, CM_CYLINDER, CM_ELLIPSOID, CM_HULL = 0, 1, 2, 3, 4
+CM_BOX, CM_CAPSULE, CM_CYLINDER, CM_ELLIPSOID, CM_HULL, CM_SQ_UNION = 0, 1, 2, 3, 4, 5
 CM_FLAG_NO_EE, CM_FLAG_ONE_SIDED = 1, 2
 CM_MAX_K = 16
 
@@ -38,7 +38,8 @@ class cm_geometry_desc(ctypes.Structure):
 class cm_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("w_reg", ctypes.c_float), ("eps_clip", ctypes.c_float),
                 ("eps_min", ctypes.c_float), ("eps_comp", ctypes.c_float), ("K", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("top_verts", ctypes.c_int32), ("top_edges", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("top_verts", ctypes.c_int32), ("top_edges", ctypes.c_int32),
+                ("trace_iters", ctypes.c_int32)]
 
 
 class cm_request_desc(ctypes.Structure):

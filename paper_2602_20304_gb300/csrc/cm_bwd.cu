@@ -411,13 +411,17 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
 // Builds of the adjoint kernel: one CTA per SM with up to 255 registers, or two
 // CTAs per SM within 128 registers (the launch shape's CTAs per SM picks: 1 ->
 // the first); each for K <= 8 and K <= 16 (the SoftSort reverse unrolls to it).
+// Dynamic shared memory the two builds are configured for: the two-CTA build
+// takes layouts up to kBwdSmem2, larger ones run the one-CTA build.
+constexpr int kBwdSmem1 = 180 * 1024, kBwdSmem2 = 110 * 1024;
+
 template <int MB, int KM>
 static cudaError_t launch_bwd_t(const FwdArgs& a, const float* g, float* gp, float* gd, int grid, int block,
                                 cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(cm_bwd_kernel<MB, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         MB == 1 ? 180 * 1024 : 110 * 1024);
+                                         MB == 1 ? kBwdSmem1 : kBwdSmem2);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -428,7 +432,7 @@ static cudaError_t launch_bwd_t(const FwdArgs& a, const float* g, float* gp, flo
 cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,
                        int block, int per_sm, cudaStream_t s) {
   const bool k8 = a.p.K <= 8;
-  if (per_sm == 1)
+  if (per_sm == 1 || a.sm.total > kBwdSmem2)
     return k8 ? launch_bwd_t<1, 8>(a, grad_out, grad_poses, grad_dims, grid, block, s)
               : launch_bwd_t<1, 16>(a, grad_out, grad_poses, grad_dims, grid, block, s);
   return k8 ? launch_bwd_t<2, 8>(a, grad_out, grad_poses, grad_dims, grid, block, s)
@@ -437,7 +441,7 @@ cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_pose
 
 int bwd_max_blocks_per_sm(int block, int smem_bytes, int per_sm) {
   int n = 0;
-  cudaError_t e = per_sm == 1
+  cudaError_t e = (per_sm == 1 || smem_bytes > kBwdSmem2)
                       ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel<1, 16>, block, smem_bytes)
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel<2, 16>, block, smem_bytes);
   if (e != cudaSuccess) return 1;

@@ -29,6 +29,7 @@ struct cm_context {
   std::vector<float4> planes;
   int max_v = 0, max_e = 0, max_p = 0, min_v = 1 << 30, min_e = 1 << 30;
   bool dirty = false;
+  bool has_sq_union = false;  // an SQ_UNION geometry is registered (no adjoint for it)
   // device copy
   cm::GeomHeader* d_hdr = nullptr;
   float4* d_verts = nullptr;
@@ -57,6 +58,7 @@ cm_status cuda_fail(cudaError_t e, const char* what);
 cm_status sync_geometry_locked(cm_context* c);
 cm_status check_params(const cm_params* p);
 cm_status check_k(const cm_context* c, const cm_params* params);
+cm_status adjoint_supported(const cm_context* c, const cm_params* p);
 LaunchCfg pick_cfg(const cm_context* c, int bwd, int n_pairs, int flags);
 void shape(const cm_context* c, int bwd, const LaunchCfg& cfg, int n_pairs, SmemLayout& L, int& grid);
 size_t scratch_need(const cm_context* c, int bwd, int grid, int64_t stride);  // stride <= 0: max_e^2

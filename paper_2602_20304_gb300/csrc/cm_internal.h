@@ -58,9 +58,11 @@ struct LaunchCfg {
 };
 
 constexpr int kMaxK = 16;
+constexpr int kMaxSel = 32;  // soft pre-selected items per body (CM_MAX_SELECT)
+constexpr int kSqRows = 5;   // device float4 rows per superquadric of an SQ_UNION
 // Pre-selection staging: vertex depths of both bodies (2 max_v) + the soft
-// selections: per body 16 vertices (B frame 3 + A frame 3) and 16 edges (12).
-constexpr int kSelFloats = 2 * kMaxK * 6 + 2 * kMaxK * 12 + 2 * kMaxK * 6;
+// selections: per body kMaxSel vertices (B frame 3 + A frame 3) and kMaxSel edges (12).
+constexpr int kSelFloats = 2 * kMaxSel * 6 + 2 * kMaxSel * 12 + 2 * kMaxSel * 6;
 constexpr int kWarpStateFloats = kMaxK * 9 + 10 + kMaxK;  // list, C, threshold, ids
 
 cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s);

@@ -141,10 +141,11 @@ struct Params {
   float tau, w_reg, eps_clip, eps_min, eps_comp;
   int K, flags;
   int top_verts, top_edges;  // soft pre-selection counts (0: all)
+  int trace_iters;           // sphere-tracing steps of E-E witnesses (0: off)
 };
 
 // ---------------------------------------------------------------- geometry kinds
-enum Kind : int { kBox = 0, kCapsule = 1, kCylinder = 2, kEllipsoid = 3, kHull = 4 };
+enum Kind : int { kBox = 0, kCapsule = 1, kCylinder = 2, kEllipsoid = 3, kHull = 4, kSqUnion = 5 };
 
 // Local vertex of a template row u = (u_x, u_y, u_z, s) for the given dims.
 CM_HD V3 map_vertex(int kind, float ux, float uy, float uz, float s, V3 d) {
@@ -359,6 +360,62 @@ CM_HD Sdf sdf_cylinder(V3 y, float rad, float h, float tau, float inv_tau) {
   return o;
 }
 
+// log2(2^a + 2^b) without forming either power.
+CM_HD float log2_add(float a, float b) { return fmaxf(a, b) + lg2(1.f + ex2(-fabsf(a - b))); }
+
+// Smooth union of superquadrics (Sec. IV-B, IV-B1).  Five rows per primitive:
+// (M row 0, c_0), (M row 1, c_1), (M row 2, c_2) with x = M y + c its own-frame
+// point (M = R^T, c = -R^T t), (1/a, 1/b, 1/c, p1 = 2/eps1) and (p2 = 2/eps2,
+// r = eps2/eps1, h = eps1/2, -).  Per primitive, with x~ = x / (a, b, c):
+//   s = |x~_x|^p2 + |x~_y|^p2, f = s^r + |x~_z|^p1, phi_l = (1 - f^-h) |x|,
+//   d f / d x~_x = r p2 s^(r-1) |x~_x|^(p2-1) sgn x~_x  (likewise y),
+//   d f / d x~_z = p1 |x~_z|^(p1-1) sgn x~_z.
+// Everything is carried as base-2 logarithms (sums of powers by log2_add), so
+// the large powers of a boxy primitive (2/eps up to 20) neither overflow nor
+// underflow on the way; magnitudes are clamped away from 0 so that a point on
+// a primitive's axis or centre stays finite.  The union
+// phi = -tau ln sum_l exp(-phi_l / tau) is accumulated in one pass with a
+// running minimum m; its normal gradient sum_l pi_l R_l grad_x f_l
+// (pi = softmax(-phi / tau)) takes each weight into the exponent of the
+// gradient components, so a negligible weight times a huge gradient is 0.
+CM_HD Sdf sdf_sq_union(V3 y, const float4* P, int L, float tau, float inv_tau) {
+  const float k = inv_tau * kLog2e;
+  float m = 3.0e38f, S = 0.f;
+  V3 G = v3(0.f, 0.f, 0.f);
+  for (int l = 0; l < L; ++l) {
+    const float4 r0 = P[5 * l], r1 = P[5 * l + 1], r2 = P[5 * l + 2], r3 = P[5 * l + 3], r4 = P[5 * l + 4];
+    const V3 x = v3(fmaf(r0.x, y.x, fmaf(r0.y, y.y, fmaf(r0.z, y.z, r0.w))),
+                    fmaf(r1.x, y.x, fmaf(r1.y, y.y, fmaf(r1.z, y.z, r1.w))),
+                    fmaf(r2.x, y.x, fmaf(r2.y, y.y, fmaf(r2.z, y.z, r2.w))));
+    const float xx = x.x * r3.x, xy = x.y * r3.y, xz = x.z * r3.z;
+    const float p1 = r3.w, p2 = r4.x, rr = r4.y, h = r4.z;
+    const float lx = lg2(fmaxf(fabsf(xx), 1e-20f)), ly = lg2(fmaxf(fabsf(xy), 1e-20f)),
+                lz = lg2(fmaxf(fabsf(xz), 1e-20f));
+    const float ls = log2_add(p2 * lx, p2 * ly);          // log2 s
+    const float lf = log2_add(rr * ls, p1 * lz);          // log2 f
+    const float phi = (1.f - ex2(-h * lf)) * sqrt_(dot(x, x));
+    if (phi < m) {  // new running minimum: rescale what was summed relative to the old one
+      const float sc = ex2((phi - m) * k);
+      S *= sc;
+      G = G * sc;
+      m = phi;
+    }
+    const float le = (m - phi) * k;                        // log2 of the union weight
+    S += ex2(le);
+    const float ex = le + (rr - 1.f) * ls;
+    const float gx = copysignf(rr * p2 * r3.x * ex2(ex + (p2 - 1.f) * lx), xx);
+    const float gy = copysignf(rr * p2 * r3.y * ex2(ex + (p2 - 1.f) * ly), xy);
+    const float gz = copysignf(p1 * r3.z * ex2(le + (p1 - 1.f) * lz), xz);
+    G.x += fmaf(gx, r0.x, fmaf(gy, r1.x, gz * r2.x));
+    G.y += fmaf(gx, r0.y, fmaf(gy, r1.y, gz * r2.y));
+    G.z += fmaf(gx, r0.z, fmaf(gy, r1.z, gz * r2.z));
+  }
+  Sdf o;
+  o.phi = m - tau * kLn2 * lg2(S);
+  o.g = G * rcp(S);
+  return o;
+}
+
 // Regularised normal g / sqrt(tau + |g|^2) (Sec. IV-B).
 CM_HD V3 normal_of(V3 g, float tau) { return g * rsq(tau + dot(g, g)); }
 
@@ -377,6 +434,7 @@ CM_HD Sdf body_sdf(const Body& b, V3 y, float tau, float inv_tau) {
     case kEllipsoid: return sdf_ellipsoid(y, b.dims);
     case kCapsule: return sdf_capsule(y, b.dims.x, b.dims.y, tau, inv_tau);
     case kCylinder: return sdf_cylinder(y, b.dims.x, b.dims.y, tau, inv_tau);
+    case kSqUnion: return sdf_sq_union(y, b.planes, b.n_planes / 5, tau, inv_tau);
     default: return sdf_planes(y, b.planes, b.n_planes, tau, inv_tau);
   }
 }

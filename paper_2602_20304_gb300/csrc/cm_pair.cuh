@@ -22,6 +22,7 @@ struct PairShared {
   float tau, inv_tau, k2;
   int bad;  // invalid geometry id
   int preselect;  // soft pre-selection active for this pair
+  int trace;      // sphere-tracing steps of E-E witnesses
 };
 
 struct PairSmem {
@@ -92,6 +93,7 @@ __device__ inline void pair_setup(const FwdArgs& a, int pi, PairShared& ps) {
   ps.neA = A.n_edges; ps.neB = B.n_edges;
   ps.npA = A.n_planes; ps.npB = B.n_planes;
   ps.preselect = (a.p.top_verts > 0 || a.p.top_edges > 0) ? 1 : 0;
+  ps.trace = a.p.trace_iters;
   ps.tau = a.tau ? a.tau[pi] : a.p.tau;
   ps.inv_tau = 1.0f / ps.tau;
   ps.k2 = ps.inv_tau * kLog2e;
@@ -138,15 +140,16 @@ __device__ inline void pair_stage(const FwdArgs& a, int pi, const PairShared& ps
     sm.eB6[i] = l0.x; sm.eB6[es + i] = l0.y; sm.eB6[2 * es + i] = l0.z;
     sm.eB6[3 * es + i] = l1.x; sm.eB6[4 * es + i] = l1.y; sm.eB6[5 * es + i] = l1.z;
   }
-  // hull planes pre-scaled by k = log2(e) / tau (see sdf_planes)
-  const float k = ps.k2;
+  // hull planes pre-scaled by k = log2(e) / tau (see sdf_planes); superquadric
+  // rows as packed
+  const float kA = ps.kindA == kHull ? ps.k2 : 1.f, kB = ps.kindB == kHull ? ps.k2 : 1.f;
   for (int i = threadIdx.x; i < ps.npA; i += blockDim.x) {
     const float4 q = a.planes[A.p_off + i];
-    sm.pA[i] = make_float4(q.x * k, q.y * k, q.z * k, q.w * k);
+    sm.pA[i] = make_float4(q.x * kA, q.y * kA, q.z * kA, q.w * kA);
   }
   for (int i = threadIdx.x; i < ps.npB; i += blockDim.x) {
     const float4 q = a.planes[B.p_off + i];
-    sm.pB[i] = make_float4(q.x * k, q.y * k, q.z * k, q.w * k);
+    sm.pB[i] = make_float4(q.x * kB, q.y * kB, q.z * kB, q.w * kB);
   }
 }
 
@@ -260,25 +263,47 @@ __device__ __forceinline__ Witness ee_witness(const EdgePair& e, const Params& p
 // sdf_out (optional): the four SDF evaluations of the element, kept for the
 // adjoint as 10 arrays of stride sdf_stride at index idx: phi_B(e1*), phi_B(e2*),
 // grad_B(e2*) (3), phi_A(e2*), phi_A(e1*), grad_A(e1*) in A's frame (3).
+// Sphere tracing of a witness onto its own body's SDF surface (Supplement,
+// mesh-SDF discrepancies): `iters` steps x <- x - phi(x) u along the fixed
+// direction u = grad phi(x_0) / |grad phi(x_0)|, in the body's own frame.
+__device__ __forceinline__ V3 trace_to_surface(const Body& b, V3 x, int iters, float tau, float it) {
+  Sdf s = body_sdf(b, x, tau, it);
+  const V3 u = s.g * rsq(dot(s.g, s.g));
+  for (int i = 0; i < iters; ++i) {
+    if (i) s = body_sdf(b, x, tau, it);
+    x = fma3(-s.phi, u, x);
+  }
+  return x;
+}
+
 __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSmem& sm,
                                               const PairBodies& bb, const EdgePair& ep,
                                               const Witness& w, float rowL, float colL,
                                               float (&y1)[8], float (&y2)[8], float& s1, float& s2,
                                               float* sdf_out = nullptr, int64_t sdf_stride = 0, int idx = 0) {
   const float tau = ps.tau, it = ps.inv_tau;
-  V3 nbar = w.delta * rsq(dot(w.delta, w.delta) + tau * tau);
   const int es = sm.es, k = ep.k;
   const V3 la0 = v3(sm.eAl6[k], sm.eAl6[es + k], sm.eAl6[2 * es + k]);
   const V3 la1 = v3(sm.eAl6[3 * es + k], sm.eAl6[4 * es + k], sm.eAl6[5 * es + k]);
-  const V3 e1l = fma3(w.qp.a1, la1 - la0, la0);
+  V3 e1l = fma3(w.qp.a1, la1 - la0, la0);
+  V3 e1 = w.e1, e2 = w.e2, delta = w.delta;
+  float dbar = w.dbar;
+  if (ps.trace) {  // witnesses onto their own body's SDF surface (e1* on A, e2* on B)
+    e1l = trace_to_surface(bb.A, e1l, ps.trace, tau, it);
+    e2 = trace_to_surface(bb.B, e2, ps.trace, tau, it);
+    e1 = mul(ps.Rrel, e1l) + ps.trel;
+    delta = e1 - e2;
+    dbar = sqrt_(dot(delta, delta));
+  }
+  V3 nbar = delta * rsq(dot(delta, delta) + tau * tau);
   Sdf B_e1, B_e2, A_e2, A_e1;
-  body_sdf2(bb.B, w.e1, w.e2, tau, it, B_e1, B_e2);     // phi_B(e1*), nu_B(e2*)
-  const V3 x2 = mulT(ps.Rrel, w.e2 - ps.trel);
+  body_sdf2(bb.B, e1, e2, tau, it, B_e1, B_e2);         // phi_B(e1*), nu_B(e2*)
+  const V3 x2 = mulT(ps.Rrel, e2 - ps.trel);
   // A hull's sums without a shift (sdf_planes_ee) when only the forward's
   // quantities are wanted and e1* is within a scaled distance of 60 of A's edge.
   float pen2 = -1.f, safe1 = 1.f;
   bool fast = false;
-  if (!sdf_out && bb.A.kind == kHull) {
+  if (!sdf_out && !ps.trace && bb.A.kind == kHull) {
     const V3 t1 = la1 - la0;
     const float ex = fmaxf(fmaxf(-w.qp.a1, w.qp.a1 - 1.f), 0.f) * ps.k2;
     fast = ex * ex * dot(t1, t1) <= 3600.f;
@@ -314,10 +339,10 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
     w1 *= safe1;
     w2 *= sigmoid(-B_e2.phi * it);
   }
-  float d1 = g1 * w.dbar, d2 = g2 * w.dbar;
-  y1[0] = w.e1.x; y1[1] = w.e1.y; y1[2] = w.e1.z; y1[3] = d1;
+  float d1 = g1 * dbar, d2 = g2 * dbar;
+  y1[0] = e1.x; y1[1] = e1.y; y1[2] = e1.z; y1[3] = d1;
   y1[4] = g1 * nbar.x; y1[5] = g1 * nbar.y; y1[6] = g1 * nbar.z; y1[7] = w1;
-  y2[0] = w.e2.x; y2[1] = w.e2.y; y2[2] = w.e2.z; y2[3] = d2;
+  y2[0] = e2.x; y2[1] = e2.y; y2[2] = e2.z; y2[3] = d2;
   y2[4] = -g2 * nbar.x; y2[5] = -g2 * nbar.y; y2[6] = -g2 * nbar.z; y2[7] = w2;
   s1 = -w1 * d1;
   s2 = -w2 * d2;
@@ -416,10 +441,10 @@ __device__ inline void preselect_pair(const FwdArgs& a, PairShared& ps, const Pa
   for (int i = threadIdx.x; i < ps.nvA; i += blockDim.x) mA[i] = sdfB_at(ps, bb.B, ld3(sm.vA[i])).phi;
   for (int i = threadIdx.x; i < ps.nvB; i += blockDim.x) mB[i] = sdfA_at(ps, bb.A, ld3(sm.vB[i])).phi;
   __syncthreads();
-  float* stA = sm.sel + 2 * sm.vs;          // 16 x 6: A's soft vertices (B frame, A frame)
-  float* stB = stA + kMaxK * 6;             // 16 x 3: B's soft vertices
-  float* seA = stB + kMaxK * 6;             // 16 x 12: A's soft edges (B frame, A frame)
-  float* seB = seA + kMaxK * 12;            // 16 x 6: B's soft edges
+  float* stA = sm.sel + 2 * sm.vs;          // kMaxSel x 6: A's soft vertices (B frame, A frame)
+  float* stB = stA + kMaxSel * 6;           // kMaxSel x 3: B's soft vertices
+  float* seA = stB + kMaxSel * 6;           // kMaxSel x 12: A's soft edges (B frame, A frame)
+  float* seB = seA + kMaxSel * 12;          // kMaxSel x 6: B's soft edges
   const int kvA = a.p.top_verts ? min(a.p.top_verts, ps.nvA) : 0;
   const int kvB = a.p.top_verts ? min(a.p.top_verts, ps.nvB) : 0;
   const int keA = a.p.top_edges ? min(a.p.top_edges, ps.neA) : 0;

@@ -80,8 +80,10 @@ cm_status check_params(const cm_params* p) {
     return fail(CM_ERR_INVALID_ARG, "w_reg must be finite and > 0 (the E-E QP needs it to be strictly convex)");
   if (p->K < 1 || p->K > CM_MAX_K) return fail(CM_ERR_INVALID_ARG, "K must be in 1..16");
   if (p->flags & ~3) return fail(CM_ERR_INVALID_ARG, "unknown flag bits");
-  if (p->top_verts < 0 || p->top_verts > CM_MAX_K || p->top_edges < 0 || p->top_edges > CM_MAX_K)
-    return fail(CM_ERR_INVALID_ARG, "top_verts and top_edges must be in 0..16");
+  if (p->top_verts < 0 || p->top_verts > CM_MAX_SELECT || p->top_edges < 0 || p->top_edges > CM_MAX_SELECT)
+    return fail(CM_ERR_INVALID_ARG, "top_verts and top_edges must be in 0..32");
+  if (p->trace_iters < 0 || p->trace_iters > CM_MAX_TRACE)
+    return fail(CM_ERR_INVALID_ARG, "trace_iters must be in 0..8");
   return CM_OK;
 }
 
@@ -175,8 +177,19 @@ LaunchCfg pick_cfg(const cm_context* c, int bwd, int n_pairs, int flags) {
   return it != c->tuned.end() ? it->second : default_cfg(c, bwd, n_pairs);
 }
 
+// The adjoint covers the plain manifold only: no pre-selection, no sphere
+// tracing, no superquadric unions.  Call with the context lock held.
+cm_status adjoint_supported(const cm_context* c, const cm_params* p) {
+  if (p->top_verts || p->top_edges)
+    return fail(CM_ERR_INVALID_ARG, "the adjoint does not support pre-selection (top_verts / top_edges)");
+  if (p->trace_iters) return fail(CM_ERR_INVALID_ARG, "the adjoint does not support sphere tracing (trace_iters)");
+  if (c->has_sq_union) return fail(CM_ERR_INVALID_ARG, "the adjoint is not built for SQ_UNION geometry");
+  return CM_OK;
+}
+
 Params to_params(const cm_params* p) {
-  return Params{p->tau, p->w_reg, p->eps_clip, p->eps_min, p->eps_comp, p->K, p->flags, p->top_verts, p->top_edges};
+  return Params{p->tau, p->w_reg, p->eps_clip, p->eps_min, p->eps_comp, p->K, p->flags, p->top_verts, p->top_edges,
+                p->trace_iters};
 }
 
 // Grid and shared-memory layout of one launch shape.
@@ -263,6 +276,7 @@ void cm_default_params(cm_params* p) {
   p->flags = 0;
   p->top_verts = 0;
   p->top_edges = 0;
+  p->trace_iters = 0;
 }
 
 const char* cm_last_error(void) { return g_last_error.c_str(); }
@@ -317,9 +331,49 @@ void cm_destroy_context(cm_context* c) {
   delete c;
 }
 
+namespace {
+
+// Device rows of one superquadric of an SQ_UNION geometry (five float4): the
+// rows of R^T with -R^T t (x = R^T (y - t) = M y + c), then (1/a, 1/b, 1/c,
+// 2/eps1) and (2/eps2, eps2/eps1, eps1/2, 0).
+void pack_sq(const float* r, std::vector<float4>& out) {
+  double qw = r[0], qx = r[1], qy = r[2], qz = r[3];
+  const double qn = std::sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+  qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+  const double R[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+                          {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+                          {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+  const double t[3] = {r[4], r[5], r[6]};
+  for (int i = 0; i < 3; ++i) {  // row i of R^T is column i of R
+    const double c = -(R[0][i] * t[0] + R[1][i] * t[1] + R[2][i] * t[2]);
+    out.push_back(make_float4((float)R[0][i], (float)R[1][i], (float)R[2][i], (float)c));
+  }
+  const double e1 = r[7], e2 = r[11];
+  out.push_back(make_float4((float)(1.0 / r[8]), (float)(1.0 / r[9]), (float)(1.0 / r[10]), (float)(2.0 / e1)));
+  out.push_back(make_float4((float)(2.0 / e2), (float)(e2 / e1), (float)(0.5 * e1), 0.f));
+}
+
+cm_status check_sq_rows(const cm_geometry_desc* d) {
+  if (d->n_planes < 3 || d->n_planes % 3 || d->n_planes / 3 > CM_MAX_PRIMS || !d->planes)
+    return fail(CM_ERR_INVALID_ARG, "an SQ_UNION needs 3 rows per superquadric, 1..32 superquadrics");
+  for (int l = 0; l < d->n_planes / 3; ++l) {
+    const float* r = d->planes + 12 * l;
+    if (!(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3] > 1e-12f))
+      return fail(CM_ERR_INVALID_ARG, "superquadric orientation quaternion is zero");
+    if (!finite_pos(r[8]) || !finite_pos(r[9]) || !finite_pos(r[10]))
+      return fail(CM_ERR_INVALID_ARG, "superquadric semi-axes must be finite and > 0");
+    for (int e : {7, 11})
+      if (!(r[e] >= 0.1f && r[e] <= 1.9f))
+        return fail(CM_ERR_INVALID_ARG, "superquadric exponents must be in [0.1, 1.9]");
+  }
+  return CM_OK;
+}
+
+}  // namespace
+
 cm_status cm_create_geometry(cm_context* c, const cm_geometry_desc* d, int32_t* geom_id) {
   if (!c || !d || !geom_id) return fail(CM_ERR_INVALID_ARG, "NULL argument");
-  if (d->kind < CM_BOX || d->kind > CM_HULL) return fail(CM_ERR_INVALID_ARG, "unknown geometry kind");
+  if (d->kind < CM_BOX || d->kind > CM_SQ_UNION) return fail(CM_ERR_INVALID_ARG, "unknown geometry kind");
   if (d->n_verts < 1 || d->n_verts > CM_MAX_VERTS || !d->verts)
     return fail(CM_ERR_INVALID_ARG, "n_verts must be in 1..256 with a vertex array");
   if (d->n_edges < 0 || d->n_edges > CM_MAX_EDGES || (d->n_edges > 0 && !d->edges))
@@ -328,8 +382,13 @@ cm_status cm_create_geometry(cm_context* c, const cm_geometry_desc* d, int32_t* 
     if (d->n_planes < 4 || d->n_planes > CM_MAX_PLANES || !d->planes)
       return fail(CM_ERR_INVALID_ARG, "a hull needs 4..512 planes");
     if (d->n_verts < 4) return fail(CM_ERR_INVALID_ARG, "a hull needs at least 4 vertices");
+  } else if (d->kind == CM_SQ_UNION) {
+    for (int i = 0; i < 4 * d->n_planes && d->planes; ++i)
+      if (!std::isfinite(d->planes[i])) return fail(CM_ERR_INVALID_ARG, "non-finite superquadric row");
+    cm_status st = check_sq_rows(d);
+    if (st != CM_OK) return st;
   } else {
-    if (d->n_planes != 0) return fail(CM_ERR_INVALID_ARG, "planes are only given for hulls");
+    if (d->n_planes != 0) return fail(CM_ERR_INVALID_ARG, "planes are only given for hulls and SQ unions");
     int need = (d->kind == CM_CAPSULE || d->kind == CM_CYLINDER) ? 2 : 3;
     for (int i = 0; i < need; ++i)
       if (!finite_pos(d->dims[i])) return fail(CM_ERR_INVALID_ARG, "primitive dims must be finite and > 0");
@@ -340,33 +399,42 @@ cm_status cm_create_geometry(cm_context* c, const cm_geometry_desc* d, int32_t* 
     if (d->edges[i] < 0 || d->edges[i] >= d->n_verts) return fail(CM_ERR_INVALID_ARG, "edge index out of range");
   for (int i = 0; i < d->n_edges; ++i)
     if (d->edges[2 * i] == d->edges[2 * i + 1]) return fail(CM_ERR_INVALID_ARG, "degenerate edge");
-  for (int i = 0; i < 4 * d->n_planes; ++i)
-    if (!std::isfinite(d->planes[i])) return fail(CM_ERR_INVALID_ARG, "non-finite plane");
-  for (int i = 0; i < d->n_planes; ++i) {
-    const float* p = d->planes + 4 * i;
-    float nn = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
-    if (std::fabs(nn - 1.f) > 1e-3f) return fail(CM_ERR_INVALID_ARG, "hull plane normals must be unit length");
+  if (d->kind == CM_HULL) {
+    for (int i = 0; i < 4 * d->n_planes; ++i)
+      if (!std::isfinite(d->planes[i])) return fail(CM_ERR_INVALID_ARG, "non-finite plane");
+    for (int i = 0; i < d->n_planes; ++i) {
+      const float* p = d->planes + 4 * i;
+      float nn = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+      if (std::fabs(nn - 1.f) > 1e-3f) return fail(CM_ERR_INVALID_ARG, "hull plane normals must be unit length");
+    }
   }
   std::lock_guard<std::mutex> lk(c->mu);
   GeomHeader h{};
   h.kind = d->kind;
   h.n_verts = d->n_verts;
   h.n_edges = d->n_edges;
-  h.n_planes = d->n_planes;
   h.v_off = (int)c->verts.size();
   h.e_off = (int)c->edges.size();
   h.p_off = (int)c->planes.size();
   for (int i = 0; i < 3; ++i) h.dims[i] = d->dims[i];
+  if (d->kind == CM_SQ_UNION) {
+    h.dims[0] = h.dims[1] = h.dims[2] = 1.f;
+    for (int l = 0; l < d->n_planes / 3; ++l) pack_sq(d->planes + 12 * l, c->planes);
+    h.n_planes = kSqRows * (d->n_planes / 3);
+    c->has_sq_union = true;
+  } else {
+    for (int i = 0; i < d->n_planes; ++i)
+      c->planes.push_back(make_float4(d->planes[4 * i], d->planes[4 * i + 1], d->planes[4 * i + 2], d->planes[4 * i + 3]));
+    h.n_planes = d->n_planes;
+  }
   for (int i = 0; i < d->n_verts; ++i)
     c->verts.push_back(make_float4(d->verts[4 * i], d->verts[4 * i + 1], d->verts[4 * i + 2], d->verts[4 * i + 3]));
   for (int i = 0; i < d->n_edges; ++i)
     c->edges.push_back((uint32_t)d->edges[2 * i] | ((uint32_t)d->edges[2 * i + 1] << 16));
-  for (int i = 0; i < d->n_planes; ++i)
-    c->planes.push_back(make_float4(d->planes[4 * i], d->planes[4 * i + 1], d->planes[4 * i + 2], d->planes[4 * i + 3]));
   c->hdr.push_back(h);
   c->max_v = std::max(c->max_v, d->n_verts);
   c->max_e = std::max(c->max_e, d->n_edges);
-  c->max_p = std::max(c->max_p, d->n_planes);
+  c->max_p = std::max(c->max_p, h.n_planes);
   c->min_v = std::min(c->min_v, d->n_verts);
   c->min_e = std::min(c->min_e, d->n_edges);
   c->dirty = true;
@@ -432,9 +500,8 @@ extern "C" cm_status cm_contact_manifold_bwd(cm_context* c, int32_t n_pairs, con
   if (n_pairs == 0) return CM_OK;
   if (!pair_geoms || !poses || !grad_out || !grad_poses)
     return fail(CM_ERR_INVALID_ARG, "pair_geoms, poses, grad_out and grad_poses are required");
-  if (params->top_verts || params->top_edges)
-    return fail(CM_ERR_INVALID_ARG, "the adjoint does not support pre-selection (top_verts / top_edges)");
   std::lock_guard<std::mutex> lk(c->mu);
+  if ((st = adjoint_supported(c, params)) != CM_OK) return st;
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
   cudaSetDevice(c->device);
@@ -533,7 +600,7 @@ extern "C" cm_status cm_contact_manifold_fwd_noalloc(cm_context* c, int32_t n_pa
   a.poses = poses;
   a.dims = dims;
   a.tau = tau;
-  a.p = Params{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K, params->flags, params->top_verts, params->top_edges};
+  a.p = to_params(params);
   a.out = out;
   a.scratch = scratch;  // written before it is read: no clearing needed
   a.scratch_stride = stride;
@@ -558,9 +625,8 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
   if (st != CM_OK) return st;
   if (n_pairs <= 0 || !pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "a non-empty batch is required");
   if (grad_out && !grad_poses) return fail(CM_ERR_INVALID_ARG, "grad_poses is required with grad_out");
-  if (grad_out && (params->top_verts || params->top_edges))
-    return fail(CM_ERR_INVALID_ARG, "the adjoint does not support pre-selection (top_verts / top_edges)");
   std::lock_guard<std::mutex> lk(c->mu);
+  if (grad_out && (st = adjoint_supported(c, params)) != CM_OK) return st;
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
   cudaSetDevice(c->device);
@@ -660,9 +726,8 @@ extern "C" cm_status cm_plan_create(cm_context* c, int32_t n_pairs, const int32_
   if (st != CM_OK) return st;
   if (n_pairs <= 0 || !pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "a non-empty batch is required");
   if (grad_out && !grad_poses) return fail(CM_ERR_INVALID_ARG, "grad_poses is required with grad_out");
-  if (grad_out && (params->top_verts || params->top_edges))
-    return fail(CM_ERR_INVALID_ARG, "the adjoint does not support pre-selection (top_verts / top_edges)");
   std::lock_guard<std::mutex> lk(c->mu);
+  if (grad_out && (st = adjoint_supported(c, params)) != CM_OK) return st;
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
   cudaSetDevice(c->device);

@@ -362,13 +362,15 @@ cm_status cm_submit(cm_context* c, const cm_request_desc* d, uint64_t* ticket) {
   if (!d->pair_geoms || !d->poses || !d->out) return fail(CM_ERR_INVALID_ARG, "pair_geoms, poses and out are required");
   if (d->with_backward && (!d->grad_out || !d->grad_poses))
     return fail(CM_ERR_INVALID_ARG, "a backward request needs grad_out and grad_poses");
-  if (d->with_backward && (s->params.top_verts || s->params.top_edges))
-    return fail(CM_ERR_INVALID_ARG, "the adjoint does not support pre-selection (top_verts / top_edges)");
   auto r = std::make_unique<Request>();
   r->d = *d;
   r->bytes = request_bytes(*d, s->params.K);
   {
     std::lock_guard<std::mutex> lk(c->mu);
+    if (d->with_backward) {
+      cm_status st = adjoint_supported(c, &s->params);
+      if (st != CM_OK) return st;
+    }
     const int ng = (int)c->hdr.size();
     int64_t m = 1;
     for (int i = 0; i < d->n_pairs; ++i) {

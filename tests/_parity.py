@@ -29,7 +29,8 @@ def tol_for_tau(tau):
 
 def oracle_params(p):
     return oracle.Params(K=p.K, w_reg=p.w_reg, eps_clip=p.eps_clip, eps_min=p.eps_min,
-                         eps_comp=p.eps_comp, no_ee=bool(p.flags & 1), one_sided=bool(p.flags & 2))
+                         eps_comp=p.eps_comp, no_ee=bool(p.flags & 1), one_sided=bool(p.flags & 2),
+                         trace_iters=int(getattr(p, "trace_iters", 0)))
 
 
 def oracle_forward(w, params, idx=None):

@@ -100,3 +100,64 @@ def test_bad_params_are_rejected_before_any_work(api, ctx):
     assert lib.cm_contact_manifold_fwd(ctx, 0, None, None, None, None, ctypes.byref(p), None, None) == api.CM_OK
     assert lib.cm_contact_manifold_fwd(ctx, 3, None, None, None, None, ctypes.byref(p), None, None) == \
         api.CM_ERR_INVALID_ARG
+
+
+def sq_body(seed=0, n=4):
+    return synth.random_sq_union(np.random.default_rng(seed), n)
+
+
+def test_sq_union_geometry_is_accepted(api, ctx):
+    ids = [add(api, ctx, sq_body(s, n)) for s, n in ((0, 1), (1, 5), (2, 18))]
+    assert ids == [0, 1, 2]
+
+
+@pytest.mark.parametrize("case", ["rows", "eps_high", "eps_low", "zero_quat", "scale", "too_many", "nan"])
+def test_invalid_sq_union_is_rejected(api, ctx, case):
+    g = sq_body()
+    P = g.planes.copy()
+    if case == "rows":
+        P = P[:-1]
+    elif case == "eps_high":
+        P[1, 3] = 2.5
+    elif case == "eps_low":
+        P[5, 3] = 0.05
+    elif case == "zero_quat":
+        P[0] = 0.0
+    elif case == "scale":
+        P[2, 1] = -0.2
+    elif case == "too_many":
+        P = np.concatenate([P] * 9)           # 36 superquadrics
+    elif case == "nan":
+        P[4, 0] = np.nan
+    with pytest.raises(api.CMError) as ei:
+        add(api, ctx, g, planes=P)
+    assert ei.value.status == api.CM_ERR_INVALID_ARG and api.cm_last_error()
+    assert api.cm_num_geometries(ctx) == 0
+
+
+def test_selection_and_tracing_limits(api, ctx):
+    import ctypes
+    lib = api._lib
+    add(api, ctx, synth.primitive_geometry(synth.KIND_BOX, (0.5, 0.5, 0.5)))
+    for over in (dict(top_edges=33), dict(top_verts=-1), dict(trace_iters=9), dict(trace_iters=-1)):
+        p = api.cm_default_params(**over)
+        st = lib.cm_contact_manifold_fwd(ctx, 1, ctypes.c_void_p(8), ctypes.c_void_p(8), None, None,
+                                         ctypes.byref(p), ctypes.c_void_p(8), None)
+        assert st == api.CM_ERR_INVALID_ARG, over
+    assert api.cm_default_params().trace_iters == 0
+
+
+def test_adjoint_refuses_tracing_and_sq_unions(api, ctx):
+    import ctypes
+    lib = api._lib
+    add(api, ctx, synth.primitive_geometry(synth.KIND_BOX, (0.5, 0.5, 0.5)))
+    v = ctypes.c_void_p(8)
+    p = api.cm_default_params(trace_iters=2)
+    assert lib.cm_contact_manifold_bwd(ctx, 1, v, v, None, None, ctypes.byref(p), v, v, None, None) == \
+        api.CM_ERR_INVALID_ARG
+    assert "tracing" in api.cm_last_error()
+    add(api, ctx, sq_body())
+    p = api.cm_default_params()
+    assert lib.cm_contact_manifold_bwd(ctx, 1, v, v, None, None, ctypes.byref(p), v, v, None, None) == \
+        api.CM_ERR_INVALID_ARG
+    assert "SQ_UNION" in api.cm_last_error()
