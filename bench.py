@@ -309,6 +309,27 @@ def extra_settings(Engine, api, local, steps, flush):
                                 "speedup_no_ee": ne / full, "speedup_one_sided_vs_no_ee": nes / ne}}
 
 
+def sq_union_rates(Engine, api, local, steps, flush):
+    """Pairs/s of the multi-superquadric bodies in the paper's armadillo setting (Sec. V:
+    L superquadrics per body, every vertex, the L deepest soft edges per body), at the
+    largest batch the paper vectorises (1024 pairs), with and without sphere tracing."""
+    eng = Engine(local)  # its own context: SQ_UNION geometry disables the adjoint there
+    try:
+        res = {"workload": "1024 pairs of synthetic multi-superquadric bodies (pool of 8 per L), tau=1e-2, "
+                           "K=8, all vertices, top_edges=L (one soft edge per superquadric)"}
+        for L in (5, 18):
+            w = synth.config_sq_union(n=1024, n_prims=L, seed=rank_seed(60 + L))
+            res[f"L{L}"] = {"verts_mean": float(np.mean([g.n_verts for g in w.geoms])),
+                            "edges_mean": float(np.mean([g.n_edges for g in w.geoms]))}
+            r, ms = plan_rate(eng, api, w, eng.params(top_edges=L), steps, False, flush)
+            res[f"L{L}"].update(fwd_pairs_per_s=r, fwd_ms=ms)
+            r, ms = plan_rate(eng, api, w, eng.params(top_edges=L, trace_iters=3), steps, False, flush)
+            res[f"L{L}"].update(trace3_fwd_pairs_per_s=r, trace3_fwd_ms=ms)
+    finally:
+        eng.close()
+    return res
+
+
 def witness_rates(api, n=10_000_000, steps=5):
     """Queries/s of the batched E-E and V-F witness routines, queries uniform in the unit
     cube; the rows (48 B in, 32 / 16 B out) exceed L2, so each launch streams from HBM."""
@@ -470,6 +491,7 @@ def main():
     if not args.no_extra and world == 1:
         extra = extra_settings(Engine, api, local, max(3, min(args.steps, 5)), flush)
         extra["witness_points"] = witness_rates(api)
+        extra["sq_union"] = sq_union_rates(Engine, api, local, max(3, min(args.steps, 5)), flush)
         for k in ("ee", "vf"):
             extra["witness_points"][k]["hbm_frac_of_measured"] = extra["witness_points"][k]["hbm_gbs"] / _hbm_peak()
 
