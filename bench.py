@@ -313,7 +313,7 @@ def sq_union_rates(Engine, api, local, steps, flush):
     """Pairs/s of the multi-superquadric bodies in the paper's armadillo setting (Sec. V:
     L superquadrics per body, every vertex, the L deepest soft edges per body), at the
     largest batch the paper vectorises (1024 pairs), with and without sphere tracing."""
-    eng = Engine(local)  # its own context: SQ_UNION geometry disables the adjoint there
+    eng = Engine(local)
     try:
         res = {"workload": "1024 pairs of synthetic multi-superquadric bodies (pool of 8 per L), tau=1e-2, "
                            "K=8, all vertices, top_edges=L (one soft edge per superquadric)"}

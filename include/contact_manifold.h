@@ -131,7 +131,8 @@ typedef struct {
    * the QP witness; signed distances, normals, penetration and clashing
    * indicators and the output points then use the moved witnesses, while the
    * nearest-neighbour indicators keep the QP witnesses' distances.
-   * 0 (default) .. CM_MAX_TRACE; forward only (the adjoint rejects it). */
+   * 0 (default) .. CM_MAX_TRACE; the adjoint differentiates through the
+   * unrolled steps and the direction. */
   int32_t trace_iters;
 } cm_params;
 
@@ -185,9 +186,8 @@ cm_status cm_contact_manifold_fwd(cm_context* ctx, int32_t n_pairs, const int32_
  * grad_dims: device, n_pairs x 6 or NULL, receives dL/d dims of A then B (the
  *   dims in use; zero for hulls).
  * The forward is recomputed per pair inside the call; nothing is kept between
- * the forward and backward calls.  Not built for SQ_UNION geometry: returns
- * CM_ERR_INVALID_ARG when the context holds any (as for pre-selection and
- * sphere tracing in params). */
+ * the forward and backward calls.  Pre-selection in params is refused
+ * (CM_ERR_INVALID_ARG). */
 cm_status cm_contact_manifold_bwd(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms,
                                   const float* poses, const float* dims, const float* tau,
                                   const cm_params* params, const float* grad_out, float* grad_poses,

@@ -167,6 +167,73 @@ CM_HD void sdf_cylinder_bwd(V3 y, float rad, float h, const Sdf& f, float inv_ta
   dbar += v3(-sb0, -sb1 - sb2, 0.f);
 }
 
+// Superquadric union (rows as in sdf_sq_union).  With pi_l = exp((phi - phi_l) / tau)
+// and G_l = R_l grad_x f_l the forward has phi = -tau ln sum exp(-phi_l / tau) and
+// g = sum_l pi_l G_l, so
+//   phibar_l = pi_l (phibar - (gbar . G_l - gbar . g) / tau),
+//   xbar_l   = phibar_l grad_x phi_l + H_l (pi_l R_l^T gbar),   ybar += R_l xbar_l,
+// with grad_x phi_l = h f^(-h-1) |x| grad_x f + (1 - f^-h) x / |x| and H_l the
+// Hessian of f_l:  d2f/dx~2 = r (r-1) s^(r-2) u'^2 + r s^(r-1) u'',
+// d2f/dx~dy~ = r (r-1) s^(r-2) u' v', d2f/dz~2 = p1 (p1-1) |z~|^(p1-2), u' = p2
+// |x~|^(p2-1) sgn x~, u'' = p2 (p2-1) |x~|^(p2-2), divided by the semi-axes of
+// both indices.  As in the forward every power is an exp2 of a sum of base-2
+// logarithms with log2 pi_l folded in.
+CM_HD void sdf_sq_union_bwd(V3 y, const float4* P, int L, const Sdf& f, float inv_tau, float phibar, V3 gbar,
+                            V3& ybar) {
+  const float k = inv_tau * kLog2e;
+  const float gg = dot(gbar, f.g);
+  V3 acc = v3(0.f, 0.f, 0.f);
+  for (int l = 0; l < L; ++l) {
+    const float4 r0 = P[5 * l], r1 = P[5 * l + 1], r2 = P[5 * l + 2], r3 = P[5 * l + 3], r4 = P[5 * l + 4];
+    const V3 x = v3(fmaf(r0.x, y.x, fmaf(r0.y, y.y, fmaf(r0.z, y.z, r0.w))),
+                    fmaf(r1.x, y.x, fmaf(r1.y, y.y, fmaf(r1.z, y.z, r1.w))),
+                    fmaf(r2.x, y.x, fmaf(r2.y, y.y, fmaf(r2.z, y.z, r2.w))));
+    const float xx = x.x * r3.x, xy = x.y * r3.y, xz = x.z * r3.z;
+    const float p1 = r3.w, p2 = r4.x, rr = r4.y, h = r4.z;
+    const float lx = lg2(fmaxf(fabsf(xx), 1e-20f)), ly = lg2(fmaxf(fabsf(xy), 1e-20f)),
+                lz = lg2(fmaxf(fabsf(xz), 1e-20f));
+    const float ls = log2_add(p2 * lx, p2 * ly);
+    const float lf = log2_add(rr * ls, p1 * lz);
+    const float fh = ex2(-h * lf);
+    const float rho2 = dot(x, x);
+    const float irho = rho2 > 0.f ? rsq(rho2) : 0.f;
+    const float rho = rho2 * irho;
+    const float le = (f.phi - (1.f - fh) * rho) * k;        // log2 pi_l
+    const float pi = ex2(le);
+    const V3 w = v3(dot(v3(r0.x, r0.y, r0.z), gbar), dot(v3(r1.x, r1.y, r1.z), gbar),
+                    dot(v3(r2.x, r2.y, r2.z), gbar));     // R_l^T gbar
+    const float Ex = (rr - 1.f) * ls + (p2 - 1.f) * lx, Ey = (rr - 1.f) * ls + (p2 - 1.f) * ly,
+                Ez = (p1 - 1.f) * lz;
+    const float cxy = rr * p2;
+    // pi_l grad_x f
+    const V3 gp = v3(copysignf(cxy * ex2(le + Ex), xx) * r3.x, copysignf(cxy * ex2(le + Ey), xy) * r3.y,
+                     copysignf(p1 * ex2(le + Ez), xz) * r3.z);
+    const float phib = pi * phibar - (dot(gp, w) - pi * gg) * inv_tau;
+    // grad_x phi_l
+    const float q = -(h + 1.f) * lf, hr = h * rho, om = (1.f - fh) * irho;
+    const V3 dp = v3(fmaf(hr, copysignf(cxy * ex2(Ex + q), xx) * r3.x, om * x.x),
+                     fmaf(hr, copysignf(cxy * ex2(Ey + q), xy) * r3.y, om * x.y),
+                     fmaf(hr, copysignf(p1 * ex2(Ez + q), xz) * r3.z, om * x.z));
+    V3 xb = dp * phib;
+    // Hessian of f applied to pi_l R_l^T gbar
+    const float T = le + (rr - 2.f) * ls;
+    const float c2 = rr * (rr - 1.f) * p2 * p2, c1 = rr * p2 * (p2 - 1.f);
+    const float Bx = (p2 - 1.f) * lx, By = (p2 - 1.f) * ly;
+    const float hxx = c2 * ex2(T + 2.f * Bx) + c1 * ex2(le + (rr - 1.f) * ls + Bx - lx);
+    const float hyy = c2 * ex2(T + 2.f * By) + c1 * ex2(le + (rr - 1.f) * ls + By - ly);
+    const float hxy = copysignf(1.f, xx) * copysignf(1.f, xy) * c2 * ex2(T + Bx + By);
+    const float hzz = p1 * (p1 - 1.f) * ex2(le + (p1 - 2.f) * lz);
+    const float wx = w.x * r3.x, wy = w.y * r3.y, wz = w.z * r3.z;
+    xb.x = fmaf(r3.x, fmaf(hxx, wx, hxy * wy), xb.x);
+    xb.y = fmaf(r3.y, fmaf(hxy, wx, hyy * wy), xb.y);
+    xb.z = fmaf(r3.z, hzz * wz, xb.z);
+    acc.x += fmaf(xb.x, r0.x, fmaf(xb.y, r1.x, xb.z * r2.x));
+    acc.y += fmaf(xb.x, r0.y, fmaf(xb.y, r1.y, xb.z * r2.y));
+    acc.z += fmaf(xb.x, r0.z, fmaf(xb.y, r1.z, xb.z * r2.z));
+  }
+  ybar += acc;
+}
+
 CM_HD void body_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_tau, float phibar, V3 gbar,
                         V3& ybar, V3& dbar) {
   switch (b.kind) {
@@ -174,6 +241,7 @@ CM_HD void body_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_
     case kEllipsoid: sdf_ellipsoid_bwd(y, b.dims, phibar, gbar, ybar, dbar); break;
     case kCapsule: sdf_capsule_bwd(y, b.dims.x, b.dims.y, tau, inv_tau, phibar, gbar, ybar, dbar); break;
     case kCylinder: sdf_cylinder_bwd(y, b.dims.x, b.dims.y, f, inv_tau, phibar, gbar, ybar, dbar); break;
+    case kSqUnion: sdf_sq_union_bwd(y, b.planes, b.n_planes / 5, f, inv_tau, phibar, gbar, ybar); break;
     default: sdf_planes_bwd(y, b.planes, b.n_planes, f, inv_tau, phibar, gbar, ybar); break;
   }
 }
@@ -211,6 +279,33 @@ CM_HD void body_sdf2_bwd(const Body& b, V3 y1, V3 y2, const Sdf& f1, const Sdf& 
     body_sdf_bwd(b, y1, f1, tau, inv_tau, phibar1, v3(0.f, 0.f, 0.f), ybar1, dbar);
     body_sdf_bwd(b, y2, f2, tau, inv_tau, 0.f, gbar2, ybar2, dbar);
   }
+}
+
+// Reverse of trace_to_surface from x0 (iters <= 8): xbar of the traced point ->
+// xbar of x0; SDF parameter adjoints into dbar.  Step i maps x_i to
+// x_i - phi(x_i) u, so xbar_i = xbar_(i+1) - grad phi(x_i) (u . xbar_(i+1)) and
+// ubar += -phi(x_i) xbar_(i+1); u = g_0 / |g_0| hands (ubar - (ubar . u) u) / |g_0|
+// to the gradient adjoint of the SDF at x0.
+CM_HD V3 trace_bwd(const Body& b, V3 x0, int iters, float tau, float it, V3 xbar, V3& dbar) {
+  V3 xs[8];
+  const Sdf s0 = body_sdf(b, x0, tau, it);
+  const float ig = rsq(dot(s0.g, s0.g));
+  const V3 u = s0.g * ig;
+  V3 x = x0;
+  for (int i = 0; i < iters; ++i) {
+    xs[i] = x;
+    x = fma3(-(i ? body_sdf(b, x, tau, it).phi : s0.phi), u, x);
+  }
+  V3 ub = v3(0.f, 0.f, 0.f);
+  for (int i = iters - 1; i >= 0; --i) {
+    const Sdf si = i ? body_sdf(b, xs[i], tau, it) : s0;
+    const float phib = -dot(u, xbar);
+    ub = fma3(-si.phi, xbar, ub);
+    V3 gb = v3(0.f, 0.f, 0.f);
+    if (i == 0) gb = (ub - u * dot(ub, u)) * ig;
+    body_sdf_bwd(b, xs[i], si, tau, it, phib, gb, xbar, dbar);
+  }
+  return xbar;
 }
 
 // ---------------------------------------------------------------- vertex templates
@@ -444,6 +539,16 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
   QPOut o = stored ? *stored : qp_solve(q, p.w_reg, p);
   V3 e1 = fma3(o.a1, a1 - a0, a0), e2 = fma3(o.a2, b1 - b0, b0);
   V3 e1L = fma3(o.a1, a1L - a0L, a0L);
+  // nn indicators rank the QP witnesses' distances; sphere tracing (if on) moves
+  // the witnesses everything else uses
+  const float dbar_qp = sqrt_(dot(e1 - e2, e1 - e2));
+  const int nt = p.trace_iters;
+  const V3 e1Lq = e1L, e2q = e2;
+  if (nt) {
+    e1L = trace_to_surface(A, e1L, nt, tau, it);
+    e2 = trace_to_surface(B, e2, nt, tau, it);
+    e1 = mul(F.R, e1L) + F.t;
+  }
   V3 D = e1 - e2;
   float r2 = dot(D, D);
   float dbar = sqrt_(r2);
@@ -466,7 +571,7 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
   float g1 = tanh_(dot(nuB, nbar) * it), g2 = tanh_(-dot(nuA, nbar) * it);
   float pen1 = sigmoid(-SB1.phi * it), pen2 = sigmoid(-SA2.phi * it);
   float cl = sigmoid(-dot(nuA, nuB) * it);
-  float nn1 = ex2((rowL - dbar) * F.k2), nn2 = ex2((colL - dbar) * F.k2);
+  float nn1 = ex2((rowL - dbar_qp) * F.k2), nn2 = ex2((colL - dbar_qp) * F.k2);
   float con = o.con;
   float w1 = con * cl * pen1 * nn1, w2 = con * cl * pen2 * nn2;
   EECand c;
@@ -512,6 +617,12 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
   body_sdf2_bwd(A, x2, e1L, SA2, SA1, tau, it, phibA2, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b, e1Lb,
                 adj.dA);
   e2b += pull_point_bwd(F, e2, x2b, adj);
+  if (nt) {  // traced e1 = R_rel e1L + t_rel; back through both traces to the QP witnesses
+    e1Lb += push_point_bwd(F, e1L, e1b, adj);
+    e1Lb = trace_bwd(A, e1Lq, nt, tau, it, e1Lb, adj.dA);
+    e2b = trace_bwd(B, e2q, nt, tau, it, e2b, adj.dB);
+    e1b = v3(0.f, 0.f, 0.f);
+  }
   witness_bwd(F, A, B, p, g, q, o, e1b, e1Lb, e2b, conb, adj);
 }
 

@@ -29,7 +29,6 @@ struct cm_context {
   std::vector<float4> planes;
   int max_v = 0, max_e = 0, max_p = 0, min_v = 1 << 30, min_e = 1 << 30;
   bool dirty = false;
-  bool has_sq_union = false;  // an SQ_UNION geometry is registered (no adjoint for it)
   // device copy
   cm::GeomHeader* d_hdr = nullptr;
   float4* d_verts = nullptr;

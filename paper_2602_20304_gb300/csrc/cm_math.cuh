@@ -449,6 +449,19 @@ CM_HD void body_sdf2(const Body& b, V3 y1, V3 y2, float tau, float inv_tau, Sdf&
   }
 }
 
+// Sphere tracing of a witness onto its own body's SDF surface (Supplement,
+// mesh-SDF discrepancies): `iters` steps x <- x - phi(x) u along the fixed
+// direction u = grad phi(x_0) / |grad phi(x_0)|, in the body's own frame.
+CM_HD V3 trace_to_surface(const Body& b, V3 x, int iters, float tau, float it) {
+  Sdf s = body_sdf(b, x, tau, it);
+  const V3 u = s.g * rsq(dot(s.g, s.g));
+  for (int i = 0; i < iters; ++i) {
+    if (i) s = body_sdf(b, x, tau, it);
+    x = fma3(-s.phi, u, x);
+  }
+  return x;
+}
+
 // ---------------------------------------------------------------- E-E witness QP (Sec. IV-D2)
 // Box QP  min 1/2 a^T Q a + c^T a  on [0,1]^2 with Q = A^T A + lam I,
 // c = A^T b - lam/2 (1, 1), A = [t1, t2], t1 = a1 - a0, t2 = b0 - b1, b = a0 - b0.

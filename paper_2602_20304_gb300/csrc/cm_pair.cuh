@@ -263,19 +263,6 @@ __device__ __forceinline__ Witness ee_witness(const EdgePair& e, const Params& p
 // sdf_out (optional): the four SDF evaluations of the element, kept for the
 // adjoint as 10 arrays of stride sdf_stride at index idx: phi_B(e1*), phi_B(e2*),
 // grad_B(e2*) (3), phi_A(e2*), phi_A(e1*), grad_A(e1*) in A's frame (3).
-// Sphere tracing of a witness onto its own body's SDF surface (Supplement,
-// mesh-SDF discrepancies): `iters` steps x <- x - phi(x) u along the fixed
-// direction u = grad phi(x_0) / |grad phi(x_0)|, in the body's own frame.
-__device__ __forceinline__ V3 trace_to_surface(const Body& b, V3 x, int iters, float tau, float it) {
-  Sdf s = body_sdf(b, x, tau, it);
-  const V3 u = s.g * rsq(dot(s.g, s.g));
-  for (int i = 0; i < iters; ++i) {
-    if (i) s = body_sdf(b, x, tau, it);
-    x = fma3(-s.phi, u, x);
-  }
-  return x;
-}
-
 __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSmem& sm,
                                               const PairBodies& bb, const EdgePair& ep,
                                               const Witness& w, float rowL, float colL,

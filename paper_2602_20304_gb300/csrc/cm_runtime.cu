@@ -177,13 +177,11 @@ LaunchCfg pick_cfg(const cm_context* c, int bwd, int n_pairs, int flags) {
   return it != c->tuned.end() ? it->second : default_cfg(c, bwd, n_pairs);
 }
 
-// The adjoint covers the plain manifold only: no pre-selection, no sphere
-// tracing, no superquadric unions.  Call with the context lock held.
+// What the adjoint does not cover: pre-selection.  Call with the context lock held.
 cm_status adjoint_supported(const cm_context* c, const cm_params* p) {
+  (void)c;
   if (p->top_verts || p->top_edges)
     return fail(CM_ERR_INVALID_ARG, "the adjoint does not support pre-selection (top_verts / top_edges)");
-  if (p->trace_iters) return fail(CM_ERR_INVALID_ARG, "the adjoint does not support sphere tracing (trace_iters)");
-  if (c->has_sq_union) return fail(CM_ERR_INVALID_ARG, "the adjoint is not built for SQ_UNION geometry");
   return CM_OK;
 }
 
@@ -421,7 +419,6 @@ cm_status cm_create_geometry(cm_context* c, const cm_geometry_desc* d, int32_t* 
     h.dims[0] = h.dims[1] = h.dims[2] = 1.f;
     for (int l = 0; l < d->n_planes / 3; ++l) pack_sq(d->planes + 12 * l, c->planes);
     h.n_planes = kSqRows * (d->n_planes / 3);
-    c->has_sq_union = true;
   } else {
     for (int i = 0; i < d->n_planes; ++i)
       c->planes.push_back(make_float4(d->planes[4 * i], d->planes[4 * i + 1], d->planes[4 * i + 2], d->planes[4 * i + 3]));

@@ -216,31 +216,32 @@ def support(geom: Geometry, dims, u):
 
 def superellipsoid_surface(rings, segs, scale, eps1, eps2):
     """Mesh of one superquadric's surface in its own frame: ``rings`` latitude rings of
-    ``segs`` points plus the two poles, from the standard superellipsoid parametrisation
+    ``segs`` points from the standard superellipsoid parametrisation
     (x, y, z) = (a C(eta)^eps1 C(w)^eps2, b C(eta)^eps1 S(w)^eps2, c S(eta)^eps1) with
-    C(t)^e = sign(cos t)|cos t|^e and S(t)^e = sign(sin t)|sin t|^e.  Every vertex lies on
-    the surface.  Returns (points (V, 3) float64, edges (E, 2)): ring, meridian and pole
-    edges."""
+    C(t)^e = sign(cos t)|cos t|^e and S(t)^e = sign(sin t)|sin t|^e, at
+    eta_i = -pi/2 + pi (i + 1/2) / rings and w_j = 2 pi (j + 1/2) / segs (``rings`` even,
+    ``segs`` a multiple of 4, so that no eta_i is 0 and no w_j a multiple of pi/2).
+    Every vertex lies on the surface and none on a principal plane (x = 0, y = 0 or z = 0)
+    or at a pole, where a superquadric's curvature is singular for exponents above 1 (its
+    Hessian has |x~|^(2/eps - 2) terms); the polar caps are closed by their rings.  Returns (points (V, 3) float64, edges (E, 2)): ring and
+    meridian edges."""
     def pw(c, e):
         return np.sign(c) * np.abs(c) ** e
+    if rings % 2 or segs % 4:
+        raise ValueError("rings must be even and segs a multiple of 4 (no vertex on a principal plane)")
     a, b, c = scale
-    eta = -np.pi / 2 + np.pi * np.arange(1, rings + 1) / (rings + 1)
-    om = 2 * np.pi * np.arange(segs) / segs
+    eta = -np.pi / 2 + np.pi * (np.arange(rings) + 0.5) / rings
+    om = 2 * np.pi * (np.arange(segs) + 0.5) / segs
     E, W = np.meshgrid(eta, om, indexing="ij")
     pts = np.stack([a * pw(np.cos(E), eps1) * pw(np.cos(W), eps2),
                     b * pw(np.cos(E), eps1) * pw(np.sin(W), eps2),
                     c * pw(np.sin(E), eps1) * np.ones_like(W)], -1).reshape(-1, 3)
-    pts = np.concatenate([pts, [[0.0, 0.0, -c], [0.0, 0.0, c]]])
-    south, north = rings * segs, rings * segs + 1
     edges = []
     for i in range(rings):
         for j in range(segs):
             edges.append((i * segs + j, i * segs + (j + 1) % segs))
             if i + 1 < rings:
                 edges.append((i * segs + j, (i + 1) * segs + j))
-    for j in range(segs):
-        edges.append((south, j))
-        edges.append(((rings - 1) * segs + j, north))
     return pts, np.array(edges, dtype=np.int32)
 
 

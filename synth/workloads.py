@@ -183,7 +183,7 @@ def config_mixed_pooled(n=65536, pool=4096, seed=SEED_BASE + 4):
     return Workload("mixed-uneven-pooled", geoms, pg, poses, dims, tau)
 
 
-SQ_RESOLUTIONS = ((4, 10), (3, 8), (2, 8), (2, 6), (1, 6), (1, 4))
+SQ_RESOLUTIONS = ((4, 12), (4, 8), (2, 12), (2, 8), (2, 4))
 
 
 def random_sq_union(rng, n_prims, step=0.22, scale=(0.12, 0.28), eps=(0.3, 1.5), max_verts=256,

@@ -79,3 +79,50 @@ def test_one_unit_exponent_primitive_equals_the_ellipsoid_kind(engine):
     a, _ = run(engine, w_ell)
     b, _ = run(engine, w_sq)
     assert np.abs(a - b).max() < 2e-5
+
+
+@pytest.mark.parametrize("n_prims,n", [(1, 8), (3, 8), (5, 4)])
+def test_union_adjoint_matches_oracle_autograd(engine, n_prims, n):
+    """dL/d poses of multi-superquadric pairs (every vertex and edge pair) against the
+    FP64 oracle's autograd, relative 1e-3 of each pair's largest component."""
+    import oracle
+    from _parity import oracle_params
+    from paper_2602_20304_gb300.engine import workload_tensors
+    w = synth.config_sq_union(n=n, n_prims=n_prims, pool=3, seed=synth.SEED_BASE + 70 + n_prims)
+    ids = engine.add_geometries(w.geoms)
+    pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+    params = engine.params()
+    g = np.random.default_rng(n_prims).normal(size=(n, 8, 8))
+    gp, gd = engine.backward(pg, poses, dims, tau, torch.as_tensor(g, dtype=torch.float32, device="cuda"), params)
+    torch.cuda.synchronize()
+    engine.check()
+    gp = gp.cpu().numpy().astype(np.float64)
+    op, _ = oracle.batch_manifold_grad(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, g, oracle_params(params))
+    rel = np.abs(gp - op).max(1) / np.abs(op).max(1)
+    print(f"sq union L={n_prims} grad rel", rel.max())
+    assert np.isfinite(gp).all() and rel.max() <= 1e-3
+    assert np.abs(gd.cpu().numpy()).max() == 0.0     # dims are unused by the union kind
+
+
+@pytest.mark.parametrize("cfg,n", [(1, 16), (2, 12), ("sq", 6)])
+@pytest.mark.parametrize("iters", [1, 3])
+def test_traced_adjoint_matches_oracle_autograd(engine, cfg, n, iters):
+    """The adjoint through sphere tracing (fixed direction from the SDF gradient at the QP
+    witness, unrolled steps) against the oracle's autograd."""
+    import oracle
+    from _parity import oracle_params
+    from paper_2602_20304_gb300.engine import workload_tensors
+    w = synth.config_sq_union(n=n, n_prims=3, pool=3) if cfg == "sq" else synth.make_config(cfg, n)
+    ids = engine.add_geometries(w.geoms)
+    pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+    params = engine.params(trace_iters=iters)
+    g = np.random.default_rng(iters).normal(size=(n, 8, 8))
+    gp, gd = engine.backward(pg, poses, dims, tau, torch.as_tensor(g, dtype=torch.float32, device="cuda"), params)
+    torch.cuda.synchronize()
+    engine.check()
+    got = np.concatenate([gp.cpu().numpy(), gd.cpu().numpy()], 1).astype(np.float64)
+    op, od = oracle.batch_manifold_grad(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, g, oracle_params(params))
+    ref = np.concatenate([op, od], 1)
+    rel = np.abs(got - ref).max(1) / np.abs(ref).max(1)
+    print(f"trace {iters} on {cfg} grad rel", rel.max())
+    assert np.isfinite(got).all() and rel.max() <= 1e-3

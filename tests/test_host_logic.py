@@ -147,17 +147,12 @@ def test_selection_and_tracing_limits(api, ctx):
     assert api.cm_default_params().trace_iters == 0
 
 
-def test_adjoint_refuses_tracing_and_sq_unions(api, ctx):
+def test_adjoint_refuses_preselection(api, ctx):
     import ctypes
     lib = api._lib
     add(api, ctx, synth.primitive_geometry(synth.KIND_BOX, (0.5, 0.5, 0.5)))
     v = ctypes.c_void_p(8)
-    p = api.cm_default_params(trace_iters=2)
+    p = api.cm_default_params(top_edges=4)
     assert lib.cm_contact_manifold_bwd(ctx, 1, v, v, None, None, ctypes.byref(p), v, v, None, None) == \
         api.CM_ERR_INVALID_ARG
-    assert "tracing" in api.cm_last_error()
-    add(api, ctx, sq_body())
-    p = api.cm_default_params()
-    assert lib.cm_contact_manifold_bwd(ctx, 1, v, v, None, None, ctypes.byref(p), v, v, None, None) == \
-        api.CM_ERR_INVALID_ARG
-    assert "SQ_UNION" in api.cm_last_error()
+    assert "pre-selection" in api.cm_last_error()
