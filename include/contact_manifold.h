@@ -122,7 +122,8 @@ typedef struct {
    * generate contacts, each a SoftSort average (temperature tau) of the
    * vertices / edge endpoints; E-E witnesses are then also weighted by the soft
    * indicator of lying inside their own body.  0 keeps all (no selection).
-   * At most CM_MAX_SELECT each; forward only (the adjoint rejects them). */
+   * At most CM_MAX_SELECT each.  The adjoint differentiates through the
+   * selection too (the SoftSort weights through the vertex depths). */
   int32_t top_verts;
   int32_t top_edges;
   /* Sphere tracing of E-E witness points (Supplement, mesh-SDF
@@ -186,8 +187,7 @@ cm_status cm_contact_manifold_fwd(cm_context* ctx, int32_t n_pairs, const int32_
  * grad_dims: device, n_pairs x 6 or NULL, receives dL/d dims of A then B (the
  *   dims in use; zero for hulls).
  * The forward is recomputed per pair inside the call; nothing is kept between
- * the forward and backward calls.  Pre-selection in params is refused
- * (CM_ERR_INVALID_ARG). */
+ * the forward and backward calls. */
 cm_status cm_contact_manifold_bwd(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms,
                                   const float* poses, const float* dims, const float* tau,
                                   const cm_params* params, const float* grad_out, float* grad_poses,

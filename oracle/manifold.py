@@ -46,14 +46,18 @@ def _t(x):
 
 
 class _Body:
+    """A posed body.  Its geometry takes the dtype of ``pose`` (float64 everywhere in the
+    parity path; float32 only where a test measures how a plain FP32 evaluation of these
+    same steps deviates)."""
+
     def __init__(self, geom, pose, dims, tau):
         self.kind = int(geom.kind)
         self.R = quat_to_rot(pose[:4])
         self.t = pose[4:7]
         self.dims = dims
-        self.planes = _t(geom.planes)
+        self.planes = torch.as_tensor(np.asarray(geom.planes), dtype=pose.dtype)
         self.edges = torch.as_tensor(np.asarray(geom.edges), dtype=torch.long)
-        vloc = local_vertices(self.kind, _t(geom.verts), dims)
+        vloc = local_vertices(self.kind, torch.as_tensor(np.asarray(geom.verts), dtype=pose.dtype), dims)
         self.verts = vloc @ self.R.T + self.t
         self.tau = tau
 

@@ -246,14 +246,14 @@ CM_HD void body_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_
   }
 }
 
-// Reverse of sdf_planes2: the value at y1 (adjoint phibar1) and the gradient
-// at y2 (adjoint gbar2) in one pass over the (pre-scaled) planes.
+// Reverse of sdf_planes2: the value at y1 (adjoint phibar1) and the value and
+// gradient at y2 (adjoints phibar2, gbar2) in one pass over the (pre-scaled) planes.
 CM_HD void sdf_planes2_bwd(V3 y1, V3 y2, const float4* P, int nP, const Sdf& f1, const Sdf& f2, float inv_tau,
-                           float phibar1, V3 gbar2, V3& ybar1, V3& ybar2) {
+                           float phibar1, float phibar2, V3 gbar2, V3& ybar1, V3& ybar2) {
   const float k = inv_tau * kLog2e, ik = rcp(k);
   const float2 X = make_float2(y1.x, y2.x), Y = make_float2(y1.y, y2.y), Z = make_float2(y1.z, y2.z);
   const float2 mk = make_float2(-f1.phi * k, -f2.phi * k);
-  const float base2 = -dot(gbar2, f2.g) * inv_tau;
+  const float base2 = phibar2 - dot(gbar2, f2.g) * inv_tau;
   const float gk = inv_tau * ik;
   float2 ax = dup2(0.f), ay = dup2(0.f), az = dup2(0.f);
   for (int i = 0; i < nP; ++i) {
@@ -270,14 +270,29 @@ CM_HD void sdf_planes2_bwd(V3 y1, V3 y2, const float4* P, int nP, const Sdf& f1,
   ybar2 += v3(ax.y, ay.y, az.y) * ik;
 }
 
-// Reverse of body_sdf2 (value at y1, gradient at y2).
+// Reverse of body_sdf2 (value at y1; value and gradient at y2).
 CM_HD void body_sdf2_bwd(const Body& b, V3 y1, V3 y2, const Sdf& f1, const Sdf& f2, float tau, float inv_tau,
-                         float phibar1, V3 gbar2, V3& ybar1, V3& ybar2, V3& dbar) {
+                         float phibar1, float phibar2, V3 gbar2, V3& ybar1, V3& ybar2, V3& dbar) {
   if (b.kind == kHull) {
-    sdf_planes2_bwd(y1, y2, b.planes, b.n_planes, f1, f2, inv_tau, phibar1, gbar2, ybar1, ybar2);
+    sdf_planes2_bwd(y1, y2, b.planes, b.n_planes, f1, f2, inv_tau, phibar1, phibar2, gbar2, ybar1, ybar2);
   } else {
     body_sdf_bwd(b, y1, f1, tau, inv_tau, phibar1, v3(0.f, 0.f, 0.f), ybar1, dbar);
-    body_sdf_bwd(b, y2, f2, tau, inv_tau, 0.f, gbar2, ybar2, dbar);
+    body_sdf_bwd(b, y2, f2, tau, inv_tau, phibar2, gbar2, ybar2, dbar);
+  }
+}
+
+// Adds a local-frame adjoint to a pre-selected item's export slot (shared memory).
+CM_HD void export3(float* dst, V3 v) {
+  if (dst) {
+#if defined(__CUDA_ARCH__)
+    atomicAdd(dst, v.x);
+    atomicAdd(dst + 1, v.y);
+    atomicAdd(dst + 2, v.z);
+#else
+    dst[0] += v.x;
+    dst[1] += v.y;
+    dst[2] += v.z;
+#endif
   }
 }
 
@@ -452,7 +467,7 @@ CM_HD V3 push_point_bwd(const Frame& F, V3 v, V3 ybar, Adj& adj) {
 // the score s = -w d.
 template <bool kOfA>
 CM_HD void vs_bwd(const Frame& F, const Body& A, const Body& B, float4 vL, V3 vB, const float (&yb)[8], float sb,
-                  Adj& adj) {
+                  Adj& adj, float* vexp = nullptr) {
   const float tau = F.tau, it = F.inv_tau;
   if (kOfA) {
     Sdf f = body_sdf(B, vB, tau, it);
@@ -465,6 +480,7 @@ CM_HD void vs_bwd(const Frame& F, const Body& A, const Body& B, float4 vL, V3 vB
     V3 vl = v3(vL.x, vL.y, vL.z);
     V3 vbar = push_point_bwd(F, vl, pb, adj);
     map_vertex_bwd(A.kind, vl, vL.w, A.dims, vbar, adj.dA);
+    export3(vexp, vbar);
   } else {
     V3 x = mulT(F.R, vB - F.t);
     Sdf f = body_sdf(A, x, tau, it);
@@ -479,6 +495,7 @@ CM_HD void vs_bwd(const Frame& F, const Body& A, const Body& B, float4 vL, V3 vB
     body_sdf_bwd(A, x, f, tau, it, phib, gb, xb, adj.dA);
     V3 pb = v3(yb[0], yb[1], yb[2]) + pull_point_bwd(F, vB, xb, adj);
     map_vertex_bwd(B.kind, vB, vL.w, B.dims, pb, adj.dB);
+    export3(vexp, pb);
   }
 }
 
@@ -494,7 +511,8 @@ CM_HD V3 xyz(float4 f) { return v3(f.x, f.y, f.z); }
 // Backpropagates e1bar, e1Lbar, e2bar and extra alpha / con adjoints through the
 // witness interpolation and the QP into the parameters.
 CM_HD void witness_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g,
-                       const QPPre& q, const QPOut& o, V3 e1b, V3 e1Lb, V3 e2b, float conb, Adj& adj) {
+                       const QPPre& q, const QPOut& o, V3 e1b, V3 e1Lb, V3 e2b, float conb, Adj& adj,
+                       float* eAexp = nullptr, float* eBexp = nullptr) {
   V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
   V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L);
   float ab1 = dot(e1b, a1 - a0) + dot(e1Lb, a1L - a0L);
@@ -509,6 +527,15 @@ CM_HD void witness_bwd(const Frame& F, const Body& A, const Body& B, const Param
   map_vertex_bwd(A.kind, a1L, g.a1L.w, A.dims, l1, adj.dA);
   map_vertex_bwd(B.kind, b0, g.b0.w, B.dims, b0b, adj.dB);
   map_vertex_bwd(B.kind, b1, g.b1.w, B.dims, b1b, adj.dB);
+  // pre-selected edges: their endpoints' local adjoints feed the selection's reverse
+  if (eAexp) {
+    export3(eAexp, l0);
+    export3(eAexp + 3, l1);
+  }
+  if (eBexp) {
+    export3(eBexp, b0b);
+    export3(eBexp + 3, b1b);
+  }
 }
 
 // ---------------------------------------------------------------- E-E element
@@ -530,7 +557,7 @@ struct SdfQuad {
 template <class Upstream>
 CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float rowL,
                   float colL, const QPOut* stored, Upstream&& up, float& t1, float& t2, Adj& adj,
-                  const SdfQuad* sdf = nullptr) {
+                  const SdfQuad* sdf = nullptr, float* eAexp = nullptr, float* eBexp = nullptr) {
   const float tau = F.tau, it = F.inv_tau;
   V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
   V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L);
@@ -573,6 +600,12 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
   float cl = sigmoid(-dot(nuA, nuB) * it);
   float nn1 = ex2((rowL - dbar_qp) * F.k2), nn2 = ex2((colL - dbar_qp) * F.k2);
   float con = o.con;
+  // pre-selection's safeguard (Supplement B): each witness inside its own body
+  const bool guard = p.top_verts > 0 || p.top_edges > 0;
+  const float sg1 = guard ? sigmoid(-SA1.phi * it) : 1.f, sg2 = guard ? sigmoid(-SB2.phi * it) : 1.f;
+  const float pr1 = pen1, pr2 = pen2;  // the penetration indicators without the safeguard
+  pen1 *= sg1;
+  pen2 *= sg2;
   float w1 = con * cl * pen1 * nn1, w2 = con * cl * pen2 * nn2;
   EECand c;
   c.y1[0] = e1.x; c.y1[1] = e1.y; c.y1[2] = e1.z; c.y1[3] = g1 * dbar;
@@ -596,8 +629,11 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
   float penb1 = wb1 * con * cl * nn1, penb2 = wb2 * con * cl * nn2;
   t1 = wb1 * con * cl * pen1 * nn1;
   t2 = wb2 * con * cl * pen2 * nn2;
-  float phibB1 = -penb1 * sigmoid_grad_from(pen1) * it;
-  float phibA2 = -penb2 * sigmoid_grad_from(pen2) * it;
+  // pen_b here includes the safeguard factor: split the adjoint between the two
+  float phibB1 = -penb1 * sg1 * sigmoid_grad_from(pr1) * it;
+  float phibA2 = -penb2 * sg2 * sigmoid_grad_from(pr2) * it;
+  const float phibA1 = guard ? -penb1 * pr1 * sigmoid_grad_from(sg1) * it : 0.f;
+  const float phibB2 = guard ? -penb2 * pr2 * sigmoid_grad_from(sg2) * it : 0.f;
   float cclb = -clb * sigmoid_grad_from(cl) * it;
   V3 nuAb = nuB * cclb, nuBb = nuA * cclb;
   float xb1 = gb1 * (1.f - g1 * g1) * it;
@@ -611,11 +647,11 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
   V3 e1b = Db + v3(yb1[0], yb1[1], yb1[2]);
   V3 e2b = -Db + v3(yb2[0], yb2[1], yb2[2]);
   // SDF reverses (one pass per body for its two points)
-  body_sdf2_bwd(B, e1, e2, SB1, SB2, tau, it, phibB1, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
+  body_sdf2_bwd(B, e1, e2, SB1, SB2, tau, it, phibB1, phibB2, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
   V3 x2b = v3(0.f, 0.f, 0.f), e1Lb = v3(0.f, 0.f, 0.f);
   add_outer(adj.R, nuAb, nuAL);
-  body_sdf2_bwd(A, x2, e1L, SA2, SA1, tau, it, phibA2, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b, e1Lb,
-                adj.dA);
+  body_sdf2_bwd(A, x2, e1L, SA2, SA1, tau, it, phibA2, phibA1, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b,
+                e1Lb, adj.dA);
   e2b += pull_point_bwd(F, e2, x2b, adj);
   if (nt) {  // traced e1 = R_rel e1L + t_rel; back through both traces to the QP witnesses
     e1Lb += push_point_bwd(F, e1L, e1b, adj);
@@ -623,12 +659,12 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
     e2b = trace_bwd(B, e2q, nt, tau, it, e2b, adj.dB);
     e1b = v3(0.f, 0.f, 0.f);
   }
-  witness_bwd(F, A, B, p, g, q, o, e1b, e1Lb, e2b, conb, adj);
+  witness_bwd(F, A, B, p, g, q, o, e1b, e1Lb, e2b, conb, adj, eAexp, eBexp);
 }
 
 // Distance-matrix adjoint of one element: Dbar flows through dbar = |e1* - e2*|.
 CM_HD void ee_dbar_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float Dbar,
-                       const QPOut* stored, Adj& adj) {
+                       const QPOut* stored, Adj& adj, float* eAexp = nullptr, float* eBexp = nullptr) {
   V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
   QPPre q = qp_setup(a0, a1, b0, b1, p.w_reg);
   QPOut o = stored ? *stored : qp_solve(q, p.w_reg, p);
@@ -637,7 +673,7 @@ CM_HD void ee_dbar_bwd(const Frame& F, const Body& A, const Body& B, const Param
   float r2 = dot(D, D);
   if (!(r2 > 0.f)) return;
   V3 Db = D * (Dbar * rsq(r2));
-  witness_bwd(F, A, B, p, g, q, o, Db, v3(0.f, 0.f, 0.f), -Db, 0.f, adj);
+  witness_bwd(F, A, B, p, g, q, o, Db, v3(0.f, 0.f, 0.f), -Db, 0.f, adj, eAexp, eBexp);
 }
 
 // ---------------------------------------------------------------- pose epilogue

@@ -34,15 +34,40 @@ struct BwdShared {
   float adj[18];      // CTA-reduced Adj: R (9), t (3), dA (3), dB (3)
 };
 
-__device__ __forceinline__ EEGeom ee_geom(const PairSmem& sm, int k, int l) {
-  uint32_t ea = sm.eA[k], eb = sm.eB[l];
+// Edge pair (k, l) from the staged endpoint arrays (pre-selected or not).  The
+// capsule-template cap signs come with the selected payloads, else from the
+// geometry's template rows in global memory.
+__device__ __forceinline__ EEGeom ee_geom(const FwdArgs& a, const PairShared& ps, const PairSmem& sm, int k, int l) {
+  const int es = sm.es;
   EEGeom g;
-  g.a0 = sm.vA[ea & 0xffffu];
-  g.a1 = sm.vA[ea >> 16];
-  g.a0L = sm.vAl[ea & 0xffffu];
-  g.a1L = sm.vAl[ea >> 16];
-  g.b0 = sm.vB[eb & 0xffffu];
-  g.b1 = sm.vB[eb >> 16];
+  g.a0 = make_float4(sm.eA6[k], sm.eA6[es + k], sm.eA6[2 * es + k], 0.f);
+  g.a1 = make_float4(sm.eA6[3 * es + k], sm.eA6[4 * es + k], sm.eA6[5 * es + k], 0.f);
+  g.a0L = make_float4(sm.eAl6[k], sm.eAl6[es + k], sm.eAl6[2 * es + k], 0.f);
+  g.a1L = make_float4(sm.eAl6[3 * es + k], sm.eAl6[4 * es + k], sm.eAl6[5 * es + k], 0.f);
+  g.b0 = make_float4(sm.eB6[l], sm.eB6[es + l], sm.eB6[2 * es + l], 0.f);
+  g.b1 = make_float4(sm.eB6[3 * es + l], sm.eB6[4 * es + l], sm.eB6[5 * es + l], 0.f);
+  if (ps.kindA == kCapsule) {
+    if (ps.kv[2]) {
+      const float* v = sel_area(sm).item[2] + 14 * k;
+      g.a0L.w = v[12];
+      g.a1L.w = v[13];
+    } else {
+      const uint32_t e = sm.eA[k];
+      g.a0L.w = a.verts[ps.voffA + (e & 0xffffu)].w;
+      g.a1L.w = a.verts[ps.voffA + (e >> 16)].w;
+    }
+  }
+  if (ps.kindB == kCapsule) {
+    if (ps.kv[3]) {
+      const float* v = sel_area(sm).item[3] + 8 * l;
+      g.b0.w = v[6];
+      g.b1.w = v[7];
+    } else {
+      const uint32_t e = sm.eB[l];
+      g.b0.w = a.verts[ps.voffB + (e & 0xffffu)].w;
+      g.b1.w = a.verts[ps.voffB + (e >> 16)].w;
+    }
+  }
   return g;
 }
 
@@ -105,7 +130,22 @@ struct BwdPair {
   PairBodies bb;
   float *Dm, *T1, *T2, *QA1, *QA2, *QCN, *rowR, *colC;
   int nvs, neB, nee, K;
+  float* sadj;  // pre-selection adjoint slots (null when nothing is selected)
 };
+
+// Export slots of the pre-selected items (see kSelAdjFloats): A's vertices,
+// B's vertices, A's edges, B's edges, then the vertex-depth adjoints of A and B.
+__device__ __forceinline__ float* vexp_of(const BwdPair& P, int c) {
+  if (!P.sadj) return nullptr;
+  if (c < P.ps->nvA) return P.ps->kv[0] ? P.sadj + 3 * c : nullptr;
+  return P.ps->kv[1] ? P.sadj + 3 * kMaxSel + 3 * (c - P.ps->nvA) : nullptr;
+}
+__device__ __forceinline__ float* eAexp_of(const BwdPair& P, int k) {
+  return P.sadj && P.ps->kv[2] ? P.sadj + 6 * kMaxSel + 6 * k : nullptr;
+}
+__device__ __forceinline__ float* eBexp_of(const BwdPair& P, int l) {
+  return P.sadj && P.ps->kv[3] ? P.sadj + 12 * kMaxSel + 6 * l : nullptr;
+}
 
 template <int KMAX>
 __device__ __forceinline__ void shb_reduce(const float (&shb)[KMAX], int K, BwdShared& bs) {
@@ -132,8 +172,9 @@ __device__ __forceinline__ void vs_reverse_phase(const BwdPair P) {
     const float s = vs_candidate(ps, P.sm, P.bb, c, y);
     float yb[8], sb;
     ss_bwd<KMAX>(*P.bs, P.K, P.F.inv_tau, P.F.k2, y, s, yb, sb, shb);
-    if (c < ps.nvA) vs_bwd<true>(P.F, P.bb.A, P.bb.B, P.sm.vAl[c], ld3(P.sm.vA[c]), yb, sb, adj);
-    else vs_bwd<false>(P.F, P.bb.A, P.bb.B, P.sm.vB[c - ps.nvA], ld3(P.sm.vB[c - ps.nvA]), yb, sb, adj);
+    if (c < ps.nvA) vs_bwd<true>(P.F, P.bb.A, P.bb.B, P.sm.vAl[c], ld3(P.sm.vA[c]), yb, sb, adj, vexp_of(P, c));
+    else
+      vs_bwd<false>(P.F, P.bb.A, P.bb.B, P.sm.vB[c - ps.nvA], ld3(P.sm.vB[c - ps.nvA]), yb, sb, adj, vexp_of(P, c));
   }
   shb_reduce<KMAX>(shb, P.K, *P.bs);
   adj_reduce(adj, P.bs->adj);
@@ -149,13 +190,15 @@ __device__ __forceinline__ void fixup_phase(const BwdPair P) {
   Adj adj;
   adj_zero(adj);
   if (id >= 0 && id < P.nvs) {
-    if (id < ps.nvA) vs_bwd<true>(P.F, P.bb.A, P.bb.B, P.sm.vAl[id], ld3(P.sm.vA[id]), zero, sx, adj);
-    else vs_bwd<false>(P.F, P.bb.A, P.bb.B, P.sm.vB[id - ps.nvA], ld3(P.sm.vB[id - ps.nvA]), zero, sx, adj);
+    if (id < ps.nvA) vs_bwd<true>(P.F, P.bb.A, P.bb.B, P.sm.vAl[id], ld3(P.sm.vA[id]), zero, sx, adj, vexp_of(P, id));
+    else
+      vs_bwd<false>(P.F, P.bb.A, P.bb.B, P.sm.vB[id - ps.nvA], ld3(P.sm.vB[id - ps.nvA]), zero, sx, adj,
+                    vexp_of(P, id));
   } else if (id >= P.nvs) {
     const int e = id - P.nvs, i = e >> 1, b = e & 1, kk = i / P.neB, ll = i - kk * P.neB;
     float t1, t2;
     const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
-    ee_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(P.sm, kk, ll), P.sm.rowL[kk], P.sm.colL[ll], &qs,
+    ee_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, ps, P.sm, kk, ll), P.sm.rowL[kk], P.sm.colL[ll], &qs,
            [&](const EECand&, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
              for (int c = 0; c < 8; ++c) {
                yb1[c] = 0.f;
@@ -164,7 +207,7 @@ __device__ __forceinline__ void fixup_phase(const BwdPair P) {
              sb1 = b == 0 ? sx : 0.f;
              sb2 = b == 1 ? sx : 0.f;
            },
-           t1, t2, adj);
+           t1, t2, adj, nullptr, eAexp_of(P, kk), eBexp_of(P, ll));
     atomicAdd(&P.T1[i], t1);
     atomicAdd(&P.T2[i], t2);
     atomicAdd(&P.rowR[kk], t1);
@@ -189,7 +232,113 @@ __device__ __forceinline__ void dbar_phase(const BwdPair P) {
     const float Db = (nn1 * P.rowR[k] - P.T1[i] + nn2 * P.colC[l] - P.T2[i]) * it;
     if (Db != 0.f) {
       const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
-      ee_dbar_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(P.sm, k, l), Db, &qs, adj);
+      ee_dbar_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, *P.ps, P.sm, k, l), Db, &qs, adj, eAexp_of(P, k),
+                  eBexp_of(P, l));
+    }
+  }
+  adj_reduce(adj, P.bs->adj);
+}
+
+// Reverse of the four soft selections (one warp each): the items' local-frame
+// payload adjoints xbar_k give every item's score adjoint through
+// Gamma_ki = exp(-|s^_k - s_i| / tau) / Z_k (and s^_k through the k-th top
+// item), and scores pass to the vertex depths (-m for a vertex, -(m_0 + m_1)/2
+// for an edge).  Needs the pair's original vertices / edges staged again.
+__device__ __forceinline__ void sel_reverse_phase(const BwdPair P) {
+  const PairShared& ps = *P.ps;
+  const PairSmem& sm = P.sm;
+  const SelArea A = sel_area(sm);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  float* mbar[2] = {P.sadj + kSelAdjFloats, P.sadj + kSelAdjFloats + sm.vs};
+  const float k2 = P.F.k2, it = P.F.inv_tau;
+  const int es = sm.es;
+  // score adjoint of item i of selection `kind` -> depth adjoints
+  auto to_depths = [&](int kind, int i, float sbar) {
+    if (kind < 2) {
+      atomicAdd(&mbar[kind][i], -sbar);
+    } else {
+      const uint32_t e = kind == 2 ? sm.eA[i] : sm.eB[i];
+      atomicAdd(&mbar[kind - 2][e & 0xffffu], -0.5f * sbar);
+      atomicAdd(&mbar[kind - 2][e >> 16], -0.5f * sbar);
+    }
+  };
+  for (int kind = warp; kind < 4; kind += nwarps) {
+    const int K = ps.kv[kind];
+    if (!K) continue;
+    const int n = kind == 0 ? ps.nvA0 : kind == 1 ? ps.nvB0 : kind == 2 ? ps.neA0 : ps.neB0;
+    const int P3 = kind < 2 ? 3 : 6;                       // local payload width
+    const int off = kind == 0 ? 3 : kind == 1 ? 0 : kind == 2 ? 6 : 0;  // local part in the payload
+    const float* xb = P.sadj + (kind == 0 ? 0 : kind == 1 ? 3 * kMaxSel : kind == 2 ? 6 * kMaxSel : 12 * kMaxSel);
+    const float* item = A.item[kind];
+    const float* info = A.info[kind];
+    const int W = sel_width(kind);
+    for (int k = 0; k < K; ++k) {
+      const float sh = info[k], iz = 1.f / info[kMaxSel + k];
+      const float* xk = xb + P3 * k;
+      float xs = 0.f;  // xbar_k . x_sel_k
+      for (int c = 0; c < P3; ++c) xs = fmaf(xk[c], item[W * k + off + c], xs);
+      float shb = 0.f;
+      for (int i = lane; i < n; i += 32) {
+        const float si = sel_score(sm, A, kind, i);
+        float xi[6];
+        if (kind == 0) {
+          const float4 v = sm.vAl[i];
+          xi[0] = v.x; xi[1] = v.y; xi[2] = v.z;
+        } else if (kind == 1) {
+          const float4 v = sm.vB[i];
+          xi[0] = v.x; xi[1] = v.y; xi[2] = v.z;
+        } else {
+          const float* src = kind == 2 ? sm.eAl6 : sm.eB6;
+          for (int c = 0; c < 6; ++c) xi[c] = src[c * es + i];
+        }
+        float ax = -xs;
+        for (int c = 0; c < P3; ++c) ax = fmaf(xk[c], xi[c], ax);
+        const float d = sh - si;
+        const float gam = ex2(-fabsf(d) * k2) * iz;
+        const float t = gam * ax * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * it;
+        if (t != 0.f) to_depths(kind, i, t);
+        shb -= t;
+      }
+      shb = warp_sum(shb);
+      if (lane == 0 && shb != 0.f) to_depths(kind, __float_as_int(info[2 * kMaxSel + k]), shb);
+    }
+  }
+}
+
+// Depth adjoints: m_A[i] = phi_B(v_i) for A's original vertices and
+// m_B[j] = phi_A(v_j) for B's, back to both poses and dims.
+__device__ __forceinline__ void depth_adjoint_phase(const BwdPair P) {
+  const PairShared& ps = *P.ps;
+  const PairSmem& sm = P.sm;
+  const float* mbarA = P.sadj + kSelAdjFloats;
+  const float* mbarB = mbarA + sm.vs;
+  const float tau = P.F.tau, it = P.F.inv_tau;
+  Adj adj;
+  adj_zero(adj);
+  for (int i = threadIdx.x; i < ps.nvA0 + ps.nvB0; i += blockDim.x) {
+    if (i < ps.nvA0) {
+      const float mb = mbarA[i];
+      if (mb == 0.f) continue;
+      const V3 y = ld3(sm.vA[i]);
+      const float4 vL = sm.vAl[i];
+      const Sdf f = body_sdf(P.bb.B, y, tau, it);
+      V3 yb = v3(0.f, 0.f, 0.f);
+      body_sdf_bwd(P.bb.B, y, f, tau, it, mb, v3(0.f, 0.f, 0.f), yb, adj.dB);
+      const V3 vl = v3(vL.x, vL.y, vL.z);
+      const V3 vb = push_point_bwd(P.F, vl, yb, adj);
+      map_vertex_bwd(ps.kindA, vl, vL.w, P.bb.A.dims, vb, adj.dA);
+    } else {
+      const int j = i - ps.nvA0;
+      const float mb = mbarB[j];
+      if (mb == 0.f) continue;
+      const float4 vv = sm.vB[j];
+      const V3 y = v3(vv.x, vv.y, vv.z);
+      const V3 x = mulT(P.F.R, y - P.F.t);
+      const Sdf f = body_sdf(P.bb.A, x, tau, it);
+      V3 xb = v3(0.f, 0.f, 0.f);
+      body_sdf_bwd(P.bb.A, x, f, tau, it, mb, v3(0.f, 0.f, 0.f), xb, adj.dA);
+      const V3 pb = pull_point_bwd(P.F, y, xb, adj);
+      map_vertex_bwd(ps.kindB, y, vv.w, P.bb.B.dims, pb, adj.dB);
     }
   }
   adj_reduce(adj, P.bs->adj);
@@ -230,6 +379,12 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     pair_stage(a, pi, ps, sm);
     __syncthreads();
     const PairBodies bb = pair_bodies(ps, sm);
+    float* sadj = nullptr;
+    if (ps.preselect) {
+      preselect_pair(a, ps, sm, bb);
+      sadj = sm.sadj;
+      for (int i = threadIdx.x; i < kSelAdjFloats + 2 * sm.vs; i += blockDim.x) sadj[i] = 0.f;
+    }
     const float k2 = ps.k2, it = ps.inv_tau;
     Frame F;
     F.R = ps.Rrel;
@@ -346,6 +501,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     P.bb = bb;
     P.Dm = Dm; P.T1 = T1; P.T2 = T2; P.QA1 = QA1; P.QA2 = QA2; P.QCN = QCN; P.rowR = rowR; P.colC = colC;
     P.nvs = nvs; P.neB = neB; P.nee = nee; P.K = K;
+    P.sadj = sadj;
     vs_reverse_phase<KMAX>(P);
     {
       Adj adj;
@@ -368,12 +524,12 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
         sq.A2.g = v3(0.f, 0.f, 0.f);
         sq.A1.phi = q[6 * st];
         sq.A1.g = v3(q[7 * st], q[8 * st], q[9 * st]);
-        ee_bwd(F, bb.A, bb.B, a.p, ee_geom(sm, k, l), sm.rowL[k], sm.colL[l], &qs,
+        ee_bwd(F, bb.A, bb.B, a.p, ee_geom(a, ps, sm, k, l), sm.rowL[k], sm.colL[l], &qs,
                [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
                  ss_bwd<KMAX>(bs, K, it, k2, cc.y1, cc.s1, yb1, sb1, shb);
                  ss_bwd<KMAX>(bs, K, it, k2, cc.y2, cc.s2, yb2, sb2, shb);
                },
-               t1, t2, adj, &sq);
+               t1, t2, adj, &sq, eAexp_of(P, k), eBexp_of(P, l));
         T1[i] = t1;
         T2[i] = t2;
         atomicAdd(&rowR[k], t1);
@@ -387,6 +543,18 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     __syncthreads();
     dbar_phase(P);
     __syncthreads();
+    if (sadj) {  // pre-selection: stage the original geometry again, then its reverse
+      if (threadIdx.x == 0) {
+        ps.nvA = ps.nvA0; ps.nvB = ps.nvB0; ps.neA = ps.neA0; ps.neB = ps.neB0;
+      }
+      __syncthreads();
+      pair_stage(a, pi, ps, sm);
+      __syncthreads();
+      sel_reverse_phase(P);
+      __syncthreads();
+      depth_adjoint_phase(P);
+      __syncthreads();
+    }
     if (threadIdx.x == 0) {
       Adj r;
       for (int i = 0; i < 9; ++i) r.R[i] = bs.adj[i];

@@ -57,7 +57,6 @@ cm_status cuda_fail(cudaError_t e, const char* what);
 cm_status sync_geometry_locked(cm_context* c);
 cm_status check_params(const cm_params* p);
 cm_status check_k(const cm_context* c, const cm_params* params);
-cm_status adjoint_supported(const cm_context* c, const cm_params* p);
 LaunchCfg pick_cfg(const cm_context* c, int bwd, int n_pairs, int flags);
 void shape(const cm_context* c, int bwd, const LaunchCfg& cfg, int n_pairs, SmemLayout& L, int& grid);
 size_t scratch_need(const cm_context* c, int bwd, int grid, int64_t stride);  // stride <= 0: max_e^2

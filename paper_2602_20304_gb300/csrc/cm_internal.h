@@ -22,7 +22,7 @@ static_assert(sizeof(GeomHeader) == 48, "GeomHeader layout");
 // Byte offsets of the per-CTA shared-memory carve-up (sized on the host from the
 // largest registered geometry).
 struct SmemLayout {
-  int vA, vAl, vB, pA, pB, eA, eB, rowL, colL, warp, eA6, eAl6, eB6, sel;
+  int vA, vAl, vB, pA, pB, eA, eB, rowL, colL, warp, eA6, eAl6, eB6, sel, sadj;
   int total;
   int max_v, max_e, max_p;
 };
@@ -60,9 +60,14 @@ struct LaunchCfg {
 constexpr int kMaxK = 16;
 constexpr int kMaxSel = 32;  // soft pre-selected items per body (CM_MAX_SELECT)
 constexpr int kSqRows = 5;   // device float4 rows per superquadric of an SQ_UNION
-// Pre-selection staging: vertex depths of both bodies (2 max_v) + the soft
-// selections: per body kMaxSel vertices (B frame 3 + A frame 3) and kMaxSel edges (12).
-constexpr int kSelFloats = 2 * kMaxSel * 6 + 2 * kMaxSel * 12 + 2 * kMaxSel * 6;
+// Pre-selection staging: vertex depths of both bodies (2 max_v) + the four soft
+// selections' payloads (7, 4, 14 and 8 floats per item: positions in B's frame,
+// A's local positions, capsule cap signs) and per selection s^_k, Z_k and the
+// index of the k-th top item.
+constexpr int kSelFloats = kMaxSel * (7 + 4 + 14 + 8) + 4 * 3 * kMaxSel;
+// Adjoint of a pre-selection: local-frame adjoints of the selected items
+// (3 + 3 + 6 + 6 floats) and the vertex-depth adjoints of both bodies (2 max_v).
+constexpr int kSelAdjFloats = kMaxSel * (3 + 3 + 6 + 6);
 constexpr int kWarpStateFloats = kMaxK * 9 + 10 + kMaxK;  // list, C, threshold, ids
 
 cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s);

@@ -23,6 +23,9 @@ struct PairShared {
   int bad;  // invalid geometry id
   int preselect;  // soft pre-selection active for this pair
   int trace;      // sphere-tracing steps of E-E witnesses
+  int nvA0, nvB0, neA0, neB0;  // counts before pre-selection
+  int kv[4];                   // selected counts (0: that selection is off)
+  int voffA, voffB;            // template rows of A and B in the vertex store
 };
 
 struct PairSmem {
@@ -37,6 +40,7 @@ struct PairSmem {
   float* eAl6;     // A's edge endpoints in A's frame, same layout
   float* eB6;      // B's edge endpoints, same layout
   float* sel;      // pre-selection: vertex depths of A and B, then the staged soft selections
+  float* sadj;     // adjoint kernel only: pre-selection adjoint slots (kSelAdjFloats + 2 vs)
   int es;          // SoA stride (largest edge count)
   int vs;          // vertex stride (largest vertex count)
   float* rowL;     // soft row minima of the E-E distance matrix (nn-Gamma_1)
@@ -60,6 +64,7 @@ __device__ __forceinline__ PairSmem carve(unsigned char* base, const SmemLayout&
   s.eAl6 = reinterpret_cast<float*>(base + L.eAl6);
   s.eB6 = reinterpret_cast<float*>(base + L.eB6);
   s.sel = reinterpret_cast<float*>(base + L.sel);
+  s.sadj = reinterpret_cast<float*>(base + L.sadj);
   s.es = L.max_e;
   s.vs = L.max_v;
   return s;
@@ -94,6 +99,10 @@ __device__ inline void pair_setup(const FwdArgs& a, int pi, PairShared& ps) {
   ps.npA = A.n_planes; ps.npB = B.n_planes;
   ps.preselect = (a.p.top_verts > 0 || a.p.top_edges > 0) ? 1 : 0;
   ps.trace = a.p.trace_iters;
+  ps.nvA0 = ps.nvA; ps.nvB0 = ps.nvB; ps.neA0 = ps.neA; ps.neB0 = ps.neB;
+  ps.kv[0] = ps.kv[1] = ps.kv[2] = ps.kv[3] = 0;
+  ps.voffA = A.v_off;
+  ps.voffB = B.v_off;
   ps.tau = a.tau ? a.tau[pi] : a.p.tau;
   ps.inv_tau = 1.0f / ps.tau;
   ps.k2 = ps.inv_tau * kLog2e;
@@ -336,42 +345,78 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
 }
 
 // ---------------------------------------------------------------- soft pre-selection
-// (Sec. IV-A; Supplement B).  One warp per selection: the K largest depth scores
-// by K arg-max passes in (score desc, index asc) order, then the SoftSort rows
-// exp(-|s^_k - x_i| / tau) / Z_k applied to the items' payloads.
+// (Sec. IV-A; Supplement B).  Four selections per pair: A's vertices (kind 0),
+// B's vertices (1), A's edges (2), B's edges (3).  An item's score is its depth
+// -phi_other (vertices) or the mean of its corners' (edges); its payload is what
+// the contacts use: positions in B's frame, A's local positions and the
+// capsule-template cap signs (sel_width floats).
+__host__ __device__ constexpr int sel_width(int kind) { return kind == 0 ? 7 : kind == 1 ? 4 : kind == 2 ? 14 : 8; }
+
+struct SelArea {
+  float* m[2];      // vertex depths of A and B (phi of the other body)
+  float* item[4];   // kMaxSel x kSelPayload selected payloads per selection
+  float* info[4];   // per selection: s^_k, Z_k, index of the k-th top item (bits)
+};
+__device__ __forceinline__ SelArea sel_area(const PairSmem& sm) {
+  SelArea A;
+  A.m[0] = sm.sel;
+  A.m[1] = sm.sel + sm.vs;
+  float* q = sm.sel + 2 * sm.vs;
+  for (int j = 0; j < 4; ++j) {
+    A.item[j] = q;
+    q += kMaxSel * sel_width(j);
+  }
+  for (int j = 0; j < 4; ++j) {
+    A.info[j] = q;
+    q += 3 * kMaxSel;
+  }
+  return A;
+}
+
+__device__ __forceinline__ float sel_score(const PairSmem& sm, const SelArea& A, int kind, int i) {
+  switch (kind) {
+    case 0: return -A.m[0][i];
+    case 1: return -A.m[1][i];
+    case 2: { const uint32_t e = sm.eA[i]; return -0.5f * (A.m[0][e & 0xffffu] + A.m[0][e >> 16]); }
+    default: { const uint32_t e = sm.eB[i]; return -0.5f * (A.m[1][e & 0xffffu] + A.m[1][e >> 16]); }
+  }
+}
+
 template <int P>
-__device__ __forceinline__ void warp_soft_select(int n, int K, float k2, const float* score_src, int kind,
-                                                 const PairSmem& sm, float* dst) {
-  const int lane = threadIdx.x & 31;
-  const float* mA = sm.sel;
-  const float* mB = sm.sel + sm.vs;
+__device__ __forceinline__ void sel_payload(const PairSmem& sm, int kind, int i, float (&v)[P]) {
   const int es = sm.es;
-  auto score = [&](int i) -> float {
-    switch (kind) {
-      case 0: return -mA[i];
-      case 1: return -mB[i];
-      case 2: { const uint32_t e = sm.eA[i]; return -0.5f * (mA[e & 0xffffu] + mA[e >> 16]); }
-      default: { const uint32_t e = sm.eB[i]; return -0.5f * (mB[e & 0xffffu] + mB[e >> 16]); }
-    }
-  };
-  auto payload = [&](int i, float (&v)[P]) {
-    if (kind == 0) {
-      const float4 a = sm.vA[i], b = sm.vAl[i];
-      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = b.x; v[4] = b.y; v[5] = b.z;
-    } else if (kind == 1) {
-      const float4 a = sm.vB[i];
-      v[0] = a.x; v[1] = a.y; v[2] = a.z;
-    } else if (kind == 2) {
+  if (kind == 0) {
+    const float4 a = sm.vA[i], b = sm.vAl[i];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = b.x; v[4] = b.y; v[5] = b.z; v[6] = b.w;
+  } else if (kind == 1) {
+    const float4 a = sm.vB[i];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else if (kind == 2) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) v[c] = sm.eA6[c * es + i];
+    for (int c = 0; c < 6; ++c) v[c] = sm.eA6[c * es + i];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) v[6 + c] = sm.eAl6[c * es + i];
-    } else {
+    for (int c = 0; c < 6; ++c) v[6 + c] = sm.eAl6[c * es + i];
+    const uint32_t e = sm.eA[i];
+    v[12] = sm.vAl[e & 0xffffu].w;
+    v[13] = sm.vAl[e >> 16].w;
+  } else {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) v[c] = sm.eB6[c * es + i];
-    }
-  };
-  (void)score_src;
+    for (int c = 0; c < 6; ++c) v[c] = sm.eB6[c * es + i];
+    const uint32_t e = sm.eB[i];
+    v[6] = sm.vB[e & 0xffffu].w;
+    v[7] = sm.vB[e >> 16].w;
+  }
+}
+
+// One warp per selection: the K largest scores by K arg-max passes in (score
+// desc, index asc) order, then the SoftSort rows exp(-|s^_k - x_i| / tau) / Z_k
+// applied to the items' payloads.  Records s^_k, Z_k and the k-th item's index.
+template <int P>
+__device__ __forceinline__ void warp_soft_select(int n, int K, float k2, int kind, const PairSmem& sm,
+                                                 const SelArea& A) {
+  const int lane = threadIdx.x & 31;
+  float* dst = A.item[kind];
+  float* info = A.info[kind];
   float prev_s = 3.0e38f;
   int prev_i = -1;
   for (int k = 0; k < K; ++k) {
@@ -379,7 +424,7 @@ __device__ __forceinline__ void warp_soft_select(int n, int K, float k2, const f
     float bs = -3.0e38f;
     int bi = 0x7fffffff;
     for (int i = lane; i < n; i += 32) {
-      const float x = score(i);
+      const float x = sel_score(sm, A, kind, i);
       const bool after = x < prev_s || (x == prev_s && i > prev_i);
       if (after && (x > bs || (x == bs && i < bi))) {
         bs = x;
@@ -402,9 +447,9 @@ __device__ __forceinline__ void warp_soft_select(int n, int K, float k2, const f
 #pragma unroll
     for (int c = 0; c <= P; ++c) acc[c] = 0.f;
     for (int i = lane; i < n; i += 32) {
-      const float e = ex2(-fabsf(bs - score(i)) * k2);
+      const float e = ex2(-fabsf(bs - sel_score(sm, A, kind, i)) * k2);
       float v[P];
-      payload(i, v);
+      sel_payload<P>(sm, kind, i, v);
       acc[0] += e;
 #pragma unroll
       for (int c = 0; c < P; ++c) acc[1 + c] = fmaf(e, v[c], acc[1 + c]);
@@ -415,57 +460,58 @@ __device__ __forceinline__ void warp_soft_select(int n, int K, float k2, const f
       const float iz = 1.0f / acc[0];
 #pragma unroll
       for (int c = 0; c < P; ++c) dst[k * P + c] = acc[1 + c] * iz;
+      info[k] = bs;
+      info[kMaxSel + k] = acc[0];
+      info[2 * kMaxSel + k] = __int_as_float(bi);
     }
   }
 }
 
-// Replaces the pair's staged vertices and edges by their soft selections.
-// Called by every thread between __syncthreads.
+// Cooperative: vertex depths, the four soft selections, and the selected items
+// copied over the pair's staged vertices / edge endpoints (the original counts
+// are kept in ps.n*0).  Contains __syncthreads: all threads must call.
 __device__ inline void preselect_pair(const FwdArgs& a, PairShared& ps, const PairSmem& sm, const PairBodies& bb) {
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  float* mA = sm.sel;
-  float* mB = sm.sel + sm.vs;
-  for (int i = threadIdx.x; i < ps.nvA; i += blockDim.x) mA[i] = sdfB_at(ps, bb.B, ld3(sm.vA[i])).phi;
-  for (int i = threadIdx.x; i < ps.nvB; i += blockDim.x) mB[i] = sdfA_at(ps, bb.A, ld3(sm.vB[i])).phi;
+  const SelArea A = sel_area(sm);
+  for (int i = threadIdx.x; i < ps.nvA; i += blockDim.x) A.m[0][i] = sdfB_at(ps, bb.B, ld3(sm.vA[i])).phi;
+  for (int i = threadIdx.x; i < ps.nvB; i += blockDim.x) A.m[1][i] = sdfA_at(ps, bb.A, ld3(sm.vB[i])).phi;
   __syncthreads();
-  float* stA = sm.sel + 2 * sm.vs;          // kMaxSel x 6: A's soft vertices (B frame, A frame)
-  float* stB = stA + kMaxSel * 6;           // kMaxSel x 3: B's soft vertices
-  float* seA = stB + kMaxSel * 6;           // kMaxSel x 12: A's soft edges (B frame, A frame)
-  float* seB = seA + kMaxSel * 12;          // kMaxSel x 6: B's soft edges
   const int kvA = a.p.top_verts ? min(a.p.top_verts, ps.nvA) : 0;
   const int kvB = a.p.top_verts ? min(a.p.top_verts, ps.nvB) : 0;
   const int keA = a.p.top_edges ? min(a.p.top_edges, ps.neA) : 0;
   const int keB = a.p.top_edges ? min(a.p.top_edges, ps.neB) : 0;
   for (int job = warp; job < 4; job += nwarps) {
-    if (job == 0 && kvA) warp_soft_select<6>(ps.nvA, kvA, ps.k2, nullptr, 0, sm, stA);
-    if (job == 1 && kvB) warp_soft_select<3>(ps.nvB, kvB, ps.k2, nullptr, 1, sm, stB);
-    if (job == 2 && keA) warp_soft_select<12>(ps.neA, keA, ps.k2, nullptr, 2, sm, seA);
-    if (job == 3 && keB) warp_soft_select<6>(ps.neB, keB, ps.k2, nullptr, 3, sm, seB);
+    if (job == 0 && kvA) warp_soft_select<7>(ps.nvA, kvA, ps.k2, 0, sm, A);
+    if (job == 1 && kvB) warp_soft_select<4>(ps.nvB, kvB, ps.k2, 1, sm, A);
+    if (job == 2 && keA) warp_soft_select<14>(ps.neA, keA, ps.k2, 2, sm, A);
+    if (job == 3 && keB) warp_soft_select<8>(ps.neB, keB, ps.k2, 3, sm, A);
   }
   __syncthreads();
   const int es = sm.es;
   for (int i = threadIdx.x; i < kvA; i += blockDim.x) {
-    const float* v = stA + 6 * i;
+    const float* v = A.item[0] + 7 * i;
     sm.vA[i] = make_float4(v[0], v[1], v[2], 0.f);
-    sm.vAl[i] = make_float4(v[3], v[4], v[5], 0.f);
+    sm.vAl[i] = make_float4(v[3], v[4], v[5], v[6]);
   }
   for (int i = threadIdx.x; i < kvB; i += blockDim.x) {
-    const float* v = stB + 3 * i;
-    sm.vB[i] = make_float4(v[0], v[1], v[2], 0.f);
+    const float* v = A.item[1] + 4 * i;
+    sm.vB[i] = make_float4(v[0], v[1], v[2], v[3]);
   }
   for (int i = threadIdx.x; i < keA; i += blockDim.x) {
-    const float* v = seA + 12 * i;
+    const float* v = A.item[2] + 14 * i;
     for (int c = 0; c < 6; ++c) {
       sm.eA6[c * es + i] = v[c];
       sm.eAl6[c * es + i] = v[6 + c];
     }
   }
   for (int i = threadIdx.x; i < keB; i += blockDim.x) {
-    const float* v = seB + 6 * i;
+    const float* v = A.item[3] + 8 * i;
     for (int c = 0; c < 6; ++c) sm.eB6[c * es + i] = v[c];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    ps.nvA0 = ps.nvA; ps.nvB0 = ps.nvB; ps.neA0 = ps.neA; ps.neB0 = ps.neB;
+    ps.kv[0] = kvA; ps.kv[1] = kvB; ps.kv[2] = keA; ps.kv[3] = keB;
     if (kvA) ps.nvA = kvA;
     if (kvB) ps.nvB = kvB;
     if (keA) ps.neA = keA;

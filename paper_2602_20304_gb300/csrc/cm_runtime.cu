@@ -87,7 +87,7 @@ cm_status check_params(const cm_params* p) {
   return CM_OK;
 }
 
-SmemLayout make_layout(const cm_context* c, int nwarps) {
+SmemLayout make_layout(const cm_context* c, int nwarps, int bwd) {
   SmemLayout L;
   int o = 0;
   L.max_v = c->max_v;
@@ -107,6 +107,8 @@ SmemLayout make_layout(const cm_context* c, int nwarps) {
   L.eAl6 = o; o = align16(o + 24 * c->max_e);
   L.eB6 = o; o = align16(o + 24 * c->max_e);
   L.sel = o; o = align16(o + 4 * (2 * c->max_v + kSelFloats));
+  L.sadj = o;
+  if (bwd) o = align16(o + 4 * (kSelAdjFloats + 2 * c->max_v));  // pre-selection adjoint slots
   L.total = o;
   return L;
 }
@@ -177,14 +179,6 @@ LaunchCfg pick_cfg(const cm_context* c, int bwd, int n_pairs, int flags) {
   return it != c->tuned.end() ? it->second : default_cfg(c, bwd, n_pairs);
 }
 
-// What the adjoint does not cover: pre-selection.  Call with the context lock held.
-cm_status adjoint_supported(const cm_context* c, const cm_params* p) {
-  (void)c;
-  if (p->top_verts || p->top_edges)
-    return fail(CM_ERR_INVALID_ARG, "the adjoint does not support pre-selection (top_verts / top_edges)");
-  return CM_OK;
-}
-
 Params to_params(const cm_params* p) {
   return Params{p->tau, p->w_reg, p->eps_clip, p->eps_min, p->eps_comp, p->K, p->flags, p->top_verts, p->top_edges,
                 p->trace_iters};
@@ -192,7 +186,7 @@ Params to_params(const cm_params* p) {
 
 // Grid and shared-memory layout of one launch shape.
 void shape(const cm_context* c, int bwd, const LaunchCfg& cfg, int n_pairs, SmemLayout& L, int& grid) {
-  L = make_layout(c, cfg.block / 32);
+  L = make_layout(c, cfg.block / 32, bwd);
   int per_sm = bwd ? bwd_max_blocks_per_sm(cfg.block, L.total, cfg.per_sm) : fwd_max_blocks_per_sm(cfg.block, L.total);
   if (cfg.per_sm > 0) per_sm = std::min(per_sm, cfg.per_sm);
   grid = std::max(1, std::min<int>(n_pairs, c->num_sms * per_sm));
@@ -498,7 +492,6 @@ extern "C" cm_status cm_contact_manifold_bwd(cm_context* c, int32_t n_pairs, con
   if (!pair_geoms || !poses || !grad_out || !grad_poses)
     return fail(CM_ERR_INVALID_ARG, "pair_geoms, poses, grad_out and grad_poses are required");
   std::lock_guard<std::mutex> lk(c->mu);
-  if ((st = adjoint_supported(c, params)) != CM_OK) return st;
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
   cudaSetDevice(c->device);
@@ -584,7 +577,7 @@ extern "C" cm_status cm_contact_manifold_fwd_noalloc(cm_context* c, int32_t n_pa
 
   const int block = 256;
   FwdArgs a{};
-  a.sm = make_layout(c, block / 32);
+  a.sm = make_layout(c, block / 32, 0);
   const int per_sm = fwd_max_blocks_per_sm(block, a.sm.total);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)n_pairs, (int64_t)c->num_sms * per_sm, slices}));
   a.hdr = c->d_hdr;
@@ -623,7 +616,6 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
   if (n_pairs <= 0 || !pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "a non-empty batch is required");
   if (grad_out && !grad_poses) return fail(CM_ERR_INVALID_ARG, "grad_poses is required with grad_out");
   std::lock_guard<std::mutex> lk(c->mu);
-  if (grad_out && (st = adjoint_supported(c, params)) != CM_OK) return st;
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
   cudaSetDevice(c->device);
@@ -724,7 +716,6 @@ extern "C" cm_status cm_plan_create(cm_context* c, int32_t n_pairs, const int32_
   if (n_pairs <= 0 || !pair_geoms || !poses || !out) return fail(CM_ERR_INVALID_ARG, "a non-empty batch is required");
   if (grad_out && !grad_poses) return fail(CM_ERR_INVALID_ARG, "grad_poses is required with grad_out");
   std::lock_guard<std::mutex> lk(c->mu);
-  if (grad_out && (st = adjoint_supported(c, params)) != CM_OK) return st;
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
   cudaSetDevice(c->device);

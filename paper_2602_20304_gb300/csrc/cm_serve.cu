@@ -367,10 +367,6 @@ cm_status cm_submit(cm_context* c, const cm_request_desc* d, uint64_t* ticket) {
   r->bytes = request_bytes(*d, s->params.K);
   {
     std::lock_guard<std::mutex> lk(c->mu);
-    if (d->with_backward) {
-      cm_status st = adjoint_supported(c, &s->params);
-      if (st != CM_OK) return st;
-    }
     const int ng = (int)c->hdr.size();
     int64_t m = 1;
     for (int i = 0; i < d->n_pairs; ++i) {

@@ -145,14 +145,3 @@ def test_selection_and_tracing_limits(api, ctx):
                                          ctypes.byref(p), ctypes.c_void_p(8), None)
         assert st == api.CM_ERR_INVALID_ARG, over
     assert api.cm_default_params().trace_iters == 0
-
-
-def test_adjoint_refuses_preselection(api, ctx):
-    import ctypes
-    lib = api._lib
-    add(api, ctx, synth.primitive_geometry(synth.KIND_BOX, (0.5, 0.5, 0.5)))
-    v = ctypes.c_void_p(8)
-    p = api.cm_default_params(top_edges=4)
-    assert lib.cm_contact_manifold_bwd(ctx, 1, v, v, None, None, ctypes.byref(p), v, v, None, None) == \
-        api.CM_ERR_INVALID_ARG
-    assert "pre-selection" in api.cm_last_error()
