@@ -40,13 +40,13 @@ def _sdf_mufu(kind, n_planes):
     if kind == synth.KIND_ELLIPSOID:
         return 2                # |y| and f^-1/2
     if kind == synth.KIND_CAPSULE:
-        return 9                # soft clip (2 exp + 2 log), |w|, its inverse, two sigmoids (2 exp + 2 rcp)
+        return 6                # e^-|x| per clip side (2), log of the softplus ratio, two sigmoid reciprocals, 1/|w|
     if kind == synth.KIND_CYLINDER:
         return 7                # rho, 1/rho, 3-term LSE (3 exp, log, rcp)
     raise ValueError(kind)
 
 
-QP_MUFU = 32        # 3 reciprocals, 4 soft clips (16), soft argmin (4 exp + rcp), 4 sigmoids (8)
+QP_MUFU = 29        # 3 reciprocals, 4 soft clips (16), soft argmin (4 exp + rcp), 4 sigmoids under one reciprocal (5)
 EE_EXTRA = 2 + 2 + 4 + 4 + 2 + 4 + 2   # dbar, nbar, 2 soft signs, 2 pen, cl, nn (2 row/col exps + 2 values), SoftSort 2
 VS_EXTRA = 1 + 2 + 1                   # normal, activity sigmoid, SoftSort
 
@@ -61,6 +61,12 @@ def mufu_ops_per_pair(w, flags=0):
         ee = 0 if flags & 3 else neA[i] * neB[i] * (QP_MUFU + EE_EXTRA + 2 * sa + 2 * sb)
         out[i] = vs + ee
     return out
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one forward-kernel launch
+# on this workload at 4096 pairs, from one ncu capture of the current kernel; scaled
+# by the pairs a launch processes (traffic grows in proportion).
+FWD_TRAFFIC_BYTES_4096 = 5.444352e6 + 21.681920e6
 
 
 def _hbm_peak():
@@ -99,7 +105,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -359,7 +365,7 @@ def witness_rates(api, n=10_000_000, steps=5):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -483,7 +489,9 @@ def main():
     kernel_s = float(np.mean(step_ms)) * 1e-3
     achieved = ops / kernel_s
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": mufu_peak / 1e9, "unit": "Gop/s (MUFU)",
-            "frac": achieved / mufu_peak, "traffic": None,
+            "frac": achieved / mufu_peak, "traffic": FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096,
+            "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "algorithmic_bytes": 348 * w.n_pairs,
             "peak_source": "measured ex2.approx throughput (cm_measure_pipe_peaks)",
             "fma_peak_tflops": fma_peak / 1e12}
 

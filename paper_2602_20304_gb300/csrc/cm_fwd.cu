@@ -12,7 +12,7 @@
 //      the distance matrix (nn indicators of Sec. IV-D3, Eq. nn_check);
 //   5. E-E pass 2: witness QP again, four SDF evaluations, sign, pen, nn, cl and
 //      activity -> two candidates per edge pair, streamed into the warp state;
-//   6. merge the warps' states and write the K rows, rotated back to world.
+//   6. merge the warps' states pairwise and write the K rows, rotated back to world.
 #include "cm_pair.cuh"
 
 namespace cm {
@@ -119,12 +119,13 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
       }
     }
 
-    // ---- merge warps and write the K rows
-    float* ws = sm.warp + warp * kWarpStateFloats;
-    wtk_store(st, ws, K);
-    __syncthreads();
+    // ---- merge the warps' states pairwise (log2(nwarps) levels) and write the K rows
+    for (int h = 1; h < nwarps; h <<= 1) {
+      if ((warp & (2 * h - 1)) == h) wtk_store(st, sm.warp + warp * kWarpStateFloats, K);
+      __syncthreads();
+      if ((warp & (2 * h - 1)) == 0 && warp + h < nwarps) wtk_merge(st, sm.warp + (warp + h) * kWarpStateFloats, K, k2);
+    }
     if (warp == 0) {
-      for (int w = 1; w < nwarps; ++w) wtk_merge(st, sm.warp + w * kWarpStateFloats, K, k2);
       wtk_finish(st, K, k2, y);
       if (lane < K) {
         V3 p = mul(ps.RB, v3(y[0], y[1], y[2])) + ps.tB;

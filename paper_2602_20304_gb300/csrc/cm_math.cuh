@@ -328,14 +328,19 @@ CM_HD Sdf sdf_ellipsoid(V3 y, V3 d) {
 
 // Capsule of radius r around the z segment [-h, h] with a soft-clipped axial
 // coordinate: phi = |y - clip_s(y_z, -h, h) z| - r.
+// The soft clip's two softplus terms and their sigmoids share e^-|x| per side:
+// softplus(x) = max(x, 0) + ln(1 + e^-|x|), sigmoid(x) = (x >= 0 ? 1 : e^-|x|) / (1 + e^-|x|),
+// and the difference of the two logarithms is the logarithm of a ratio.
 CM_HD Sdf sdf_capsule(V3 y, float rad, float h, float tau, float inv_tau) {
   float up = (y.z + h) * inv_tau, dn = (y.z - h) * inv_tau;
-  float c = -h + tau * (softplus(up) - softplus(dn));
+  const float Eu = exp_(-fabsf(up)), Ed = exp_(-fabsf(dn));
+  const float iu = rcp(1.f + Eu), id = rcp(1.f + Ed);
+  float c = -h + tau * ((fmaxf(up, 0.f) - fmaxf(dn, 0.f)) + kLn2 * lg2((1.f + Eu) * id));
   V3 w = v3(y.x, y.y, y.z - c);
   float r2 = dot(w, w);
   float ir = r2 > 0.f ? rsq(r2) : 0.f;
   float r = r2 * ir;
-  float dc = sigmoid(up) - sigmoid(dn);
+  float dc = (up >= 0.f ? iu : Eu * iu) - (dn >= 0.f ? id : Ed * id);
   Sdf o;
   o.phi = r - rad;
   o.g = v3(w.x * ir, w.y * ir, w.z * (1.f - dc) * ir);
@@ -526,8 +531,11 @@ CM_HD QPOut qp_solve(const QPPre& q, float lam, const Params& p) {
   float iw = rcp((w1 + w2) + (w3 + w4));
   float ac1 = (w1 + w3 * s3 + w4 * s4) * iw;
   float ac2 = (w1 * s1 + w2 * s2 + w3) * iw;
+  // con = within01(au1) within01(au2), the four sigmoids under one reciprocal:
+  // 1 / prod (1 + e^-x_i); a factor that overflows makes con 0, as it should.
   float ic = rcp(p.eps_comp);
-  float con = within01(au1, ic) * within01(au2, ic);
+  float con = rcp(((1.f + exp_(-au1 * ic)) * (1.f + exp_((au1 - 1.f) * ic))) *
+                  ((1.f + exp_(-au2 * ic)) * (1.f + exp_((au2 - 1.f) * ic))));
   QPOut o;
   o.a1 = fmaf(con, au1 - ac1, ac1);
   o.a2 = fmaf(con, au2 - ac2, ac2);

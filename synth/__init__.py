@@ -15,7 +15,8 @@ from .geometry import (  # noqa: F401
 )
 from .workloads import (  # noqa: F401
     Workload, random_quaternions, config_box_box, config_hull_vs_primitive,
-    config_box_vs_sphere_hull, config_mixed, config_mixed_pooled, serving_trace, make_config,
+    config_box_vs_sphere_hull, config_hull_vs_hull, config_mixed, config_mixed_pooled, serving_trace,
+    make_config,
     SQ_RESOLUTIONS, random_sq_union, config_sq_union,
     SEED_BASE,
 )

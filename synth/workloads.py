@@ -136,6 +136,22 @@ def config_hull_vs_primitive(n=4096, seed=SEED_BASE + 2, n_points=(8, 64), log_u
     return Workload(name, geoms, pg, poses, dims, tau.astype(np.float32))
 
 
+def config_hull_vs_hull(n=64, seed=SEED_BASE + 7, n_points=(8, 64), tau=1e-2):
+    """Hull against hull, each of N ~ U{8..64} points uniform in the unit ball."""
+    rng = np.random.default_rng(seed)
+    geoms = []
+    pg = np.zeros((n, 2), dtype=np.int32)
+    lo, hi = n_points
+    for i in range(n):
+        for side in range(2):
+            geoms.append(hull_from_points(_ball_points(rng, int(rng.integers(lo, hi + 1)))))
+            pg[i, side] = len(geoms) - 1
+    dims = np.ones((n, 6), dtype=np.float32)
+    delta = rng.uniform(0.0, 0.1, n)
+    poses = _place(rng, geoms, pg, dims, delta)
+    return Workload("hull-vs-hull", geoms, pg, poses, dims, np.full(n, tau, np.float32))
+
+
 def config_box_vs_sphere_hull(n=1024, seed=SEED_BASE + 3, n_sphere=32, tau=1e-2):
     """Box (dims U[0.2, 1]) against the hull of 32 points uniform on the unit sphere."""
     rng = np.random.default_rng(seed)

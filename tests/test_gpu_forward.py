@@ -59,6 +59,17 @@ def test_box_vs_sphere_hull_subset(engine):
     print("box-vs-hull32", assert_close(gpu, oracle_forward(w, params), what="box-vs-hull32"))
 
 
+@pytest.mark.parametrize("tau", [1e-2, 1e-1])
+def test_hull_vs_hull(engine, tau):
+    """Both bodies hulls (each of 8..64 points), either one with more planes."""
+    w = synth.config_hull_vs_hull(n=48, tau=tau)
+    npl = np.array([g.n_planes for g in w.geoms])
+    a, b = npl[w.pair_geoms[:, 0]], npl[w.pair_geoms[:, 1]]
+    assert (a > b).any() and (b > a).any()
+    gpu, params = run(engine, w)
+    print("hull-vs-hull", assert_close(gpu, oracle_forward(w, params), what="hull-vs-hull"))
+
+
 @pytest.mark.parametrize("tau", [1e-3, 1e-2, 1e-1])
 def test_mixed_sizes_per_tau(engine, tau):
     """Hulls of 8..256 points against all primitive kinds at each smoothing level."""
