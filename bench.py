@@ -63,10 +63,50 @@ def mufu_ops_per_pair(w, flags=0):
     return out
 
 
+# FP32 operations of the method (FMA = 2, add / mul / min / max = 1), from the formulas
+# the oracle evaluates, per SDF evaluation ("grad": value and gradient) and per step.
+def _sdf_flops(kind, n_planes, grad):
+    if kind == synth.KIND_HULL:            # per plane: n . y - o (6), shift (1), sum (1); gradient 3 FMA
+        return n_planes * (14 if grad else 8) + (6 if grad else 3)
+    if kind == synth.KIND_BOX:             # six axis planes (+-y_i - h_i), same LSE
+        return 39 if grad else 33
+    if kind == synth.KIND_ELLIPSOID:
+        return 21
+    if kind == synth.KIND_CAPSULE:
+        return 40
+    if kind == synth.KIND_CYLINDER:
+        return 25
+    raise ValueError(kind)
+
+
+QP_FLOPS = 260      # set-up (38), unconstrained solve (60), 4 soft clips (68), 4 side costs (40), soft argmin, indicator, blend
+EE_FLOPS = 180      # witnesses, n-bar, frame moves, 2 normals, soft signs, pen, cl, nn, weights, 2 SoftSort pushes, row/col minima
+VS_FLOPS = 34       # normal, activity, score, SoftSort push
+
+
+def fp32_flops_per_pair(w, flags=0):
+    nvA, nvB, neA, neB = w.pair_counts()
+    out = np.zeros(w.n_pairs)
+    for i in range(w.n_pairs):
+        ga, gb = w.geoms[w.pair_geoms[i, 0]], w.geoms[w.pair_geoms[i, 1]]
+        vs = nvA[i] * (_sdf_flops(gb.kind, gb.n_planes, True) + VS_FLOPS)
+        if not flags & 2:
+            vs += nvB[i] * (_sdf_flops(ga.kind, ga.n_planes, True) + VS_FLOPS)
+        ee = 0 if flags & 3 else neA[i] * neB[i] * (
+            QP_FLOPS + EE_FLOPS + _sdf_flops(ga.kind, ga.n_planes, False) + _sdf_flops(ga.kind, ga.n_planes, True)
+            + _sdf_flops(gb.kind, gb.n_planes, False) + _sdf_flops(gb.kind, gb.n_planes, True))
+        out[i] = vs + ee
+    return out
+
+
+# Pipe activity of the forward kernel on this workload (4096 pairs) from the same ncu
+# capture: sm__pipe_fma_cycles_active and sm__inst_executed_pipe_xu, % of peak.
+FWD_NCU_PIPE_PCT = None
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one forward-kernel launch
 # on this workload at 4096 pairs, from one ncu capture of the current kernel; scaled
 # by the pairs a launch processes (traffic grows in proportion).
-FWD_TRAFFIC_BYTES_4096 = 5.444352e6 + 21.681920e6
+FWD_TRAFFIC_BYTES_4096 = None
 
 
 def _hbm_peak():
@@ -315,6 +355,56 @@ def extra_settings(Engine, api, local, steps, flush):
                                 "speedup_no_ee": ne / full, "speedup_one_sided_vs_no_ee": nes / ne}}
 
 
+def small_config_rates(Engine, api, local, steps, flush):
+    """The two 1024-pair settings: box-box poses (batched launch, and the plain path of
+    one launch per pose) and box vs the hull of 32 points on the sphere (forward and
+    forward+backward)."""
+    import torch
+    from paper_2602_20304_gb300.engine import workload_tensors
+    eng = Engine(local)
+    try:
+        res = {}
+        w1 = synth.make_config(1)
+        params = eng.params()
+        r, ms = plan_rate(eng, api, w1, params, steps, False, flush)
+        ids = eng.add_geometries(w1.geoms)
+        pg, poses, dims, tau = workload_tensors(w1, id_map=ids)
+        out = torch.empty((w1.n_pairs, params.K, 8), device="cuda")
+        for i in range(8):   # warm the one-pair path
+            eng.forward(pg[i:i + 1], poses[i:i + 1], dims[i:i + 1], tau[i:i + 1], params, out=out[i:i + 1])
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record()
+        for i in range(w1.n_pairs):
+            eng.forward(pg[i:i + 1], poses[i:i + 1], dims[i:i + 1], tau[i:i + 1], params, out=out[i:i + 1])
+        b.record()
+        b.synchronize()
+        plain = w1.n_pairs / (a.elapsed_time(b) * 1e-3)
+        res["box_box_1024"] = {"workload": "two cubes h=0.5, 1024 poses, tau=1e-2, K=8", "fwd_pairs_per_s": r,
+                               "fwd_ms": ms, "plain_one_launch_per_pose_pairs_per_s": plain}
+        w3 = synth.make_config(3)
+        f, fms = plan_rate(eng, api, w3, params, steps, False, flush)
+        fb, fbms = plan_rate(eng, api, w3, params, steps, True, flush)
+        res["box_vs_hull32_1024"] = {"workload": "box (dims U[0.2,1]) vs hull of 32 points on the unit sphere, "
+                                                 "1024 pairs, tau=1e-2, K=8",
+                                     "fwd_pairs_per_s": f, "fwd_ms": fms, "fwd_bwd_pairs_per_s": fb, "fwd_bwd_ms": fbms}
+    finally:
+        eng.close()
+    return res
+
+
+def oracle_rates(seconds=4.0):
+    """FP64 oracle pairs/s (as it stands) on bounded samples of the other settings."""
+    res = {}
+    for name, w in (("box_box_1024", synth.make_config(1)), ("box_vs_hull32_1024", synth.make_config(3)),
+                    ("uneven_65536", synth.config_mixed_pooled())):
+        r, n, dt, cores = cpu_oracle_rate(w, budget_s=seconds)
+        res[name] = {"pairs_per_s": r, "pairs": n, "seconds": dt, "cores": cores,
+                     "sample": f"first {n} pairs of the workload (forward)"}
+    return res
+
+
 def sq_union_rates(Engine, api, local, steps, flush):
     """Pairs/s of the multi-superquadric bodies in the paper's armadillo setting (Sec. V:
     L superquadrics per body, every vertex, the L deepest soft edges per body), at the
@@ -482,24 +572,30 @@ def main():
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the forward kernel: MUFU work per launch / step duration (the step
-    # also holds the few-microsecond work-order kernel, so this slightly understates it)
+    # ---- roofline of the forward kernel: algorithmic work per launch / step duration (the
+    # step also holds the few-microsecond work-order kernel, so this slightly understates it).
+    # Both arithmetic pipes are reported; the binding one is the larger fraction.
     fma_peak, mufu_peak = api.cm_measure_pipe_peaks(local)
-    ops = float(mufu_ops_per_pair(w).sum())
     kernel_s = float(np.mean(step_ms)) * 1e-3
-    achieved = ops / kernel_s
-    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": mufu_peak / 1e9, "unit": "Gop/s (MUFU)",
-            "frac": achieved / mufu_peak, "traffic": FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096,
+    mufu = float(mufu_ops_per_pair(w).sum()) / kernel_s
+    flops = float(fp32_flops_per_pair(w).sum()) / kernel_s
+    pipes = {"mufu": {"achieved": mufu / 1e9, "peak": mufu_peak / 1e9, "unit": "Gop/s", "frac": mufu / mufu_peak,
+                      "peak_source": "measured ex2.approx throughput (cm_measure_pipe_peaks)"},
+             "fp32": {"achieved": flops / 1e12, "peak": fma_peak / 1e12, "unit": "TFLOP/s", "frac": flops / fma_peak,
+                      "peak_source": "measured FFMA throughput (cm_measure_pipe_peaks)"}}
+    binding = max(pipes, key=lambda k: pipes[k]["frac"])
+    roof = {"bound": "alu", "pipe": binding, **pipes[binding],
+            "traffic": None if FWD_TRAFFIC_BYTES_4096 is None else FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096,
             "traffic_unit": "bytes per launch (ncu dram read + write)",
-            "algorithmic_bytes": 348 * w.n_pairs,
-            "peak_source": "measured ex2.approx throughput (cm_measure_pipe_peaks)",
-            "fma_peak_tflops": fma_peak / 1e12}
+            "algorithmic_bytes": 348 * w.n_pairs, "pipes": pipes,
+            "ncu_pipe_active_pct": FWD_NCU_PIPE_PCT}
 
     extra = None
     if not args.no_extra and world == 1:
         extra = extra_settings(Engine, api, local, max(3, min(args.steps, 5)), flush)
         extra["witness_points"] = witness_rates(api)
         extra["sq_union"] = sq_union_rates(Engine, api, local, max(3, min(args.steps, 5)), flush)
+        extra.update(small_config_rates(Engine, api, local, max(3, min(args.steps, 5)), flush))
         for k in ("ee", "vf"):
             extra["witness_points"][k]["hbm_frac_of_measured"] = extra["witness_points"][k]["hbm_gbs"] / _hbm_peak()
 
@@ -512,6 +608,8 @@ def main():
         r, n, dt, cores = cpu_oracle_rate(w, budget_s=args.cpu_seconds)
         cpu = {"value": r, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                "sample": f"first {n} pairs of the workload ({dt:.1f} s)"}
+        if extra is not None:
+            cpu["other_settings"] = oracle_rates()
 
     line = {"metric": "contact pairs/s (forward manifold)", "value": value, "unit": "pairs/s",
             "fwd_bwd": {"value": value_fb, "unit": "pairs/s", "ms_per_step": total_fb_ms / args.steps,

@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
 
     // ================= forward recompute
     WarpTopK st;
-    wtk_init(st);
+    wtk_init(st, sm.warp + warp * kWarpStateFloats);
     float y[8], y2[8];
     for (int base = warp * 32; base < nvs; base += nwarps * 32) {
       const int c = base + lane;
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
         wtk_push(st, valid, s2, y2, K, k2, nvs + 2 * i + 1);
       }
     }
-    wtk_store(st, sm.warp + warp * kWarpStateFloats, K);
+    wtk_store(st, K);
     __syncthreads();
     if (warp == 0) {
       for (int w = 1; w < nwarps; ++w) wtk_merge(st, sm.warp + w * kWarpStateFloats, K, k2);

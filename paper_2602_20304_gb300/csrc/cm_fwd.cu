@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
     const float k2 = ps.k2;
 
     WarpTopK st;
-    wtk_init(st);
+    wtk_init(st, sm.warp + warp * kWarpStateFloats);
     float y[8], y2[8];
 
     // ---- vertex-SDF candidates
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
 
     // ---- merge the warps' states pairwise (log2(nwarps) levels) and write the K rows
     for (int h = 1; h < nwarps; h <<= 1) {
-      if ((warp & (2 * h - 1)) == h) wtk_store(st, sm.warp + warp * kWarpStateFloats, K);
+      if ((warp & (2 * h - 1)) == h) wtk_store(st, K);
       __syncthreads();
       if ((warp & (2 * h - 1)) == 0 && warp + h < nwarps) wtk_merge(st, sm.warp + (warp + h) * kWarpStateFloats, K, k2);
     }

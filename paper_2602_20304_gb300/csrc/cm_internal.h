@@ -68,7 +68,9 @@ constexpr int kSelFloats = kMaxSel * (7 + 4 + 14 + 8) + 4 * 3 * kMaxSel;
 // Adjoint of a pre-selection: local-frame adjoints of the selected items
 // (3 + 3 + 6 + 6 floats) and the vertex-depth adjoints of both bodies (2 max_v).
 constexpr int kSelAdjFloats = kMaxSel * (3 + 3 + 6 + 6);
-constexpr int kWarpStateFloats = kMaxK * 9 + 10 + kMaxK;  // list, C, threshold, ids
+// Per-warp SoftSort area: kMaxK payload slots of 8 floats, the list's scores, ids
+// and slots, C (9), the K-th score and C's reference (see cm_softsort.cuh).
+constexpr int kWarpStateFloats = 188;
 
 cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s);
 int fwd_max_blocks_per_sm(int block, int smem_bytes);

@@ -13,6 +13,8 @@
 
 namespace cm {
 
+static_assert(kSsFloats <= kWarpStateFloats && kMaxK <= 16, "per-warp SoftSort area");
+
 struct PairShared {
   M3 RA, RB, Rrel;
   V3 tA, tB, trel;
