@@ -41,6 +41,13 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
       continue;
     }
     pair_stage(a, pi, ps, sm);
+    // column statistics of the E-E distance matrix: running minimum (as the bits of
+    // a non-negative float) and the soft-minimum sum
+    float* colS = sm.colL + a.sm.max_e;
+    for (int l = threadIdx.x; l < ps.neB; l += blockDim.x) {
+      sm.colL[l] = 3.0e38f;
+      colS[l] = 0.f;
+    }
     __syncthreads();
     const PairBodies bb = pair_bodies(ps, sm);
     if (ps.preselect) preselect_pair(a, ps, sm, bb);
@@ -50,11 +57,12 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
     wtk_init(st, sm.warp + warp * kWarpStateFloats);
     float y[8], y2[8];
 
-    // ---- vertex-SDF candidates
+    // ---- vertex-SDF candidates, from the last warp down: the thread-strided E-E
+    // pass 1 gives its extra elements to the first warps
     const bool one_sided = (a.p.flags & 2) != 0;
     const bool no_ee = one_sided || (a.p.flags & 1) != 0;
     const int nvs = one_sided ? ps.nvA : ps.nvA + ps.nvB;
-    for (int base = warp * 32; base < nvs; base += nwarps * 32) {
+    for (int base = (nwarps - 1 - warp) * 32; base < nvs; base += nwarps * 32) {
       const int c = base + lane;
       const bool valid = c < nvs;
       float s = 0.f;
@@ -69,6 +77,7 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
         const int k = i / neB, l = i - k * neB;
         Witness w = ee_witness(edge_pair(sm, k, l), a.p);
         D[i] = w.dbar;
+        atomicMin(reinterpret_cast<int*>(sm.colL) + l, __float_as_int(w.dbar));
         if (a.store_alpha) {
           A1[i] = w.qp.a1;
           A2[i] = w.qp.a2;
@@ -76,23 +85,23 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
         }
       }
       __syncthreads();
-      // ---- soft row minima (warp per row) and column minima (thread per column)
+      // ---- soft row minima (warp per row, coalesced over the row) and, in the same
+      // sweep, the column sums against the column minima found in pass 1
       for (int k = warp; k < neA; k += nwarps) {
         float m = 3.0e38f;
         for (int l = lane; l < neB; l += 32) m = fminf(m, D[k * neB + l]);
         m = warp_min(m);
         float S = 0.f;
-        for (int l = lane; l < neB; l += 32) S += ex2((m - D[k * neB + l]) * k2);
+        for (int l = lane; l < neB; l += 32) {
+          const float d = D[k * neB + l];
+          S += ex2((m - d) * k2);
+          atomicAdd(colS + l, ex2((sm.colL[l] - d) * k2));
+        }
         S = warp_sum(S);
         if (lane == 0) sm.rowL[k] = m - ps.tau * kLn2 * lg2(S);
       }
-      for (int l = threadIdx.x; l < neB; l += blockDim.x) {
-        float m = 3.0e38f;
-        for (int k = 0; k < neA; ++k) m = fminf(m, D[k * neB + l]);
-        float S = 0.f;
-        for (int k = 0; k < neA; ++k) S += ex2((m - D[k * neB + l]) * k2);
-        sm.colL[l] = m - ps.tau * kLn2 * lg2(S);
-      }
+      __syncthreads();
+      for (int l = threadIdx.x; l < neB; l += blockDim.x) sm.colL[l] -= ps.tau * kLn2 * lg2(colS[l]);
       __syncthreads();
       // ---- E-E pass 2: candidates
       for (int base = warp * 32; base < nee; base += nwarps * 32) {

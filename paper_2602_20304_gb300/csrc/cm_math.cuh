@@ -129,12 +129,19 @@ CM_HD M3 mulTM(const M3& A, const M3& B) {
 CM_HD float sigmoid(float x) { return rcp(1.0f + exp_(-x)); }
 // log(1 + e^x) as max(x, 0) + log(1 + e^-|x|)
 CM_HD float softplus(float x) { return fmaxf(x, 0.0f) + kLn2 * lg2(1.0f + exp_(-fabsf(x))); }
-CM_HD float relu_s(float x, float inv_eps, float eps) { return eps * softplus(x * inv_eps); }
+// eps softplus(x / eps) = max(x, 0) + eps ln(1 + e^-|x|/eps), in base 2
+CM_HD float relu_s(float x, float inv_eps, float eps) {
+  return fmaxf(x, 0.0f) + (eps * kLn2) * lg2(1.0f + ex2(-fabsf(x) * (inv_eps * kLog2e)));
+}
 CM_HD float clip_s(float x, float lo, float hi, float inv_eps, float eps) {
   return lo + relu_s(x - lo, inv_eps, eps) - relu_s(x - hi, inv_eps, eps);
 }
 // tanh(x) = 1 - 2 / (e^{2x} + 1); saturates cleanly to +-1.
 CM_HD float tanh_(float x) { return 1.0f - 2.0f * rcp(exp_(2.0f * x) + 1.0f); }
+// tanh(x / tau) given k2 = log2(e) / tau
+CM_HD float tanh_k(float x, float k2) { return 1.0f - 2.0f * rcp(ex2(x * (2.0f * k2)) + 1.0f); }
+// sigmoid(x / tau) given k2 = log2(e) / tau
+CM_HD float sigmoid_k(float x, float k2) { return rcp(1.0f + ex2(-x * k2)); }
 CM_HD float within01(float x, float inv_eps) { return sigmoid(x * inv_eps) * sigmoid((1.0f - x) * inv_eps); }
 
 struct Params {

@@ -325,10 +325,10 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
   A_e1.g = mul(ps.Rrel, A_e1.g);
   V3 nuB = normal_of(B_e2.g, tau);
   V3 nuA = normal_of(A_e1.g, tau);
-  float g1 = tanh_(dot(nuB, nbar) * it);
-  float g2 = tanh_(-dot(nuA, nbar) * it);
-  float pen1 = sigmoid(-B_e1.phi * it);
-  float cl = sigmoid(-dot(nuA, nuB) * it);
+  float g1 = tanh_k(dot(nuB, nbar), ps.k2);
+  float g2 = tanh_k(-dot(nuA, nbar), ps.k2);
+  float pen1 = sigmoid_k(-B_e1.phi, ps.k2);
+  float cl = sigmoid_k(-dot(nuA, nuB), ps.k2);
   float nn1 = ex2((rowL - w.dbar) * ps.k2);
   float nn2 = ex2((colL - w.dbar) * ps.k2);
   float base = w.con * cl;

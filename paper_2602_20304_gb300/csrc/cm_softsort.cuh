@@ -163,40 +163,96 @@ __device__ __forceinline__ void wtk_store(const WarpTopK& st, int K) {
   }
 }
 
-// Folds another warp's stored state (its area) into this warp's state.
+// Folds another warp's stored state (its area) into this warp's state in one
+// parallel step: lanes 0..K-1 hold this warp's entries, lanes K..2K-1 the other
+// warp's; each computes its rank among the 2K (score descending, this warp's
+// entries first on ties, list order within a list), the first K stay, the rest
+// join C.  The other warp's survivors move their payloads into this warp's
+// slots freed by its evicted entries (or unused when its list was not full).
 __device__ __forceinline__ void wtk_merge(WarpTopK& st, const float* src, int K, float k2) {
   const int lane = threadIdx.x & 31;
-  float y[8];
-  float s = kNegInf;
-  bool valid = false;
-  int id = -1;
-  if (lane < K) {
-    s = src[kSsScore + lane];
-    valid = s != kNegInf;
-    id = __float_as_int(src[kSsId + lane]);
-    const float* ys = src + kSsSlots + 8 * __float_as_int(src[kSsSlot + lane]);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) y[c] = valid ? ys[c] : 0.f;
-  } else {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) y[c] = 0.f;
+  const bool own = lane < K, other = lane >= K && lane < 2 * K;
+  float cs = kNegInf;
+  int cid = -1, cslot = 0;
+  if (own) {
+    cs = st.ls;
+    cid = st.lid;
+    cslot = st.lslot;
+  } else if (other) {
+    cs = src[kSsScore + lane - K];
+    cid = __float_as_int(src[kSsId + lane - K]);
+    cslot = __float_as_int(src[kSsSlot + lane - K]);
   }
-  wtk_push(st, valid, s, y, K, k2, id);
+  const bool valid = cs != kNegInf;
+  int rank = 0;
+  for (int j = 0; j < 2 * K; ++j) {
+    const float sj = __shfl_sync(kFull, cs, j);
+    rank += (sj > cs || (sj == cs && j < lane)) ? 1 : 0;
+  }
+  const bool keep = valid && rank < K, evict = valid && rank >= K;
+  const int nvalid = __popc(__ballot_sync(kFull, valid));
+  const int cnt = min(nvalid, K);
+  const unsigned kth = __ballot_sync(kFull, keep && rank == K - 1);
+  const float thr = cnt == K ? __shfl_sync(kFull, cs, __ffs(kth) - 1) : kNegInf;
+  // C's new reference: the larger of the two (both at or below the new K-th score)
   const float ref_w = src[kSsRef];
-  if (ref_w != kNegInf) {
-    // both references lie at or below this warp's K-th score now: take the larger
-    // and scale both accumulators down to it
-    const float r = fmaxf(st.ref, ref_w);
-    const float fo = st.ref == kNegInf ? 0.f : ex2((st.ref - r) * k2);
+  float r = fmaxf(st.ref, ref_w);
+  if (r == kNegInf && cnt == K) r = thr;
+  const float fo = st.ref == kNegInf ? 0.f : ex2((st.ref - r) * k2);
 #pragma unroll
-    for (int c = 0; c < 9; ++c) st.C[c] *= fo;
-    if (lane == 0) {
-      const float fw = ex2((ref_w - r) * k2);
+  for (int c = 0; c < 9; ++c) st.C[c] *= fo;
+  if (lane == 0 && ref_w != kNegInf) {
+    const float fw = ex2((ref_w - r) * k2);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) st.C[c] = fmaf(fw, src[kSsC + c], st.C[c]);
-    }
-    st.ref = r;
+    for (int c = 0; c < 9; ++c) st.C[c] = fmaf(fw, src[kSsC + c], st.C[c]);
   }
+  if (evict) {  // evicted entries join C (r is finite: the merged list is full)
+    const float e = ex2((cs - r) * k2);
+    const float* ys = (own ? st.area : src) + kSsSlots + 8 * cslot;
+    st.C[0] += e;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) st.C[1 + c] = fmaf(e, ys[c], st.C[1 + c]);
+  }
+  __syncwarp();
+  // the m-th surviving entry of the other warp takes the m-th freed slot of this one
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned ev_own = __ballot_sync(kFull, evict && own);
+  const int own_cnt = __popc(__ballot_sync(kFull, own && valid));
+  const int m = __popc(__ballot_sync(kFull, keep && other) & lt);
+  const int nev = __popc(ev_own);
+  int from = 0;
+  if (keep && other && m < nev) {  // lane of the m-th evicted entry of this warp
+    unsigned mm = ev_own;
+    for (int t = 0; t < m; ++t) mm &= mm - 1u;
+    from = __ffs(mm) - 1;
+  }
+  const int freed = __shfl_sync(kFull, cslot, from);
+  if (keep && other) {
+    const int slot = m < nev ? freed : own_cnt + (m - nev);
+    const float* ys = src + kSsSlots + 8 * cslot;
+    float* yd = st.area + kSsSlots + 8 * slot;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) yd[c] = ys[c];
+    cslot = slot;
+  }
+  // the kept entries take list positions = their ranks (this warp's store area as scratch)
+  if (keep) {
+    st.area[kSsScore + rank] = cs;
+    st.area[kSsId + rank] = __int_as_float(cid);
+    st.area[kSsSlot + rank] = __int_as_float(cslot);
+  }
+  __syncwarp();
+  if (lane < K) {
+    const bool has = lane < cnt;
+    st.ls = has ? st.area[kSsScore + lane] : kNegInf;
+    st.lid = has ? __float_as_int(st.area[kSsId + lane]) : -1;
+    st.lslot = has ? __float_as_int(st.area[kSsSlot + lane]) : 0;
+  }
+  __syncwarp();
+  st.cnt = cnt;
+  st.thr = thr;
+  st.ref = cnt == K ? r : kNegInf;
+  if (cnt == K) wtk_rebase(st, k2);
 }
 
 // Final rows: lane k < K returns out_k in y (weights normalised) and, in Z, the
