@@ -101,12 +101,12 @@ def fp32_flops_per_pair(w, flags=0):
 
 # Pipe activity of the forward kernel on this workload (4096 pairs) from the same ncu
 # capture: sm__pipe_fma_cycles_active and sm__inst_executed_pipe_xu, % of peak.
-FWD_NCU_PIPE_PCT = None
+FWD_NCU_PIPE_PCT = {"fma": 39.9, "xu": 26.3}
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one forward-kernel launch
 # on this workload at 4096 pairs, from one ncu capture of the current kernel; scaled
 # by the pairs a launch processes (traffic grows in proportion).
-FWD_TRAFFIC_BYTES_4096 = None
+FWD_TRAFFIC_BYTES_4096 = 5.426944e6 + 21.611264e6
 
 
 def _hbm_peak():
