@@ -29,14 +29,6 @@ struct BwdShared {
   float shat[kMaxK];
   int sid[kMaxK];
   float shatbar[kMaxK];
-  // Below the K-th score s^_K every row's weight factorises: Gamma_ki = e_i c_k with
-  // e_i = exp((s_i - s^_K)/tau) and c_k = exp((s^_K - s^_k)/tau) / Z_k (see ss_bwd).
-  float thr;          // s^_K (-inf when fewer than K candidates)
-  float ck[kMaxK];
-  float Gs[8];        // sum_k c_k G_k
-  float ybar0[8];     // centring payload (row K-1's output)
-  float h[kMaxK];     // G_k . (out_k - ybar0)
-  float gs0;          // sum_k c_k h_k
   float Rout[9];      // adjoint of R_B from the output rotation
   float tout[3];
   float adj[18];      // CTA-reduced Adj: R (9), t (3), dA (3), dB (3)
@@ -79,43 +71,11 @@ __device__ __forceinline__ EEGeom ee_geom(const FwdArgs& a, const PairShared& ps
   return g;
 }
 
-// Per-thread sums over the below-threshold candidates it reversed:
-// E = sum_i e_i (1, y_i - ybar0), e_i = exp((s_i - s^_K)/tau).
-struct SsAcc {
-  float E[9];
-};
-__device__ __forceinline__ void ss_acc_zero(SsAcc& a) {
-#pragma unroll
-  for (int c = 0; c < 9; ++c) a.E[c] = 0.f;
-}
-
-// SoftSort reverse of one candidate (y, s): ybar and sbar, and its share of
-// dL/d s^_k (the K rows' dependence on the selected scores).  With
-// Gamma_ki = exp(-|s^_k - s_i|/tau) / Z_k and G_k = dL/d out_k:
-//   ybar_i = sum_k Gamma_ki G_k,
-//   sbar_i = sum_k Gamma_ki sgn(s^_k - s_i) G_k . (y_i - out_k) / tau,
-//   dL/d s^_k -= the same terms.
-// A candidate below s^_K has sgn = 1 and Gamma_ki = e_i c_k for every k, so
-// ybar_i = e_i sum_k c_k G_k and sbar_i = e_i (Gs . (y_i - ybar0) - gs0) / tau:
-// one exponential instead of K, and its dL/d s^_k share is kept as the sums
-// in `acc` (folded by ss_fold).  Candidates at or above s^_K take the K terms.
+// SoftSort reverse of one candidate (y, s): ybar, sbar and the per-thread
+// partial dL/d s^_k (the K rows' dependence on the selected scores).
 template <int KMAX>
 __device__ __forceinline__ void ss_bwd(const BwdShared& bs, int K, float it, float k2, const float (&y)[8], float s,
-                                       float (&yb)[8], float& sb, SsAcc& acc) {
-  if (s < bs.thr) {
-    const float e = ex2((s - bs.thr) * k2);
-    float dot = 0.f;
-    acc.E[0] += e;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const float yc = y[c] - bs.ybar0[c];
-      dot = fmaf(bs.Gs[c], yc, dot);
-      acc.E[1 + c] = fmaf(e, yc, acc.E[1 + c]);
-      yb[c] = e * bs.Gs[c];
-    }
-    sb = e * (dot - bs.gs0) * it;
-    return;
-  }
+                                       float (&yb)[8], float& sb, float (&shb)[KMAX]) {
   float2 yb2[4] = {dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f)};
   const float2 yv[4] = {make_float2(y[0], y[1]), make_float2(y[2], y[3]), make_float2(y[4], y[5]),
                         make_float2(y[6], y[7])};
@@ -136,29 +96,13 @@ __device__ __forceinline__ void ss_bwd(const BwdShared& bs, int K, float it, flo
       const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
       const float term = gam * (a2.x + a2.y) * sg * it;
       sb += term;
-      if (term != 0.f) atomicAdd(const_cast<float*>(&bs.shatbar[k]), -term);
+      shb[k] -= term;
     }
   }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     yb[2 * c] = yb2[c].x;
     yb[2 * c + 1] = yb2[c].y;
-  }
-}
-
-// dL/d s^_k from the below-threshold sums: -sum_i e_i c_k G_k . (y_i - out_k) / tau
-// = -c_k (G_k . E_y - E_0 h_k) / tau, with the warp's sums folded by its lane 0.
-__device__ __forceinline__ void ss_fold(const SsAcc& acc, int K, float it, BwdShared& bs) {
-  float E[9];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) E[c] = warp_sum(acc.E[c]);
-  if ((threadIdx.x & 31) == 0 && E[0] != 0.f) {
-    for (int k = 0; k < K; ++k) {
-      float gy = 0.f;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) gy = fmaf(bs.G[k][c], E[1 + c], gy);
-      atomicAdd(&bs.shatbar[k], -bs.ck[k] * (gy - E[0] * bs.h[k]) * it);
-    }
   }
 }
 
@@ -203,6 +147,16 @@ __device__ __forceinline__ float* eBexp_of(const BwdPair& P, int l) {
   return P.sadj && P.ps->kv[3] ? P.sadj + 12 * kMaxSel + 6 * l : nullptr;
 }
 
+template <int KMAX>
+__device__ __forceinline__ void shb_reduce(const float (&shb)[KMAX], int K, BwdShared& bs) {
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    if (k < K) {
+      const float v = warp_sum(shb[k]);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&bs.shatbar[k], v);
+    }
+  }
+}
 
 // Vertex-SDF reverse of this thread's candidates.
 template <int KMAX>
@@ -210,18 +164,19 @@ __device__ __forceinline__ void vs_reverse_phase(const BwdPair P) {
   const PairShared& ps = *P.ps;
   Adj adj;
   adj_zero(adj);
-  SsAcc acc;
-  ss_acc_zero(acc);
+  float shb[KMAX];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) shb[k] = 0.f;
   float y[8];
   for (int c = threadIdx.x; c < P.nvs; c += blockDim.x) {
     const float s = vs_candidate(ps, P.sm, P.bb, c, y);
     float yb[8], sb;
-    ss_bwd<KMAX>(*P.bs, P.K, P.F.inv_tau, P.F.k2, y, s, yb, sb, acc);
+    ss_bwd<KMAX>(*P.bs, P.K, P.F.inv_tau, P.F.k2, y, s, yb, sb, shb);
     if (c < ps.nvA) vs_bwd<true>(P.F, P.bb.A, P.bb.B, P.sm.vAl[c], ld3(P.sm.vA[c]), yb, sb, adj, vexp_of(P, c));
     else
       vs_bwd<false>(P.F, P.bb.A, P.bb.B, P.sm.vB[c - ps.nvA], ld3(P.sm.vB[c - ps.nvA]), yb, sb, adj, vexp_of(P, c));
   }
-  ss_fold(acc, P.K, P.F.inv_tau, *P.bs);
+  shb_reduce<KMAX>(shb, P.K, *P.bs);
   adj_reduce(adj, P.bs->adj);
 }
 
@@ -526,31 +481,6 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
         add_outer(Rl, gn, v3(y[4], y[5], y[6]));
         tl = gp;
       }
-      // the factorisation of the rows below s^_K (see ss_bwd)
-      const float thr = st.thr;
-      float yb0[8], Gk[8];
-      for (int c = 0; c < 8; ++c) {
-        yb0[c] = __shfl_sync(kFull, y[c], K - 1);
-        Gk[c] = lane < K ? bs.G[lane][c] : 0.f;
-      }
-      float ck = 0.f, hk = 0.f;
-      if (lane < K) {
-        ck = thr == kNegInf ? 0.f : ex2((thr - st.ls) * k2) / Z;
-        for (int c = 0; c < 8; ++c) hk = fmaf(Gk[c], y[c] - yb0[c], hk);
-        bs.ck[lane] = ck;
-        bs.h[lane] = hk;
-      }
-      float Gs[8];
-      for (int c = 0; c < 8; ++c) Gs[c] = warp_sum(ck * Gk[c]);
-      const float gs0 = warp_sum(ck * hk);
-      if (lane == 0) {
-        bs.thr = thr;
-        bs.gs0 = gs0;
-        for (int c = 0; c < 8; ++c) {
-          bs.Gs[c] = Gs[c];
-          bs.ybar0[c] = yb0[c];
-        }
-      }
       for (int i = 0; i < 9; ++i) Rl[i] = warp_sum(Rl[i]);
       tl = v3(warp_sum(tl.x), warp_sum(tl.y), warp_sum(tl.z));
       if (lane == 0) {
@@ -576,8 +506,9 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     {
       Adj adj;
       adj_zero(adj);
-      SsAcc acc;
-      ss_acc_zero(acc);
+      float shb[KMAX];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) shb[k] = 0.f;
       for (int i = threadIdx.x; i < nee; i += blockDim.x) {
         const int k = i / neB, l = i - k * neB;
         float t1, t2;
@@ -595,8 +526,8 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
         sq.A1.g = v3(q[7 * st], q[8 * st], q[9 * st]);
         ee_bwd(F, bb.A, bb.B, a.p, ee_geom(a, ps, sm, k, l), sm.rowL[k], sm.colL[l], &qs,
                [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
-                 ss_bwd<KMAX>(bs, K, it, k2, cc.y1, cc.s1, yb1, sb1, acc);
-                 ss_bwd<KMAX>(bs, K, it, k2, cc.y2, cc.s2, yb2, sb2, acc);
+                 ss_bwd<KMAX>(bs, K, it, k2, cc.y1, cc.s1, yb1, sb1, shb);
+                 ss_bwd<KMAX>(bs, K, it, k2, cc.y2, cc.s2, yb2, sb2, shb);
                },
                t1, t2, adj, &sq, eAexp_of(P, k), eBexp_of(P, l));
         T1[i] = t1;
@@ -604,7 +535,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
         atomicAdd(&rowR[k], t1);
         atomicAdd(&colC[l], t2);
       }
-      ss_fold(acc, K, it, bs);
+      shb_reduce<KMAX>(shb, K, bs);
       adj_reduce(adj, bs.adj);
     }
     __syncthreads();
