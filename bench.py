@@ -197,7 +197,7 @@ def run_reference(args, rank):
         return
     w = synth.make_config(2)
     steps = []
-    per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step_budget = max(0.5, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_oracle_rate(w, budget_s=per_step_budget / 4)
     total_pairs, total_t = 0, 0.0
