@@ -4,14 +4,17 @@
 // pairs).  Per pair:
 //   1. stage both meshes and A's planes/B's planes in shared memory, A moved
 //      into B's frame;
-//   2. vertex-SDF candidates (Sec. IV-C), warp-strided, streamed into the
-//      warp's SoftSort top-K state;
-//   3. E-E pass 1: witness QP of every edge pair -> unsigned distance dbar_kl,
-//      kept in the CTA's scratch slice (global memory, L2-resident);
+//   2. vertex-SDF candidates (Sec. IV-C), warp-strided from the last warp down,
+//      streamed into the warp's SoftSort top-K state;
+//   3. E-E pass 1: witness QP of every edge pair -> unsigned distance dbar_kl and
+//      the QP result, kept in the CTA's scratch slice (global memory, L2-resident),
+//      and each column's minimum (shared-memory atomicMin);
 //   4. soft row and column minima L = m - tau log sum exp(-(dbar - m)/tau) of
-//      the distance matrix (nn indicators of Sec. IV-D3, Eq. nn_check);
-//   5. E-E pass 2: witness QP again, four SDF evaluations, sign, pen, nn, cl and
-//      activity -> two candidates per edge pair, streamed into the warp state;
+//      the distance matrix (nn indicators of Sec. IV-D3, Eq. nn_check): one sweep,
+//      a warp per row, also adds the column sums;
+//   5. E-E pass 2: witnesses from the kept QP results, four SDF evaluations,
+//      sign, pen, nn, cl and activity -> two candidates per edge pair, streamed
+//      into the warp state;
 //   6. merge the warps' states pairwise and write the K rows, rotated back to world.
 #include "cm_pair.cuh"
 
