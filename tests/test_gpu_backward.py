@@ -74,6 +74,14 @@ def test_mixed_kinds_and_tau(engine, tau):
     print(f"mixed tau={tau} grad rel", check_against_oracle(engine, w, g))
 
 
+def test_hull_vs_hull(engine):
+    """Both bodies hulls (8..64 points each): the adjoint takes both hulls' plane
+    reverses (value at the other witness, Hessian-vector product at its own)."""
+    w = synth.config_hull_vs_hull(n=24, tau=1e-2)
+    g = np.random.default_rng(11).normal(size=(w.n_pairs, 8, 8))
+    print("hull-vs-hull grad rel", check_against_oracle(engine, w, g))
+
+
 def test_vertex_contacts_only(engine):
     w = synth.make_config(2, 32)
     g = np.random.default_rng(3).normal(size=(w.n_pairs, 4, 8))
