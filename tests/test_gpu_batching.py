@@ -126,3 +126,46 @@ def test_full_size_uneven_batch_sampled():
         assert rel.max() <= 1e-3, rel
     finally:
         eng.close()
+
+
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_full_size_autotuned_step_sampled(cfg):
+    """The benchmark's launch configuration at full size: 4096 hull-vs-primitive pairs or
+    1024 box-vs-hull32 pairs, autotuned launch shapes, one graph-replayed forward+adjoint
+    step; seeded samples against the oracle's values and gradients."""
+    from paper_2602_20304_gb300 import api
+    from paper_2602_20304_gb300.engine import Engine, workload_tensors
+
+    import oracle
+    from _parity import oracle_params
+    w = synth.make_config(cfg)
+    eng = Engine(0)
+    try:
+        ids = eng.add_geometries(w.geoms)
+        pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+        params = eng.params()
+        out = torch.empty((w.n_pairs, params.K, 8), device="cuda")
+        go = torch.randn(out.shape, device="cuda", generator=torch.Generator(device="cuda").manual_seed(cfg))
+        gp, gd = torch.empty_like(poses), torch.empty_like(dims)
+        api.cm_autotune(eng.ctx, pg, poses, dims, tau, params, out, go, gp, gd)
+        plan = api.cm_plan_create(eng.ctx, pg, poses, dims, tau, params, out, go, gp, gd)
+        try:
+            for _ in range(2):
+                api.cm_plan_launch(plan)
+            torch.cuda.synchronize()
+        finally:
+            api.cm_plan_destroy(plan)
+        eng.check()
+        o, gpn, gdn, gon = out.cpu().numpy(), gp.cpu().numpy(), gd.cpu().numpy(), go.cpu().numpy()
+        assert np.isfinite(o).all() and np.isfinite(gpn).all() and np.isfinite(gdn).all()
+        idx = np.random.default_rng(10 + cfg).choice(w.n_pairs, 8, replace=False)
+        assert_close(o[idx].astype(np.float64), oracle_forward(w, params, idx=idx), what=f"config {cfg} sample")
+        gi = list(idx[:4])
+        rp, rd = oracle.batch_manifold_grad(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, gon[gi],
+                                            oracle_params(params), idx=gi)
+        got = np.concatenate([gpn[gi], gdn[gi]], 1)
+        refg = np.concatenate([rp, rd], 1)
+        rel = np.abs(got - refg).max(1) / np.abs(refg).max(1)
+        assert rel.max() <= 1e-3, rel
+    finally:
+        eng.close()
