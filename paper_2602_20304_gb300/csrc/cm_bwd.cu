@@ -453,10 +453,13 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
         wtk_push(st, valid, s2, y2, K, k2, nvs + 2 * i + 1);
       }
     }
-    wtk_store(st, K);
-    __syncthreads();
+    // merge the warps' states pairwise (log2(nwarps) levels)
+    for (int h = 1; h < nwarps; h <<= 1) {
+      if ((warp & (2 * h - 1)) == h) wtk_store(st, K);
+      __syncthreads();
+      if ((warp & (2 * h - 1)) == 0 && warp + h < nwarps) wtk_merge(st, sm.warp + (warp + h) * kWarpStateFloats, K, k2);
+    }
     if (warp == 0) {
-      for (int w = 1; w < nwarps; ++w) wtk_merge(st, sm.warp + w * kWarpStateFloats, K, k2);
       float Z = 1.f;
       wtk_finish(st, K, k2, y, &Z);
       // upstream of row k in B's frame and the output-rotation adjoints
