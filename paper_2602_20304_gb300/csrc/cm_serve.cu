@@ -31,7 +31,6 @@ using Clock = std::chrono::steady_clock;
 struct Request {
   uint64_t ticket = 0;
   cm_request_desc d{};
-  size_t bytes = 0;          // device bytes of its share of a batch (inputs + outputs)
   int64_t max_ee = 1;        // largest E_A x E_B among its pairs (scratch slice size)
   Clock::time_point t_submit, t_done;
   int state = 0;             // 0 queued, 1 running, 2 done, 3 failed
@@ -49,11 +48,14 @@ struct Batch {
 
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t request_bytes(const cm_request_desc& d, int K) {
-  size_t n = (size_t)d.n_pairs;
-  size_t b = round256(8 * n) + round256(56 * n) + round256(24 * n) + round256(4 * n) + round256(32 * K * n);
-  if (d.with_backward) b += round256(32 * K * n) + round256(56 * n) + round256(24 * n);
-  return b;
+// Device bytes of one batch's block, exactly as Server::issue carves it: n pairs
+// of which nb with the adjoint, `grid` scratch slices of max_ee edge pairs (16
+// floats each with an adjoint in the batch, else 4), the work list and its counter.
+size_t batch_layout_bytes(size_t n, size_t nb, int K, size_t grid, int64_t max_ee) {
+  const size_t nb1 = std::max<size_t>(nb, 1);
+  return round256(8 * n) + round256(56 * n) + round256(24 * n) + round256(4 * n) + round256(32 * K * n) +
+         round256(32 * K * nb1) + round256(56 * nb1) + round256(24 * nb1) +
+         round256(grid * (size_t)max_ee * (nb ? 16 : 4) * sizeof(float)) + round256(4 * n) + round256(4);
 }
 }  // namespace
 
@@ -93,11 +95,11 @@ struct Server {
 
   size_t budget() const { return ctx->budget ? ctx->budget : (size_t)1 << 62; }
 
-  // Scratch of a batch: one slice of max_ee edge pairs per CTA, 16 floats per
-  // edge pair with an adjoint in the batch, else 4; plus the work list.
-  size_t scratch_bytes(int64_t max_ee, bool bwd, int pairs) const {
-    const size_t grid = (size_t)std::min(grid_max, std::max(pairs, 1));  // a launch never has more CTAs than pairs
-    return round256(grid * (size_t)max_ee * (bwd ? 16 : 4) * sizeof(float)) + round256((size_t)pairs * 4 + 4);
+  // Device block of a batch of `pairs` pairs (`bwd_pairs` with the adjoint) whose
+  // largest E_A x E_B is max_ee (a launch never has more CTAs than pairs).
+  size_t batch_bytes(int pairs, int bwd_pairs, int64_t max_ee) const {
+    const size_t grid = (size_t)std::min(grid_max, std::max(pairs, 1));
+    return batch_layout_bytes((size_t)std::max(pairs, 1), (size_t)bwd_pairs, params.K, grid, max_ee);
   }
 
   // Runs in the scheduler thread with `mu` held on entry and exit.
@@ -138,22 +140,19 @@ struct Server {
       }
     if (s < 0) return nullptr;
     auto b = std::make_unique<Batch>();
-    size_t io = 0;
-    int pairs = 0;
+    int pairs = 0, bwd_pairs = 0;
     int64_t mee = 1;
-    bool bwd = false;
     size_t bytes = 0;
     while (!queue.empty()) {
       Request* r = queue.front();
       if (!b->reqs.empty() && pairs + r->d.n_pairs > max_batch_pairs) break;
       const int64_t m2 = std::max(mee, r->max_ee);
-      const bool b2 = bwd || r->d.with_backward;
-      const size_t total = io + r->bytes + scratch_bytes(m2, b2, pairs + r->d.n_pairs);
+      const int nb2 = bwd_pairs + (r->d.with_backward ? r->d.n_pairs : 0);
+      const size_t total = batch_bytes(pairs + r->d.n_pairs, nb2, m2);
       if (bytes_in_use + total > budget()) break;
-      io += r->bytes;
       pairs += r->d.n_pairs;
+      bwd_pairs = nb2;
       mee = m2;
-      bwd = b2;
       bytes = total;
       b->reqs.push_back(r);
       queue.pop_front();
@@ -197,6 +196,8 @@ struct Server {
     float* scratch = (float*)take(grid * (size_t)b->max_ee * (nb ? 16 : 4) * sizeof(float));
     int32_t* order = (int32_t*)take(4 * n);
     int32_t* counter = (int32_t*)take(4);
+    if ((size_t)(p - static_cast<char*>(b->mem)) > b->bytes)  // the admission size and the carve disagree
+      return fail(CM_ERR_INVALID_ARG, "internal: batch layout exceeds its block");
     cudaStream_t s = b->stream;
     // inputs
     size_t off = 0, offb = 0;
@@ -338,7 +339,7 @@ cm_status cm_server_start(cm_context* c, const cm_params* params, int32_t max_ba
     }
   }
   srv->grid_max = gmax;
-  if (c->budget && srv->scratch_bytes(1, true, 1) + request_bytes(cm_request_desc{1, 1}, params->K) > c->budget)
+  if (c->budget && srv->batch_bytes(1, 1, 1) > c->budget)
     return fail(CM_ERR_ADMISSION, "the HBM budget does not even hold a one-pair batch");
   // batch memory comes from the stream-ordered pool: keep freed blocks cached
   // (up to the budget) instead of returning them to the driver
@@ -364,7 +365,6 @@ cm_status cm_submit(cm_context* c, const cm_request_desc* d, uint64_t* ticket) {
     return fail(CM_ERR_INVALID_ARG, "a backward request needs grad_out and grad_poses");
   auto r = std::make_unique<Request>();
   r->d = *d;
-  r->bytes = request_bytes(*d, s->params.K);
   {
     std::lock_guard<std::mutex> lk(c->mu);
     const int ng = (int)c->hdr.size();
@@ -376,7 +376,7 @@ cm_status cm_submit(cm_context* c, const cm_request_desc* d, uint64_t* ticket) {
     }
     r->max_ee = m;
   }
-  if (r->bytes + s->scratch_bytes(r->max_ee, d->with_backward != 0, d->n_pairs) > s->budget())
+  if (s->batch_bytes(d->n_pairs, d->with_backward ? d->n_pairs : 0, r->max_ee) > s->budget())
     return fail(CM_ERR_ADMISSION, "request does not fit the HBM budget even alone");
   r->t_submit = Clock::now();
   {
