@@ -99,6 +99,15 @@ def fp32_flops_per_pair(w, flags=0):
     return out
 
 
+def pipe_fracs(w, ms, peaks, flags=0):
+    """Useful-work fractions of the measured FP32 and MUFU peaks for one forward step of
+    `w` taking `ms` milliseconds (the step also holds the work-order kernel)."""
+    fma_peak, mufu_peak = peaks
+    s = ms * 1e-3
+    return {"fp32": float(fp32_flops_per_pair(w, flags).sum()) / s / fma_peak,
+            "mufu": float(mufu_ops_per_pair(w, flags).sum()) / s / mufu_peak}
+
+
 # Pipe activity of the forward kernel on this workload (4096 pairs) from the same ncu
 # capture: sm__pipe_fma_cycles_active and sm__inst_executed_pipe_xu, % of peak.
 FWD_NCU_PIPE_PCT = {"fma": 39.9, "xu": 26.3}
@@ -328,7 +337,7 @@ def plan_rate(eng, api, w, params, steps, with_bwd, flush, tune=True):
     return w.n_pairs * steps / (ms * 1e-3), ms / steps
 
 
-def extra_settings(Engine, api, local, steps, flush):
+def extra_settings(Engine, api, local, steps, flush, peaks):
     """The uneven 65536-pair batch (forward and forward+backward) and the paper's two
     simplifications (vertex-SDF contacts only; one-sided) on the default workload."""
     eng = Engine(local)
@@ -349,13 +358,14 @@ def extra_settings(Engine, api, local, steps, flush):
     return {"uneven_65536": {"workload": "65536 pairs, hull(8-256 pts, pool of 4096) vs mixed primitives, "
                                          "tau in {1e-3,1e-2,1e-1}, one persistent launch per step, CUDA graph",
                              "fwd_pairs_per_s": f4, "fwd_ms": f4_ms, "fwd_bwd_pairs_per_s": fb4, "fwd_bwd_ms": fb4_ms,
+                             "fwd_pipe_fracs": pipe_fracs(w4, f4_ms, peaks),
                              "preselect_top_edges_16_fwd_pairs_per_s": sel4, "preselect_fwd_ms": sel4_ms},
             "simplifications": {"workload": WORKLOAD.replace("K=8", "K=4"), "full_fwd_pairs_per_s": full,
                                 "no_ee_fwd_pairs_per_s": ne, "one_sided_fwd_pairs_per_s": nes,
                                 "speedup_no_ee": ne / full, "speedup_one_sided_vs_no_ee": nes / ne}}
 
 
-def small_config_rates(Engine, api, local, steps, flush):
+def small_config_rates(Engine, api, local, steps, flush, peaks):
     """The two 1024-pair settings: box-box poses (batched launch, and the plain path of
     one launch per pose) and box vs the hull of 32 points on the sphere (forward and
     forward+backward)."""
@@ -382,13 +392,15 @@ def small_config_rates(Engine, api, local, steps, flush):
         b.synchronize()
         plain = w1.n_pairs / (a.elapsed_time(b) * 1e-3)
         res["box_box_1024"] = {"workload": "two cubes h=0.5, 1024 poses, tau=1e-2, K=8", "fwd_pairs_per_s": r,
-                               "fwd_ms": ms, "plain_one_launch_per_pose_pairs_per_s": plain}
+                               "fwd_ms": ms, "fwd_pipe_fracs": pipe_fracs(w1, ms, peaks),
+                               "plain_one_launch_per_pose_pairs_per_s": plain}
         w3 = synth.make_config(3)
         f, fms = plan_rate(eng, api, w3, params, steps, False, flush)
         fb, fbms = plan_rate(eng, api, w3, params, steps, True, flush)
         res["box_vs_hull32_1024"] = {"workload": "box (dims U[0.2,1]) vs hull of 32 points on the unit sphere, "
                                                  "1024 pairs, tau=1e-2, K=8",
-                                     "fwd_pairs_per_s": f, "fwd_ms": fms, "fwd_bwd_pairs_per_s": fb, "fwd_bwd_ms": fbms}
+                                     "fwd_pairs_per_s": f, "fwd_ms": fms, "fwd_pipe_fracs": pipe_fracs(w3, fms, peaks),
+                                     "fwd_bwd_pairs_per_s": fb, "fwd_bwd_ms": fbms}
     finally:
         eng.close()
     return res
@@ -592,10 +604,10 @@ def main():
 
     extra = None
     if not args.no_extra and world == 1:
-        extra = extra_settings(Engine, api, local, max(3, min(args.steps, 5)), flush)
+        extra = extra_settings(Engine, api, local, max(3, min(args.steps, 5)), flush, (fma_peak, mufu_peak))
         extra["witness_points"] = witness_rates(api)
         extra["sq_union"] = sq_union_rates(Engine, api, local, max(3, min(args.steps, 5)), flush)
-        extra.update(small_config_rates(Engine, api, local, max(3, min(args.steps, 5)), flush))
+        extra.update(small_config_rates(Engine, api, local, max(3, min(args.steps, 5)), flush, (fma_peak, mufu_peak)))
         for k in ("ee", "vf"):
             extra["witness_points"][k]["hbm_frac_of_measured"] = extra["witness_points"][k]["hbm_gbs"] / _hbm_peak()
 
