@@ -625,12 +625,12 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   for (int bwd = 0; bwd < (grad_out ? 2 : 1); ++bwd) {
-    const int blocks[3] = {128, 256, 512};
+    const int blocks[4] = {64, 128, 256, 512};
     const int per_sms[3] = {1, 2, 0};
     LaunchCfg best = default_cfg(c, bwd, n_pairs);
     float best_ms = 3.0e38f;
-    for (int bi = 0; bi < 3; ++bi) {
-      if (bwd && blocks[bi] > 256) continue;  // the adjoint kernel is built for <= 256 threads
+    for (int bi = 0; bi < 4; ++bi) {
+      if (bwd && (blocks[bi] > 256 || blocks[bi] < 128)) continue;  // the adjoint kernel: 128..256 threads
       for (int pi = 0; pi < 3; ++pi)
         for (int ord = 0; ord < 2; ++ord) {
           LaunchCfg g{blocks[bi], per_sms[pi], ord};

@@ -326,12 +326,12 @@ cm_status cm_server_start(cm_context* c, const cm_params* params, int32_t max_ba
   }
   // the most CTAs any launch shape of a batch may use (scratch slices per batch)
   int gmax = 1;
-  for (int blk : {128, 256, 512}) {
+  for (int blk : {64, 128, 256, 512}) {
     SmemLayout L;
     int g = 1;
     shape(c, 0, LaunchCfg{blk, 0, 1}, max_batch_pairs, L, g);
     gmax = std::max(gmax, g);
-    if (blk <= 256) {
+    if (blk >= 128 && blk <= 256) {  // the adjoint's shapes
       for (int ps : {1, 2}) {
         shape(c, 1, LaunchCfg{blk, ps, 1}, max_batch_pairs, L, g);
         gmax = std::max(gmax, g);
