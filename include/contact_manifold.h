@@ -161,7 +161,15 @@ cm_status cm_create_geometry(cm_context* ctx, const cm_geometry_desc* desc, int3
  * graph that launches compute calls, so that the capture contains no copies. */
 cm_status cm_sync_geometry(cm_context* ctx);
 
-/* Number of registered geometries. */
+/* Unregisters geometry `geom_id`: later calls treat a pair that names it like a
+ * pair with an unknown id (NaN rows / gradients and the sticky device error
+ * flag, see cm_check_device_error).  Ids are never reused and the packed copy
+ * keeps the data until the context is destroyed.  Plans made before become
+ * invalid.  Destroy only geometry that no call still in flight (including a
+ * serving batch) uses.  CM_ERR_INVALID_ARG for an unknown or already destroyed id. */
+cm_status cm_destroy_geometry(cm_context* ctx, int32_t geom_id);
+
+/* Number of registered geometries (destroyed ones included: ids are not reused). */
 int32_t cm_num_geometries(const cm_context* ctx);
 
 /* Forward manifold of n_pairs independent pairs (Sec. IV-A's g_{1,2} per pair).

@@ -59,6 +59,7 @@ _SIGS = {
     "cm_create_geometry": (ctypes.c_int, [_vp, ctypes.POINTER(cm_geometry_desc),
                                           ctypes.POINTER(ctypes.c_int32)]),
     "cm_sync_geometry": (ctypes.c_int, [_vp]),
+    "cm_destroy_geometry": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "cm_num_geometries": (ctypes.c_int32, [_vp]),
     "cm_check_device_error": (ctypes.c_int, [_vp]),
     "cm_contact_manifold_fwd": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
@@ -149,6 +150,10 @@ def cm_create_geometry(ctx, kind, dims, verts, edges, planes=None) -> int:
 
 def cm_sync_geometry(ctx) -> None:
     _check(_lib.cm_sync_geometry(ctx))
+
+
+def cm_destroy_geometry(ctx, geom_id) -> None:
+    _check(_lib.cm_destroy_geometry(ctx, int(geom_id)))
 
 
 def cm_num_geometries(ctx) -> int:

@@ -79,6 +79,10 @@ __device__ inline void pair_setup(const FwdArgs& a, int pi, PairShared& ps) {
   if (ps.bad) return;
   const GeomHeader& A = a.hdr[ga];
   const GeomHeader& B = a.hdr[gb];
+  if (A.n_verts <= 0 || B.n_verts <= 0) {  // destroyed geometry (cm_destroy_geometry)
+    ps.bad = 1;
+    return;
+  }
   const float* P = a.poses + 14 * (size_t)pi;
   ps.RA = quat_rot(P[0], P[1], P[2], P[3]);
   ps.tA = v3(P[4], P[5], P[6]);

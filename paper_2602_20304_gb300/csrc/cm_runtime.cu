@@ -440,6 +440,26 @@ cm_status cm_sync_geometry(cm_context* c) {
   return sync_geometry_locked(c);
 }
 
+cm_status cm_destroy_geometry(cm_context* c, int32_t geom_id) {
+  if (!c) return fail(CM_ERR_INVALID_ARG, "NULL context");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (geom_id < 0 || geom_id >= (int32_t)c->hdr.size()) return fail(CM_ERR_INVALID_ARG, "unknown geometry id");
+  GeomHeader& h = c->hdr[geom_id];
+  if (h.n_verts <= 0) return fail(CM_ERR_INVALID_ARG, "geometry already destroyed");
+  // the kernels treat a header without vertices as an invalid id; its packed data stays
+  h.n_verts = h.n_edges = h.n_planes = 0;
+  // the smallest live geometry bounds K and the E-E checks
+  c->min_v = c->min_e = 1 << 30;
+  for (const GeomHeader& g : c->hdr)
+    if (g.n_verts > 0) {
+      c->min_v = std::min(c->min_v, g.n_verts);
+      c->min_e = std::min(c->min_e, g.n_edges);
+    }
+  c->dirty = true;
+  ++c->geom_gen;  // plans made before hold the old headers: invalid from now on
+  return CM_OK;
+}
+
 int32_t cm_num_geometries(const cm_context* c) { return c ? (int32_t)c->hdr.size() : 0; }
 
 cm_status cm_check_device_error(cm_context* c) {
@@ -454,7 +474,7 @@ cm_status cm_check_device_error(cm_context* c) {
   if (v != 0) {
     cudaMemset(c->d_err, 0, sizeof(int));
     char buf[128];
-    std::snprintf(buf, sizeof buf, "pair %d names an unknown geometry id", v - 1);
+    std::snprintf(buf, sizeof buf, "pair %d names an unknown or destroyed geometry id", v - 1);
     return fail(CM_ERR_DEVICE, buf);
   }
   return CM_OK;

@@ -130,6 +130,42 @@ def test_invalid_geometry_id_sets_flag(engine):
     engine.check()                                   # flag was cleared
 
 
+def test_destroyed_geometry_acts_as_unknown_id():
+    """After cm_destroy_geometry a pair naming the geometry gets NaN rows and the error
+    flag while the other pairs are unchanged; a plan made before is refused."""
+    from paper_2602_20304_gb300 import api
+    from paper_2602_20304_gb300.engine import Engine, workload_tensors
+    w = synth.make_config(1, 16)
+    eng = Engine(0)
+    try:
+        ids = eng.add_geometries(w.geoms)
+        spare = eng.add_geometries(w.geoms)[0]          # a second copy of the cube
+        pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+        pg[8:, 1] = int(spare)
+        before = eng.forward(pg, poses, dims, tau).cpu().numpy()
+        eng.check()
+        plan = api.cm_plan_create(eng.ctx, pg, poses, dims, tau, eng.params(), torch.empty((16, 8, 8), device="cuda"))
+        api.cm_destroy_geometry(eng.ctx, int(spare))
+        with pytest.raises(api.CMError) as ei:
+            api.cm_plan_launch(plan)
+        assert ei.value.status == api.CM_ERR_INVALID_ARG
+        api.cm_plan_destroy(plan)
+        after = eng.forward(pg, poses, dims, tau).cpu().numpy()
+        with pytest.raises(api.CMError) as ei:
+            eng.check()
+        assert ei.value.status == api.CM_ERR_DEVICE
+        assert np.isnan(after[8:]).all()
+        np.testing.assert_allclose(after[:8], before[:8], atol=1e-6, rtol=0)
+        gp, _ = eng.backward(pg, poses, dims, tau, torch.ones((16, 8, 8), device="cuda"))
+        g = gp.cpu().numpy()
+        with pytest.raises(api.CMError):
+            eng.check()
+        assert np.isnan(g[8:]).all() and np.isfinite(g[:8]).all()
+        eng.check()
+    finally:
+        eng.close()
+
+
 def test_empty_and_argument_errors(engine):
     from paper_2602_20304_gb300 import api
     engine.add_geometries(synth.make_config(1, 2).geoms)

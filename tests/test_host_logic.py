@@ -145,3 +145,17 @@ def test_selection_and_tracing_limits(api, ctx):
                                          ctypes.byref(p), ctypes.c_void_p(8), None)
         assert st == api.CM_ERR_INVALID_ARG, over
     assert api.cm_default_params().trace_iters == 0
+
+
+def test_destroy_geometry(api, ctx):
+    """Unregistering keeps ids stable (never reused), rejects unknown and twice-destroyed
+    ids, and new geometry still gets the next id."""
+    w = synth.make_config(2, 4)
+    ids = [add(api, ctx, g) for g in w.geoms]
+    api.cm_destroy_geometry(ctx, ids[1])
+    assert api.cm_num_geometries(ctx) == len(ids)
+    for bad in (ids[1], -1, len(ids)):
+        with pytest.raises(api.CMError) as ei:
+            api.cm_destroy_geometry(ctx, bad)
+        assert ei.value.status == api.CM_ERR_INVALID_ARG
+    assert add(api, ctx, w.geoms[0]) == len(ids)
