@@ -18,5 +18,5 @@ from .workloads import (  # noqa: F401
     config_box_vs_sphere_hull, config_hull_vs_hull, config_mixed, config_mixed_pooled, serving_trace,
     make_config,
     SQ_RESOLUTIONS, random_sq_union, config_sq_union,
-    SEED_BASE,
+    SEED_BASE, PRIMITIVE_KINDS,
 )
