@@ -25,6 +25,34 @@ def test_edge_edge_witness_batch():
     assert np.abs(got[:, 7] - torch.linalg.vector_norm(e1 - e2, dim=1).numpy()).max() < 1e-5
 
 
+def test_edge_edge_witness_near_parallel():
+    """Edge pairs 1e-6 .. 1e-3 rad from parallel, the subset where the 2x2 solve is
+    worst conditioned (Q^T Q is singular without the L2 term): the FP32 kernel holds the
+    same 1e-5 as on generic queries, so the solve needs no FP64."""
+    from paper_2602_20304_gb300 import api
+    rng = np.random.default_rng(5)
+    n = 200_000
+    unit = lambda v: v / np.linalg.norm(v, axis=1, keepdims=True)  # noqa: E731
+    u = unit(rng.standard_normal((n, 3)))
+    perp = unit(np.cross(u, rng.standard_normal((n, 3))))
+    th = 10.0 ** rng.uniform(-6, -3, n)
+    u2 = np.cos(th)[:, None] * u + np.sin(th)[:, None] * perp
+    a0 = rng.uniform(0, 1, (n, 3))
+    b0 = a0 + rng.uniform(-0.3, 0.3, (n, 3))
+    q = np.concatenate([a0, a0 + rng.uniform(0.2, 1, (n, 1)) * u,
+                        b0, b0 + rng.uniform(0.2, 1, (n, 1)) * u2], 1).astype(np.float32)
+    out = torch.empty((n, 8), device="cuda")
+    api.cm_ee_witness_batch(torch.from_numpy(q).cuda(), api.cm_default_params(), out)
+    got = out.cpu().numpy().astype(np.float64)
+    t = torch.from_numpy(q.astype(np.float64))
+    e1, e2, _, _, con = oracle.ee_witness(t[:, 0:3], t[:, 3:6], t[:, 6:9], t[:, 9:12])
+    err = [np.abs(got[:, 0:3] - e1.numpy()).max(), np.abs(got[:, 3:6] - e2.numpy()).max(),
+           np.abs(got[:, 6] - con.numpy()).max(),
+           np.abs(got[:, 7] - torch.linalg.vector_norm(e1 - e2, dim=1).numpy()).max()]
+    print("near-parallel e1, e2, con, dbar max errors", err)
+    assert max(err) < 1e-5, err
+
+
 def test_vertex_face_witness_batch():
     from paper_2602_20304_gb300 import api
     rng = np.random.default_rng(2)

@@ -113,3 +113,42 @@ def test_fig4_sweep_continuity_and_unsmoothed_jump():
     th_even = np.linspace(np.pi / 2 - 0.02, np.pi / 2 + 0.02, 1600)
     hard = _rotating_sweep(th_even, w_reg=1e-12, eps_clip=1e-9, eps_min=1e-9, eps_comp=1e-9)
     assert np.linalg.norm(np.diff(hard, axis=0), axis=1).max() > 1.5
+
+
+def test_crossing_penetrating_edges():
+    """A unit cube A and a box B (half-extents 1, 0.5, 0.5) turned 45 degrees about x so
+    that its lowest edge runs along x at height 0.5 - delta and crosses A's top edge
+    x = 0.5 (along y) at right angles (Sec. IV-D3).  By symmetry A's witness is the middle
+    of its edge, (0.5, 0, 0.5), exactly; B's witness lies on its lowest edge (y = 0,
+    z = 0.5 - delta), pulled along x only by the QP's alpha-space smoothing.  A's witness
+    sits inside B, both soft signs are -1, so both signed distances are -|e1* - e2*|
+    (<= -delta), the two normals are exactly opposite (n1 = -n2), n1 points down into A
+    (B's outward side there), and the normals clash (cl ~ 1)."""
+    from oracle.manifold import _Body
+    import synth
+    box = synth.primitive_geometry(synth.KIND_BOX)
+    tau, delta = 1e-2, 0.05
+    c, s = np.cos(np.pi / 8), np.sin(np.pi / 8)
+    A = _Body(box, t([1, 0, 0, 0, 0, 0, 0]), t([0.5, 0.5, 0.5]), tau)
+    B = _Body(box, t([c, s, 0, 0, 0, 0, 0.5 - delta + np.sqrt(0.5)]), t([1.0, 0.5, 0.5]), tau)
+    a0, a1 = A.verts[A.edges[:, 0]], A.verts[A.edges[:, 1]]
+    b0, b1 = B.verts[B.edges[:, 0]], B.verts[B.edges[:, 1]]
+    cand = oracle.ee_candidates(a0, a1, b0, b1, A.sdf, B.sdf, tau)
+    miss = (cand["p1"] - t([0.5, 0, 0.5])).norm(dim=-1)
+    miss = miss + (cand["p2"][..., 1:] - t([0, 0.5 - delta])).norm(dim=-1)
+    k, l = np.unravel_index(int(torch.argmin(miss)), miss.shape)
+    p1, p2 = cand["p1"][k, l].numpy(), cand["p2"][k, l].numpy()
+    np.testing.assert_allclose(p1, [0.5, 0, 0.5], atol=1e-12)
+    np.testing.assert_allclose(p2[1:], [0, 0.5 - delta], atol=1e-12)
+    assert abs(p2[0] - 0.5) < 2e-2
+    g1, g2 = float(cand["gamma1"][k, l]), float(cand["gamma2"][k, l])
+    assert g1 < -0.999999 and g2 < -0.999999
+    dbar = np.linalg.norm(p1 - p2)
+    assert dbar >= delta
+    for d in (float(cand["d1"][k, l]), float(cand["d2"][k, l])):
+        assert abs(d + dbar) < 1e-9, (d, dbar)
+    n1, n2 = cand["n1"][k, l].numpy(), cand["n2"][k, l].numpy()
+    np.testing.assert_allclose(n1, -n2, atol=1e-12)
+    assert n1[2] < -0.9 and abs(n1[1]) < 1e-9
+    assert float(cand["pen1"][k, l]) > 0.9
+    assert float(cand["cl"][k, l]) > 0.99
