@@ -188,17 +188,24 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- reference arm
-def cpu_oracle_rate(w, budget_s=15.0, max_pairs=None):
-    """Pairs/s of the FP64 oracle (as it stands) on the first pairs of ``w`` within ``budget_s``."""
+def cpu_oracle_rate(w, budget_s=15.0, max_pairs=None, threads=None):
+    """Pairs/s of the FP64 oracle (as it stands) on the first pairs of ``w`` within ``budget_s``,
+    on PyTorch's intra-op threads (``threads`` of them if given, else the default)."""
     import torch
     import oracle
-    done, t0 = 0, time.perf_counter()
-    limit = w.n_pairs if max_pairs is None else min(max_pairs, w.n_pairs)
-    while done < limit and time.perf_counter() - t0 < budget_s:
-        oracle.batch_manifold(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, idx=[done])
-        done += 1
-    dt = time.perf_counter() - t0
-    return done / dt, done, dt, torch.get_num_threads()
+    saved = torch.get_num_threads()
+    if threads:
+        torch.set_num_threads(int(threads))
+    try:
+        done, t0 = 0, time.perf_counter()
+        limit = w.n_pairs if max_pairs is None else min(max_pairs, w.n_pairs)
+        while done < limit and time.perf_counter() - t0 < budget_s:
+            oracle.batch_manifold(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, idx=[done])
+            done += 1
+        dt = time.perf_counter() - t0
+        return done / dt, done, dt, torch.get_num_threads()
+    finally:
+        torch.set_num_threads(saved)
 
 
 def run_reference(args, rank):
@@ -631,6 +638,9 @@ def main():
         r, n, dt, cores = cpu_oracle_rate(w, budget_s=args.cpu_seconds)
         cpu = {"value": r, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                "sample": f"first {n} pairs of the workload ({dt:.1f} s)"}
+        r1, n1, dt1, _ = cpu_oracle_rate(w, budget_s=min(5.0, args.cpu_seconds / 3), threads=1)
+        cpu["single_thread"] = {"value": r1, "unit": "pairs/s", "cores": 1,
+                                "sample": f"first {n1} pairs of the workload ({dt1:.1f} s)"}
         if extra is not None:
             cpu["other_settings"] = oracle_rates()
 

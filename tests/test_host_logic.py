@@ -159,3 +159,16 @@ def test_destroy_geometry(api, ctx):
             api.cm_destroy_geometry(ctx, bad)
         assert ei.value.status == api.CM_ERR_INVALID_ARG
     assert add(api, ctx, w.geoms[0]) == len(ids)
+
+
+def test_bench_oracle_rate_restores_thread_count():
+    """The benchmark's CPU-baseline leg times the oracle on one thread and on the default
+    intra-op pool; the single-thread leg leaves the pool as it found it."""
+    import torch
+    import bench
+    import synth
+    w = synth.make_config(1, 4)
+    before = torch.get_num_threads()
+    r, n, dt, cores = bench.cpu_oracle_rate(w, budget_s=30.0, max_pairs=2, threads=1)
+    assert cores == 1 and n == 2 and r > 0
+    assert torch.get_num_threads() == before
