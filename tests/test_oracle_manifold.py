@@ -91,6 +91,36 @@ def test_softsort_limits():
     assert np.abs(out - eq.numpy().mean(0)).max() < 1e-14
 
 
+def test_softsort_two_score_levels_closed_form():
+    """Sec. III SoftSort on two score levels a gap tau ln 3 apart: one candidate x0 on top,
+    three (x1..x3) below.  Row 1 sits on the top score: weights 1 and e^{-ln 3} = 1/3 each,
+    normalised to 1/2 and 1/6.  Row 2 sits on the lower level: x0 gets 1/3 against 1 for
+    each of the others, i.e. 1/10 and 3/10.  (Without the absolute value in the logits
+    row 2 would weigh x0 by 3 instead of 1/3.)"""
+    tau = 0.05
+    rng = np.random.default_rng(11)
+    cand = t(rng.normal(size=(4, 8)))
+    cand[:, 7] = 1.0
+    cand[0, 3] = -0.5
+    cand[1:, 3] = -0.5 + tau * np.log(3.0)
+    out = soft_topk_reduce(cand, tau, 2).numpy()
+    x = cand.numpy()
+    np.testing.assert_allclose(out[0], x[0] / 2 + x[1:].sum(0) / 6, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(out[1], x[0] / 10 + 3 * x[1:].sum(0) / 10, rtol=0, atol=1e-13)
+
+
+def test_softsort_ignores_candidate_order():
+    """The reduction depends on the candidate set, not on the order of the rows."""
+    rng = np.random.default_rng(12)
+    cand = t(rng.normal(size=(50, 8)))
+    cand[:, 7] = t(rng.uniform(0.0, 1.0, 50))
+    perm = torch.as_tensor(rng.permutation(50))
+    for tau in (1e-3, 1e-2, 1e-1):
+        a = soft_topk_reduce(cand, tau, 8).numpy()
+        b = soft_topk_reduce(cand[perm], tau, 8).numpy()
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+
+
 def test_resting_box_closed_form():
     """Small cube (h = 0.3) resting axis-aligned on a larger one (h = 0.5) with depth delta.
     As tau -> 0 its four bottom vertices read d = -delta with normal +z and activity 1."""
