@@ -113,9 +113,13 @@ def pipe_fracs(w, ms, peaks, flags=0):
 FWD_NCU_PIPE_PCT = {"fma": 39.9, "xu": 26.3}
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one forward-kernel launch
-# on this workload at 4096 pairs, from one ncu capture of the current kernel; scaled
-# by the pairs a launch processes (traffic grows in proportion).
+# on this workload at 4096 pairs, from one ncu capture; scaled by the pairs a launch
+# processes (traffic grows in proportion).  The kernel has changed since that capture
+# (pair setup now also rejects destroyed geometry, one branch on header fields it
+# already reads), so the roofline's "traffic" is null and the figure is reported beside
+# it as the last capture's.
 FWD_TRAFFIC_BYTES_4096 = 5.426944e6 + 21.611264e6
+FWD_TRAFFIC_CURRENT = False
 
 
 def _hbm_peak():
@@ -604,8 +608,11 @@ def main():
                       "peak_source": "measured FFMA throughput (cm_measure_pipe_peaks)"}}
     binding = max(pipes, key=lambda k: pipes[k]["frac"])
     roof = {"bound": "alu", "pipe": binding, **pipes[binding],
-            "traffic": None if FWD_TRAFFIC_BYTES_4096 is None else FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096,
+            "traffic": FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096 if FWD_TRAFFIC_CURRENT else None,
             "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "traffic_last_capture": {"value": FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096,
+                                     "note": "ncu capture taken before the destroyed-geometry check "
+                                             "was added to pair setup"},
             "algorithmic_bytes": 348 * w.n_pairs, "pipes": pipes,
             "ncu_pipe_active_pct": FWD_NCU_PIPE_PCT}
 
