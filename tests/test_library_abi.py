@@ -62,3 +62,19 @@ def test_no_device_is_an_error_not_a_crash(libpath):
         api.cm_create_context(0)
     assert ei.value.status in (api.CM_ERR_CUDA, api.CM_ERR_INVALID_ARG)
     assert api.cm_last_error()
+
+
+def test_device_code_has_no_trap_assert_or_unbounded_wait():
+    """Failures on the device are reported, never raised by faulting: the kernels hold no
+    __trap, no device assert and no PTX trap or breakpoint, and no spin on a barrier or
+    flag (no mbarrier waits); bad input sets the sticky error flag and skips the pair."""
+    srcs = glob.glob(os.path.join(ROOT, "paper_2602_20304_gb300", "csrc", "*.cu*"))
+    srcs += glob.glob(os.path.join(ROOT, "paper_2602_20304_gb300", "csrc", "*.h"))
+    assert srcs
+    for f in srcs:
+        code = open(f).read()
+        code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        code = code.replace("static_assert", "")
+        for bad in (r"__trap\s*\(", r"\bassert\s*\(", r"\btrap;", r"\bbrkpt\b", r"mbarrier\.try_wait"):
+            assert not re.search(bad, code), (os.path.basename(f), bad)
