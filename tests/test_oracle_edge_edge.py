@@ -152,3 +152,8 @@ def test_crossing_penetrating_edges():
     assert n1[2] < -0.9 and abs(n1[1]) < 1e-9
     assert float(cand["pen1"][k, l]) > 0.9
     assert float(cand["cl"][k, l]) > 0.99
+    # nearest-neighbour indicators: A's edge has one near edge of B (nn over B's edges
+    # ~ 1); B's lowest edge crosses both of A's top edges along y, at x = +-0.5, at
+    # mirror-equal distances (nn over A's edges = 1/2; the next edges are ~0.45 farther)
+    assert float(cand["nn1"][k, l]) > 0.999
+    assert abs(float(cand["nn2"][k, l]) - 0.5) < 1e-9
