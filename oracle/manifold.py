@@ -15,8 +15,9 @@ largest scores; the SoftSort rows Gamma_{k,i} = softmax_i(-|s^_k - s_i| / tau)
 out_k = sum_i Gamma_{k,i} (p_i, d_i, n_i, w_i), a (K, 8) array per pair laid out
 (p_x, p_y, p_z, d, n_x, n_y, n_z, w).  Parity of this step is unpinned by the
 paper's own numbers; tests pin its limits (hard top-K as tau -> 0, rows that
-sum to one, uniform rows for equal scores) and the swap/rigid-motion
-invariances of the whole manifold.
+sum to one, uniform rows for equal scores), its exact weights on two score
+levels tau ln 3 apart, its independence of candidate order, and the
+swap/rigid-motion invariances of the whole manifold.
 """
 import dataclasses
 
