@@ -99,13 +99,52 @@ def fp32_flops_per_pair(w, flags=0):
     return out
 
 
-def pipe_fracs(w, ms, peaks, flags=0):
-    """Useful-work fractions of the measured FP32 and MUFU peaks for one forward step of
-    `w` taking `ms` milliseconds (the step also holds the work-order kernel)."""
+# Peaks of the two arithmetic pipes from unit counts and the maximum SM clock, the
+# denominators of the ALU roofline: 152 SMs x 128 FP32 lanes x 2 flops (FFMA) x 2070 MHz
+# = 80.5 TFLOP/s, and 152 SMs x 32 ex2 results per clock x 2070 MHz = 10.1 Top/s.  The
+# bench also measures an FFMA loop and an ex2.approx loop on the device and reports each
+# fraction of those beside.
+N_SMS, FP32_LANES_PER_SM, MUFU_EX2_PER_SM_CLK, SM_MAX_MHZ = 152, 128, 32, 2070
+FP32_PEAK_DERIVED = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+MUFU_PEAK_DERIVED = N_SMS * MUFU_EX2_PER_SM_CLK * SM_MAX_MHZ * 1e6
+ALU_PEAKS = (FP32_PEAK_DERIVED, MUFU_PEAK_DERIVED)
+
+
+def pipe_fracs(w, ms, peaks=ALU_PEAKS, flags=0):
+    """Useful-work fractions of the FP32 and MUFU peaks (default: from unit counts and
+    clock) for one forward step of `w` taking `ms` milliseconds (the step also holds the
+    work-order kernel)."""
     fma_peak, mufu_peak = peaks
     s = ms * 1e-3
     return {"fp32": float(fp32_flops_per_pair(w, flags).sum()) / s / fma_peak,
             "mufu": float(mufu_ops_per_pair(w, flags).sum()) / s / mufu_peak}
+
+
+def alu_roofline(w, step_s, measured):
+    """Roofline object of the forward kernel for one step of ``w`` taking ``step_s`` seconds:
+    both pipes' achieved rates against the peaks from unit counts and clock, the larger
+    fraction binding, with the fractions of the measured loop throughputs
+    ``measured = (FFMA flop/s, ex2 op/s)`` beside them."""
+    fma_meas, mufu_meas = measured
+    mufu = float(mufu_ops_per_pair(w).sum()) / step_s
+    flops = float(fp32_flops_per_pair(w).sum()) / step_s
+    pipes = {"mufu": {"achieved": mufu / 1e9, "peak": MUFU_PEAK_DERIVED / 1e9, "unit": "Gop/s",
+                      "frac": mufu / MUFU_PEAK_DERIVED,
+                      "peak_source": "152 SMs x 32 ex2 per clock x 2070 MHz",
+                      "peak_measured": mufu_meas / 1e9, "frac_of_measured": mufu / mufu_meas},
+             "fp32": {"achieved": flops / 1e12, "peak": FP32_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
+                      "frac": flops / FP32_PEAK_DERIVED,
+                      "peak_source": "152 SMs x 128 lanes x 2 flops x 2070 MHz",
+                      "peak_measured": fma_meas / 1e12, "frac_of_measured": flops / fma_meas}}
+    binding = max(pipes, key=lambda k: pipes[k]["frac"])
+    return {"bound": "alu", "pipe": binding, **pipes[binding],
+            "traffic": FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096 if FWD_TRAFFIC_CURRENT else None,
+            "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "traffic_last_capture": {"value": FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096,
+                                     "note": "ncu capture taken before the destroyed-geometry check "
+                                             "was added to pair setup"},
+            "algorithmic_bytes": 348 * w.n_pairs, "pipes": pipes,
+            "ncu_pipe_active_pct": FWD_NCU_PIPE_PCT}
 
 
 # Pipe activity of the forward kernel on this workload (4096 pairs) from the same ncu
@@ -599,29 +638,14 @@ def main():
     # step also holds the few-microsecond work-order kernel, so this slightly understates it).
     # Both arithmetic pipes are reported; the binding one is the larger fraction.
     fma_peak, mufu_peak = api.cm_measure_pipe_peaks(local)
-    kernel_s = float(np.mean(step_ms)) * 1e-3
-    mufu = float(mufu_ops_per_pair(w).sum()) / kernel_s
-    flops = float(fp32_flops_per_pair(w).sum()) / kernel_s
-    pipes = {"mufu": {"achieved": mufu / 1e9, "peak": mufu_peak / 1e9, "unit": "Gop/s", "frac": mufu / mufu_peak,
-                      "peak_source": "measured ex2.approx throughput (cm_measure_pipe_peaks)"},
-             "fp32": {"achieved": flops / 1e12, "peak": fma_peak / 1e12, "unit": "TFLOP/s", "frac": flops / fma_peak,
-                      "peak_source": "measured FFMA throughput (cm_measure_pipe_peaks)"}}
-    binding = max(pipes, key=lambda k: pipes[k]["frac"])
-    roof = {"bound": "alu", "pipe": binding, **pipes[binding],
-            "traffic": FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096 if FWD_TRAFFIC_CURRENT else None,
-            "traffic_unit": "bytes per launch (ncu dram read + write)",
-            "traffic_last_capture": {"value": FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096,
-                                     "note": "ncu capture taken before the destroyed-geometry check "
-                                             "was added to pair setup"},
-            "algorithmic_bytes": 348 * w.n_pairs, "pipes": pipes,
-            "ncu_pipe_active_pct": FWD_NCU_PIPE_PCT}
+    roof = alu_roofline(w, float(np.mean(step_ms)) * 1e-3, (fma_peak, mufu_peak))
 
     extra = None
     if not args.no_extra and world == 1:
-        extra = extra_settings(Engine, api, local, max(3, min(args.steps, 5)), flush, (fma_peak, mufu_peak))
+        extra = extra_settings(Engine, api, local, max(3, min(args.steps, 5)), flush, ALU_PEAKS)
         extra["witness_points"] = witness_rates(api)
         extra["sq_union"] = sq_union_rates(Engine, api, local, max(3, min(args.steps, 5)), flush)
-        extra.update(small_config_rates(Engine, api, local, max(3, min(args.steps, 5)), flush, (fma_peak, mufu_peak)))
+        extra.update(small_config_rates(Engine, api, local, max(3, min(args.steps, 5)), flush, ALU_PEAKS))
         for k in ("ee", "vf"):
             extra["witness_points"][k]["hbm_frac_of_measured"] = extra["witness_points"][k]["hbm_gbs"] / _hbm_peak()
 

@@ -172,3 +172,22 @@ def test_bench_oracle_rate_restores_thread_count():
     r, n, dt, cores = bench.cpu_oracle_rate(w, budget_s=30.0, max_pairs=2, threads=1)
     assert cores == 1 and n == 2 and r > 0
     assert torch.get_num_threads() == before
+
+
+def test_bench_alu_roofline_object():
+    """The benchmark's roofline object: both pipes against the peaks from unit counts and
+    the 2070 MHz clock, the larger fraction binding, the measured loop throughputs beside."""
+    import bench
+    import synth
+    w = synth.make_config(2, 16)
+    assert abs(bench.FP32_PEAK_DERIVED - 152 * 128 * 2 * 2.07e9) < 1.0
+    assert abs(bench.MUFU_PEAK_DERIVED - 152 * 32 * 2.07e9) < 1.0
+    r = bench.alu_roofline(w, 1e-5, (76e12, 9.8e12))
+    assert r["bound"] == "alu" and r["pipe"] in ("fp32", "mufu")
+    for k, p in r["pipes"].items():
+        scale = 1e12 if k == "fp32" else 1e9
+        assert abs(p["frac"] - p["achieved"] / p["peak"]) < 1e-12
+        assert abs(p["frac_of_measured"] - p["achieved"] * scale / (76e12 if k == "fp32" else 9.8e12)) < 1e-12
+    assert r["frac"] == max(p["frac"] for p in r["pipes"].values())
+    assert r["algorithmic_bytes"] == 348 * 16
+    assert (r["traffic"] is None) == (not bench.FWD_TRAFFIC_CURRENT)
