@@ -42,6 +42,11 @@ class cm_params(ctypes.Structure):
                 ("trace_iters", ctypes.c_int32)]
 
 
+class cm_geometry_info(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dims", ctypes.c_float * 3), ("n_verts", ctypes.c_int32),
+                ("n_edges", ctypes.c_int32), ("n_planes", ctypes.c_int32)]
+
+
 class cm_request_desc(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int32), ("with_backward", ctypes.c_int32),
                 ("pair_geoms", ctypes.c_void_p), ("poses", ctypes.c_void_p), ("dims", ctypes.c_void_p),
@@ -61,6 +66,8 @@ _SIGS = {
     "cm_sync_geometry": (ctypes.c_int, [_vp]),
     "cm_destroy_geometry": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "cm_num_geometries": (ctypes.c_int32, [_vp]),
+    "cm_create_hull_geometry": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "cm_get_geometry": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(cm_geometry_info), _vp, _vp, _vp]),
     "cm_check_device_error": (ctypes.c_int, [_vp]),
     "cm_contact_manifold_fwd": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
                                                ctypes.POINTER(cm_params), _vp, _vp]),
@@ -158,6 +165,30 @@ def cm_destroy_geometry(ctx, geom_id) -> None:
 
 def cm_num_geometries(ctx) -> int:
     return int(_lib.cm_num_geometries(ctx))
+
+
+def cm_create_hull_geometry(ctx, points) -> int:
+    """Registers the convex hull of ``points`` ((n, 3), converted to float64) and returns its id."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    if pts.ndim != 2 or pts.shape[1] != 3:
+        raise ValueError("points must have shape (n, 3)")
+    gid = ctypes.c_int32()
+    _check(_lib.cm_create_hull_geometry(ctx, pts.ctypes.data, int(pts.shape[0]), ctypes.byref(gid)))
+    return gid.value
+
+
+def cm_get_geometry(ctx, geom_id) -> dict:
+    """A registered geometry as the library holds it: kind, dims, verts (V, 4), edges (E, 2),
+    planes (F, 4; hulls only)."""
+    info = cm_geometry_info()
+    _check(_lib.cm_get_geometry(ctx, int(geom_id), ctypes.byref(info), None, None, None))
+    v = np.zeros((info.n_verts, 4), dtype=np.float32)
+    e = np.zeros((info.n_edges, 2), dtype=np.int32)
+    p = np.zeros((info.n_planes, 4), dtype=np.float32)
+    _check(_lib.cm_get_geometry(ctx, int(geom_id), ctypes.byref(info), v.ctypes.data, e.ctypes.data,
+                                p.ctypes.data if info.n_planes else None))
+    return {"kind": int(info.kind), "dims": np.array(list(info.dims), dtype=np.float32),
+            "verts": v, "edges": e, "planes": p}
 
 
 def cm_check_device_error(ctx) -> None:

@@ -31,6 +31,10 @@ class Engine:
         return api.cm_create_geometry(self.ctx, g.kind, g.dims, g.verts, g.edges,
                                       g.planes if len(g.planes) else None)
 
+    def add_hull(self, points) -> int:
+        """Registers the convex hull of ``points`` ((n, 3)), built by the library."""
+        return api.cm_create_hull_geometry(self.ctx, points)
+
     def add_geometries(self, geoms) -> np.ndarray:
         ids = np.array([self.add_geometry(g) for g in geoms], dtype=np.int32)
         api.cm_sync_geometry(self.ctx)

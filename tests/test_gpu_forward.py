@@ -178,3 +178,30 @@ def test_empty_and_argument_errors(engine):
     with pytest.raises(api.CMError):
         engine.forward(torch.zeros((1, 2), dtype=torch.int32, device="cuda"),
                        torch.zeros((1, 14), device="cuda"), params=engine.params(tau=0.0))
+
+
+def test_library_built_hull_gives_the_same_manifold():
+    """A hull registered from its points (the library builds mesh and planes) gives the
+    manifold of the same hull registered from the input generator's mesh and planes, and
+    both match the oracle."""
+    from paper_2602_20304_gb300.engine import Engine, workload_tensors
+    w = synth.make_config(2, 16)
+    eng = Engine(0)
+    try:
+        ids = eng.add_geometries(w.geoms)
+        pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+        a = eng.forward(pg, poses, dims, tau).cpu().numpy()
+        eng.check()
+        # the same pairs with every hull rebuilt from its vertices by the library
+        hull_ids = ids.copy()
+        for j, g in enumerate(w.geoms):
+            if g.kind == synth.KIND_HULL:
+                hull_ids[j] = eng.add_hull(g.verts[:, :3].astype(np.float64))
+        pg2, _, _, _ = workload_tensors(w, id_map=hull_ids)
+        b = eng.forward(pg2, poses, dims, tau).cpu().numpy()
+        eng.check()
+        np.testing.assert_allclose(b, a, rtol=0, atol=2e-6)
+        params = eng.params()
+        assert_close(b.astype(np.float64), oracle_forward(w, params), what="library-built hulls")
+    finally:
+        eng.close()

@@ -1,0 +1,124 @@
+"""The library's own convex hull (cm_create_hull_geometry) and the geometry read-back
+(cm_get_geometry), on a host-only context: no GPU needed.  The hull is compared with
+qhull's (scipy), the input generator's hull, on point sets in general position, and
+checked on a cube (coplanar facets, repeated points) and on degenerate inputs."""
+import numpy as np
+import pytest
+
+import synth
+
+
+@pytest.fixture()
+def api():
+    from paper_2602_20304_gb300 import build_lib
+    build_lib.build()
+    from paper_2602_20304_gb300 import api
+    return api
+
+
+@pytest.fixture()
+def ctx(api):
+    c = api.cm_create_context(-1)
+    yield c
+    api.cm_destroy_context(c)
+
+
+def ball_points(seed, n):
+    rng = np.random.default_rng(seed)
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    return u * rng.uniform(0, 1, (n, 1)) ** (1 / 3)
+
+
+def match_planes(a, b, tol=1e-6):
+    """Every plane of ``a`` equals one plane of ``b`` and vice versa (same count)."""
+    assert a.shape == b.shape
+    used = np.zeros(len(b), dtype=bool)
+    for p in a:
+        d = np.abs(b - p).max(1)
+        d[used] = np.inf
+        j = int(np.argmin(d))
+        assert d[j] <= tol, (p, b[j])
+        used[j] = True
+
+
+@pytest.mark.parametrize("n,seed", [(8, 0), (20, 1), (64, 2), (200, 3), (5000, 4)])
+def test_hull_equals_qhull_in_general_position(api, ctx, n, seed):
+    pts = ball_points(seed, n)
+    if n > 1000:   # many interior points around a hull that fits the vertex limit
+        pts = np.concatenate([0.5 * pts, ball_points(seed + 100, 150)])
+        pts = pts[np.random.default_rng(seed).permutation(len(pts))]
+    gid = api.cm_create_hull_geometry(ctx, pts)
+    got = api.cm_get_geometry(ctx, gid)
+    ref = synth.hull_from_points(pts)
+    assert got["kind"] == api.CM_HULL
+    np.testing.assert_array_equal(got["verts"], ref.verts)
+    np.testing.assert_array_equal(got["edges"], ref.edges)
+    match_planes(got["planes"], ref.planes)
+
+
+def test_hull_is_closed_convex_and_contains_its_points(api, ctx):
+    pts = ball_points(9, 300)
+    g = api.cm_get_geometry(ctx, api.cm_create_hull_geometry(ctx, pts))
+    V, E, F = len(g["verts"]), len(g["edges"]), len(g["planes"])
+    assert V - E + F == 2 and 2 * E == 3 * F            # closed triangulated sphere
+    n, o = g["planes"][:, :3].astype(np.float64), g["planes"][:, 3].astype(np.float64)
+    np.testing.assert_allclose(np.linalg.norm(n, axis=1), 1.0, atol=1e-6)
+    assert (pts @ n.T - o).max() <= 1e-6                # every input point inside every plane
+    on = np.abs(g["verts"][:, :3].astype(np.float64) @ n.T - o) <= 1e-6
+    assert (on.sum(0) == 3).all()                       # each plane through its triangle's three vertices
+
+
+def test_cube_with_repeated_and_interior_points(api, ctx):
+    """A cube's corners (each facet two coplanar triangles), repeated corners and interior
+    points: the 8 corners in first-occurrence order, 12 cube edges plus 6 face diagonals,
+    12 planes, two per face, with normals +-e_i and offset 1."""
+    rng = np.random.default_rng(5)
+    corners = np.array([[x, y, z] for x in (-1.0, 1.0) for y in (-1.0, 1.0) for z in (-1.0, 1.0)])
+    inner = rng.uniform(-0.9, 0.9, (20, 3))
+    pts = np.concatenate([inner[:10], corners[::-1], inner[10:], corners])
+    g = api.cm_get_geometry(ctx, api.cm_create_hull_geometry(ctx, pts))
+    np.testing.assert_array_equal(g["verts"][:, :3], corners[::-1])
+    assert len(g["edges"]) == 18 and len(g["planes"]) == 12
+    n, o = g["planes"][:, :3], g["planes"][:, 3]
+    np.testing.assert_allclose(o, 1.0, atol=1e-7)
+    axes = np.concatenate([np.eye(3), -np.eye(3)])
+    for a in axes:
+        assert int((np.abs(n - a).max(1) < 1e-7).sum()) == 2
+    lengths = np.linalg.norm(np.diff(g["verts"][g["edges"]][:, :, :3], axis=1)[:, 0], axis=1)
+    np.testing.assert_allclose(np.sort(lengths), [2.0] * 12 + [np.sqrt(8.0)] * 6, atol=1e-6)
+
+
+@pytest.mark.parametrize("case", ["three", "equal", "collinear", "coplanar", "nan", "too_many"])
+def test_degenerate_point_sets_are_rejected(api, ctx, case):
+    rng = np.random.default_rng(6)
+    pts = {
+        "three": rng.normal(size=(3, 3)),
+        "equal": np.ones((10, 3)),
+        "collinear": np.outer(rng.normal(size=12), [1.0, 2.0, 3.0]),
+        "coplanar": np.concatenate([rng.normal(size=(12, 2)), np.zeros((12, 1))], 1),
+        "nan": np.concatenate([rng.normal(size=(9, 3)), [[np.nan, 0, 0]]]),
+        "too_many": (lambda u: u / np.linalg.norm(u, axis=1, keepdims=True))(rng.normal(size=(300, 3))),
+    }[case]
+    with pytest.raises(api.CMError) as ei:
+        api.cm_create_hull_geometry(ctx, pts)
+    assert ei.value.status == api.CM_ERR_INVALID_ARG
+    assert api.cm_num_geometries(ctx) == 0
+
+
+def test_get_geometry_returns_what_was_registered(api, ctx):
+    w = synth.make_config(2, 3)
+    for g in w.geoms:
+        gid = api.cm_create_geometry(ctx, g.kind, g.dims, g.verts, g.edges,
+                                     g.planes if len(g.planes) else None)
+        got = api.cm_get_geometry(ctx, gid)
+        assert got["kind"] == g.kind
+        np.testing.assert_array_equal(got["dims"], g.dims)
+        np.testing.assert_array_equal(got["verts"], g.verts)
+        np.testing.assert_array_equal(got["edges"], g.edges)
+        np.testing.assert_array_equal(got["planes"], g.planes if g.kind == synth.KIND_HULL else np.zeros((0, 4)))
+    api.cm_destroy_geometry(ctx, 0)
+    for bad in (0, -1, api.cm_num_geometries(ctx)):
+        with pytest.raises(api.CMError) as ei:
+            api.cm_get_geometry(ctx, bad)
+        assert ei.value.status == api.CM_ERR_INVALID_ARG
