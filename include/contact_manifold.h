@@ -194,6 +194,24 @@ int32_t cm_num_geometries(const cm_context* ctx);
  * CM_MAX_EDGES or CM_MAX_PLANES. */
 cm_status cm_create_hull_geometry(cm_context* ctx, const double* points, int32_t n_points, int32_t* geom_id);
 
+/* Registers an analytic primitive with a mesh the library generates, `tess`
+ * setting its resolution, and returns its id as cm_create_geometry does.  The
+ * mesh rows are unit templates (see cm_geometry_desc) scaled by the dims in
+ * use, every vertex on the exact surface:
+ *   BOX       the 8 corners and 12 edges (tess ignored);
+ *   CYLINDER  tess points on each rim (3..128): rim polygons and tess vertical
+ *             edges (2 tess vertices, 3 tess edges);
+ *   CAPSULE   per cap, rings of tess points (3..63) at latitudes 0 and pi/4 and
+ *             a pole: ring polygons, meridian edges ring to ring and ring to
+ *             pole, and tess edges joining the equators (4 tess + 2 vertices,
+ *             9 tess edges);
+ *   ELLIPSOID the icosahedron on the unit sphere subdivided tess times (0..2:
+ *             12 / 42 / 162 vertices, 30 / 120 / 480 edges).
+ * dims: host, 3 floats as in cm_geometry_desc.  CM_ERR_INVALID_ARG for another
+ * kind, tess out of range or dims that cm_create_geometry refuses. */
+cm_status cm_create_primitive_geometry(cm_context* ctx, int32_t kind, const float* dims, int32_t tess,
+                                       int32_t* geom_id);
+
 /* What cm_get_geometry reports about a registered geometry. */
 typedef struct {
   int32_t kind;

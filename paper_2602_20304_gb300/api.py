@@ -68,6 +68,8 @@ _SIGS = {
     "cm_num_geometries": (ctypes.c_int32, [_vp]),
     "cm_create_hull_geometry": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "cm_get_geometry": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(cm_geometry_info), _vp, _vp, _vp]),
+    "cm_create_primitive_geometry": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                                                    ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "cm_check_device_error": (ctypes.c_int, [_vp]),
     "cm_contact_manifold_fwd": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
                                                ctypes.POINTER(cm_params), _vp, _vp]),
@@ -174,6 +176,14 @@ def cm_create_hull_geometry(ctx, points) -> int:
         raise ValueError("points must have shape (n, 3)")
     gid = ctypes.c_int32()
     _check(_lib.cm_create_hull_geometry(ctx, pts.ctypes.data, int(pts.shape[0]), ctypes.byref(gid)))
+    return gid.value
+
+
+def cm_create_primitive_geometry(ctx, kind, dims, tess=0) -> int:
+    """Registers a primitive whose mesh the library generates at resolution ``tess``."""
+    d = (ctypes.c_float * 3)(*[float(x) for x in dims])
+    gid = ctypes.c_int32()
+    _check(_lib.cm_create_primitive_geometry(ctx, int(kind), d, int(tess), ctypes.byref(gid)))
     return gid.value
 
 

@@ -19,8 +19,10 @@
 // (smaller, larger) index, one plane (unit outward n, offset n . p) per
 // triangle.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
+#include <map>
 #include <unordered_set>
 #include <vector>
 
@@ -194,6 +196,163 @@ extern "C" cm_status cm_create_hull_geometry(cm_context* c, const double* points
   d.edges = edges.data();
   d.n_planes = nf;
   d.planes = planes.data();
+  return cm_create_geometry(c, &d, geom_id);
+}
+
+namespace {
+
+// Unit template meshes of the analytic primitives.  A row (u_x, u_y, u_z, s) maps to a
+// body-frame vertex from the dims in use: BOX / ELLIPSOID (d0 u_x, d1 u_y, d2 u_z),
+// CYLINDER (r u_x, r u_y, h u_z), CAPSULE (r u_x, r u_y, r u_z + s h).  Every vertex lies
+// on the exact surface of its primitive.
+struct Mesh {
+  std::vector<float> v;        // rows of 4
+  std::vector<int32_t> e;      // pairs
+  int nv() const { return (int)v.size() / 4; }
+  void vert(double x, double y, double z, double s) {
+    v.insert(v.end(), {(float)x, (float)y, (float)z, (float)s});
+  }
+  void edge(int a, int b) { e.insert(e.end(), {std::min(a, b), std::max(a, b)}); }
+};
+
+constexpr double kPi = 3.14159265358979323846;
+
+// box: the 8 corners of [-1, 1]^3 and the 12 edges between corners that differ in one axis
+void box_mesh(Mesh& m) {
+  for (int i = 0; i < 8; ++i) m.vert(i & 4 ? 1 : -1, i & 2 ? 1 : -1, i & 1 ? 1 : -1, 0);
+  for (int i = 0; i < 8; ++i)
+    for (int j = i + 1; j < 8; ++j) {
+      int d = i ^ j;
+      if (d == 1 || d == 2 || d == 4) m.edge(i, j);
+    }
+}
+
+// cylinder: n points on each rim (z = -1, +1), the rim polygons and n vertical edges
+void cylinder_mesh(Mesh& m, int n) {
+  for (int r = 0; r < 2; ++r)
+    for (int i = 0; i < n; ++i) m.vert(std::cos(2 * kPi * i / n), std::sin(2 * kPi * i / n), r ? 1 : -1, 0);
+  for (int r = 0; r < 2; ++r)
+    for (int i = 0; i < n; ++i) m.edge(r * n + i, r * n + (i + 1) % n);
+  for (int i = 0; i < n; ++i) m.edge(i, n + i);
+}
+
+// capsule: per cap (s = -1, +1) rings of n points at latitudes 0 and pi/4 and a pole; ring
+// polygons, meridian edges ring to ring and ring to pole, and the n edges between the
+// two equators (the cylinder part)
+void capsule_mesh(Mesh& m, int n) {
+  const double lats[2] = {0.0, kPi / 4};
+  int ring[2][2];
+  for (int c = 0; c < 2; ++c) {
+    double s = c ? 1.0 : -1.0;
+    for (int l = 0; l < 2; ++l) {
+      ring[c][l] = m.nv();
+      for (int i = 0; i < n; ++i) {
+        double t = 2 * kPi * i / n;
+        m.vert(std::cos(lats[l]) * std::cos(t), std::cos(lats[l]) * std::sin(t), s * std::sin(lats[l]), s);
+      }
+    }
+  }
+  int pole[2];
+  for (int c = 0; c < 2; ++c) {
+    pole[c] = m.nv();
+    m.vert(0, 0, c ? 1 : -1, c ? 1 : -1);
+  }
+  for (int c = 0; c < 2; ++c)
+    for (int l = 0; l < 2; ++l)
+      for (int i = 0; i < n; ++i) m.edge(ring[c][l] + i, ring[c][l] + (i + 1) % n);
+  for (int c = 0; c < 2; ++c) {
+    for (int i = 0; i < n; ++i) m.edge(ring[c][0] + i, ring[c][1] + i);
+    for (int i = 0; i < n; ++i) m.edge(ring[c][1] + i, pole[c]);
+  }
+  for (int i = 0; i < n; ++i) m.edge(ring[0][0] + i, ring[1][0] + i);
+}
+
+// ellipsoid: the icosahedron on the unit sphere, each triangle split in four `level`
+// times with the new vertices pushed onto the sphere; the edges of the triangles
+void icosphere_mesh(Mesh& m, int level) {
+  const double g = (1.0 + std::sqrt(5.0)) / 2.0;
+  std::vector<V3> P;
+  // the 12 icosahedron vertices are the cyclic permutations of (0, +-1, +-g)
+  for (int perm = 0; perm < 3; ++perm)
+    for (int a = -1; a <= 1; a += 2)
+      for (int b = -1; b <= 1; b += 2) {
+        double q[3];
+        q[perm] = 0.0, q[(perm + 1) % 3] = a, q[(perm + 2) % 3] = b * g;
+        double l = std::sqrt(1.0 + g * g);
+        P.push_back({q[0] / l, q[1] / l, q[2] / l});
+      }
+  // the 20 faces: triples of mutually adjacent vertices (edge length 2 before scaling)
+  const double edge2 = 4.0 / (1.0 + g * g);
+  auto adj = [&](int i, int j) { return std::fabs(dot(sub(P[i], P[j]), sub(P[i], P[j])) - edge2) < 1e-9; };
+  std::vector<std::array<int, 3>> F;
+  for (int i = 0; i < 12; ++i)
+    for (int j = i + 1; j < 12; ++j)
+      for (int k = j + 1; k < 12; ++k)
+        if (adj(i, j) && adj(j, k) && adj(i, k)) F.push_back({i, j, k});
+  for (int it = 0; it < level; ++it) {
+    std::map<std::pair<int, int>, int> mid;
+    auto midpoint = [&](int a, int b) {
+      auto key = std::make_pair(std::min(a, b), std::max(a, b));
+      auto f = mid.find(key);
+      if (f != mid.end()) return f->second;
+      V3 s{P[a].x + P[b].x, P[a].y + P[b].y, P[a].z + P[b].z};
+      double l = norm(s);
+      P.push_back({s.x / l, s.y / l, s.z / l});
+      return mid[key] = (int)P.size() - 1;
+    };
+    std::vector<std::array<int, 3>> G;
+    for (auto& f : F) {
+      int ab = midpoint(f[0], f[1]), bc = midpoint(f[1], f[2]), ca = midpoint(f[2], f[0]);
+      G.push_back({f[0], ab, ca});
+      G.push_back({f[1], bc, ab});
+      G.push_back({f[2], ca, bc});
+      G.push_back({ab, bc, ca});
+    }
+    F.swap(G);
+  }
+  for (const V3& p : P) m.vert(p.x, p.y, p.z, 0);
+  std::vector<std::pair<int, int>> E;
+  for (auto& f : F)
+    for (int k = 0; k < 3; ++k) E.emplace_back(std::min(f[k], f[(k + 1) % 3]), std::max(f[k], f[(k + 1) % 3]));
+  std::sort(E.begin(), E.end());
+  E.erase(std::unique(E.begin(), E.end()), E.end());
+  for (auto& e : E) m.edge(e.first, e.second);
+}
+
+}  // namespace
+
+extern "C" cm_status cm_create_primitive_geometry(cm_context* c, int32_t kind, const float* dims, int32_t tess,
+                                                 int32_t* geom_id) {
+  if (!c || !dims || !geom_id) return fail(CM_ERR_INVALID_ARG, "NULL argument");
+  Mesh m;
+  switch (kind) {
+    case CM_BOX:
+      box_mesh(m);
+      break;
+    case CM_CYLINDER:
+      if (tess < 3 || tess > 128) return fail(CM_ERR_INVALID_ARG, "cylinder tess (points per rim) must be in 3..128");
+      cylinder_mesh(m, tess);
+      break;
+    case CM_CAPSULE:
+      if (tess < 3 || tess > 63) return fail(CM_ERR_INVALID_ARG, "capsule tess (points per ring) must be in 3..63");
+      capsule_mesh(m, tess);
+      break;
+    case CM_ELLIPSOID:
+      if (tess < 0 || tess > 2) return fail(CM_ERR_INVALID_ARG, "ellipsoid tess (icosphere level) must be in 0..2");
+      icosphere_mesh(m, tess);
+      break;
+    default:
+      return fail(CM_ERR_INVALID_ARG, "cm_create_primitive_geometry takes BOX, CAPSULE, CYLINDER or ELLIPSOID");
+  }
+  cm_geometry_desc d{};
+  d.kind = kind;
+  for (int i = 0; i < 3; ++i) d.dims[i] = dims[i];
+  d.n_verts = m.nv();
+  d.verts = m.v.data();
+  d.n_edges = (int32_t)m.e.size() / 2;
+  d.edges = m.e.data();
+  d.n_planes = 0;
+  d.planes = nullptr;
   return cm_create_geometry(c, &d, geom_id);
 }
 

@@ -35,6 +35,10 @@ class Engine:
         """Registers the convex hull of ``points`` ((n, 3)), built by the library."""
         return api.cm_create_hull_geometry(self.ctx, points)
 
+    def add_primitive(self, kind, dims, tess=0) -> int:
+        """Registers a primitive whose mesh the library generates (resolution ``tess``)."""
+        return api.cm_create_primitive_geometry(self.ctx, kind, dims, tess)
+
     def add_geometries(self, geoms) -> np.ndarray:
         ids = np.array([self.add_geometry(g) for g in geoms], dtype=np.int32)
         api.cm_sync_geometry(self.ctx)

@@ -122,3 +122,59 @@ def test_get_geometry_returns_what_was_registered(api, ctx):
         with pytest.raises(api.CMError) as ei:
             api.cm_get_geometry(ctx, bad)
         assert ei.value.status == api.CM_ERR_INVALID_ARG
+
+
+def same_mesh_up_to_order(got, ref_verts, ref_edges, tol=1e-6):
+    """The two meshes have the same vertex rows (matched one to one within ``tol``) and,
+    through that matching, the same edge set."""
+    gv, rv = got["verts"].astype(np.float64), np.asarray(ref_verts, dtype=np.float64)
+    assert gv.shape == rv.shape
+    to_ref = np.full(len(gv), -1)
+    for i, row in enumerate(gv):
+        d = np.abs(rv - row).max(1)
+        j = int(np.argmin(d))
+        assert d[j] <= tol, (i, row, rv[j])
+        to_ref[i] = j
+    assert len(set(to_ref.tolist())) == len(gv)
+    ge = {tuple(sorted((int(to_ref[a]), int(to_ref[b])))) for a, b in got["edges"]}
+    re_ = {tuple(sorted((int(a), int(b)))) for a, b in np.asarray(ref_edges)}
+    assert len(ge) == len(got["edges"]) and ge == re_
+
+
+@pytest.mark.parametrize("kind,tess,nv,ne", [
+    (synth.KIND_BOX, 0, 8, 12),
+    (synth.KIND_CYLINDER, 16, 32, 48), (synth.KIND_CYLINDER, 7, 14, 21),
+    (synth.KIND_CAPSULE, 16, 66, 144), (synth.KIND_CAPSULE, 5, 22, 45),
+    (synth.KIND_ELLIPSOID, 0, 12, 30), (synth.KIND_ELLIPSOID, 1, 42, 120), (synth.KIND_ELLIPSOID, 2, 162, 480)])
+def test_primitive_meshes_equal_the_generator_templates(api, ctx, kind, tess, nv, ne):
+    """The library's primitive meshes are the input generator's templates (the same unit
+    rows and edges, vertex order aside) at the resolutions the settings use and others."""
+    dims = (0.5, 0.3, 0.2)
+    g = api.cm_get_geometry(ctx, api.cm_create_primitive_geometry(ctx, kind, dims, tess))
+    assert g["kind"] == kind and len(g["verts"]) == nv and len(g["edges"]) == ne
+    np.testing.assert_array_equal(g["dims"], np.float32(dims))
+    ref = {synth.KIND_BOX: lambda: synth.box_template(),
+           synth.KIND_CYLINDER: lambda: synth.cylinder_template(tess),
+           synth.KIND_CAPSULE: lambda: synth.capsule_template(tess),
+           synth.KIND_ELLIPSOID: lambda: synth.icosphere_template(tess)}[kind]()
+    same_mesh_up_to_order(g, *ref)
+    # the unit rows lie on the unit template surface
+    u = g["verts"][:, :3].astype(np.float64)
+    if kind == synth.KIND_ELLIPSOID:
+        np.testing.assert_allclose(np.linalg.norm(u, axis=1), 1.0, atol=1e-6)
+    if kind == synth.KIND_CYLINDER:
+        np.testing.assert_allclose(np.hypot(u[:, 0], u[:, 1]), 1.0, atol=1e-6)
+    if kind == synth.KIND_CAPSULE:
+        np.testing.assert_allclose(np.linalg.norm(u, axis=1), 1.0, atol=1e-6)
+        assert (np.sign(g["verts"][:, 3]) * u[:, 2] >= -1e-7).all()   # each cap's rows on its side
+
+
+@pytest.mark.parametrize("kind,tess,dims", [
+    (synth.KIND_CYLINDER, 2, (1, 1, 0)), (synth.KIND_CYLINDER, 129, (1, 1, 0)),
+    (synth.KIND_CAPSULE, 64, (1, 1, 0)), (synth.KIND_ELLIPSOID, 3, (1, 1, 1)),
+    (synth.KIND_HULL, 0, (1, 1, 1)), (synth.KIND_BOX, 0, (1, -1, 1)), (7, 0, (1, 1, 1))])
+def test_primitive_arguments_are_checked(api, ctx, kind, tess, dims):
+    with pytest.raises(api.CMError) as ei:
+        api.cm_create_primitive_geometry(ctx, kind, dims, tess)
+    assert ei.value.status == api.CM_ERR_INVALID_ARG
+    assert api.cm_num_geometries(ctx) == 0
