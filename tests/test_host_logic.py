@@ -191,3 +191,11 @@ def test_bench_alu_roofline_object():
     assert r["frac"] == max(p["frac"] for p in r["pipes"].values())
     assert r["algorithmic_bytes"] == 348 * 16
     assert (r["traffic"] is None) == (not bench.FWD_TRAFFIC_CURRENT)
+
+
+def test_bench_oracle_over_pairs_pool():
+    """The pair-parallel oracle timing: single-threaded spawned processes, each on its own
+    share of the pairs, returning a positive rate within its time limit."""
+    import bench
+    r, pairs, span, procs = bench.cpu_oracle_rate_over_pairs(1, 16, budget_s=1.0, procs=2, timeout_s=120.0)
+    assert procs == 2 and 0 < pairs <= 16 and span > 0 and r > 0
