@@ -182,6 +182,19 @@ extern "C" cm_status cm_create_hull_geometry(cm_context* c, const double* points
   }
   std::sort(E.begin(), E.end());
   E.erase(std::unique(E.begin(), E.end()), E.end());
+  // a closed, consistently oriented triangulated sphere: every directed edge once, its
+  // reverse present, V - E + F = 2 (near-degenerate input can break this; refuse it)
+  {
+    std::unordered_set<uint64_t> directed;
+    bool ok = true;
+    for (const Face& f : F)
+      if (f.alive)
+        for (int k = 0; k < 3 && ok; ++k) ok = directed.insert(dkey(f.v[k], f.v[(k + 1) % 3])).second;
+    for (uint64_t key : directed)
+      if (ok && !directed.count(((key & 0xffffffffull) << 32) | (key >> 32))) ok = false;
+    if (!ok || nv - (int)E.size() + nf != 2)
+      return fail(CM_ERR_INVALID_ARG, "the point set is too close to degenerate for a closed hull");
+  }
   if (nv > CM_MAX_VERTS || (int)E.size() > CM_MAX_EDGES || nf > CM_MAX_PLANES)
     return fail(CM_ERR_INVALID_ARG, "the hull exceeds the geometry limits (256 vertices, 768 edges, 512 planes)");
   std::vector<int32_t> edges;

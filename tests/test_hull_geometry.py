@@ -178,3 +178,38 @@ def test_primitive_arguments_are_checked(api, ctx, kind, tess, dims):
         api.cm_create_primitive_geometry(ctx, kind, dims, tess)
     assert ei.value.status == api.CM_ERR_INVALID_ARG
     assert api.cm_num_geometries(ctx) == 0
+
+
+def test_coplanar_rims_give_a_closed_triangulated_hull(api, ctx):
+    """Two rims of 16 points (every cap 16 coplanar points): all 32 are vertices, the caps
+    are triangulated (14 triangles each, normals -+z) and the side is 32 triangles."""
+    t = 2 * np.pi * np.arange(16) / 16
+    pts = np.concatenate([np.stack([np.cos(t), np.sin(t), np.full(16, z)], 1) for z in (-0.5, 0.5)])
+    g = api.cm_get_geometry(ctx, api.cm_create_hull_geometry(ctx, pts))
+    V, E, F = len(g["verts"]), len(g["edges"]), len(g["planes"])
+    assert (V, E, F) == (32, 90, 60)
+    n = g["planes"][:, :3]
+    assert int((np.abs(n[:, 2] - 1) < 1e-6).sum()) == 14 and int((np.abs(n[:, 2] + 1) < 1e-6).sum()) == 14
+    assert int((np.abs(n[:, 2]) < 1e-6).sum()) == 32
+    assert (pts @ n.T.astype(np.float64) - g["planes"][:, 3]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_nearly_degenerate_sets_give_a_closed_hull_or_a_clean_refusal(api, ctx, seed):
+    """Cube corners jittered by 1e-12, repeated, with points on the faces and inside:
+    either a closed triangulated hull containing every point, or CM_ERR_INVALID_ARG."""
+    rng = np.random.default_rng(seed)
+    corners = np.array([[x, y, z] for x in (-1.0, 1.0) for y in (-1.0, 1.0) for z in (-1.0, 1.0)])
+    face = rng.uniform(-1, 1, (30, 3))
+    face[np.arange(30), rng.integers(0, 3, 30)] = rng.choice([-1.0, 1.0], 30)
+    pts = np.concatenate([corners, corners + 1e-12 * rng.normal(size=(8, 3)), face, rng.uniform(-1, 1, (30, 3))])
+    pts = pts[rng.permutation(len(pts))]
+    try:
+        g = api.cm_get_geometry(ctx, api.cm_create_hull_geometry(ctx, pts))
+    except api.CMError as e:
+        assert e.status == api.CM_ERR_INVALID_ARG
+        return
+    V, E, F = len(g["verts"]), len(g["edges"]), len(g["planes"])
+    assert V - E + F == 2 and 2 * E == 3 * F
+    n, o = g["planes"][:, :3].astype(np.float64), g["planes"][:, 3].astype(np.float64)
+    assert (pts @ n.T - o).max() <= 1e-6
