@@ -285,6 +285,30 @@ def cpu_oracle_rate_over_pairs(cfg, n, budget_s=10.0, procs=None, timeout_s=120.
     return pairs / span, pairs, span, procs
 
 
+def cpu_baseline_leg(w, cfg, cpu_seconds, pool_budget_s=10.0):
+    """The ``cpu_baseline`` object: the FP64 oracle (as it stands) on this host's cores over
+    a bounded sample of workload ``w`` (the seeded setting ``cfg`` at ``w.n_pairs`` pairs).
+    The reported value is the oracle run over pairs, one single-threaded process per core;
+    the same oracle on PyTorch's intra-op threads and on one thread stays beside it (and
+    is the value if the process pool cannot run)."""
+    r, n, dt, cores = cpu_oracle_rate(w, budget_s=cpu_seconds)
+    cpu = {"value": r, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+           "sample": f"first {n} pairs of the workload ({dt:.1f} s)"}
+    r1, n1, dt1, _ = cpu_oracle_rate(w, budget_s=min(5.0, cpu_seconds / 3), threads=1)
+    cpu["single_thread"] = {"value": r1, "unit": "pairs/s", "cores": 1,
+                            "sample": f"first {n1} pairs of the workload ({dt1:.1f} s)"}
+    try:
+        rp, npairs, dtp, procs = cpu_oracle_rate_over_pairs(cfg, w.n_pairs, budget_s=min(pool_budget_s, cpu_seconds))
+        cpu = {"value": rp, "unit": "pairs/s", "cores": procs, "kind": "oracle",
+               "sample": f"{npairs} pairs of the workload, every {procs}-th pair in each of {procs} "
+                         f"single-threaded processes ({dtp:.1f} s)",
+               "intra_op_threads": {k: cpu[k] for k in ("value", "unit", "cores", "sample")},
+               "single_thread": cpu["single_thread"]}
+    except Exception as e:  # this timing never costs the bench line
+        cpu["over_pairs_error"] = f"{type(e).__name__}: {e}"
+    return cpu
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -700,23 +724,7 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        r, n, dt, cores = cpu_oracle_rate(w, budget_s=args.cpu_seconds)
-        cpu = {"value": r, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {n} pairs of the workload ({dt:.1f} s)"}
-        r1, n1, dt1, _ = cpu_oracle_rate(w, budget_s=min(5.0, args.cpu_seconds / 3), threads=1)
-        cpu["single_thread"] = {"value": r1, "unit": "pairs/s", "cores": 1,
-                                "sample": f"first {n1} pairs of the workload ({dt1:.1f} s)"}
-        # the oracle over pairs on every host core (one single-threaded process per core);
-        # when it runs, it is the reported baseline and the intra-op figure stays beside it
-        try:
-            rp, npairs, dtp, procs = cpu_oracle_rate_over_pairs(2, w.n_pairs, budget_s=min(10.0, args.cpu_seconds))
-            cpu = {"value": rp, "unit": "pairs/s", "cores": procs, "kind": "oracle",
-                   "sample": f"{npairs} pairs of the workload, every {procs}-th pair in each of {procs} "
-                             f"single-threaded processes ({dtp:.1f} s)",
-                   "intra_op_threads": {k: cpu[k] for k in ("value", "unit", "cores", "sample")},
-                   "single_thread": cpu["single_thread"]}
-        except Exception as e:  # this timing never costs the bench line
-            cpu["over_pairs_error"] = f"{type(e).__name__}: {e}"
+        cpu = cpu_baseline_leg(w, 2, args.cpu_seconds)
         if extra is not None:
             cpu["other_settings"] = oracle_rates()
 

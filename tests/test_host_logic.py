@@ -193,6 +193,19 @@ def test_bench_alu_roofline_object():
     assert (r["traffic"] is None) == (not bench.FWD_TRAFFIC_CURRENT)
 
 
+def test_bench_cpu_baseline_leg():
+    """The benchmark's cpu_baseline object: the over-pairs value with the intra-op and
+    single-thread figures beside it, every figure positive."""
+    import bench
+    import synth
+    w = synth.make_config(1, 8)
+    cpu = bench.cpu_baseline_leg(w, 1, cpu_seconds=1.0, pool_budget_s=1.0)
+    assert cpu["kind"] == "oracle" and cpu["unit"] == "pairs/s" and "over_pairs_error" not in cpu
+    assert cpu["value"] > 0 and cpu["cores"] >= 1 and "single-threaded processes" in cpu["sample"]
+    for k in ("intra_op_threads", "single_thread"):
+        assert cpu[k]["value"] > 0 and cpu[k]["unit"] == "pairs/s"
+
+
 def test_bench_oracle_over_pairs_pool():
     """The pair-parallel oracle timing: single-threaded spawned processes, each on its own
     share of the pairs, returning a positive rate within its time limit."""
