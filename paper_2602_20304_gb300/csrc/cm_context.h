@@ -21,7 +21,7 @@ struct cm_context {
   int device = 0;
   size_t budget = 0;
   int num_sms = 0;
-  std::mutex mu;
+  mutable std::mutex mu;  // also taken by the read-only calls
   // host copy of the packed geometry store
   std::vector<cm::GeomHeader> hdr;
   std::vector<float4> verts;

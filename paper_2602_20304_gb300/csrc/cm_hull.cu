@@ -369,9 +369,8 @@ extern "C" cm_status cm_create_primitive_geometry(cm_context* c, int32_t kind, c
   return cm_create_geometry(c, &d, geom_id);
 }
 
-extern "C" cm_status cm_get_geometry(const cm_context* cc, int32_t geom_id, cm_geometry_info* info, float* verts,
+extern "C" cm_status cm_get_geometry(const cm_context* c, int32_t geom_id, cm_geometry_info* info, float* verts,
                                      int32_t* edges, float* planes) {
-  cm_context* c = const_cast<cm_context*>(cc);
   if (!c || !info) return fail(CM_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> lk(c->mu);
   if (geom_id < 0 || geom_id >= (int32_t)c->hdr.size() || c->hdr[geom_id].n_verts <= 0)
