@@ -460,7 +460,11 @@ cm_status cm_destroy_geometry(cm_context* c, int32_t geom_id) {
   return CM_OK;
 }
 
-int32_t cm_num_geometries(const cm_context* c) { return c ? (int32_t)c->hdr.size() : 0; }
+int32_t cm_num_geometries(const cm_context* c) {
+  if (!c) return 0;
+  std::lock_guard<std::mutex> lk(c->mu);
+  return (int32_t)c->hdr.size();
+}
 
 cm_status cm_check_device_error(cm_context* c) {
   if (!c) return fail(CM_ERR_INVALID_ARG, "NULL context");
@@ -691,6 +695,7 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
 extern "C" cm_status cm_get_launch_shape(const cm_context* c, int32_t n_pairs, int32_t backward, int32_t flags,
                                          int32_t* block, int32_t* ctas_per_sm, int32_t* ordered) {
   if (!c || !block || !ctas_per_sm || !ordered) return fail(CM_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(c->mu);
   LaunchCfg g = pick_cfg(c, backward ? 1 : 0, n_pairs, flags);
   *block = g.block;
   *ctas_per_sm = g.per_sm;
