@@ -194,9 +194,10 @@ int32_t cm_num_geometries(const cm_context* ctx);
  * CM_MAX_EDGES or CM_MAX_PLANES. */
 cm_status cm_create_hull_geometry(cm_context* ctx, const double* points, int32_t n_points, int32_t* geom_id);
 
-/* Registers an analytic primitive with a mesh the library generates, `tess`
- * setting its resolution, and returns its id as cm_create_geometry does.  The
- * mesh rows are unit templates (see cm_geometry_desc) scaled by the dims in
+/* Registers an analytic primitive (Sec. IV-B) with the mesh half of its two
+ * representations (Sec. IV-A) generated by the library, `tess` setting its
+ * resolution, and returns its id as cm_create_geometry does.  The mesh rows
+ * are unit templates (see cm_geometry_desc) scaled by the dims in
  * use, every vertex on the exact surface:
  *   BOX       the 8 corners and 12 edges (tess ignored);
  *   CYLINDER  tess points on each rim (3..128): rim polygons and tess vertical
@@ -221,7 +222,8 @@ typedef struct {
   int32_t n_planes; /* HULL: its planes; 0 for every other kind */
 } cm_geometry_info;
 
-/* Reads back a registered geometry as the library holds it.  info (required)
+/* Reads back a registered geometry as the library holds it (both
+ * representations of Sec. IV-A: mesh rows and, for hulls, planes).  info (required)
  * gets the kind, registered dims and counts.  Each array that is not NULL gets
  * the data (host memory owned by the caller, sized from the counts of a first
  * call with NULL arrays): verts n_verts x 4 floats (the rows as registered),
