@@ -53,7 +53,7 @@ typedef enum {
   CM_ERR_INVALID_ARG = 1, /* a size, pointer, id or parameter is out of range */
   CM_ERR_OOM = 2,         /* a device or host allocation failed */
   CM_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
-  CM_ERR_ADMISSION = 4,   /* a request does not fit the context's HBM budget */
+  CM_ERR_ADMISSION = 4,   /* a request does not fit the HBM budget or the device's free memory */
   CM_ERR_TIMEOUT = 5,     /* cm_wait deadline passed before the request finished */
   CM_ERR_NOT_FOUND = 6,   /* unknown geometry id or request ticket */
   CM_ERR_DEVICE = 7       /* a kernel raised the sticky device error flag */
@@ -294,8 +294,12 @@ void cm_plan_destroy(cm_plan* plan);
 
 /* Serving (not part of the paper's method): a scheduler thread per context
  * continuously batches requests from many clients.  Requests are admitted in
- * arrival order as the context's HBM budget (cm_create_context) and the batch
- * pair limit allow; each admitted group becomes one batch (forward over all
+ * arrival order as the context's HBM budget (cm_create_context), the device's
+ * free memory (cudaMemGetInfo plus what the stream-ordered pool holds unused,
+ * less a 256 MiB reserve) and the batch pair limit allow; a request that does
+ * not fit the free memory while none of the server's batches is running fails
+ * with CM_ERR_ADMISSION (from cm_wait / cm_poll).  Each admitted group becomes
+ * one batch (forward over all
  * its pairs, adjoint over the pairs of forward+backward requests) issued on
  * one of n_streams streams, so batches formed while others run overlap on the
  * GPU.  Geometry stays resident; pair data is copied in and results copied out
@@ -333,23 +337,32 @@ cm_status cm_server_stats(cm_context* ctx, uint64_t* pairs_done, uint64_t* batch
 /* Drains queued and running requests, then stops the loop. */
 cm_status cm_server_stop(cm_context* ctx);
 
-/* Same computation and arguments as cm_contact_manifold_fwd, but the call
+/* Same manifold and arguments as cm_contact_manifold_fwd, but the call
  * allocates no memory (no cudaMalloc, no library allocation).  The paper has no
- * counterpart: this exists for callers that cannot allocate while they run the
- * manifold -- a simulator step inside a CUDA stream capture, a real-time loop
- * with a fixed memory footprint, a host that owns all device memory through its
- * own pool.  Its E-E distance scratch is one fixed 64 MiB device array (16 Mi
- * floats) in the library, present on every GPU that loads it until exit.
+ * counterpart.  It is for callers that cannot allocate while they run the
+ * manifold: a host application that hands out every device allocation from its
+ * own pool (so its accounting and limit stay exact), or a real-time loop that
+ * was promised a fixed memory footprint and cannot absorb the blocking and
+ * synchronisation of cudaMalloc / cudaFree.  Its E-E distance scratch is one
+ * fixed 64 MiB device array (16 Mi floats) in the library, present on every GPU
+ * that loads the library until the process exits.
+ *   - It keeps one scratch float per edge pair (the distance) and solves each
+ *     witness QP a second time in pass 2, where the regular forward keeps four
+ *     floats per edge pair and reads the QP back: same results, more arithmetic.
  *   - Limit: the largest registered geometry may have at most
- *     floor(sqrt(16 Mi / number_of_SMs)) edges (332 on a 152-SM GB300);
- *     otherwise CM_ERR_INVALID_ARG with a message stating the limit.
+ *     floor(sqrt(16 Mi / number_of_SMs)) edges (332 on a 152-SM GB300), so that
+ *     a max_e^2 slice fits per SM; otherwise CM_ERR_INVALID_ARG with a message
+ *     stating the limit.  Parameters are validated as cm_contact_manifold_fwd
+ *     validates them (the same K and flag checks).
  *   - Geometry must already be uploaded (cm_sync_geometry); a pending upload is
  *     an error here instead of an allocation.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
- *   - Every call, from any context, shares the one array per device: calls whose
- *     kernels overlap on the GPU (other streams, other threads) race on it and
- *     must be serialised by the caller.  Nothing in it needs to start at zero. */
+ *     (cudaGetSymbolAddress) and sets the kernel's shared-memory limit; make that
+ *     first call before any stream capture.
+ *   - Every call, from any context, shares the one array per device and it keeps
+ *     the last call's contents: calls whose kernels overlap on the GPU (other
+ *     streams, other threads) race on it and must be serialised by the caller.
+ *     Every entry a call reads it has written first, so nothing needs clearing. */
 cm_status cm_contact_manifold_fwd_noalloc(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms,
                                           const float* poses, const float* dims, const float* tau,
                                           const cm_params* params, float* out, void* stream);

@@ -594,13 +594,9 @@ constexpr int kBwdSmem1 = 180 * 1024, kBwdSmem2 = 110 * 1024;
 template <int MB, int KM>
 cudaError_t launch_bwd_t(const FwdArgs& a, const float* g, float* gp, float* gd, int grid, int block,
                                 cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(cm_bwd_kernel<MB, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         MB == 1 ? kBwdSmem1 : kBwdSmem2);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(cm_bwd_kernel<MB, KM>),
+                                   MB == 1 ? kBwdSmem1 : kBwdSmem2);
+  if (e != cudaSuccess) return e;
   cm_bwd_kernel<MB, KM><<<grid, block, a.sm.total, s>>>(a, g, gp, gd);
   return cudaGetLastError();
 }

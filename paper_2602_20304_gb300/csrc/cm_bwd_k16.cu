@@ -10,6 +10,9 @@ template cudaError_t launch_bwd_t<2, 16>(const FwdArgs&, const float*, float*, f
 // CTAs per SM of the one-CTA (mb = 1) or two-CTA (mb = 2) build at this shape.
 int bwd_occupancy(int mb, int block, int smem_bytes) {
   int n = 0;
+  const void* k = mb == 1 ? reinterpret_cast<const void*>(cm_bwd_kernel<1, 16>)
+                          : reinterpret_cast<const void*>(cm_bwd_kernel<2, 16>);
+  if (ensure_smem_attr(k, mb == 1 ? kBwdSmem1 : kBwdSmem2) != cudaSuccess) return 1;
   const cudaError_t e =
       mb == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel<1, 16>, block, smem_bytes)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_bwd_kernel<2, 16>, block, smem_bytes);

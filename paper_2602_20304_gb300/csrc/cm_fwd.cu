@@ -150,20 +150,18 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
   }
 }
 
+constexpr int kFwdSmemMax = 200 * 1024;
+
 cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(cm_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = ensure_smem_attr(reinterpret_cast<const void*>(cm_fwd_kernel), kFwdSmemMax);
+  if (e != cudaSuccess) return e;
   cm_fwd_kernel<<<grid, block, a.sm.total, s>>>(a);
   return cudaGetLastError();
 }
 
 int fwd_max_blocks_per_sm(int block, int smem_bytes) {
   int n = 0;
+  if (ensure_smem_attr(reinterpret_cast<const void*>(cm_fwd_kernel), kFwdSmemMax) != cudaSuccess) return 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cm_fwd_kernel, block, smem_bytes) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;

@@ -72,6 +72,12 @@ constexpr int kSelAdjFloats = kMaxSel * (3 + 3 + 6 + 6);
 // and slots, C (9), the K-th score and C's reference (see cm_softsort.cuh).
 constexpr int kWarpStateFloats = 188;
 
+// Raises `kernel`'s dynamic shared-memory limit to `bytes` on the current device,
+// once per (kernel, device): the attribute belongs to the device's context, so a
+// process that uses several GPUs sets it on each.  Occupancy queries above 48 KB
+// and launches call it first.
+cudaError_t ensure_smem_attr(const void* kernel, int bytes);
+
 cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s);
 int fwd_max_blocks_per_sm(int block, int smem_bytes);
 cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,

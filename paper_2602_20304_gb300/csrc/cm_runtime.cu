@@ -37,6 +37,21 @@ using namespace cm::rt;
 
 
 namespace cm {
+
+cudaError_t ensure_smem_attr(const void* kernel, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> bytes set
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find({kernel, dev});
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[{kernel, dev}] = bytes;
+  return e;
+}
+
 namespace rt {
 
 template <class T>
@@ -528,12 +543,13 @@ extern "C" cm_status cm_contact_manifold_bwd(cm_context* c, int32_t n_pairs, con
 // Allocation-free forward entry point.
 //
 // Some callers must not allocate device memory while they run the manifold:
-// a simulator stepping inside a CUDA stream capture (cudaMalloc is not allowed
-// there), a real-time control loop that was promised a fixed memory footprint,
-// or a host application that owns every device allocation through its own
-// pool.  cm_contact_manifold_fwd may grow its scratch on a call, so those
-// callers use this variant instead: its E-E distance scratch is the fixed
-// file-scope device array below, sized once for the whole process.
+// a host application that hands out every device allocation from its own pool
+// (so that its accounting and its limit stay exact), or a real-time control loop
+// that was promised a fixed memory footprint and cannot absorb the blocking and
+// device-wide synchronisation that cudaMalloc / cudaFree may bring.
+// cm_contact_manifold_fwd may grow its scratch on a call, so those callers use
+// this variant instead: its E-E distance scratch is the fixed file-scope device
+// array below, sized once for the whole process.
 // ---------------------------------------------------------------------------
 #define CM_NOALLOC_SCRATCH_FLOATS (16u * 1024u * 1024u)  // 64 MiB of FP32 per GPU
 
@@ -575,13 +591,7 @@ extern "C" cm_status cm_contact_manifold_fwd_noalloc(cm_context* c, int32_t n_pa
   if (c->device < 0) return fail(CM_ERR_INVALID_ARG, "host-only context: no device work");
   if (c->dirty)
     return fail(CM_ERR_INVALID_ARG, "geometry not uploaded: call cm_sync_geometry before the no-alloc entry point");
-  if (params->flags & (CM_FLAG_NO_EE | CM_FLAG_ONE_SIDED)) {
-    const int min_cands = (params->flags & CM_FLAG_ONE_SIDED) ? c->min_v : 2 * c->min_v;
-    if (params->K > min_cands)
-      return fail(CM_ERR_INVALID_ARG, "K exceeds the vertex-contact count of the smallest registered geometry");
-  } else if (c->min_e < 3) {
-    return fail(CM_ERR_INVALID_ARG, "E-E contacts need every registered geometry to have >= 3 edges");
-  }
+  if ((st = check_k(c, params)) != CM_OK) return st;
   // one scratch slice of max_e^2 floats per CTA; the fixed array must hold a
   // slice for every SM so that the launch still fills the GPU
   const int64_t stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
@@ -621,6 +631,11 @@ extern "C" cm_status cm_contact_manifold_fwd_noalloc(cm_context* c, int32_t n_pa
   a.err = c->d_err;
   a.work_counter = nullptr;
   a.order = nullptr;
+  // One scratch float per edge pair (its distance): pass 2 solves each witness QP
+  // again instead of reading it back, unlike the regular forward, which keeps four
+  // floats per edge pair.  That single float is what lets max_e^2 floats per CTA,
+  // and so the edge limit above, fit the fixed array.
+  a.store_alpha = 0;
   cudaError_t e = launch_fwd(a, grid, block, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "no-alloc forward launch");
   return CM_OK;

@@ -3,7 +3,7 @@
 // Clients submit requests (a set of body pairs, forward or forward+backward)
 // from any thread.  One scheduler thread per context
 //   * admits queued requests in arrival order while their device memory fits
-//     the context's HBM budget and the batch's pair limit,
+//     the context's HBM budget, the device's free memory and the batch's pair limit,
 //   * packs each admitted group into one batch (forward-only requests first,
 //     forward+backward requests as a contiguous tail), copies its inputs to the
 //     device, runs work ordering + forward over the whole batch and ordering +
@@ -65,6 +65,7 @@ struct Server {
   int max_batch_pairs = 0;
   std::vector<cudaStream_t> streams;
   std::vector<int> stream_busy;
+  cudaMemPool_t mempool = nullptr;  // this server's stream-ordered pool of batch blocks
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> queue;
@@ -91,6 +92,7 @@ struct Server {
     }
     for (cudaStream_t s : streams) cudaStreamSynchronize(s);
     for (cudaStream_t s : streams) cudaStreamDestroy(s);
+    if (mempool) cudaMemPoolDestroy(mempool);  // returns the cached blocks to the driver
   }
 
   size_t budget() const { return ctx->budget ? ctx->budget : (size_t)1 << 62; }
@@ -129,7 +131,25 @@ struct Server {
     }
   }
 
+  // Device memory a new batch block can take now: what the device has free plus
+  // what the stream-ordered pool holds cached but unused, less a reserve for the
+  // driver and the other users of this GPU.
+  size_t free_hbm() const {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(mempool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(mempool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+      fr += (size_t)(reserved - used);
+    return fr > kHbmReserve ? fr - kHbmReserve : 0;
+  }
+  static constexpr size_t kHbmReserve = (size_t)256 << 20;
+
   // Takes the longest admissible prefix of the queue; nullptr if nothing fits now.
+  // A request is admitted while the batch fits both the context's budget (with
+  // the batches already running) and the device's free memory.  A request that
+  // cannot fit the free memory with nothing running fails with CM_ERR_ADMISSION
+  // instead of waiting for memory that no batch of this server will release.
   std::unique_ptr<Batch> form_batch() {
     if (queue.empty()) return nullptr;
     int s = -1;
@@ -139,6 +159,7 @@ struct Server {
         break;
       }
     if (s < 0) return nullptr;
+    const size_t avail = free_hbm();
     auto b = std::make_unique<Batch>();
     int pairs = 0, bwd_pairs = 0;
     int64_t mee = 1;
@@ -149,7 +170,15 @@ struct Server {
       const int64_t m2 = std::max(mee, r->max_ee);
       const int nb2 = bwd_pairs + (r->d.with_backward ? r->d.n_pairs : 0);
       const size_t total = batch_bytes(pairs + r->d.n_pairs, nb2, m2);
-      if (bytes_in_use + total > budget()) break;
+      if (total > avail && b->reqs.empty() && running.empty()) {
+        r->state = 3;
+        r->status = CM_ERR_ADMISSION;
+        r->t_done = Clock::now();
+        queue.pop_front();
+        cv_done.notify_all();
+        continue;
+      }
+      if (bytes_in_use + total > budget() || total > avail) break;
       pairs += r->d.n_pairs;
       bwd_pairs = nb2;
       mee = m2;
@@ -176,7 +205,7 @@ struct Server {
       n += r->d.n_pairs;
       if (r->d.with_backward) nb += r->d.n_pairs;
     }
-    cudaError_t e = cudaMallocAsync(&b->mem, b->bytes, b->stream);
+    cudaError_t e = cudaMallocFromPoolAsync(&b->mem, b->bytes, mempool, b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch memory");
     char* p = static_cast<char*>(b->mem);
     auto take = [&](size_t bytes) {
@@ -341,13 +370,19 @@ cm_status cm_server_start(cm_context* c, const cm_params* params, int32_t max_ba
   srv->grid_max = gmax;
   if (c->budget && srv->batch_bytes(1, 1, 1) > c->budget)
     return fail(CM_ERR_ADMISSION, "the HBM budget does not even hold a one-pair batch");
-  // batch memory comes from the stream-ordered pool: keep freed blocks cached
-  // (up to the budget) instead of returning them to the driver
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
-    uint64_t keep = c->budget ? (uint64_t)c->budget : UINT64_MAX;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  // batch memory comes from the server's own stream-ordered pool, which keeps freed
+  // blocks cached (up to the budget) instead of returning them to the driver
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = c->device;
+  cudaError_t pe = cudaMemPoolCreate(&srv->mempool, &props);
+  if (pe != cudaSuccess) {
+    srv->mempool = nullptr;
+    return cuda_fail(pe, "server memory pool");
   }
+  uint64_t keep = c->budget ? (uint64_t)c->budget : UINT64_MAX;
+  cudaMemPoolSetAttribute(srv->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
   Server* raw = srv.get();
   c->server = std::move(srv);
   raw->thread = std::thread([raw] { raw->loop(); });
@@ -420,7 +455,10 @@ cm_status cm_wait(cm_context* c, uint64_t ticket, int32_t timeout_ms) {
     if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && r->state < 2)
       return fail(CM_ERR_TIMEOUT, "request not finished before the deadline");
   }
-  return r->state == 3 ? fail(r->status, "request failed on the device") : CM_OK;
+  if (r->state == 3)
+    return fail(r->status, r->status == CM_ERR_ADMISSION ? "request does not fit the device's free memory"
+                                                         : "request failed on the device");
+  return CM_OK;
 }
 
 cm_status cm_request_latency(cm_context* c, uint64_t ticket, double* seconds) {

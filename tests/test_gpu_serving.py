@@ -177,3 +177,41 @@ def test_single_request_batches_match_alone(pool):
         eng.check()
     finally:
         eng.close()
+
+
+def test_admission_by_free_device_memory(pool):
+    """Without a budget, admission follows the device's free memory: with most of the GPU
+    held elsewhere, a forward+backward request whose batch block (at least 152 scratch
+    slices of its largest E_A x E_B at 16 floats, ~290 MB here) exceeds what is free
+    fails with CM_ERR_ADMISSION instead of waiting forever, and a small request is still
+    served."""
+    from paper_2602_20304_gb300 import api
+    from paper_2602_20304_gb300.engine import Engine
+    w = pool
+    nvA, nvB, neA, neB = w.pair_counts()
+    big_idx = int(np.argmax(neA * neB))
+    assert 152 * int(neA[big_idx] * neB[big_idx]) * 64 > 256 << 20
+    eng = Engine(0)
+    hog = None
+    try:
+        ids = eng.add_geometries(w.geoms)
+        params = eng.params()
+        api.cm_server_start(eng.ctx, params, max_batch_pairs=8192, n_streams=2)
+        torch.cuda.synchronize()
+        free, _ = torch.cuda.mem_get_info()
+        hog = torch.empty(free - (512 << 20), dtype=torch.uint8, device="cuda")   # leave 512 MiB
+        rng = np.random.default_rng(3)
+        ws = w.subset(np.full(64, big_idx))
+        big = make_requests(ws, ids, rng, [64], [True])[0]
+        t = submit(api, eng.ctx, big)
+        with pytest.raises(api.CMError) as ei:
+            api.cm_wait(eng.ctx, t, 60000)
+        assert ei.value.status == api.CM_ERR_ADMISSION and "free memory" in str(ei.value)
+        tiny = make_requests(w, ids, rng, [2], [False])[0]
+        api.cm_wait(eng.ctx, submit(api, eng.ctx, tiny), 60000)
+        assert np.isfinite(tiny["out"].numpy()).all()
+        api.cm_server_stop(eng.ctx)
+    finally:
+        del hog
+        torch.cuda.empty_cache()
+        eng.close()
