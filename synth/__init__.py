@@ -10,7 +10,7 @@ independently, in ``oracle/`` (FP64 CPU) and in the CUDA library.
 from .geometry import (  # noqa: F401
     KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID, KIND_HULL, KIND_SQ_UNION, KIND_NAMES,
     Geometry, box_template, cylinder_template, capsule_template,
-    icosphere_template, hull_from_points, primitive_geometry, support,
+    icosphere_template, hull_from_points, primitive_geometry, support, support_point, interior_point,
     superellipsoid_surface, sq_union_geometry,
 )
 from .workloads import (  # noqa: F401

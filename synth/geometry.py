@@ -214,6 +214,53 @@ def support(geom: Geometry, dims, u):
     raise ValueError(geom.kind)
 
 
+def support_point(geom: Geometry, dims, u):
+    """A point of the exact (unsmoothed) shape that attains its support function in
+    direction ``u`` (local frame, (3,)): argmax_{x in S} u . x (the smallest vertex index
+    on ties for meshes; the +1 side of a zero component for the box and the caps).
+    Used only to place bodies in contact; it is not part of the method."""
+    u = np.asarray(u, dtype=np.float64)
+    d = np.asarray(dims, dtype=np.float64)
+    sgn = np.where(u >= 0.0, 1.0, -1.0)
+    if geom.kind == KIND_BOX:
+        return sgn * d
+    if geom.kind in (KIND_HULL, KIND_SQ_UNION):
+        v = geom.verts[:, :3].astype(np.float64)
+        return v[int(np.argmax(v @ u))]
+    if geom.kind == KIND_CAPSULE:
+        return d[0] * u / np.linalg.norm(u) + np.array([0.0, 0.0, d[1] * sgn[2]])
+    if geom.kind == KIND_CYLINDER:
+        r = np.hypot(u[0], u[1])
+        radial = d[0] * np.array([u[0], u[1], 0.0]) / r if r > 0 else np.zeros(3)
+        return radial + np.array([0.0, 0.0, d[1] * sgn[2]])
+    if geom.kind == KIND_ELLIPSOID:
+        return d * d * u / np.linalg.norm(d * u)
+    raise ValueError(geom.kind)
+
+
+def interior_point(geom: Geometry, dims, near=None):
+    """A point strictly inside the exact shape: the centre of a primitive, the vertex
+    mean of a hull (inside, since the vertices are in general position).  For a union of
+    superquadrics: the centre of the superquadric on whose surface ``near`` lies (the
+    one whose inside-outside function is closest to 1 there); every superquadric with
+    exponents <= 2 is convex, so the segment from ``near`` to that centre stays in the
+    body."""
+    if geom.kind == KIND_HULL:
+        return geom.verts[:, :3].astype(np.float64).mean(0)
+    if geom.kind == KIND_SQ_UNION:
+        best, centre = np.inf, None
+        for l in range(geom.n_planes // 3):
+            q, t = geom.planes[3 * l].astype(np.float64), geom.planes[3 * l + 1, :3].astype(np.float64)
+            e1, sc, e2 = float(geom.planes[3 * l + 1, 3]), geom.planes[3 * l + 2, :3].astype(np.float64), \
+                float(geom.planes[3 * l + 2, 3])
+            x = _quat_matrix(q).T @ (np.asarray(near, np.float64) - t) / sc
+            f = (np.abs(x[0]) ** (2 / e2) + np.abs(x[1]) ** (2 / e2)) ** (e2 / e1) + np.abs(x[2]) ** (2 / e1)
+            if abs(f - 1.0) < best:
+                best, centre = abs(f - 1.0), t
+        return centre
+    return np.zeros(3)
+
+
 def superellipsoid_surface(rings, segs, scale, eps1, eps2):
     """Mesh of one superquadric's surface in its own frame: ``rings`` latitude rings of
     ``segs`` points from the standard superellipsoid parametrisation

@@ -4,11 +4,15 @@ Every workload is a batch of independent body pairs (A, B).  Pair ``i`` names
 two geometries, carries both rigid poses as ``(qw, qx, qy, qz, tx, ty, tz)``
 per body, the per-body primitive dimensions and the smoothing ``tau``.
 
-Placement: A's orientation and B's are uniform random (Shoemake), ``t_A`` is
-uniform in ``[-1, 1]^3``; a random unit direction ``u`` is drawn and B is put
-along ``u`` so that the two shapes' projections on ``u`` overlap by ``delta``
-(exact support functions).  The true penetration depth is then in
-``[0, delta]``.
+Placement (bodies always in contact): A's orientation and B's are uniform
+random (Shoemake), ``t_A`` is uniform in ``[-1, 1]^3`` and a random unit
+direction ``u`` is drawn.  On the exact (unsmoothed) shapes, p_A is A's support
+point in direction u and c_A a point inside A; B is translated so that its
+support point in direction -u lands on q = p_A + delta' w, w the unit vector
+from p_A to c_A and delta' = min(delta, |c_A - p_A| / 2).  q lies in A (A is
+convex and holds p_A and c_A) and in B, so the bodies intersect; moving B back
+by delta' w puts its support point on p_A, where the plane u . x = u . p_A
+separates the two, so the penetration depth is in (0, delta'], delta' <= delta.
 """
 from __future__ import annotations
 
@@ -16,7 +20,8 @@ import dataclasses
 import numpy as np
 
 from .geometry import (KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID,
-                       Geometry, hull_from_points, primitive_geometry, support, sq_union_geometry)
+                       Geometry, hull_from_points, interior_point, primitive_geometry, sq_union_geometry,
+                       support_point)
 
 SEED_BASE = 20261203
 PRIMITIVE_KINDS = (KIND_BOX, KIND_CAPSULE, KIND_CYLINDER, KIND_ELLIPSOID)
@@ -31,6 +36,7 @@ class Workload:
     dims: np.ndarray            # (n, 6) float32
     tau: np.ndarray             # (n,) float32
     K: int = 8
+    contact: np.ndarray = None  # (n, 3) float64 world point inside A and on B's surface (placement)
 
     @property
     def n_pairs(self):
@@ -39,7 +45,8 @@ class Workload:
     def subset(self, idx):
         idx = np.asarray(idx)
         return Workload(self.name + "[sub]", self.geoms, self.pair_geoms[idx].copy(),
-                        self.poses[idx].copy(), self.dims[idx].copy(), self.tau[idx].copy(), self.K)
+                        self.poses[idx].copy(), self.dims[idx].copy(), self.tau[idx].copy(), self.K,
+                        None if self.contact is None else self.contact[idx].copy())
 
     def pair_counts(self):
         """(V_A, V_B, E_A, E_B) per pair."""
@@ -75,7 +82,9 @@ def _ball_points(rng, n):
     return _unit_vectors(rng, n) * rng.random(n)[:, None] ** (1.0 / 3.0)
 
 
-def _place(rng, geoms, pair_geoms, dims, delta):
+def _place(rng, geoms, pair_geoms, dims, delta, contact_out=None):
+    """Poses (n, 14) placing every pair in contact (module docstring); the common points
+    q go to ``contact_out`` ((n, 3)) when given."""
     n = pair_geoms.shape[0]
     qa, qb = random_quaternions(rng, n), random_quaternions(rng, n)
     ta = rng.uniform(-1.0, 1.0, size=(n, 3))
@@ -84,9 +93,15 @@ def _place(rng, geoms, pair_geoms, dims, delta):
     tb = np.empty_like(ta)
     for i in range(n):
         ga, gb = geoms[pair_geoms[i, 0]], geoms[pair_geoms[i, 1]]
-        ha = support(ga, dims[i, :3], Ra[i].T @ u[i])
-        hb = support(gb, dims[i, 3:], Rb[i].T @ (-u[i]))
-        tb[i] = ta[i] + (ha + hb - delta[i]) * u[i]
+        pa = support_point(ga, dims[i, :3], Ra[i].T @ u[i])                # A's frame
+        ca = interior_point(ga, dims[i, :3], near=pa)
+        pb = support_point(gb, dims[i, 3:], Rb[i].T @ (-u[i]))             # B's frame
+        w = Ra[i] @ (ca - pa)
+        dist = np.linalg.norm(w)
+        q = ta[i] + Ra[i] @ pa + min(delta[i], 0.5 * dist) * w / dist      # in A and on B
+        tb[i] = q - Rb[i] @ pb
+        if contact_out is not None:
+            contact_out[i] = q
     poses = np.concatenate([qa, ta, qb, tb], axis=1).astype(np.float32)
     return poses
 
@@ -98,8 +113,9 @@ def config_box_box(n=1024, seed=SEED_BASE + 1, tau=1e-2, half=0.5):
     pg = np.zeros((n, 2), dtype=np.int32)
     dims = np.full((n, 6), half, dtype=np.float32)
     delta = rng.uniform(0.0, 0.1, n)
-    poses = _place(rng, geoms, pg, dims, delta)
-    return Workload("box-box", geoms, pg, poses, dims, np.full(n, tau, np.float32))
+    contact = np.zeros((n, 3))
+    poses = _place(rng, geoms, pg, dims, delta, contact)
+    return Workload("box-box", geoms, pg, poses, dims, np.full(n, tau, np.float32), contact=contact)
 
 
 def _primitive_dims(rng, kind):
@@ -131,9 +147,10 @@ def config_hull_vs_primitive(n=4096, seed=SEED_BASE + 2, n_points=(8, 64), log_u
         dims[i, :3] = 1.0
         dims[i, 3:] = _primitive_dims(rng, k)
     delta = rng.uniform(0.0, 0.1, n)
-    poses = _place(rng, geoms, pg, dims, delta)
+    contact = np.zeros((n, 3))
+    poses = _place(rng, geoms, pg, dims, delta, contact)
     tau = np.asarray(taus, dtype=np.float32)[rng.integers(0, len(taus), n)]
-    return Workload(name, geoms, pg, poses, dims, tau.astype(np.float32))
+    return Workload(name, geoms, pg, poses, dims, tau.astype(np.float32), contact=contact)
 
 
 def config_hull_vs_hull(n=64, seed=SEED_BASE + 7, n_points=(8, 64), tau=1e-2):
@@ -148,8 +165,9 @@ def config_hull_vs_hull(n=64, seed=SEED_BASE + 7, n_points=(8, 64), tau=1e-2):
             pg[i, side] = len(geoms) - 1
     dims = np.ones((n, 6), dtype=np.float32)
     delta = rng.uniform(0.0, 0.1, n)
-    poses = _place(rng, geoms, pg, dims, delta)
-    return Workload("hull-vs-hull", geoms, pg, poses, dims, np.full(n, tau, np.float32))
+    contact = np.zeros((n, 3))
+    poses = _place(rng, geoms, pg, dims, delta, contact)
+    return Workload("hull-vs-hull", geoms, pg, poses, dims, np.full(n, tau, np.float32), contact=contact)
 
 
 def config_box_vs_sphere_hull(n=1024, seed=SEED_BASE + 3, n_sphere=32, tau=1e-2):
@@ -163,8 +181,9 @@ def config_box_vs_sphere_hull(n=1024, seed=SEED_BASE + 3, n_sphere=32, tau=1e-2)
         pg[i] = (0, len(geoms) - 1)
         dims[i, :3] = rng.uniform(0.2, 1.0, 3)
     delta = rng.uniform(0.0, 0.1, n)
-    poses = _place(rng, geoms, pg, dims, delta)
-    return Workload("box-vs-hull32", geoms, pg, poses, dims, np.full(n, tau, np.float32))
+    contact = np.zeros((n, 3))
+    poses = _place(rng, geoms, pg, dims, delta, contact)
+    return Workload("box-vs-hull32", geoms, pg, poses, dims, np.full(n, tau, np.float32), contact=contact)
 
 
 def config_mixed(n=65536, seed=SEED_BASE + 4):
@@ -194,9 +213,10 @@ def config_mixed_pooled(n=65536, pool=4096, seed=SEED_BASE + 4):
     d[np.isin(kinds, [1, 2]), 2] = 0.0            # capsule / cylinder use (r, h)
     dims[:, 3:] = d
     delta = rng.uniform(0.0, 0.1, n)
-    poses = _place(rng, geoms, pg, dims, delta)
+    contact = np.zeros((n, 3))
+    poses = _place(rng, geoms, pg, dims, delta, contact)
     tau = np.asarray((1e-3, 1e-2, 1e-1), dtype=np.float32)[rng.integers(0, 3, n)]
-    return Workload("mixed-uneven-pooled", geoms, pg, poses, dims, tau)
+    return Workload("mixed-uneven-pooled", geoms, pg, poses, dims, tau, contact=contact)
 
 
 SQ_RESOLUTIONS = ((4, 12), (4, 8), (2, 12), (2, 8), (2, 4))
@@ -233,8 +253,9 @@ def config_sq_union(n=1024, n_prims=18, pool=8, seed=SEED_BASE + 6, tau=1e-2):
     pg = rng.integers(0, pool, size=(n, 2)).astype(np.int32)
     dims = np.ones((n, 6), dtype=np.float32)
     delta = rng.uniform(0.0, 0.1, n)
-    poses = _place(rng, geoms, pg, dims, delta)
-    return Workload(f"sq-union{n_prims}", geoms, pg, poses, dims, np.full(n, tau, np.float32))
+    contact = np.zeros((n, 3))
+    poses = _place(rng, geoms, pg, dims, delta, contact)
+    return Workload(f"sq-union{n_prims}", geoms, pg, poses, dims, np.full(n, tau, np.float32), contact=contact)
 
 
 def serving_trace(seed=SEED_BASE + 5, rate=2000.0, duration=10.0, max_pairs=8192):
