@@ -9,6 +9,10 @@ top-K) and its vector-Jacobian product on a dozen pairs, so that a change of
 the oracle's arithmetic shows up as a failing CPU test and the CUDA path can be
 compared with FP64 values without re-running the oracle.
 
+With each pair it stores the pair's one-ulp conditioning (how far the oracle's
+manifold and gradient move when every FP32 input of the pair moves by one ulp,
+four draws; tests/_parity.py), so the GPU test applies the per-pair bar.
+
 The case holds every input in full (the geometries used, the pair table,
 poses, dimensions, smoothing and the upstream gradient), so it does not depend
 on the generators staying unchanged:
@@ -22,6 +26,7 @@ on the generators staying unchanged:
 import json
 import os
 import sys
+from types import SimpleNamespace
 
 import numpy as np
 
@@ -32,6 +37,9 @@ if ROOT not in sys.path:
 
 import oracle  # noqa: E402
 import synth  # noqa: E402
+
+sys.path.insert(0, os.path.dirname(HERE))
+import _parity  # noqa: E402  (the one-ulp conditioning of the oracle, tests/_parity.py)
 
 OUT = os.path.join(HERE, "oracle_small.json")
 GRAD_SEED = 7
@@ -113,6 +121,14 @@ def main():
     params = oracle.Params()
     manifold = oracle.batch_manifold(geoms, pg, poses, dims, tau, params)
     gp, gd = oracle.batch_manifold_grad(geoms, pg, poses, dims, tau, grad_out, params)
+    # each pair's one-ulp conditioning (the per-pair bar of tests/_parity.py), so the GPU
+    # test of this case applies the same bar without running the oracle
+    w = synth.Workload("golden", geoms, pg, poses, dims, tau)
+    idx = np.arange(len(pg))
+    p = SimpleNamespace(K=params.K, w_reg=params.w_reg, eps_clip=params.eps_clip, eps_min=params.eps_min,
+                        eps_comp=params.eps_comp, flags=0, top_verts=0, top_edges=0, trace_iters=0)
+    fwd_spread = _parity.forward_spread(w, p, idx, manifold)
+    grad_spread = _parity.grad_spread(w, p, idx, grad_out, np.concatenate([gp, gd], 1))
     doc = {
         "about": "FP64 oracle output on a small seeded case; written by tests/golden/make_golden.py "
                  "from oracle/ only (whole manifold: Sec. IV-A, IV-C, IV-D, Sec. III).",
@@ -127,6 +143,8 @@ def main():
         "manifold": manifold.tolist(),
         "grad_poses": gp.tolist(),
         "grad_dims": gd.tolist(),
+        "spread_fwd": fwd_spread.tolist(),
+        "spread_grad": grad_spread.tolist(),
     }
     with open(OUT, "w") as f:
         json.dump(doc, f, separators=(",", ":"))

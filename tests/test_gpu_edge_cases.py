@@ -6,7 +6,7 @@ import torch
 
 import oracle
 import synth
-from _parity import assert_close, oracle_forward, oracle_params
+from _parity import check_forward, check_grad, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -57,11 +57,8 @@ def test_largest_geometry_forward_and_adjoint(engine):
     w = make_workload([big, cap], [[0, 1]], poses, dims, [1e-2])
     g = rng.normal(size=(1, 8, 8))
     out, (gp, gd), params = run(engine, w, grad_out=g)
-    assert_close(out, oracle_forward(w, params), what="largest geometry")
-    rp, rd = oracle.batch_manifold_grad(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, g, oracle_params(params))
-    ref = np.concatenate([rp, rd], 1)
-    got = np.concatenate([gp, gd], 1)
-    assert np.abs(got - ref).max() <= 1e-3 * np.abs(ref).max()
+    check_forward(out, w, params, what="largest geometry")
+    check_grad(np.concatenate([gp, gd], 1), w, params, g, what="largest geometry gradients")
 
 
 def qz(a):
@@ -81,12 +78,8 @@ def test_exactly_parallel_edges(engine):
     w = make_workload([box], [[0, 0]] * 3, poses, dims, [1e-2] * 3)
     g = np.random.default_rng(2).normal(size=(3, 8, 8))
     out, (gp, gd), params = run(engine, w, grad_out=g)
-    assert_close(out, oracle_forward(w, params), what="parallel edges")
-    rp, rd = oracle.batch_manifold_grad(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, g, oracle_params(params))
-    ref = np.concatenate([rp, rd], 1)
-    got = np.concatenate([gp, gd], 1)
-    rel = np.abs(got - ref).max(1) / np.abs(ref).max(1)
-    assert rel.max() <= 1e-3, rel
+    check_forward(out, w, params, what="parallel edges")
+    check_grad(np.concatenate([gp, gd], 1), w, params, g, what="parallel edges gradients")
 
 
 def test_symmetric_configurations(engine):
@@ -104,7 +97,7 @@ def test_symmetric_configurations(engine):
     w = make_workload([box], [[0, 0]] * 3, poses, dims, [1e-2] * 3)
     g = np.random.default_rng(3).normal(size=(3, 8, 8))
     out, (gp, gd), params = run(engine, w, grad_out=g)
-    assert_close(out, oracle_forward(w, params), what="symmetric boxes")
+    check_forward(out, w, params, what="symmetric boxes")
     assert np.isfinite(gp).all() and np.isfinite(gd).all()
     common = gp[:, 4:7] + gp[:, 11:14]
     expect = g[:, :, 0:3].sum(1)
@@ -124,7 +117,7 @@ def test_ragged_batch_of_tiny_and_large_pairs(engine):
     dims = [[1, 1, 1, 0.4, 0.5, 0.6]] * n
     w = make_workload([tet, big, ell], pg, poses, dims, [1e-2] * n)
     out, _, params = run(engine, w)
-    assert_close(out, oracle_forward(w, params), what="ragged batch")
+    check_forward(out, w, params, what="ragged batch")
 
 
 def test_separated_bodies(engine):
@@ -139,4 +132,4 @@ def test_separated_bodies(engine):
     dims = [[1, 1, 1, 0.4, 0.4, 0.5]] * 2
     w = make_workload([hull, cyl], [[0, 1]] * 2, poses, dims, [1e-2, 1e-1])
     out, _, params = run(engine, w)
-    assert_close(out, oracle_forward(w, params), what="separated bodies")
+    check_forward(out, w, params, what="separated bodies")

@@ -4,7 +4,7 @@ import pytest
 import torch
 
 import synth
-from _parity import TOL, assert_close, errors, oracle_forward, tol_for_tau
+from _parity import check_forward, contact_share, errors
 
 pytestmark = pytest.mark.gpu
 
@@ -32,31 +32,34 @@ def test_box_box_all_pairs(engine):
     """1024 box-box poses, tau = 1e-2, K = 8: every pair against the oracle."""
     w = synth.make_config(1)
     gpu, params = run(engine, w)
-    ref = oracle_forward(w, params)
-    err = assert_close(gpu, ref, what="box-box")
-    print("box-box max abs errors", err)
+    check_forward(gpu, w, params, what="box-box")
+    share = contact_share(w, range(128), frac_tau=0.5)
+    print("box-box: pairs with a score above tau / 2", share)
+    assert share >= 0.6
 
 
 def test_hull_vs_primitive_subset(engine):
     w = synth.make_config(2, 96)
     gpu, params = run(engine, w)
-    ref = oracle_forward(w, params)
-    print("hull-vs-primitive", assert_close(gpu, ref, what="hull-vs-primitive"))
+    check_forward(gpu, w, params, what="hull-vs-primitive")
 
 
 def test_hull_vs_primitive_full_size_sampled(engine):
-    """All 4096 pairs in one launch; 24 seeded pairs re-computed by the oracle."""
+    """All 4096 pairs in one launch; 128 seeded pairs re-computed by the oracle, most of
+    them in active contact."""
     w = synth.make_config(2)
     gpu, params = run(engine, w)
-    idx = np.random.default_rng(0).choice(w.n_pairs, 24, replace=False)
-    ref = oracle_forward(w, params, idx=idx)
-    print("hull-vs-primitive sampled", assert_close(gpu[idx], ref, what="full-size sample"))
+    idx = np.random.default_rng(0).choice(w.n_pairs, 128, replace=False)
+    check_forward(gpu[idx], w, params, idx, what="hull-vs-primitive full-size sample")
+    share = contact_share(w, idx, frac_tau=0.5)
+    print("pairs with a score above tau / 2", share)
+    assert share >= 0.6
 
 
 def test_box_vs_sphere_hull_subset(engine):
     w = synth.make_config(3, 64)
     gpu, params = run(engine, w)
-    print("box-vs-hull32", assert_close(gpu, oracle_forward(w, params), what="box-vs-hull32"))
+    check_forward(gpu, w, params, what="box-vs-hull32")
 
 
 @pytest.mark.parametrize("tau", [1e-2, 1e-1])
@@ -67,29 +70,26 @@ def test_hull_vs_hull(engine, tau):
     a, b = npl[w.pair_geoms[:, 0]], npl[w.pair_geoms[:, 1]]
     assert (a > b).any() and (b > a).any()
     gpu, params = run(engine, w)
-    print("hull-vs-hull", assert_close(gpu, oracle_forward(w, params), what="hull-vs-hull"))
+    check_forward(gpu, w, params, what=f"hull-vs-hull tau={tau}")
 
 
 @pytest.mark.parametrize("tau", [1e-3, 1e-2, 1e-1])
 def test_mixed_sizes_per_tau(engine, tau):
-    """Hulls of 8..256 points against all primitive kinds at each smoothing level."""
+    """Hulls of 8..256 points against all primitive kinds at each smoothing level; every
+    pair within the fixed tolerance or its own one-ulp conditioning bound."""
     w = synth.config_mixed(n=48, seed=99)
     w.tau[:] = tau
     gpu, params = run(engine, w)
-    ref = oracle_forward(w, params)
-    print(f"mixed tau={tau}", assert_close(gpu, ref, tol=tol_for_tau(tau), what=f"mixed tau={tau}"))
-    if tau < 1e-2:
-        # most pairs still meet the fixed tolerance; only ill-conditioned ones need the scaled one
-        e = np.abs(gpu - ref).reshape(len(gpu), -1, 8).max(1)
-        ok = (e[:, :4].max(1) <= TOL["d"]) & (e[:, 4:7].max(1) <= TOL["n"])
-        assert ok.mean() >= 0.75, ok.mean()
+    check_forward(gpu, w, params, what=f"mixed tau={tau}")
+    if tau <= 1e-2:
+        assert contact_share(w, range(w.n_pairs), frac_tau=0.5) >= 0.6
 
 
 @pytest.mark.parametrize("flags", [1, 2])
 def test_simplification_flags(engine, flags):
     w = synth.make_config(2, 32)
     gpu, params = run(engine, w, flags=flags, K=4)
-    assert_close(gpu, oracle_forward(w, params), what=f"flags={flags}")
+    check_forward(gpu, w, params, what=f"flags={flags}")
 
 
 @pytest.mark.parametrize("K", [1, 3, 16])
@@ -97,7 +97,7 @@ def test_other_K(engine, K):
     w = synth.make_config(1, 64)
     gpu, params = run(engine, w, K=K)
     assert gpu.shape[1] == K
-    assert_close(gpu, oracle_forward(w, params), what=f"K={K}")
+    check_forward(gpu, w, params, what=f"K={K}")
 
 
 def test_swap_symmetry_on_gpu(engine):
@@ -109,9 +109,10 @@ def test_swap_symmetry_on_gpu(engine):
     ws.poses = np.concatenate([w.poses[:, 7:], w.poses[:, :7]], axis=1).copy()
     ws.dims = np.concatenate([w.dims[:, 3:], w.dims[:, :3]], axis=1).copy()
     b, _ = run(engine, ws)
-    err = errors(a, b)
-    for k in err:
-        assert err[k] <= 2 * TOL[k], err
+    # the oracle's manifold is swap-symmetric (pinned on the CPU), so the swapped batch is
+    # held to the oracle of the original pairs under the same per-pair bar
+    check_forward(b, w, params, what="swapped bodies")
+    print("swapped vs original GPU", errors(a, b))
 
 
 def test_invalid_geometry_id_sets_flag(engine):
@@ -202,6 +203,6 @@ def test_library_built_hull_gives_the_same_manifold():
         eng.check()
         np.testing.assert_allclose(b, a, rtol=0, atol=2e-6)
         params = eng.params()
-        assert_close(b.astype(np.float64), oracle_forward(w, params), what="library-built hulls")
+        check_forward(b.astype(np.float64), w, params, what="library-built hulls")
     finally:
         eng.close()

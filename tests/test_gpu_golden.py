@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import synth
-from _parity import assert_close
+from _parity import BOUND_FACTOR, SLICES, TOL, pair_errors
 
 sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
 import make_golden  # noqa: E402
@@ -32,8 +32,13 @@ def test_forward_and_adjoint_match_stored_oracle_case():
         out = eng.forward(pg, poses, dims, tau, params)
         torch.cuda.synchronize()
         eng.check()
-        print("stored case", assert_close(out.cpu().numpy().astype(np.float64), g["manifold"],
-                                          what="stored oracle case"))
+        o = out.cpu().numpy().astype(np.float64)
+        assert np.isfinite(o).all()
+        e = pair_errors(o, g["manifold"])
+        bound = np.maximum(np.array([TOL[k] for k in SLICES]), BOUND_FACTOR * g["spread_fwd"])
+        print("stored case: pairs within TOL", float((e <= np.array([TOL[k] for k in SLICES])).all(1).mean()),
+              "largest error / bound", float((e / bound).max()))
+        assert (e <= bound).all(), (e / bound).max(1)
         go = torch.as_tensor(g["grad_out"], device="cuda").contiguous()
         gp, gd = eng.backward(pg, poses, dims, tau, go, params)
         torch.cuda.synchronize()
@@ -41,7 +46,8 @@ def test_forward_and_adjoint_match_stored_oracle_case():
         got = np.concatenate([gp.cpu().numpy(), gd.cpu().numpy()], 1).astype(np.float64)
         ref = np.concatenate([g["grad_poses"], g["grad_dims"]], 1)
         assert np.isfinite(got).all()
-        rel = np.abs(got - ref).max(1) / np.maximum(np.abs(ref).max(1), 1e-12)
-        assert rel.max() <= REL, (rel.max(), int(np.argmax(rel)))
+        err = np.abs(got - ref).max(1)
+        bound = np.maximum(REL * np.abs(ref).max(1), BOUND_FACTOR * g["spread_grad"])
+        assert (err <= bound).all(), err / bound
     finally:
         eng.close()
