@@ -12,12 +12,15 @@
 // sees and is joined to the horizon (the edges between a seen and an unseen
 // face), each new triangle keeping the horizon edge's orientation so that
 // every face stays outward.  Points within eps of the hull (eps = 1e-9 x the
-// bounding-box diagonal) count as on or inside it.  The result is a
-// triangulated surface: coplanar facets (a box face) come as several triangles
-// with equal planes.  Output conventions: vertices in the order of their index
-// in the input, edges the unique undirected edges of the triangles sorted by
-// (smaller, larger) index, one plane (unit outward n, offset n . p) per
-// triangle.
+// bounding-box diagonal) count as on or inside it.  The triangulated surface is
+// then checked to be a closed, consistently oriented sphere, and its triangles
+// are merged into facets: neighbours whose vertices lie within eps of each
+// other's plane (a box face built from two triangles) form one facet with one
+// plane, so the LSE SDF counts each face once (a face split into m equal planes
+// would add tau ln m to it).  Output conventions: vertices (the endpoints of
+// facet edges) in the order of their index in the input, edges the facet
+// boundaries sorted by (smaller, larger) index, one plane (unit outward n, offset
+// n . p) per facet.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -155,14 +158,93 @@ extern "C" cm_status cm_create_hull_geometry(cm_context* c, const double* points
     }
   }
 
-  // compact vertex list in input order, edges, planes
-  std::vector<int> remap(n_points, -1);
-  int nf = 0;
+  std::vector<Face> T;  // the live triangles
   for (const Face& f : F)
-    if (f.alive) {
-      ++nf;
-      for (int k = 0; k < 3; ++k) remap[f.v[k]] = 0;
+    if (f.alive) T.push_back(f);
+  const int nt = (int)T.size();
+  // a closed, consistently oriented triangulated sphere: every directed edge once, its
+  // reverse present, V - E + F = 2 (near-degenerate input can break this; refuse it)
+  std::map<uint64_t, int> owner;  // directed edge -> triangle
+  {
+    bool ok = true;
+    std::vector<char> used(n_points, 0);
+    for (int t = 0; t < nt && ok; ++t)
+      for (int k = 0; k < 3 && ok; ++k) {
+        ok = owner.emplace(dkey(T[t].v[k], T[t].v[(k + 1) % 3]), t).second;
+        used[T[t].v[k]] = 1;
+      }
+    for (const auto& kv : owner)
+      if (ok && !owner.count(((kv.first & 0xffffffffull) << 32) | (kv.first >> 32))) ok = false;
+    int nv0 = 0;
+    for (char u : used) nv0 += u;
+    if (!ok || nv0 - (int)owner.size() / 2 + nt != 2)
+      return fail(CM_ERR_INVALID_ARG, "the point set is too close to degenerate for a closed hull");
+  }
+  // facets: triangles joined across an edge when each one's vertices lie within eps of
+  // the other's plane and their normals point the same way (a flat face of the hull,
+  // e.g. a box face split into two triangles, is one facet with one plane)
+  std::vector<int> root(nt);
+  for (int t = 0; t < nt; ++t) root[t] = t;
+  auto find = [&](int t) {
+    while (root[t] != t) t = root[t] = root[root[t]];
+    return t;
+  };
+  auto coplanar = [&](const Face& a, const Face& b) {
+    if (dot(a.n, b.n) <= 0.0) return false;
+    for (int k = 0; k < 3; ++k)
+      if (std::fabs(dot(a.n, P[b.v[k]]) - a.o) > eps || std::fabs(dot(b.n, P[a.v[k]]) - b.o) > eps) return false;
+    return true;
+  };
+  for (const auto& kv : owner) {
+    const int a = (int)(kv.first >> 32), b = (int)(kv.first & 0xffffffffull);
+    const int t0 = kv.second, t1 = owner[dkey(b, a)];
+    if (a < b && coplanar(T[t0], T[t1])) root[find(t0)] = find(t1);
+  }
+  // the facets' boundaries: undirected edges whose two triangles lie in different facets
+  std::vector<std::pair<int, int>> E;
+  for (const auto& kv : owner) {
+    const int a = (int)(kv.first >> 32), b = (int)(kv.first & 0xffffffffull);
+    if (a < b && find(kv.second) != find(owner[dkey(b, a)])) E.emplace_back(a, b);
+  }
+  // one plane per facet: the area-weighted mean normal of its triangles, offset through
+  // their vertices' mean
+  std::map<int, int> facet_of_root;
+  std::vector<V3> fn;
+  std::vector<double> fo, fcnt;
+  for (int t = 0; t < nt; ++t) {
+    const int r = find(t);
+    auto it = facet_of_root.find(r);
+    int fi;
+    if (it == facet_of_root.end()) {
+      fi = (int)fn.size();
+      facet_of_root[r] = fi;
+      fn.push_back({0, 0, 0});
+      fo.push_back(0.0);
+      fcnt.push_back(0.0);
+    } else {
+      fi = it->second;
     }
+    const V3 area = cross(sub(P[T[t].v[1]], P[T[t].v[0]]), sub(P[T[t].v[2]], P[T[t].v[0]]));
+    fn[fi] = {fn[fi].x + area.x, fn[fi].y + area.y, fn[fi].z + area.z};
+  }
+  for (int t = 0; t < nt; ++t) {
+    const int fi = facet_of_root[find(t)];
+    const double l = norm(fn[fi]);
+    const V3 u = {fn[fi].x / l, fn[fi].y / l, fn[fi].z / l};
+    for (int k = 0; k < 3; ++k) fo[fi] += dot(u, P[T[t].v[k]]);
+    fcnt[fi] += 3.0;
+  }
+  const int nf = (int)fn.size();
+  std::vector<float> planes;
+  for (int fi = 0; fi < nf; ++fi) {
+    const double l = norm(fn[fi]);
+    planes.insert(planes.end(), {(float)(fn[fi].x / l), (float)(fn[fi].y / l), (float)(fn[fi].z / l),
+                                 (float)(fo[fi] / fcnt[fi])});
+  }
+  // compact vertex list in input order: the endpoints of the remaining edges (a point in
+  // the middle of a flat facet is not a vertex of the polyhedron)
+  std::vector<int> remap(n_points, -1);
+  for (auto& e : E) remap[e.first] = remap[e.second] = 0;
   std::vector<float> verts;
   int nv = 0;
   for (int i = 0; i < n_points; ++i)
@@ -170,31 +252,13 @@ extern "C" cm_status cm_create_hull_geometry(cm_context* c, const double* points
       remap[i] = nv++;
       verts.insert(verts.end(), {(float)P[i].x, (float)P[i].y, (float)P[i].z, 0.f});
     }
-  std::vector<std::pair<int, int>> E;
-  std::vector<float> planes;
-  for (const Face& f : F) {
-    if (!f.alive) continue;
-    for (int k = 0; k < 3; ++k) {
-      int a = remap[f.v[k]], b = remap[f.v[(k + 1) % 3]];
-      E.emplace_back(std::min(a, b), std::max(a, b));
-    }
-    planes.insert(planes.end(), {(float)f.n.x, (float)f.n.y, (float)f.n.z, (float)f.o});
+  for (auto& e : E) {
+    const int a = remap[e.first], b = remap[e.second];
+    e = {std::min(a, b), std::max(a, b)};
   }
   std::sort(E.begin(), E.end());
-  E.erase(std::unique(E.begin(), E.end()), E.end());
-  // a closed, consistently oriented triangulated sphere: every directed edge once, its
-  // reverse present, V - E + F = 2 (near-degenerate input can break this; refuse it)
-  {
-    std::unordered_set<uint64_t> directed;
-    bool ok = true;
-    for (const Face& f : F)
-      if (f.alive)
-        for (int k = 0; k < 3 && ok; ++k) ok = directed.insert(dkey(f.v[k], f.v[(k + 1) % 3])).second;
-    for (uint64_t key : directed)
-      if (ok && !directed.count(((key & 0xffffffffull) << 32) | (key >> 32))) ok = false;
-    if (!ok || nv - (int)E.size() + nf != 2)
-      return fail(CM_ERR_INVALID_ARG, "the point set is too close to degenerate for a closed hull");
-  }
+  if (nv - (int)E.size() + nf != 2)
+    return fail(CM_ERR_INVALID_ARG, "the point set is too close to degenerate for a closed hull");
   if (nv > CM_MAX_VERTS || (int)E.size() > CM_MAX_EDGES || nf > CM_MAX_PLANES)
     return fail(CM_ERR_INVALID_ARG, "the hull exceeds the geometry limits (256 vertices, 768 edges, 512 planes)");
   std::vector<int32_t> edges;

@@ -149,26 +149,63 @@ def icosphere_template(level=1):
     return v, _edges_from_faces(faces)
 
 
-def hull_from_points(points):
+def hull_from_points(points, eps_rel=1e-9):
     """Convex hull of a point set: compact vertex list, unique edges, face planes.
 
-    Uses qhull (scipy).  Faces are the triangles qhull reports; each plane row
-    is ``(n, o)`` with unit outward normal ``n`` and offset ``o = n . p``.
-    """
+    Uses qhull (scipy).  qhull reports triangles; neighbouring triangles whose planes
+    agree within eps (eps_rel x the bounding-box diagonal) form one flat facet with
+    one plane (a box face is one plane, not two), the edges inside a facet are
+    dropped, and so are points left without an edge (in the middle of a facet).
+    Each plane row is ``(n, o)`` with unit outward normal ``n`` and offset
+    ``o = n . p``; vertices keep the order of their index in ``points``."""
     from scipy.spatial import ConvexHull
     pts = np.asarray(points, dtype=np.float64)
     h = ConvexHull(pts)
-    vid = np.array(sorted(h.vertices))
+    eps = eps_rel * np.linalg.norm(pts.max(0) - pts.min(0))
+    eq = h.equations                       # n . x + off <= 0 inside
+    tri = h.simplices
+    nt = len(tri)
+    root = list(range(nt))
+
+    def find(t):
+        while root[t] != t:
+            root[t] = root[root[t]]
+            t = root[t]
+        return t
+
+    def coplanar(a, b):
+        return (eq[a, :3] @ eq[b, :3] > 0 and np.abs(pts[tri[b]] @ eq[a, :3] + eq[a, 3]).max() <= eps
+                and np.abs(pts[tri[a]] @ eq[b, :3] + eq[b, 3]).max() <= eps)
+    for t in range(nt):
+        for k in range(3):
+            u = int(h.neighbors[t, k])
+            if t < u and coplanar(t, u):
+                root[find(t)] = find(u)
+    es = set()
+    for t in range(nt):
+        for k in range(3):                 # the edge opposite vertex k borders neighbour k
+            u = int(h.neighbors[t, k])
+            if find(t) != find(u):
+                a, b = int(tri[t, (k + 1) % 3]), int(tri[t, (k + 2) % 3])
+                es.add((min(a, b), max(a, b)))
+    vid = np.array(sorted({v for e in es for v in e}))
     remap = -np.ones(len(pts), dtype=np.int64)
     remap[vid] = np.arange(len(vid))
-    faces = remap[h.simplices]
+    edges = np.array(sorted((int(remap[a]), int(remap[b])) for a, b in es), dtype=np.int32)
     verts = np.zeros((len(vid), 4), dtype=np.float32)
     verts[:, :3] = pts[vid]
-    edges = _edges_from_faces(faces)
-    eq = h.equations                       # n . x + off <= 0 inside
-    planes = np.zeros((len(eq), 4), dtype=np.float32)
-    planes[:, :3] = eq[:, :3]
-    planes[:, 3] = -eq[:, 3]
+    facets = {}
+    for t in range(nt):
+        facets.setdefault(find(t), []).append(t)
+    planes = np.zeros((len(facets), 4), dtype=np.float32)
+    for j, ts in enumerate(facets.values()):
+        area = np.zeros(3)
+        for t in ts:                       # qhull's triangles are unoriented: orient each outward
+            c = np.cross(pts[tri[t, 1]] - pts[tri[t, 0]], pts[tri[t, 2]] - pts[tri[t, 0]])
+            area += c * np.sign(c @ eq[t, :3])
+        n = area / np.linalg.norm(area)
+        planes[j, :3] = n
+        planes[j, 3] = np.mean([pts[tri[t]] @ n for t in ts])
     return Geometry(KIND_HULL, np.ones(3, dtype=np.float32), verts, edges, planes)
 
 

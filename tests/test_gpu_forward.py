@@ -206,3 +206,34 @@ def test_library_built_hull_gives_the_same_manifold():
         check_forward(b.astype(np.float64), w, params, what="library-built hulls")
     finally:
         eng.close()
+
+
+def test_library_cube_hull_equals_the_box_primitive():
+    """The library's hull of the 8 corners of [-0.5, 0.5]^3 (6 facet planes, 12 edges) gives
+    the BOX primitive's manifold against the same partners, and both meet the oracle."""
+    from paper_2602_20304_gb300 import api
+    from paper_2602_20304_gb300.engine import Engine, workload_tensors
+    corners = 0.5 * np.array([[x, y, z] for x in (-1.0, 1.0) for y in (-1.0, 1.0) for z in (-1.0, 1.0)])
+    w = synth.config_hull_vs_primitive(n=64, seed=31)
+    box = synth.primitive_geometry(synth.KIND_BOX)
+    eng = Engine(0)
+    try:
+        ids = eng.add_geometries([box] + w.geoms)
+        hid = eng.add_hull(corners)
+        info = api.cm_get_geometry(eng.ctx, hid)
+        assert (len(info["verts"]), len(info["edges"]), len(info["planes"])) == (8, 12, 6)
+        wb = w.subset(np.arange(w.n_pairs))
+        wb.geoms = [box] + w.geoms
+        wb.pair_geoms = np.stack([np.zeros(w.n_pairs, np.int32), 1 + w.pair_geoms[:, 1]], 1)
+        wb.dims[:, :3] = 0.5
+        pg, poses, dims, tau = workload_tensors(wb, id_map=ids)
+        a = eng.forward(pg, poses, dims, tau).cpu().numpy().astype(np.float64)
+        pg_h = pg.clone()
+        pg_h[:, 0] = hid
+        b = eng.forward(pg_h, poses, dims, tau).cpu().numpy().astype(np.float64)
+        eng.check()
+        print("cube hull vs box primitive", errors(a, b))
+        assert np.abs(a - b).max() <= 2e-6
+        check_forward(a, wb, eng.params(), what="box primitive")
+    finally:
+        eng.close()

@@ -61,7 +61,7 @@ def test_hull_is_closed_convex_and_contains_its_points(api, ctx):
     pts = ball_points(9, 300)
     g = api.cm_get_geometry(ctx, api.cm_create_hull_geometry(ctx, pts))
     V, E, F = len(g["verts"]), len(g["edges"]), len(g["planes"])
-    assert V - E + F == 2 and 2 * E == 3 * F            # closed triangulated sphere
+    assert V - E + F == 2 and 2 * E == 3 * F            # closed sphere of triangles (no flat facets here)
     n, o = g["planes"][:, :3].astype(np.float64), g["planes"][:, 3].astype(np.float64)
     np.testing.assert_allclose(np.linalg.norm(n, axis=1), 1.0, atol=1e-6)
     assert (pts @ n.T - o).max() <= 1e-6                # every input point inside every plane
@@ -70,23 +70,28 @@ def test_hull_is_closed_convex_and_contains_its_points(api, ctx):
 
 
 def test_cube_with_repeated_and_interior_points(api, ctx):
-    """A cube's corners (each facet two coplanar triangles), repeated corners and interior
-    points: the 8 corners in first-occurrence order, 12 cube edges plus 6 face diagonals,
-    12 planes, two per face, with normals +-e_i and offset 1."""
+    """A cube's corners (each face built from two coplanar triangles, merged into one
+    facet), repeated corners and interior points: the 8 corners in first-occurrence
+    order, the 12 cube edges (no face diagonals) and 6 planes, one per face, with normals
+    +-e_i and offset 1."""
     rng = np.random.default_rng(5)
     corners = np.array([[x, y, z] for x in (-1.0, 1.0) for y in (-1.0, 1.0) for z in (-1.0, 1.0)])
     inner = rng.uniform(-0.9, 0.9, (20, 3))
     pts = np.concatenate([inner[:10], corners[::-1], inner[10:], corners])
     g = api.cm_get_geometry(ctx, api.cm_create_hull_geometry(ctx, pts))
     np.testing.assert_array_equal(g["verts"][:, :3], corners[::-1])
-    assert len(g["edges"]) == 18 and len(g["planes"]) == 12
+    assert len(g["edges"]) == 12 and len(g["planes"]) == 6
     n, o = g["planes"][:, :3], g["planes"][:, 3]
     np.testing.assert_allclose(o, 1.0, atol=1e-7)
     axes = np.concatenate([np.eye(3), -np.eye(3)])
     for a in axes:
-        assert int((np.abs(n - a).max(1) < 1e-7).sum()) == 2
+        assert int((np.abs(n - a).max(1) < 1e-7).sum()) == 1
     lengths = np.linalg.norm(np.diff(g["verts"][g["edges"]][:, :, :3], axis=1)[:, 0], axis=1)
-    np.testing.assert_allclose(np.sort(lengths), [2.0] * 12 + [np.sqrt(8.0)] * 6, atol=1e-6)
+    np.testing.assert_allclose(lengths, 2.0, atol=1e-6)
+    ref = synth.hull_from_points(pts)                  # the generator merges the same way
+    np.testing.assert_array_equal(g["verts"], ref.verts)
+    np.testing.assert_array_equal(g["edges"], ref.edges)
+    match_planes(g["planes"], ref.planes)
 
 
 @pytest.mark.parametrize("case", ["three", "equal", "collinear", "coplanar", "nan", "too_many"])
@@ -180,24 +185,26 @@ def test_primitive_arguments_are_checked(api, ctx, kind, tess, dims):
     assert api.cm_num_geometries(ctx) == 0
 
 
-def test_coplanar_rims_give_a_closed_triangulated_hull(api, ctx):
-    """Two rims of 16 points (every cap 16 coplanar points): all 32 are vertices, the caps
-    are triangulated (14 triangles each, normals -+z) and the side is 32 triangles."""
+def test_coplanar_rims_give_a_closed_hull_of_flat_facets(api, ctx):
+    """Two rims of 16 points (every cap 16 coplanar points): all 32 are vertices, each cap
+    is one facet (normal -+z) and the side 16 rectangles, 48 edges (the rims and the 16
+    vertical edges, no diagonals)."""
     t = 2 * np.pi * np.arange(16) / 16
     pts = np.concatenate([np.stack([np.cos(t), np.sin(t), np.full(16, z)], 1) for z in (-0.5, 0.5)])
     g = api.cm_get_geometry(ctx, api.cm_create_hull_geometry(ctx, pts))
     V, E, F = len(g["verts"]), len(g["edges"]), len(g["planes"])
-    assert (V, E, F) == (32, 90, 60)
+    assert (V, E, F) == (32, 48, 18)
     n = g["planes"][:, :3]
-    assert int((np.abs(n[:, 2] - 1) < 1e-6).sum()) == 14 and int((np.abs(n[:, 2] + 1) < 1e-6).sum()) == 14
-    assert int((np.abs(n[:, 2]) < 1e-6).sum()) == 32
+    assert int((np.abs(n[:, 2] - 1) < 1e-6).sum()) == 1 and int((np.abs(n[:, 2] + 1) < 1e-6).sum()) == 1
+    assert int((np.abs(n[:, 2]) < 1e-6).sum()) == 16
     assert (pts @ n.T.astype(np.float64) - g["planes"][:, 3]).max() <= 1e-6
 
 
 @pytest.mark.parametrize("seed", range(12))
 def test_nearly_degenerate_sets_give_a_closed_hull_or_a_clean_refusal(api, ctx, seed):
     """Cube corners jittered by 1e-12, repeated, with points on the faces and inside:
-    either a closed triangulated hull containing every point, or CM_ERR_INVALID_ARG."""
+    either the cube (8 vertices, 12 edges, 6 facets) containing every point, or
+    CM_ERR_INVALID_ARG."""
     rng = np.random.default_rng(seed)
     corners = np.array([[x, y, z] for x in (-1.0, 1.0) for y in (-1.0, 1.0) for z in (-1.0, 1.0)])
     face = rng.uniform(-1, 1, (30, 3))
@@ -210,6 +217,28 @@ def test_nearly_degenerate_sets_give_a_closed_hull_or_a_clean_refusal(api, ctx, 
         assert e.status == api.CM_ERR_INVALID_ARG
         return
     V, E, F = len(g["verts"]), len(g["edges"]), len(g["planes"])
-    assert V - E + F == 2 and 2 * E == 3 * F
+    assert (V, E, F) == (8, 12, 6)
     n, o = g["planes"][:, :3].astype(np.float64), g["planes"][:, 3].astype(np.float64)
     assert (pts @ n.T - o).max() <= 1e-6
+
+
+def test_cube_corner_hull_manifold_equals_the_box_primitive():
+    """The hull of the 8 corners of [-0.5, 0.5]^3 has the box's 6 planes and 12 edges, so its
+    smooth SDF (LSE over planes, Sec. IV-B2) is the BOX primitive's and the oracle gives the
+    same manifold for it as for a BOX of half-extent 0.5 (a face split into two equal planes
+    would shift the SDF by tau ln 2 = 6.9e-3 at tau = 1e-2)."""
+    import oracle
+    corners = 0.5 * np.array([[x, y, z] for x in (-1.0, 1.0) for y in (-1.0, 1.0) for z in (-1.0, 1.0)])
+    hull = synth.hull_from_points(corners)
+    assert (hull.n_verts, hull.n_edges, hull.n_planes) == (8, 12, 6)
+    w = synth.config_hull_vs_primitive(n=12, seed=31)
+    box = synth.primitive_geometry(synth.KIND_BOX)
+    # A = the box (as a primitive of half-extent 0.5, then as the cube-corner hull), B as drawn
+    geoms = [box, hull] + w.geoms
+    pg_box = np.stack([np.zeros(w.n_pairs, np.int32), 2 + w.pair_geoms[:, 1]], 1)
+    pg_hull = np.stack([np.ones(w.n_pairs, np.int32), 2 + w.pair_geoms[:, 1]], 1)
+    dims = w.dims.copy()
+    dims[:, :3] = 0.5
+    a = oracle.batch_manifold(geoms, pg_box, w.poses, dims, w.tau)
+    b = oracle.batch_manifold(geoms, pg_hull, w.poses, dims, w.tau)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-9)
