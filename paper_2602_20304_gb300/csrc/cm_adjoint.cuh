@@ -178,7 +178,7 @@ CM_HD void sdf_cylinder_bwd(V3 y, float rad, float h, const Sdf& f, float inv_ta
 // |x~|^(p2-1) sgn x~, u'' = p2 (p2-1) |x~|^(p2-2), divided by the semi-axes of
 // both indices.  As in the forward every power is an exp2 of a sum of base-2
 // logarithms with log2 pi_l folded in.
-CM_HD void sdf_sq_union_bwd(V3 y, const float4* P, int L, const Sdf& f, float inv_tau, float phibar, V3 gbar,
+CM_HD_OUTLINE void sdf_sq_union_bwd(V3 y, const float4* P, int L, const Sdf& f, float inv_tau, float phibar, V3 gbar,
                             V3& ybar) {
   const float k = inv_tau * kLog2e;
   const float gg = dot(gbar, f.g);
@@ -301,7 +301,7 @@ CM_HD void export3(float* dst, V3 v) {
 // x_i - phi(x_i) u, so xbar_i = xbar_(i+1) - grad phi(x_i) (u . xbar_(i+1)) and
 // ubar += -phi(x_i) xbar_(i+1); u = g_0 / |g_0| hands (ubar - (ubar . u) u) / |g_0|
 // to the gradient adjoint of the SDF at x0.
-CM_HD V3 trace_bwd(const Body& b, V3 x0, int iters, float tau, float it, V3 xbar, V3& dbar) {
+CM_HD_OUTLINE V3 trace_bwd(const Body& b, V3 x0, int iters, float tau, float it, V3 xbar, V3& dbar) {
   V3 xs[8];
   const Sdf s0 = body_sdf(b, x0, tau, it);
   const float ig = rsq(dot(s0.g, s0.g));
@@ -507,22 +507,14 @@ struct EEGeom {
 };
 CM_HD V3 xyz(float4 f) { return v3(f.x, f.y, f.z); }
 
-// e1 = a0 + al1 (a1 - a0) (B frame), e1L likewise in A's frame, e2 = b0 + al2 (b1 - b0).
-// Backpropagates e1bar, e1Lbar, e2bar and extra alpha / con adjoints through the
-// witness interpolation and the QP into the parameters.
-CM_HD void witness_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g,
-                       const QPPre& q, const QPOut& o, V3 e1b, V3 e1Lb, V3 e2b, float conb, Adj& adj,
-                       float* eAexp = nullptr, float* eBexp = nullptr) {
-  V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
-  V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L);
-  float ab1 = dot(e1b, a1 - a0) + dot(e1Lb, a1L - a0L);
-  float ab2 = dot(e2b, b1 - b0);
-  V3 a0b = e1b * (1.f - o.a1), a1b = e1b * o.a1;
-  V3 b0b = e2b * (1.f - o.a2), b1b = e2b * o.a2;
-  qp_bwd(q, p.w_reg, p, ab1, ab2, conb, a0b, a1b, b0b, b1b);
-  // A's endpoints: B-frame adjoint pulled to A's frame, plus the A-frame adjoint
-  V3 l0 = push_point_bwd(F, a0L, a0b, adj) + e1Lb * (1.f - o.a1);
-  V3 l1 = push_point_bwd(F, a1L, a1b, adj) + e1Lb * o.a1;
+// Endpoint adjoints -> relative pose, dims of both bodies and the pre-selected edges'
+// exports: a0b, a1b for A's endpoints in B's frame, l0x, l1x added to them in A's
+// own frame, b0b, b1b for B's.
+CM_HD void endpoints_bwd(const Frame& F, const Body& A, const Body& B, const EEGeom& g, V3 a0b, V3 a1b, V3 l0x,
+                         V3 l1x, V3 b0b, V3 b1b, Adj& adj, float* eAexp, float* eBexp) {
+  const V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L), b0 = xyz(g.b0), b1 = xyz(g.b1);
+  const V3 l0 = push_point_bwd(F, a0L, a0b, adj) + l0x;
+  const V3 l1 = push_point_bwd(F, a1L, a1b, adj) + l1x;
   map_vertex_bwd(A.kind, a0L, g.a0L.w, A.dims, l0, adj.dA);
   map_vertex_bwd(A.kind, a1L, g.a1L.w, A.dims, l1, adj.dA);
   map_vertex_bwd(B.kind, b0, g.b0.w, B.dims, b0b, adj.dB);
@@ -538,11 +530,42 @@ CM_HD void witness_bwd(const Frame& F, const Body& A, const Body& B, const Param
   }
 }
 
+// Witness reverse at a fixed QP result: e1 = a0 + al1 (a1 - a0) in B's frame (e1L
+// likewise in A's frame), e2 = b0 + al2 (b1 - b0).  The endpoints' adjoints at fixed
+// alpha go to the parameters; the alpha adjoints are returned for the QP's reverse.
+CM_HD void witness_direct_bwd(const Frame& F, const Body& A, const Body& B, const EEGeom& g, const QPOut& o, V3 e1b,
+                              V3 e1Lb, V3 e2b, Adj& adj, float& ab1, float& ab2, float* eAexp, float* eBexp) {
+  const V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
+  ab1 = dot(e1b, a1 - a0) + dot(e1Lb, xyz(g.a1L) - xyz(g.a0L));
+  ab2 = dot(e2b, b1 - b0);
+  endpoints_bwd(F, A, B, g, e1b * (1.f - o.a1), e1b * o.a1, e1Lb * (1.f - o.a1), e1Lb * o.a1, e2b * (1.f - o.a2),
+                e2b * o.a2, adj, eAexp, eBexp);
+}
+
+// The adjoints of an edge pair's QP result (alpha1, alpha2, con), summed over every use.
+struct QPBar {
+  float a1, a2, con;
+};
+
+// The QP's reverse: (abar1, abar2, conbar) through the smoothed active set, Q and c to
+// the four endpoints, and from there to the parameters.
+CM_HD void witness_qp_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g,
+                          const QPBar& qb, Adj& adj, float* eAexp, float* eBexp) {
+  const QPPre q = qp_setup(xyz(g.a0), xyz(g.a1), xyz(g.b0), xyz(g.b1), p.w_reg);
+  const V3 z = v3(0.f, 0.f, 0.f);
+  V3 a0b = z, a1b = z, b0b = z, b1b = z;
+  qp_bwd(q, p.w_reg, p, qb.a1, qb.a2, qb.con, a0b, a1b, b0b, b1b);
+  endpoints_bwd(F, A, B, g, a0b, a1b, z, z, b0b, b1b, adj, eAexp, eBexp);
+}
+
 // ---------------------------------------------------------------- E-E element
 // Recomputes both candidates of an edge pair, asks `up` for their upstream
-// adjoints, and backpropagates everything except the nearest-neighbour
-// softmax's dependence on the distance matrix, which is returned as
-// t_b = nnbar_b * nn_b for the separate distance-adjoint pass.
+// adjoints, and backpropagates them to the witness points and from there, at the
+// fixed QP result, to the parameters.  Two parts are left to the caller's last
+// pass over the edge pairs: the nearest-neighbour softmax's dependence on the
+// distance matrix, returned as t_b = nnbar_b * nn_b, and the QP's own reverse,
+// whose (alpha, con) adjoints are returned, so that it runs once per edge pair
+// with the distance adjoint's share added.
 struct EECand {
   float y1[8], y2[8];
   float s1, s2;
@@ -555,7 +578,7 @@ struct SdfQuad {
 };
 
 template <class Upstream>
-CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float rowL,
+CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float rowL,
                   float colL, const QPOut* stored, Upstream&& up, float& t1, float& t2, Adj& adj,
                   const SdfQuad* sdf = nullptr, float* eAexp = nullptr, float* eBexp = nullptr) {
   const float tau = F.tau, it = F.inv_tau;
@@ -659,21 +682,31 @@ CM_HD void ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p,
     e2b = trace_bwd(B, e2q, nt, tau, it, e2b, adj.dB);
     e1b = v3(0.f, 0.f, 0.f);
   }
-  witness_bwd(F, A, B, p, g, q, o, e1b, e1Lb, e2b, conb, adj, eAexp, eBexp);
+  QPBar qb;
+  witness_direct_bwd(F, A, B, g, o, e1b, e1Lb, e2b, adj, qb.a1, qb.a2, eAexp, eBexp);
+  qb.con = conb;
+  return qb;
 }
 
-// Distance-matrix adjoint of one element: Dbar flows through dbar = |e1* - e2*|.
-CM_HD void ee_dbar_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float Dbar,
-                       const QPOut* stored, Adj& adj, float* eAexp = nullptr, float* eBexp = nullptr) {
-  V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
-  QPPre q = qp_setup(a0, a1, b0, b1, p.w_reg);
-  QPOut o = stored ? *stored : qp_solve(q, p.w_reg, p);
-  V3 e1 = fma3(o.a1, a1 - a0, a0), e2 = fma3(o.a2, b1 - b0, b0);
-  V3 D = e1 - e2;
-  float r2 = dot(D, D);
-  if (!(r2 > 0.f)) return;
-  V3 Db = D * (Dbar * rsq(r2));
-  witness_bwd(F, A, B, p, g, q, o, Db, v3(0.f, 0.f, 0.f), -Db, 0.f, adj, eAexp, eBexp);
+// Last pass of an edge pair: the distance-matrix adjoint Dbar flows through
+// dbar = |e1* - e2*| of the QP witnesses (its direct part to the endpoints, its alpha
+// part added to the candidates' alpha adjoints), then the QP's reverse runs once on
+// the total.
+CM_HD void ee_qp_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float Dbar,
+                     const QPOut& o, QPBar qb, Adj& adj, float* eAexp = nullptr, float* eBexp = nullptr) {
+  if (Dbar != 0.f) {
+    const V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
+    const V3 D = fma3(o.a1, a1 - a0, a0) - fma3(o.a2, b1 - b0, b0);
+    const float r2 = dot(D, D);
+    if (r2 > 0.f) {
+      const V3 Db = D * (Dbar * rsq(r2));
+      float d1, d2;
+      witness_direct_bwd(F, A, B, g, o, Db, v3(0.f, 0.f, 0.f), -Db, adj, d1, d2, eAexp, eBexp);
+      qb.a1 += d1;
+      qb.a2 += d2;
+    }
+  }
+  if (qb.a1 != 0.f || qb.a2 != 0.f || qb.con != 0.f) witness_qp_bwd(F, A, B, p, g, qb, adj, eAexp, eBexp);
 }
 
 // ---------------------------------------------------------------- pose epilogue

@@ -9,12 +9,14 @@
 //      dL/d score, while accumulating dL/d s^_k of the K largest scores;
 //      vertex-SDF candidates are backpropagated to the parameters right away;
 //   2. each edge pair's reverse (indicators, sign, SDF normals through their
-//      Hessian-vector products, witnesses, 2x2 QP) except the nearest-neighbour
-//      softmax's coupling across its row and column, which is kept as
-//      t_b = dL/d nn_b * nn_b in the CTA's scratch, summed per row / column;
+//      Hessian-vector products, witnesses at the fixed QP result) except the
+//      nearest-neighbour softmax's coupling across its row and column, kept as
+//      t_b = dL/d nn_b * nn_b in the CTA's scratch, summed per row / column, and
+//      the QP's own reverse, whose (alpha, con) adjoints are kept per edge pair;
 //   3. the K top candidates receive dL/d s^_k through their own score;
 //   4. the distance-matrix adjoint dL/d D_kl = (nn1 R_k - t1 + nn2 C_l - t2) / tau
-//      flows through |e1* - e2*| and the QP;
+//      flows through |e1* - e2*|, and each edge pair's QP reverse runs once on the
+//      sum of its candidates' and its distance's (alpha, con) adjoints;
 //   5. CTA reduction of the relative-pose and dims adjoints and the chain to
 //      both quaternions and translations.
 #pragma once
@@ -34,6 +36,11 @@ struct BwdShared {
   float shat[kMaxK];
   int sid[kMaxK];
   float shatbar[kMaxK];
+  // factorised SoftSort reverse below the K-th score r = s^_K (see ss_bwd):
+  // c_k = exp((r - s^_k) / tau) / Z_k, Gc = sum_k c_k G_k, cGout = sum_k c_k Gout_k
+  __align__(16) float Gc[8];
+  float c[kMaxK];
+  float cGout, r;
   float Rout[9];      // adjoint of R_B from the output rotation
   float tout[3];
   float adj[18];      // CTA-reduced Adj: R (9), t (3), dA (3), dB (3)
@@ -76,11 +83,51 @@ __device__ __forceinline__ EEGeom ee_geom(const FwdArgs& a, const PairShared& ps
   return g;
 }
 
-// SoftSort reverse of one candidate (y, s): ybar, sbar and the per-thread
-// partial dL/d s^_k (the K rows' dependence on the selected scores).
+// Per-thread state of the SoftSort reverse: the direct dL/d s^_k of candidates at or
+// above the K-th score, and for those below it E = sum e and Y = sum e y with
+// e = exp((s - r) / tau) (see ss_bwd).
+template <int KMAX>
+struct SsAcc {
+  float shb[KMAX];
+  float E;
+  float Y[8];
+};
+
+template <int KMAX>
+__device__ __forceinline__ void ss_acc_zero(SsAcc<KMAX>& a) {
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) a.shb[k] = 0.f;
+  a.E = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a.Y[c] = 0.f;
+}
+
+// SoftSort reverse of one candidate (y, s): ybar, sbar and the per-thread partial
+// dL/d s^_k.  With G_ki = exp(-|s^_k - s_i| / tau) / Z_k and out_k = sum_i G_ki y_i,
+//   ybar_i = sum_k G_ki G_k,  sbar_i = sum_k G_ki (G_k . y_i - G_k . out_k) sgn(s^_k - s_i) / tau,
+// and s^_k collects the negated terms.  Below the K-th score r every sign is +1 and
+// G_ki = e_i c_k with e_i = exp((s_i - r) / tau), so one exponential serves all K rows:
+// ybar_i = e_i Gc, sbar_i = e_i (Gc . y_i - cGout) / tau, and the s^_k terms are summed
+// per thread as E and Y and folded in once (ss_finish).  Candidates at or above r (the
+// K top entries and exact ties with r, where a sign is 0) take the K-row loop.
 template <int KMAX>
 __device__ __forceinline__ void ss_bwd(const BwdShared& bs, int K, float it, float k2, const float (&y)[8], float s,
-                                       float (&yb)[8], float& sb, float (&shb)[KMAX]) {
+                                       float (&yb)[8], float& sb, SsAcc<KMAX>& acc) {
+  if (s < bs.r) {
+    const float e = ex2((s - bs.r) * k2);
+    const float4 g0 = *reinterpret_cast<const float4*>(bs.Gc), g1 = *reinterpret_cast<const float4*>(bs.Gc + 4);
+    const float gc[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+    float d = -bs.cGout;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      yb[c] = e * gc[c];
+      d = fmaf(gc[c], y[c], d);
+      acc.Y[c] = fmaf(e, y[c], acc.Y[c]);
+    }
+    sb = e * d * it;
+    acc.E += e;
+    return;
+  }
   float2 yb2[4] = {dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f)};
   const float2 yv[4] = {make_float2(y[0], y[1]), make_float2(y[2], y[3]), make_float2(y[4], y[5]),
                         make_float2(y[6], y[7])};
@@ -101,7 +148,7 @@ __device__ __forceinline__ void ss_bwd(const BwdShared& bs, int K, float it, flo
       const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
       const float term = gam * (a2.x + a2.y) * sg * it;
       sb += term;
-      shb[k] -= term;
+      acc.shb[k] -= term;
     }
   }
 #pragma unroll
@@ -134,6 +181,8 @@ struct BwdPair {
   Frame F;
   PairBodies bb;
   float *Dm, *T1, *T2, *QA1, *QA2, *QCN, *rowR, *colC;
+  float* QB;          // per edge pair: the QP result's adjoints (alpha1, alpha2, con) at QB[c * qbs + i]
+  int64_t qbs;
   int nvs, neB, nee, K;
   float* sadj;  // pre-selection adjoint slots (null when nothing is selected)
 };
@@ -152,12 +201,17 @@ __device__ __forceinline__ float* eBexp_of(const BwdPair& P, int l) {
   return P.sadj && P.ps->kv[3] ? P.sadj + 12 * kMaxSel + 6 * l : nullptr;
 }
 
+// Folds the below-threshold sums into dL/d s^_k (-c_k (G_k . Y - Gout_k E) / tau) and
+// adds the warp's totals to the CTA's.
 template <int KMAX>
-__device__ __forceinline__ void shb_reduce(const float (&shb)[KMAX], int K, BwdShared& bs) {
+__device__ __forceinline__ void ss_finish(SsAcc<KMAX>& acc, int K, float it, BwdShared& bs) {
 #pragma unroll
   for (int k = 0; k < KMAX; ++k) {
     if (k < K) {
-      const float v = warp_sum(shb[k]);
+      float d = -bs.Gout[k] * acc.E;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) d = fmaf(bs.G[k][c], acc.Y[c], d);
+      const float v = warp_sum(acc.shb[k] - bs.c[k] * d * it);
       if ((threadIdx.x & 31) == 0) atomicAdd(&bs.shatbar[k], v);
     }
   }
@@ -169,24 +223,23 @@ __device__ __forceinline__ void vs_reverse_phase(const BwdPair P) {
   const PairShared& ps = *P.ps;
   Adj adj;
   adj_zero(adj);
-  float shb[KMAX];
-#pragma unroll
-  for (int k = 0; k < KMAX; ++k) shb[k] = 0.f;
+  SsAcc<KMAX> acc;
+  ss_acc_zero(acc);
   float y[8];
   for (int c = threadIdx.x; c < P.nvs; c += blockDim.x) {
     const float s = vs_candidate(ps, P.sm, P.bb, c, y);
     float yb[8], sb;
-    ss_bwd<KMAX>(*P.bs, P.K, P.F.inv_tau, P.F.k2, y, s, yb, sb, shb);
+    ss_bwd<KMAX>(*P.bs, P.K, P.F.inv_tau, P.F.k2, y, s, yb, sb, acc);
     if (c < ps.nvA) vs_bwd<true>(P.F, P.bb.A, P.bb.B, P.sm.vAl[c], ld3(P.sm.vA[c]), yb, sb, adj, vexp_of(P, c));
     else
       vs_bwd<false>(P.F, P.bb.A, P.bb.B, P.sm.vB[c - ps.nvA], ld3(P.sm.vB[c - ps.nvA]), yb, sb, adj, vexp_of(P, c));
   }
-  shb_reduce<KMAX>(shb, P.K, *P.bs);
+  ss_finish<KMAX>(acc, P.K, P.F.inv_tau, *P.bs);
   adj_reduce(adj, P.bs->adj);
 }
 
 // The K selected scores pass dL/d s^_k to their own candidates (threads < K).
-__device__ __forceinline__ void fixup_phase(const BwdPair P) {
+static __device__ __forceinline__ void fixup_phase(const BwdPair P) {
   const PairShared& ps = *P.ps;
   const int k = threadIdx.x;
   const int id = P.bs->sid[k];
@@ -203,7 +256,7 @@ __device__ __forceinline__ void fixup_phase(const BwdPair P) {
     const int e = id - P.nvs, i = e >> 1, b = e & 1, kk = i / P.neB, ll = i - kk * P.neB;
     float t1, t2;
     const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
-    ee_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, ps, P.sm, kk, ll), P.sm.rowL[kk], P.sm.colL[ll], &qs,
+    const QPBar qb = ee_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, ps, P.sm, kk, ll), P.sm.rowL[kk], P.sm.colL[ll], &qs,
            [&](const EECand&, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
              for (int c = 0; c < 8; ++c) {
                yb1[c] = 0.f;
@@ -217,6 +270,9 @@ __device__ __forceinline__ void fixup_phase(const BwdPair P) {
     atomicAdd(&P.T2[i], t2);
     atomicAdd(&P.rowR[kk], t1);
     atomicAdd(&P.colC[ll], t2);
+    atomicAdd(&P.QB[i], qb.a1);
+    atomicAdd(&P.QB[P.qbs + i], qb.a2);
+    atomicAdd(&P.QB[2 * P.qbs + i], qb.con);
   }
   float* dst = P.bs->adj;
   for (int i = 0; i < 9; ++i) atomicAdd(&dst[i], adj.R[i]);
@@ -225,8 +281,10 @@ __device__ __forceinline__ void fixup_phase(const BwdPair P) {
   atomicAdd(&dst[15], adj.dB.x); atomicAdd(&dst[16], adj.dB.y); atomicAdd(&dst[17], adj.dB.z);
 }
 
-// Distance-matrix adjoint through the nearest-neighbour softmaxes.
-__device__ __forceinline__ void dbar_phase(const BwdPair P) {
+// Last pass over the edge pairs: the distance-matrix adjoint through the
+// nearest-neighbour softmaxes, then each edge pair's QP reverse once, on the sum of
+// its candidates' and its distance's (alpha, con) adjoints.
+__device__ __forceinline__ void qp_phase(const BwdPair P) {
   Adj adj;
   adj_zero(adj);
   const float k2 = P.F.k2, it = P.F.inv_tau;
@@ -235,11 +293,10 @@ __device__ __forceinline__ void dbar_phase(const BwdPair P) {
     const float D = P.Dm[i];
     const float nn1 = ex2((P.sm.rowL[k] - D) * k2), nn2 = ex2((P.sm.colL[l] - D) * k2);
     const float Db = (nn1 * P.rowR[k] - P.T1[i] + nn2 * P.colC[l] - P.T2[i]) * it;
-    if (Db != 0.f) {
-      const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
-      ee_dbar_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, *P.ps, P.sm, k, l), Db, &qs, adj, eAexp_of(P, k),
-                  eBexp_of(P, l));
-    }
+    const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
+    const QPBar qb{P.QB[i], P.QB[P.qbs + i], P.QB[2 * P.qbs + i]};
+    ee_qp_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, *P.ps, P.sm, k, l), Db, qs, qb, adj, eAexp_of(P, k),
+              eBexp_of(P, l));
   }
   adj_reduce(adj, P.bs->adj);
 }
@@ -249,7 +306,7 @@ __device__ __forceinline__ void dbar_phase(const BwdPair P) {
 // Gamma_ki = exp(-|s^_k - s_i| / tau) / Z_k (and s^_k through the k-th top
 // item), and scores pass to the vertex depths (-m for a vertex, -(m_0 + m_1)/2
 // for an edge).  Needs the pair's original vertices / edges staged again.
-__device__ __forceinline__ void sel_reverse_phase(const BwdPair P) {
+static __device__ __forceinline__ void sel_reverse_phase(const BwdPair P) {
   const PairShared& ps = *P.ps;
   const PairSmem& sm = P.sm;
   const SelArea A = sel_area(sm);
@@ -312,7 +369,7 @@ __device__ __forceinline__ void sel_reverse_phase(const BwdPair P) {
 
 // Depth adjoints: m_A[i] = phi_B(v_i) for A's original vertices and
 // m_B[j] = phi_A(v_j) for B's, back to both poses and dims.
-__device__ __forceinline__ void depth_adjoint_phase(const BwdPair P) {
+static __device__ __forceinline__ void depth_adjoint_phase(const BwdPair P) {
   const PairShared& ps = *P.ps;
   const PairSmem& sm = P.sm;
   const float* mbarA = P.sadj + kSelAdjFloats;
@@ -489,6 +546,21 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
         add_outer(Rl, gn, v3(y[4], y[5], y[6]));
         tl = gp;
       }
+      // constants of the factorised SoftSort reverse below the K-th score r
+      const float r = __shfl_sync(kFull, st.ls, K - 1);
+      const float ck = lane < K ? ex2((r - st.ls) * k2) * (1.0f / Z) : 0.f;
+      float gcs = 0.f;
+      for (int c = 0; c < 8; ++c) {
+        const float v = warp_sum(lane < K ? ck * bs.G[lane][c] : 0.f);
+        if (lane == c) gcs = v;
+      }
+      if (lane < 8) bs.Gc[lane] = gcs;
+      const float cgo = warp_sum(lane < K ? ck * bs.Gout[lane] : 0.f);
+      if (lane < K) bs.c[lane] = ck;
+      if (lane == 0) {
+        bs.cGout = cgo;
+        bs.r = r;
+      }
       for (int i = 0; i < 9; ++i) Rl[i] = warp_sum(Rl[i]);
       tl = v3(warp_sum(tl.x), warp_sum(tl.y), warp_sum(tl.z));
       if (lane == 0) {
@@ -508,15 +580,16 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     P.F = F;
     P.bb = bb;
     P.Dm = Dm; P.T1 = T1; P.T2 = T2; P.QA1 = QA1; P.QA2 = QA2; P.QCN = QCN; P.rowR = rowR; P.colC = colC;
+    P.QB = SDF;
+    P.qbs = a.scratch_stride;
     P.nvs = nvs; P.neB = neB; P.nee = nee; P.K = K;
     P.sadj = sadj;
     vs_reverse_phase<KMAX>(P);
     {
       Adj adj;
       adj_zero(adj);
-      float shb[KMAX];
-#pragma unroll
-      for (int k = 0; k < KMAX; ++k) shb[k] = 0.f;
+      SsAcc<KMAX> acc;
+      ss_acc_zero(acc);
       for (int i = threadIdx.x; i < nee; i += blockDim.x) {
         const int k = i / neB, l = i - k * neB;
         float t1, t2;
@@ -532,24 +605,29 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
         sq.A2.g = v3(0.f, 0.f, 0.f);
         sq.A1.phi = q[6 * st];
         sq.A1.g = v3(q[7 * st], q[8 * st], q[9 * st]);
-        ee_bwd(F, bb.A, bb.B, a.p, ee_geom(a, ps, sm, k, l), sm.rowL[k], sm.colL[l], &qs,
+        const QPBar qb = ee_bwd(F, bb.A, bb.B, a.p, ee_geom(a, ps, sm, k, l), sm.rowL[k], sm.colL[l], &qs,
                [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
-                 ss_bwd<KMAX>(bs, K, it, k2, cc.y1, cc.s1, yb1, sb1, shb);
-                 ss_bwd<KMAX>(bs, K, it, k2, cc.y2, cc.s2, yb2, sb2, shb);
+                 ss_bwd<KMAX>(bs, K, it, k2, cc.y1, cc.s1, yb1, sb1, acc);
+                 ss_bwd<KMAX>(bs, K, it, k2, cc.y2, cc.s2, yb2, sb2, acc);
                },
                t1, t2, adj, &sq, eAexp_of(P, k), eBexp_of(P, l));
         T1[i] = t1;
         T2[i] = t2;
+        // the element's SDF values are read above: its first three slots now keep the
+        // QP adjoints for the last pass
+        SDF[i] = qb.a1;
+        SDF[st + i] = qb.a2;
+        SDF[2 * st + i] = qb.con;
         atomicAdd(&rowR[k], t1);
         atomicAdd(&colC[l], t2);
       }
-      shb_reduce<KMAX>(shb, K, bs);
+      ss_finish<KMAX>(acc, K, it, bs);
       adj_reduce(adj, bs.adj);
     }
     __syncthreads();
     if (threadIdx.x < K) fixup_phase(P);
     __syncthreads();
-    dbar_phase(P);
+    qp_phase(P);
     __syncthreads();
     if (sadj) {  // pre-selection: stage the original geometry again, then its reverse
       if (threadIdx.x == 0) {

@@ -12,8 +12,12 @@
 
 #if defined(__CUDACC__)
 #define CM_HD __host__ __device__ __forceinline__
+// Functions of rarely taken paths (kept inline: an out-of-line call inside the hot
+// loops cost more in register allocation than it saved in code size).
+#define CM_HD_OUTLINE static __host__ __device__ __forceinline__
 #else
 #define CM_HD inline
+#define CM_HD_OUTLINE static inline
 #endif
 
 namespace cm {

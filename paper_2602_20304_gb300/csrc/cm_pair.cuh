@@ -301,11 +301,14 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
   Sdf B_e1, B_e2, A_e2, A_e1;
   body_sdf2(bb.B, e1, e2, tau, it, B_e1, B_e2);         // phi_B(e1*), nu_B(e2*)
   const V3 x2 = mulT(ps.Rrel, e2 - ps.trel);
-  // A hull's sums without a shift (sdf_planes_ee) when only the forward's
-  // quantities are wanted and e1* is within a scaled distance of 60 of A's edge.
+  // A hull's sums without a shift (sdf_planes_ee) while e1* is within a scaled
+  // distance of 60 of A's edge; the values kept for the adjoint are then tau ln S (a
+  // sum that underflows, a point deeper than 126 tau ln 2 inside every plane, keeps
+  // the value at that depth: sigma(-phi / tau) is exactly 1 either way and the
+  // adjoint's plane pass stays finite).
   float pen2 = -1.f, safe1 = 1.f;
   bool fast = false;
-  if (!sdf_out && !ps.trace && bb.A.kind == kHull) {
+  if (!ps.trace && bb.A.kind == kHull) {
     const V3 t1 = la1 - la0;
     const float ex = fmaxf(fmaxf(-w.qp.a1, w.qp.a1 - 1.f), 0.f) * ps.k2;
     fast = ex * ex * dot(t1, t1) <= 3600.f;
@@ -315,6 +318,10 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
     sdf_planes_ee(x2, e1l, bb.A.planes, bb.A.n_planes, tau, S1, S2, A_e1.g);
     pen2 = rcp(1.f + S1);
     safe1 = rcp(1.f + S2);
+    if (sdf_out) {
+      A_e2.phi = tau * kLn2 * lg2(fmaxf(S1, 1.17549435e-38f));
+      A_e1.phi = tau * kLn2 * lg2(fmaxf(S2, 1.17549435e-38f));
+    }
   } else {
     body_sdf2(bb.A, x2, e1l, tau, it, A_e2, A_e1);      // phi_A(e2*), nu_A(e1*) in A's frame
     pen2 = sigmoid(-A_e2.phi * it);

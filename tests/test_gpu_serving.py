@@ -201,8 +201,9 @@ def test_admission_by_free_device_memory(pool):
         free, _ = torch.cuda.mem_get_info()
         hog = torch.empty(free - (512 << 20), dtype=torch.uint8, device="cuda")   # leave 512 MiB
         rng = np.random.default_rng(3)
-        ws = w.subset(np.full(64, big_idx))
-        big = make_requests(ws, ids, rng, [64], [True])[0]
+        # 512 pairs: a batch gets min(512, CTAs of the launch) >= 152 scratch slices
+        ws = w.subset(np.full(512, big_idx))
+        big = make_requests(ws, ids, rng, [512], [True])[0]
         t = submit(api, eng.ctx, big)
         with pytest.raises(api.CMError) as ei:
             api.cm_wait(eng.ctx, t, 60000)
