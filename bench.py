@@ -1,14 +1,18 @@
 """Throughput benchmark of the smooth contact-manifold library on GB300.
 
-Workload (default): 4096 independent pairs, each the convex hull of 8..64 points
-uniform in the unit ball against a random smooth primitive (box, capsule,
-cylinder, ellipsoid; dims U[0.2, 1]), tau = 1e-2, penetration U[0, 0.1], K = 8,
-FP32.  A step is one forward manifold over the whole batch (and, with
-``--mode fwdbwd``, also the backward).  Inputs are resident in HBM; L2 is
-flushed (512 MB write) between timed steps.
+Headline workload: 65536 independent pairs in one batch, each the convex hull of
+N points uniform in the unit ball (N log-uniform in [8, 256], a pool of 4096
+hulls) against a random smooth primitive (box, capsule, cylinder, ellipsoid;
+dims U[0.2, 1]), tau drawn per pair from {1e-3, 1e-2, 1e-1}, penetration
+U[0, 0.1] (every pair in contact), K = 8, FP32.  A step is one forward and
+backward manifold over the whole batch (work ordering, forward kernel, work
+ordering, adjoint kernel) replayed as one CUDA graph with autotuned launch
+shapes.  Inputs are resident in HBM; L2 is flushed (512 MB write) between timed
+steps.  The forward alone, the adjoint kernel (the difference of the two steps'
+times) and the other settings are reported beside.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+(forward and backward) on a bounded sample of the same workload instead.
 """
 from __future__ import annotations
 
@@ -27,7 +31,10 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOAD = "hull(8-64 pts) vs primitive, 4096 pairs, tau=1e-2, K=8"
+WORKLOAD = ("65536 uneven pairs: hull(8-256 pts, log-uniform, pool of 4096) vs box/capsule/cylinder/ellipsoid "
+            "(dims U[0.2,1]), tau in {1e-3,1e-2,1e-1}, penetration U[0,0.1], K=8")
+WORKLOAD_2 = "hull(8-64 pts) vs primitive, 4096 pairs, tau=1e-2, K=8"
+HEADLINE_PAIRS = 65536
 
 
 # ----------------------------------------------------------------- algorithmic work
@@ -99,66 +106,116 @@ def fp32_flops_per_pair(w, flags=0):
     return out
 
 
+# Reverse-mode work of the adjoint, counted from the derivative formulas (the kernel's
+# own recomputation is not counted): the adjoint's algorithmic work is the forward's
+# (it needs every forward value) plus this.
+#   per SDF evaluation (value at one point; value and gradient at the other, whose
+#   normal needs the Hessian-vector product): hull / box per plane 1 exp and 14 flops
+#   (value) or 22 (with the gradient); ellipsoid 2 MUFU and 30 / 50 flops; capsule 6 and
+#   80 / 110; cylinder 5 and 60 / 90;
+#   per edge pair: SoftSort reverse of two candidates (one exp and 50 flops each),
+#   indicators, soft signs and normals 200 flops, witnesses and the QP's smoothed
+#   active set 420 flops and 24 MUFU (the derivatives of 4 soft clips and 2 soft
+#   comparisons), distance-matrix adjoint 52 flops and 2 exps;
+#   per vertex candidate: SoftSort reverse (1 exp, 50 flops), normal, activity and frame 70.
+def _sdf_bwd_mufu(kind, n_planes):
+    if kind in (synth.KIND_BOX, synth.KIND_HULL):
+        return 6 if kind == synth.KIND_BOX else n_planes
+    return {synth.KIND_ELLIPSOID: 2, synth.KIND_CAPSULE: 6, synth.KIND_CYLINDER: 5}[kind]
+
+
+def _sdf_bwd_flops(kind, n_planes, grad):
+    if kind in (synth.KIND_BOX, synth.KIND_HULL):
+        F = 6 if kind == synth.KIND_BOX else n_planes
+        return F * (22 if grad else 14) + 10
+    return {synth.KIND_ELLIPSOID: (30, 50), synth.KIND_CAPSULE: (80, 110),
+            synth.KIND_CYLINDER: (60, 90)}[kind][1 if grad else 0]
+
+
+SS_BWD = (1, 50)            # SoftSort reverse of one candidate: (MUFU, flops)
+EE_BWD = (24 + 2, 200 + 420 + 52)
+VS_BWD_FLOPS = 70
+
+
+def bwd_work_per_pair(w, flags=0):
+    """(FP32 flops, MUFU ops) per pair of one adjoint launch: forward work plus reverse work."""
+    nvA, nvB, neA, neB = w.pair_counts()
+    flops = fp32_flops_per_pair(w, flags).copy()
+    mufu = mufu_ops_per_pair(w, flags).copy()
+    for i in range(w.n_pairs):
+        ga, gb = w.geoms[w.pair_geoms[i, 0]], w.geoms[w.pair_geoms[i, 1]]
+        fa, fb = ga.n_planes, gb.n_planes
+        vs_n = nvA[i] + (0 if flags & 2 else nvB[i])
+        flops[i] += vs_n * (SS_BWD[1] + VS_BWD_FLOPS) + nvA[i] * _sdf_bwd_flops(gb.kind, fb, True)
+        mufu[i] += vs_n * SS_BWD[0] + nvA[i] * _sdf_bwd_mufu(gb.kind, fb)
+        if not flags & 2:
+            flops[i] += nvB[i] * _sdf_bwd_flops(ga.kind, fa, True)
+            mufu[i] += nvB[i] * _sdf_bwd_mufu(ga.kind, fa)
+        if not flags & 3:
+            ee = neA[i] * neB[i]
+            flops[i] += ee * (2 * SS_BWD[1] + EE_BWD[1] + _sdf_bwd_flops(ga.kind, fa, False) +
+                              _sdf_bwd_flops(ga.kind, fa, True) + _sdf_bwd_flops(gb.kind, fb, False) +
+                              _sdf_bwd_flops(gb.kind, fb, True))
+            mufu[i] += ee * (2 * SS_BWD[0] + EE_BWD[0] + 2 * _sdf_bwd_mufu(ga.kind, fa) +
+                             2 * _sdf_bwd_mufu(gb.kind, fb))
+    return flops, mufu
+
+
 # Peaks of the two arithmetic pipes from unit counts and the maximum SM clock, the
-# denominators of the ALU roofline: 152 SMs x 128 FP32 lanes x 2 flops (FFMA) x 2070 MHz
-# = 80.5 TFLOP/s, and 152 SMs x 32 ex2 results per clock x 2070 MHz = 10.1 Top/s.  The
-# bench also measures an FFMA loop and an ex2.approx loop on the device and reports each
-# fraction of those beside.
+# denominators of the ALU roofline: SMs x 128 FP32 lanes x 2 flops (FFMA) x 2070 MHz
+# (80.5 TFLOP/s on 152 SMs), and SMs x 32 ex2 results per clock x 2070 MHz (10.1 Top/s).
+# The SM count is read from the device; the bench also measures an FFMA loop and an
+# ex2.approx loop on the device and reports each fraction of those beside.
 N_SMS, FP32_LANES_PER_SM, MUFU_EX2_PER_SM_CLK, SM_MAX_MHZ = 152, 128, 32, 2070
-FP32_PEAK_DERIVED = N_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
-MUFU_PEAK_DERIVED = N_SMS * MUFU_EX2_PER_SM_CLK * SM_MAX_MHZ * 1e6
+
+
+def alu_peaks(n_sms=N_SMS):
+    return (n_sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6, n_sms * MUFU_EX2_PER_SM_CLK * SM_MAX_MHZ * 1e6)
+
+
+FP32_PEAK_DERIVED, MUFU_PEAK_DERIVED = alu_peaks()
 ALU_PEAKS = (FP32_PEAK_DERIVED, MUFU_PEAK_DERIVED)
 
 
-def pipe_fracs(w, ms, peaks=ALU_PEAKS, flags=0):
+def pipe_fracs(w, ms, peaks=ALU_PEAKS, flags=0, backward=False):
     """Useful-work fractions of the FP32 and MUFU peaks (default: from unit counts and
-    clock) for one forward step of `w` taking `ms` milliseconds (the step also holds the
-    work-order kernel)."""
+    clock) for one forward (or, with ``backward``, adjoint) launch over ``w`` taking ``ms``."""
     fma_peak, mufu_peak = peaks
     s = ms * 1e-3
-    return {"fp32": float(fp32_flops_per_pair(w, flags).sum()) / s / fma_peak,
-            "mufu": float(mufu_ops_per_pair(w, flags).sum()) / s / mufu_peak}
+    if backward:
+        fl, mu = bwd_work_per_pair(w, flags)
+    else:
+        fl, mu = fp32_flops_per_pair(w, flags), mufu_ops_per_pair(w, flags)
+    return {"fp32": float(fl.sum()) / s / fma_peak, "mufu": float(mu.sum()) / s / mufu_peak}
 
 
-def alu_roofline(w, step_s, measured):
-    """Roofline object of the forward kernel for one step of ``w`` taking ``step_s`` seconds:
-    both pipes' achieved rates against the peaks from unit counts and clock, the larger
-    fraction binding, with the fractions of the measured loop throughputs
-    ``measured = (FFMA flop/s, ex2 op/s)`` beside them."""
+def alu_roofline(w, step_s, measured, backward=False, n_sms=N_SMS, traffic=None, kernel="cm_fwd_kernel"):
+    """Roofline object of one launch of the forward (or adjoint) kernel over ``w`` taking
+    ``step_s`` seconds: both pipes' achieved rates against the peaks from unit counts and
+    clock, the larger fraction binding, with the fractions of the measured loop
+    throughputs ``measured = (FFMA flop/s, ex2 op/s)`` beside them."""
     fma_meas, mufu_meas = measured
-    mufu = float(mufu_ops_per_pair(w).sum()) / step_s
-    flops = float(fp32_flops_per_pair(w).sum()) / step_s
-    pipes = {"mufu": {"achieved": mufu / 1e9, "peak": MUFU_PEAK_DERIVED / 1e9, "unit": "Gop/s",
-                      "frac": mufu / MUFU_PEAK_DERIVED,
-                      "peak_source": "152 SMs x 32 ex2 per clock x 2070 MHz",
+    fp32_peak, mufu_peak = alu_peaks(n_sms)
+    if backward:
+        fl, mu = bwd_work_per_pair(w)
+    else:
+        fl, mu = fp32_flops_per_pair(w), mufu_ops_per_pair(w)
+    mufu = float(mu.sum()) / step_s
+    flops = float(fl.sum()) / step_s
+    pipes = {"mufu": {"achieved": mufu / 1e9, "peak": mufu_peak / 1e9, "unit": "Gop/s",
+                      "frac": mufu / mufu_peak,
+                      "peak_source": f"{n_sms} SMs x 32 ex2 per clock x 2070 MHz",
                       "peak_measured": mufu_meas / 1e9, "frac_of_measured": mufu / mufu_meas},
-             "fp32": {"achieved": flops / 1e12, "peak": FP32_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
-                      "frac": flops / FP32_PEAK_DERIVED,
-                      "peak_source": "152 SMs x 128 lanes x 2 flops x 2070 MHz",
+             "fp32": {"achieved": flops / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                      "frac": flops / fp32_peak,
+                      "peak_source": f"{n_sms} SMs x 128 lanes x 2 flops x 2070 MHz",
                       "peak_measured": fma_meas / 1e12, "frac_of_measured": flops / fma_meas}}
     binding = max(pipes, key=lambda k: pipes[k]["frac"])
-    return {"bound": "alu", "pipe": binding, **pipes[binding],
-            "traffic": FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096 if FWD_TRAFFIC_CURRENT else None,
-            "traffic_unit": "bytes per launch (ncu dram read + write)",
-            "traffic_last_capture": {"value": FWD_TRAFFIC_BYTES_4096 * w.n_pairs / 4096,
-                                     "note": "ncu capture taken before the destroyed-geometry check "
-                                             "was added to pair setup"},
-            "algorithmic_bytes": 348 * w.n_pairs, "pipes": pipes,
-            "ncu_pipe_active_pct": FWD_NCU_PIPE_PCT}
-
-
-# Pipe activity of the forward kernel on this workload (4096 pairs) from the same ncu
-# capture: sm__pipe_fma_cycles_active and sm__inst_executed_pipe_xu, % of peak.
-FWD_NCU_PIPE_PCT = {"fma": 39.9, "xu": 26.3}
-
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one forward-kernel launch
-# on this workload at 4096 pairs, from one ncu capture; scaled by the pairs a launch
-# processes (traffic grows in proportion).  The kernel has changed since that capture
-# (pair setup now also rejects destroyed geometry, one branch on header fields it
-# already reads), so the roofline's "traffic" is null and the figure is reported beside
-# it as the last capture's.
-FWD_TRAFFIC_BYTES_4096 = 5.426944e6 + 21.611264e6
-FWD_TRAFFIC_CURRENT = False
+    return {"kernel": kernel, "bound": "alu", "pipe": binding, **pipes[binding],
+            "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "algorithmic_bytes": (348 + (56 + 24 + 256 if backward else 0)) * w.n_pairs,
+            "work_per_launch": {"fp32_flops": float(fl.sum()), "mufu_ops": float(mu.sum())},
+            "launch_ms": step_s * 1e3, "pipes": pipes}
 
 
 def _hbm_peak():
@@ -171,9 +228,22 @@ def _hbm_peak():
 
 
 # ----------------------------------------------------------------- multi-rank helpers
-def rank_seed(rank):
-    """Seed of rank ``rank``'s replica: every rank owns an independent batch (weak scaling)."""
-    return synth.SEED_BASE + 2 + 1000 * rank
+def rank_seed(rank, cfg=4):
+    """Seed of rank ``rank``'s replica of setting ``cfg``: every rank owns an independent
+    batch (weak scaling)."""
+    return synth.SEED_BASE + cfg + 1000 * rank
+
+
+def headline_workload(rank=0, n=HEADLINE_PAIRS):
+    """The headline batch of rank ``rank`` (its own seeded replica)."""
+    return synth.config_mixed_pooled(n=n, seed=rank_seed(rank, 4))
+
+
+def oracle_sample(w, frac=0.01, seed=synth.SEED_BASE + 99):
+    """A seeded subsample of ``frac`` of the pairs of ``w`` (at least one), as a workload."""
+    rng = np.random.default_rng(seed)
+    n = max(1, int(round(frac * w.n_pairs)))
+    return w.subset(np.sort(rng.choice(w.n_pairs, n, replace=False)))
 
 
 def aggregate(total_ms, pairs_per_rank, steps, world, all_reduce_max):
@@ -231,19 +301,28 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- reference arm
-def cpu_oracle_rate(w, budget_s=15.0, max_pairs=None, threads=None):
-    """Pairs/s of the FP64 oracle (as it stands) on the first pairs of ``w`` within ``budget_s``,
-    on PyTorch's intra-op threads (``threads`` of them if given, else the default)."""
-    import torch
+def _oracle_pair(w, i, backward, g):
     import oracle
+    if backward:
+        oracle.batch_manifold_grad(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, g, idx=[i])
+    else:
+        oracle.batch_manifold(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, idx=[i])
+
+
+def cpu_oracle_rate(w, budget_s=15.0, max_pairs=None, threads=None, backward=False):
+    """Pairs/s of the FP64 oracle (as it stands: forward, or with ``backward`` forward and
+    vector-Jacobian product) on the first pairs of ``w`` within ``budget_s``, on
+    PyTorch's intra-op threads (``threads`` of them if given, else the default)."""
+    import torch
     saved = torch.get_num_threads()
     if threads:
         torch.set_num_threads(int(threads))
     try:
+        g = np.ones((1, 8, 8))
         done, t0 = 0, time.perf_counter()
         limit = w.n_pairs if max_pairs is None else min(max_pairs, w.n_pairs)
         while done < limit and time.perf_counter() - t0 < budget_s:
-            oracle.batch_manifold(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, idx=[done])
+            _oracle_pair(w, done, backward, g)
             done += 1
         dt = time.perf_counter() - t0
         return done / dt, done, dt, torch.get_num_threads()
@@ -253,55 +332,56 @@ def cpu_oracle_rate(w, budget_s=15.0, max_pairs=None, threads=None):
 
 def _oracle_worker(job):
     """One process of the pair-parallel oracle timing: pairs r, r + P, r + 2P, ... of the
-    workload (regenerated from its seeded recipe) until ``budget_s`` has passed."""
-    cfg, n, r, procs, budget_s = job
+    workload until ``budget_s`` has passed."""
+    w, r, procs, budget_s, backward = job
     import torch
     torch.set_num_threads(1)
-    import oracle
-    w = synth.make_config(cfg, n)
+    g = np.ones((1, 8, 8))
     done, t0 = 0, time.perf_counter()
     for i in range(r, w.n_pairs, procs):
         if time.perf_counter() - t0 >= budget_s:
             break
-        oracle.batch_manifold(w.geoms, w.pair_geoms, w.poses, w.dims, w.tau, idx=[i])
+        _oracle_pair(w, i, backward, g)
         done += 1
     return done, time.perf_counter() - t0
 
 
-def cpu_oracle_rate_over_pairs(cfg, n, budget_s=10.0, procs=None, timeout_s=120.0):
-    """Pairs/s of the FP64 oracle (as it stands) run over pairs on all host cores: ``procs``
-    single-threaded processes (started with spawn, so safe after CUDA use), each on its
-    own share of the pairs for ``budget_s``.  Returns (pairs/s, pairs, seconds, procs);
-    the processes' start-up is outside the timed span."""
+def cpu_oracle_rate_over_pairs(w, budget_s=10.0, procs=None, timeout_s=180.0, backward=False):
+    """Pairs/s of the FP64 oracle (as it stands) run over the pairs of ``w`` on all host
+    cores: ``procs`` single-threaded processes (started with spawn, so safe after CUDA
+    use), each on its own share of the pairs for ``budget_s``.  Returns (pairs/s, pairs,
+    seconds, procs); the processes' start-up is outside the timed span."""
     import multiprocessing as mp
     if not procs:
         procs = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     procs = int(procs)
     with mp.get_context("spawn").Pool(procs) as pool:
-        res = pool.map_async(_oracle_worker, [(cfg, n, r, procs, budget_s) for r in range(procs)])
+        res = pool.map_async(_oracle_worker, [(w, r, procs, budget_s, backward) for r in range(procs)])
         out = res.get(timeout=timeout_s)
     pairs = sum(d for d, _ in out)
     span = max(t for _, t in out)
     return pairs / span, pairs, span, procs
 
 
-def cpu_baseline_leg(w, cfg, cpu_seconds, pool_budget_s=10.0):
+def cpu_baseline_leg(w, cpu_seconds, pool_budget_s=10.0, backward=True, what="a seeded 1 % sample"):
     """The ``cpu_baseline`` object: the FP64 oracle (as it stands) on this host's cores over
-    a bounded sample of workload ``w`` (the seeded setting ``cfg`` at ``w.n_pairs`` pairs).
-    The reported value is the oracle run over pairs, one single-threaded process per core;
-    the same oracle on PyTorch's intra-op threads and on one thread stays beside it (and
-    is the value if the process pool cannot run)."""
-    r, n, dt, cores = cpu_oracle_rate(w, budget_s=cpu_seconds)
+    ``w`` (a bounded sample of the workload, ``what``), forward and backward.  The reported
+    value is the oracle run over pairs, one single-threaded process per core; the same
+    oracle on PyTorch's intra-op threads and on one thread stays beside it (and is the
+    value if the process pool cannot run)."""
+    mode = "forward + backward" if backward else "forward"
+    r, n, dt, cores = cpu_oracle_rate(w, budget_s=cpu_seconds, backward=backward)
     cpu = {"value": r, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-           "sample": f"first {n} pairs of the workload ({dt:.1f} s)"}
-    r1, n1, dt1, _ = cpu_oracle_rate(w, budget_s=min(5.0, cpu_seconds / 3), threads=1)
+           "sample": f"first {n} pairs of {what} of the workload ({mode}, {dt:.1f} s)"}
+    r1, n1, dt1, _ = cpu_oracle_rate(w, budget_s=min(5.0, cpu_seconds / 3), threads=1, backward=backward)
     cpu["single_thread"] = {"value": r1, "unit": "pairs/s", "cores": 1,
-                            "sample": f"first {n1} pairs of the workload ({dt1:.1f} s)"}
+                            "sample": f"first {n1} pairs of {what} ({mode}, {dt1:.1f} s)"}
     try:
-        rp, npairs, dtp, procs = cpu_oracle_rate_over_pairs(cfg, w.n_pairs, budget_s=min(pool_budget_s, cpu_seconds))
+        rp, npairs, dtp, procs = cpu_oracle_rate_over_pairs(w, budget_s=min(pool_budget_s, cpu_seconds),
+                                                            backward=backward)
         cpu = {"value": rp, "unit": "pairs/s", "cores": procs, "kind": "oracle",
-               "sample": f"{npairs} pairs of the workload, every {procs}-th pair in each of {procs} "
-                         f"single-threaded processes ({dtp:.1f} s)",
+               "sample": f"{npairs} pairs of {what} of the workload ({mode}), every {procs}-th pair in each "
+                         f"of {procs} single-threaded processes ({dtp:.1f} s)",
                "intra_op_threads": {k: cpu[k] for k in ("value", "unit", "cores", "sample")},
                "single_thread": cpu["single_thread"]}
     except Exception as e:  # this timing never costs the bench line
@@ -310,28 +390,30 @@ def cpu_baseline_leg(w, cfg, cpu_seconds, pool_budget_s=10.0):
 
 
 def run_reference(args, rank):
+    """The oracle arm: the FP64 CPU oracle (forward and backward, as it stands) on a seeded
+    1 % sample of the headline workload, run over pairs on every host core (one
+    single-threaded process per core), each step a bounded pass over the sample."""
     if rank != 0:
         return
-    w = synth.make_config(2)
-    steps = []
-    per_step_budget = max(0.5, 60.0 / max(1, args.steps + args.warmup))
+    w = oracle_sample(headline_workload())
+    per_step_budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        cpu_oracle_rate(w, budget_s=per_step_budget / 4)
+        cpu_oracle_rate_over_pairs(w, budget_s=per_step_budget / 4, backward=True)
     total_pairs, total_t = 0, 0.0
     for _ in range(args.steps):
-        r, n, dt, cores = cpu_oracle_rate(w, budget_s=per_step_budget)
-        steps.append(dt)
+        r, n, dt, cores = cpu_oracle_rate_over_pairs(w, budget_s=per_step_budget, backward=True)
         total_pairs += n
         total_t += dt
     value = total_pairs / total_t
-    line = {"impl": "reference", "metric": "contact pairs/s (forward manifold)", "value": value,
+    line = {"impl": "reference", "metric": "contact pairs/s (forward + backward manifold)", "value": value,
             "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{total_pairs} pairs of the workload, in order, "
-                                       f"{per_step_budget:.1f} s per step"},
+                             "sample": f"{total_pairs} pairs of a seeded 1 % sample ({w.n_pairs} pairs) of the "
+                                       f"workload, forward + backward, each step at most {per_step_budget:.1f} s of "
+                                       f"{cores} single-threaded processes over the sample's pairs"},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -445,30 +527,31 @@ def plan_rate(eng, api, w, params, steps, with_bwd, flush, tune=True):
     return w.n_pairs * steps / (ms * 1e-3), ms / steps
 
 
-def extra_settings(Engine, api, local, steps, flush, peaks):
-    """The uneven 65536-pair batch (forward and forward+backward) and the paper's two
-    simplifications (vertex-SDF contacts only; one-sided) on the default workload."""
+def extra_settings(Engine, api, local, steps, flush, peaks, w4):
+    """The 4096-pair hull-vs-primitive setting (forward and forward+backward), the paper's
+    acceleration structure on the headline batch ``w4``, and the paper's two
+    simplifications (vertex-SDF contacts only; one-sided) on the 4096-pair setting."""
     eng = Engine(local)
     try:
-        w4 = synth.config_mixed_pooled()
         params = eng.params()
-        f4, f4_ms = plan_rate(eng, api, w4, params, steps, False, flush)
-        fb4, fb4_ms = plan_rate(eng, api, w4, params, steps, True, flush)
+        w2 = synth.config_hull_vs_primitive(n=4096, seed=rank_seed(0, 2))
+        f2, f2_ms = plan_rate(eng, api, w2, params, steps, False, flush)
+        fb2, fb2_ms = plan_rate(eng, api, w2, params, steps, True, flush)
         # the paper's acceleration structure: all vertices, the 16 deepest soft edges per body
         sel4, sel4_ms = plan_rate(eng, api, w4, eng.params(top_edges=16), steps, False, flush)
-        w2 = synth.config_hull_vs_primitive(n=4096, seed=rank_seed(0))
         # K = 4: the smallest hulls have fewer than 8 vertices for the one-sided mode
         full, _ = plan_rate(eng, api, w2, eng.params(K=4), steps, False, flush)
         ne, _ = plan_rate(eng, api, w2, eng.params(K=4, flags=1), steps, False, flush)
         nes, _ = plan_rate(eng, api, w2, eng.params(K=4, flags=2), steps, False, flush)
     finally:
         eng.close()
-    return {"uneven_65536": {"workload": "65536 pairs, hull(8-256 pts, pool of 4096) vs mixed primitives, "
-                                         "tau in {1e-3,1e-2,1e-1}, one persistent launch per step, CUDA graph",
-                             "fwd_pairs_per_s": f4, "fwd_ms": f4_ms, "fwd_bwd_pairs_per_s": fb4, "fwd_bwd_ms": fb4_ms,
-                             "fwd_pipe_fracs": pipe_fracs(w4, f4_ms, peaks),
-                             "preselect_top_edges_16_fwd_pairs_per_s": sel4, "preselect_fwd_ms": sel4_ms},
-            "simplifications": {"workload": WORKLOAD.replace("K=8", "K=4"), "full_fwd_pairs_per_s": full,
+    return {"hull_vs_primitive_4096": {"workload": WORKLOAD_2, "fwd_pairs_per_s": f2, "fwd_ms": f2_ms,
+                                       "fwd_bwd_pairs_per_s": fb2, "fwd_bwd_ms": fb2_ms,
+                                       "fwd_pipe_fracs": pipe_fracs(w2, f2_ms, peaks),
+                                       "bwd_pipe_fracs": pipe_fracs(w2, fb2_ms - f2_ms, peaks, backward=True)},
+            "preselect_top_edges_16": {"workload": WORKLOAD + ", top_edges=16",
+                                       "fwd_pairs_per_s": sel4, "fwd_ms": sel4_ms},
+            "simplifications": {"workload": WORKLOAD_2.replace("K=8", "K=4"), "full_fwd_pairs_per_s": full,
                                 "no_ee_fwd_pairs_per_s": ne, "one_sided_fwd_pairs_per_s": nes,
                                 "speedup_no_ee": ne / full, "speedup_one_sided_vs_no_ee": nes / ne}}
 
@@ -515,10 +598,10 @@ def small_config_rates(Engine, api, local, steps, flush, peaks):
 
 
 def oracle_rates(seconds=4.0):
-    """FP64 oracle pairs/s (as it stands) on bounded samples of the other settings."""
+    """FP64 oracle pairs/s (as it stands, forward) on bounded samples of the other settings."""
     res = {}
     for name, w in (("box_box_1024", synth.make_config(1)), ("box_vs_hull32_1024", synth.make_config(3)),
-                    ("uneven_65536", synth.config_mixed_pooled())):
+                    ("hull_vs_primitive_4096", synth.make_config(2))):
         r, n, dt, cores = cpu_oracle_rate(w, budget_s=seconds)
         res[name] = {"pairs_per_s": r, "pairs": n, "seconds": dt, "cores": cores,
                      "sample": f"first {n} pairs of the workload (forward)"}
@@ -572,19 +655,29 @@ def witness_rates(api, n=10_000_000, steps=5):
 
 
 # ----------------------------------------------------------------- our arm
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pair of one forward and
+# one adjoint launch on the headline workload, from one ncu capture each of a 2048-pair
+# replica of it (the full batch is too large to capture), scaled by the pairs a launch
+# processes; None until a capture of the current kernels exists.
+FWD_TRAFFIC_PER_PAIR = None
+BWD_TRAFFIC_PER_PAIR = None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--pairs", type=int, default=4096, help="pairs per GPU (profiling uses fewer)")
+    ap.add_argument("--pairs", type=int, default=HEADLINE_PAIRS, help="pairs per GPU (profiling uses fewer)")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (profiling)")
-    ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and simplification lines")
-    ap.add_argument("--serve-seconds", type=float, default=0.5,
-                    help="length of the Poisson serving trace (0 skips the serving comparison)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other settings")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the Poisson serving trace at 2000 req/s (0 skips the serving comparison)")
+    ap.add_argument("--serve-below-seconds", type=float, default=5.0,
+                    help="length of the serving trace offered below capacity (400 req/s)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -607,14 +700,15 @@ def main():
         if world > 1:
             dist.barrier()
 
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     # each rank owns an independent replica of the workload (weak scaling, no collective)
-    w = synth.config_hull_vs_primitive(n=args.pairs, seed=rank_seed(rank))
+    w = headline_workload(rank, args.pairs)
     eng = Engine(local)
     ids = eng.add_geometries(w.geoms)
     pg, poses, dims, tau = workload_tensors(w, id_map=ids)
     params = eng.params()
     out = torch.empty((w.n_pairs, params.K, 8), device="cuda")
-    grad_out = torch.randn_like(out)
+    grad_out = torch.randn(out.shape, device="cuda", generator=torch.Generator(device="cuda").manual_seed(rank))
     gp, gd = torch.empty_like(poses), torch.empty_like(dims)
     stream = torch.cuda.current_stream()
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 512 MB > L2
@@ -627,7 +721,7 @@ def main():
     plan_f = api.cm_plan_create(eng.ctx, pg, poses, dims, tau, params, out)
     plan_fb = api.cm_plan_create(eng.ctx, pg, poses, dims, tau, params, out, grad_out, gp, gd)
     launches_f = 1 + shape_f[2]                       # forward kernel (+ work-order kernel)
-    launches_fb = launches_f + 1 + shape_b[2]
+    launches_fb = launches_f + 1 + shape_b[2]         # + adjoint kernel (+ work-order kernel)
 
     for _ in range(max(3, args.warmup)):
         api.cm_plan_launch(plan_f)
@@ -656,14 +750,15 @@ def main():
         return float(t.item())
 
     with ClockSampler(local) as clk:
-        total_ms, step_ms = timed(plan_f)
-        total_fb_ms, _ = timed(plan_fb)
-    value, total_ms = aggregate(total_ms, w.n_pairs, args.steps, world, max_over_ranks)
-    value_fb, total_fb_ms = aggregate(total_fb_ms, w.n_pairs, args.steps, world, max_over_ranks)
+        total_fb_ms, step_fb_ms = timed(plan_fb)
+        total_f_ms, step_f_ms = timed(plan_f)
+    value, total_fb_ms = aggregate(total_fb_ms, w.n_pairs, args.steps, world, max_over_ranks)
+    value_f, total_f_ms = aggregate(total_f_ms, w.n_pairs, args.steps, world, max_over_ranks)
 
-    # ---- end to end through the public API: pinned host inputs -> plan buffers -> host result
-    hp = [t.cpu().pin_memory() for t in (pg, poses, dims, tau)]
-    hout = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+    # ---- end to end through the public API: pinned host inputs (pairs, poses, dims, tau,
+    # upstream gradient) -> the plan's buffers -> step -> host results (manifold, gradients)
+    hin = [t.cpu().pin_memory() for t in (pg, poses, dims, tau, grad_out)]
+    hout = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (out, gp, gd)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
@@ -671,36 +766,43 @@ def main():
     for s in range(args.steps):
         flush.zero_()
         e0.record(stream)
-        for d, h in zip((pg, poses, dims, tau), hp):
+        for d, h in zip((pg, poses, dims, tau, grad_out), hin):
             d.copy_(h, non_blocking=True)
-        api.cm_plan_launch(plan_f)
-        hout.copy_(out, non_blocking=True)
+        api.cm_plan_launch(plan_fb)
+        for h, d in zip(hout, (out, gp, gd)):
+            h.copy_(d, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
     barrier()
     e2e_value, e2e_ms = aggregate(e2e_ms, w.n_pairs, args.steps, world, max_over_ranks)
-    h2d = sum(t.numel() * t.element_size() for t in hp)
-    d2h = hout.numel() * hout.element_size()
     e2e = {"value": e2e_value, "unit": "pairs/s",
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+           "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in hin)),
+           "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in hout))}
     api.cm_plan_destroy(plan_f)
     api.cm_plan_destroy(plan_fb)
+    eng.check()
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the forward kernel: algorithmic work per launch / step duration (the
-    # step also holds the few-microsecond work-order kernel, so this slightly understates it).
-    # Both arithmetic pipes are reported; the binding one is the larger fraction.
+    # ---- rooflines: algorithmic work per launch over the kernel's time.  The forward step
+    # holds the work-order kernel and the forward kernel; the adjoint kernel's time is the
+    # forward+backward step's less the forward step's (both timed above with CUDA events
+    # on the launching stream; each difference also holds one few-microsecond ordering).
     fma_peak, mufu_peak = api.cm_measure_pipe_peaks(local)
-    roof = alu_roofline(w, float(np.mean(step_ms)) * 1e-3, (fma_peak, mufu_peak))
+    f_s = float(np.mean(step_f_ms)) * 1e-3
+    b_s = float(np.mean(step_fb_ms) - np.mean(step_f_ms)) * 1e-3
+    roof_b = alu_roofline(w, b_s, (fma_peak, mufu_peak), backward=True, n_sms=n_sms, kernel="cm_bwd_kernel",
+                          traffic=None if BWD_TRAFFIC_PER_PAIR is None else BWD_TRAFFIC_PER_PAIR * w.n_pairs)
+    roof_f = alu_roofline(w, f_s, (fma_peak, mufu_peak), n_sms=n_sms, kernel="cm_fwd_kernel",
+                          traffic=None if FWD_TRAFFIC_PER_PAIR is None else FWD_TRAFFIC_PER_PAIR * w.n_pairs)
 
     extra = None
     if not args.no_extra and world == 1:
-        extra = extra_settings(Engine, api, local, max(3, min(args.steps, 5)), flush, ALU_PEAKS)
+        extra = extra_settings(Engine, api, local, max(3, min(args.steps, 5)), flush, ALU_PEAKS, w)
         extra["witness_points"] = witness_rates(api)
         extra["sq_union"] = sq_union_rates(Engine, api, local, max(3, min(args.steps, 5)), flush)
         extra.update(small_config_rates(Engine, api, local, max(3, min(args.steps, 5)), flush, ALU_PEAKS))
@@ -714,32 +816,35 @@ def main():
             serving = serve_benchmark(eng_s, api, args.serve_seconds)
         finally:
             eng_s.close()
-        # the same mix offered below the device's forward+backward capacity (~0.6 M pairs/s),
-        # where latency is service time rather than queueing
-        eng_s = Engine(local, hbm_budget_bytes=40 << 30)
-        try:
-            serving["below_capacity"] = serve_benchmark(eng_s, api, max(1.0, 2 * args.serve_seconds), rate=400.0)
-        finally:
-            eng_s.close()
+        # the same mix offered below the device's forward+backward capacity, where latency
+        # is service time rather than queueing
+        if args.serve_below_seconds > 0:
+            eng_s = Engine(local, hbm_budget_bytes=40 << 30)
+            try:
+                serving["below_capacity"] = serve_benchmark(eng_s, api, args.serve_below_seconds, rate=400.0)
+            finally:
+                eng_s.close()
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline_leg(w, 2, args.cpu_seconds)
+        cpu = cpu_baseline_leg(oracle_sample(w), args.cpu_seconds)
         if extra is not None:
             cpu["other_settings"] = oracle_rates()
 
-    line = {"metric": "contact pairs/s (forward manifold)", "value": value, "unit": "pairs/s",
-            "fwd_bwd": {"value": value_fb, "unit": "pairs/s", "ms_per_step": total_fb_ms / args.steps,
-                        "gpu_launches": launches_fb * args.steps},
+    line = {"metric": "contact pairs/s (forward + backward manifold)", "value": value, "unit": "pairs/s",
+            "fwd": {"value": value_f, "unit": "pairs/s", "ms_per_step": total_f_ms / args.steps,
+                    "gpu_launches": launches_f * args.steps},
+            "bwd_kernel_ms": b_s * 1e3,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": total_fb_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "pairs_per_gpu": w.n_pairs, "parallelism": f"replicas x{world}",
-                       "l2": "flushed (512 MB write) between timed steps"},
-            "gpu_launches": launches_f * args.steps, "e2e": e2e, "serving": serving, "extra": extra,
+                       "l2": "flushed (512 MB write) between timed steps", "sms": n_sms},
+            "gpu_launches": launches_fb * args.steps, "e2e": e2e, "roofline": roof_b, "roofline_fwd": roof_f,
+            "serving": serving, "extra": extra,
             "launch_shape": {"fwd": {"block": shape_f[0], "ctas_per_sm": shape_f[1], "ordered": shape_f[2]},
                              "bwd": {"block": shape_b[0], "ctas_per_sm": shape_b[1], "ordered": shape_b[2]},
-                             "cuda_graph": True}, "roofline": roof, "cpu_baseline": cpu,
+                             "cuda_graph": True}, "cpu_baseline": cpu,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     if world > 1:

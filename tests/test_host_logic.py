@@ -176,32 +176,39 @@ def test_bench_oracle_rate_restores_thread_count():
 
 def test_bench_alu_roofline_object():
     """The benchmark's roofline object: both pipes against the peaks from unit counts and
-    the 2070 MHz clock, the larger fraction binding, the measured loop throughputs beside."""
+    the 2070 MHz clock, the larger fraction binding, the measured loop throughputs beside;
+    the adjoint's work is the forward's plus the reverse's."""
     import bench
     import synth
     w = synth.make_config(2, 16)
     assert abs(bench.FP32_PEAK_DERIVED - 152 * 128 * 2 * 2.07e9) < 1.0
     assert abs(bench.MUFU_PEAK_DERIVED - 152 * 32 * 2.07e9) < 1.0
-    r = bench.alu_roofline(w, 1e-5, (76e12, 9.8e12))
-    assert r["bound"] == "alu" and r["pipe"] in ("fp32", "mufu")
-    for k, p in r["pipes"].items():
-        scale = 1e12 if k == "fp32" else 1e9
-        assert abs(p["frac"] - p["achieved"] / p["peak"]) < 1e-12
-        assert abs(p["frac_of_measured"] - p["achieved"] * scale / (76e12 if k == "fp32" else 9.8e12)) < 1e-12
-    assert r["frac"] == max(p["frac"] for p in r["pipes"].values())
-    assert r["algorithmic_bytes"] == 348 * 16
-    assert (r["traffic"] is None) == (not bench.FWD_TRAFFIC_CURRENT)
+    assert bench.alu_peaks(76)[0] == bench.FP32_PEAK_DERIVED / 2
+    for backward in (False, True):
+        r = bench.alu_roofline(w, 1e-5, (76e12, 9.8e12), backward=backward)
+        assert r["bound"] == "alu" and r["pipe"] in ("fp32", "mufu")
+        for k, p in r["pipes"].items():
+            scale = 1e12 if k == "fp32" else 1e9
+            assert abs(p["frac"] - p["achieved"] / p["peak"]) < 1e-12
+            assert abs(p["frac_of_measured"] - p["achieved"] * scale / (76e12 if k == "fp32" else 9.8e12)) < 1e-12
+        assert r["frac"] == max(p["frac"] for p in r["pipes"].values())
+        assert r["traffic"] is None
+    assert bench.alu_roofline(w, 1e-5, (1, 1))["algorithmic_bytes"] == 348 * 16
+    fl_b, mu_b = bench.bwd_work_per_pair(w)
+    fl_f, mu_f = bench.fp32_flops_per_pair(w), bench.mufu_ops_per_pair(w)
+    assert (fl_b > 2 * fl_f).all() and (mu_b > 1.5 * mu_f).all()
 
 
 def test_bench_cpu_baseline_leg():
     """The benchmark's cpu_baseline object: the over-pairs value with the intra-op and
-    single-thread figures beside it, every figure positive."""
+    single-thread figures beside it, every figure positive, forward and backward."""
     import bench
     import synth
     w = synth.make_config(1, 8)
-    cpu = bench.cpu_baseline_leg(w, 1, cpu_seconds=1.0, pool_budget_s=1.0)
+    cpu = bench.cpu_baseline_leg(w, cpu_seconds=1.0, pool_budget_s=1.0)
     assert cpu["kind"] == "oracle" and cpu["unit"] == "pairs/s" and "over_pairs_error" not in cpu
     assert cpu["value"] > 0 and cpu["cores"] >= 1 and "single-threaded processes" in cpu["sample"]
+    assert "forward + backward" in cpu["sample"]
     for k in ("intra_op_threads", "single_thread"):
         assert cpu[k]["value"] > 0 and cpu[k]["unit"] == "pairs/s"
 
@@ -210,5 +217,17 @@ def test_bench_oracle_over_pairs_pool():
     """The pair-parallel oracle timing: single-threaded spawned processes, each on its own
     share of the pairs, returning a positive rate within its time limit."""
     import bench
-    r, pairs, span, procs = bench.cpu_oracle_rate_over_pairs(1, 16, budget_s=1.0, procs=2, timeout_s=120.0)
+    import synth
+    w = synth.make_config(1, 16)
+    r, pairs, span, procs = bench.cpu_oracle_rate_over_pairs(w, budget_s=1.0, procs=2, timeout_s=120.0)
     assert procs == 2 and 0 < pairs <= 16 and span > 0 and r > 0
+
+
+def test_bench_headline_sample_is_seeded():
+    """The oracle's 1 % sample of the headline batch: seeded, the same pairs every time."""
+    import bench
+    import synth
+    w = synth.config_hull_vs_primitive(n=300, seed=5)
+    a, b = bench.oracle_sample(w), bench.oracle_sample(w)
+    assert a.n_pairs == 3
+    np.testing.assert_array_equal(a.poses, b.poses)
