@@ -108,12 +108,17 @@ __device__ __forceinline__ void ss_acc_zero(SsAcc<KMAX>& a) {
 // and s^_k collects the negated terms.  Below the K-th score r every sign is +1 and
 // G_ki = e_i c_k with e_i = exp((s_i - r) / tau), so one exponential serves all K rows:
 // ybar_i = e_i Gc, sbar_i = e_i (Gc . y_i - cGout) / tau, and the s^_k terms are summed
-// per thread as E and Y and folded in once (ss_finish).  Candidates at or above r (the
-// K top entries and exact ties with r, where a sign is 0) take the K-row loop.
+// per thread as E and Y and folded in once (ss_finish).  A candidate tied with r whose
+// weight w is exactly 0 (an indicator that underflowed, so s = -w d = 0 = r when fewer
+// than K scores are positive) takes the same path: ybar is exact (G_ki = c_k), and the
+// +1 it gives the tied rows' signs (instead of 0) only reaches w's adjoint and the tied
+// rows' s^_k, both of which meet only the underflowed factor's derivative, which is
+// exactly 0.  The K top entries and ties with w != 0 (a measure-zero set) take the
+// K-row loop.
 template <int KMAX>
 __device__ __forceinline__ void ss_bwd(const BwdShared& bs, int K, float it, float k2, const float (&y)[8], float s,
                                        float (&yb)[8], float& sb, SsAcc<KMAX>& acc) {
-  if (s < bs.r) {
+  if (s < bs.r || (s == bs.r && y[7] == 0.f)) {
     const float e = ex2((s - bs.r) * k2);
     const float4 g0 = *reinterpret_cast<const float4*>(bs.Gc), g1 = *reinterpret_cast<const float4*>(bs.Gc + 4);
     const float gc[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
@@ -592,9 +597,9 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
       ss_acc_zero(acc);
       for (int i = threadIdx.x; i < nee; i += blockDim.x) {
         const int k = i / neB, l = i - k * neB;
+        const int64_t st = a.scratch_stride;
         float t1, t2;
         const QPOut qs{QA1[i], QA2[i], QCN[i]};
-        const int64_t st = a.scratch_stride;
         const float* q = SDF + i;
         SdfQuad sq;
         sq.B1.phi = q[0];
