@@ -261,6 +261,32 @@ cm_status cm_contact_manifold_bwd(cm_context* ctx, int32_t n_pairs, const int32_
                                   const cm_params* params, const float* grad_out, float* grad_poses,
                                   float* grad_dims, void* stream);
 
+/* Forward records for the adjoint.  cm_contact_manifold_fwd_save is
+ * cm_contact_manifold_fwd that also writes, per pair, what the adjoint would
+ * otherwise recompute from the whole forward: the K selected SoftSort scores and
+ * their candidate ids, the K row normalisers, the K output rows in B's frame and
+ * the soft row / column minima of the E-E distance matrix behind the
+ * nearest-neighbour indicators (Sec. IV-D3) -- per-pair reductions, never a
+ * candidate.  cm_contact_manifold_bwd_saved is cm_contact_manifold_bwd reading
+ * them: it skips the forward recompute and evaluates each edge pair's candidates
+ * once, in the reverse sweep.  Both calls must see the same pairs, poses, dims,
+ * tau and params, with no geometry destroyed in between.
+ * saved: device, n_pairs x saved_stride floats, caller-owned; saved_stride (floats
+ *   per pair) >= what cm_saved_stride reports for these params and the registered
+ *   geometry (it grows with the largest edge count, so registering a geometry
+ *   with more edges makes older records too small: the call then returns
+ *   CM_ERR_INVALID_ARG).
+ * cm_saved_stride: floats per pair for `params` with the geometry registered now. */
+cm_status cm_saved_stride(const cm_context* ctx, const cm_params* params, int64_t* floats_per_pair);
+cm_status cm_contact_manifold_fwd_save(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms,
+                                       const float* poses, const float* dims, const float* tau,
+                                       const cm_params* params, float* out, float* saved, int64_t saved_stride,
+                                       void* stream);
+cm_status cm_contact_manifold_bwd_saved(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms,
+                                        const float* poses, const float* dims, const float* tau,
+                                        const cm_params* params, const float* saved, int64_t saved_stride,
+                                        const float* grad_out, float* grad_poses, float* grad_dims, void* stream);
+
 /* Batching layer (not part of the paper's method).
  *
  * cm_autotune times a few launch shapes (threads per CTA, CTAs per SM, with or

@@ -77,6 +77,12 @@ _SIGS = {
                                                ctypes.POINTER(cm_params), _vp, _vp, _vp, _vp]),
     "cm_contact_manifold_fwd_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
                                                        ctypes.POINTER(cm_params), _vp, _vp]),
+    "cm_saved_stride": (ctypes.c_int, [_vp, ctypes.POINTER(cm_params), ctypes.POINTER(ctypes.c_int64)]),
+    "cm_contact_manifold_fwd_save": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                                    ctypes.POINTER(cm_params), _vp, _vp, ctypes.c_int64, _vp]),
+    "cm_contact_manifold_bwd_saved": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                                     ctypes.POINTER(cm_params), _vp, ctypes.c_int64, _vp, _vp,
+                                                     _vp, _vp]),
     "cm_autotune": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.POINTER(cm_params),
                                    _vp, _vp, _vp, _vp, _vp]),
     "cm_get_launch_shape": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -254,6 +260,49 @@ def cm_contact_manifold_bwd(ctx, pair_geoms, poses, dims, tau, params, grad_out,
     _check(_lib.cm_contact_manifold_bwd(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau),
                                         ctypes.byref(params), _ptr(grad_out), _ptr(grad_poses),
                                         _ptr(grad_dims), _stream_handle(stream)))
+
+
+def cm_saved_stride(ctx, params) -> int:
+    """Floats per pair of the forward's record for the adjoint (cm_contact_manifold_fwd_save)."""
+    v = ctypes.c_int64()
+    _check(_lib.cm_saved_stride(ctx, ctypes.byref(params), ctypes.byref(v)))
+    return int(v.value)
+
+
+def cm_contact_manifold_fwd_save(ctx, pair_geoms, poses, dims, tau, params, out, saved, stream=None) -> None:
+    """Forward manifold that also writes each pair's record for the adjoint into ``saved``
+    ((n, stride) float32, stride >= cm_saved_stride)."""
+    import torch
+    n = int(pair_geoms.shape[0])
+    _check_tensor(pair_geoms, "pair_geoms", torch.int32, n)
+    _check_tensor(poses, "poses", torch.float32, n)
+    _check_tensor(dims, "dims", torch.float32, n)
+    _check_tensor(tau, "tau", torch.float32, n)
+    _check_tensor(out, "out", torch.float32, n)
+    _check_tensor(saved, "saved", torch.float32, n)
+    _check(_lib.cm_contact_manifold_fwd_save(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau),
+                                             ctypes.byref(params), _ptr(out), _ptr(saved),
+                                             int(saved.shape[1]) if saved.dim() == 2 else 0,
+                                             _stream_handle(stream)))
+
+
+def cm_contact_manifold_bwd_saved(ctx, pair_geoms, poses, dims, tau, params, saved, grad_out, grad_poses,
+                                  grad_dims, stream=None) -> None:
+    """Adjoint from the records a cm_contact_manifold_fwd_save call wrote for the same inputs."""
+    import torch
+    n = int(pair_geoms.shape[0])
+    _check_tensor(pair_geoms, "pair_geoms", torch.int32, n)
+    _check_tensor(poses, "poses", torch.float32, n)
+    _check_tensor(dims, "dims", torch.float32, n)
+    _check_tensor(tau, "tau", torch.float32, n)
+    _check_tensor(saved, "saved", torch.float32, n)
+    _check_tensor(grad_out, "grad_out", torch.float32, n)
+    _check_tensor(grad_poses, "grad_poses", torch.float32, n)
+    _check_tensor(grad_dims, "grad_dims", torch.float32, n)
+    _check(_lib.cm_contact_manifold_bwd_saved(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau),
+                                              ctypes.byref(params), _ptr(saved),
+                                              int(saved.shape[1]) if saved.dim() == 2 else 0, _ptr(grad_out),
+                                              _ptr(grad_poses), _ptr(grad_dims), _stream_handle(stream)))
 
 
 def cm_contact_manifold_fwd_noalloc(ctx, pair_geoms, poses, dims, tau, params, out, stream=None) -> None:

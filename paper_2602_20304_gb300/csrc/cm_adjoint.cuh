@@ -281,6 +281,75 @@ CM_HD void body_sdf2_bwd(const Body& b, V3 y1, V3 y2, const Sdf& f1, const Sdf& 
   }
 }
 
+// A body's SDF at the two points an edge pair uses, with what the reverse needs
+// (see sdf_planes2_h): value and gradient at y1 and at y2, and for a polyhedron
+// the Hessian at y2.
+struct Sdf2H {
+  Sdf f1, f2;
+  float H[6];
+};
+// The two evaluations of a primitive share one copy of its code (a loop that is
+// not unrolled), which keeps the adjoint's edge-pair loop small in the
+// instruction cache.
+CM_HD Sdf2H body_sdf2_h(const Body& b, V3 y1, V3 y2, float tau, float inv_tau) {
+  Sdf2H o;
+  if (b.kind == kHull) {
+    sdf_planes2_h(y1, y2, b.planes, b.n_planes, tau, o.f1, o.f2, o.H);
+  } else {
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+      const Sdf f = body_sdf(b, j ? y2 : y1, tau, inv_tau);
+      if (j) o.f2 = f;
+      else o.f1 = f;
+    }
+  }
+  return o;
+}
+// Reverse of body_sdf2_h: phibar1 at y1, (phibar2, gbar2) at y2.  A polyhedron needs
+// no pass over its planes: ybar1 += phibar1 g1, ybar2 += phibar2 g2 + H2 gbar2.
+CM_HD void body_sdf2_h_bwd(const Body& b, V3 y1, V3 y2, const Sdf2H& s, float tau, float inv_tau, float phibar1,
+                           float phibar2, V3 gbar2, V3& ybar1, V3& ybar2, V3& dbar) {
+  if (b.kind == kHull) {
+    const float* H = s.H;
+    ybar1 += s.f1.g * phibar1;
+    ybar2 += s.f2.g * phibar2 + v3(fmaf(H[0], gbar2.x, fmaf(H[1], gbar2.y, H[2] * gbar2.z)),
+                                   fmaf(H[1], gbar2.x, fmaf(H[3], gbar2.y, H[4] * gbar2.z)),
+                                   fmaf(H[2], gbar2.x, fmaf(H[4], gbar2.y, H[5] * gbar2.z)));
+  } else {
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+      V3 yb = v3(0.f, 0.f, 0.f);
+      body_sdf_bwd(b, j ? y2 : y1, j ? s.f2 : s.f1, tau, inv_tau, j ? phibar2 : phibar1,
+                   j ? gbar2 : v3(0.f, 0.f, 0.f), yb, dbar);
+      if (j) ybar2 += yb;
+      else ybar1 += yb;
+    }
+  }
+}
+
+// One point of body_sdf2_h / body_sdf2_h_bwd.
+struct Sdf1H {
+  Sdf f;
+  float H[6];
+};
+CM_HD Sdf1H body_sdf_h(const Body& b, V3 y, float tau, float inv_tau) {
+  Sdf1H o;
+  if (b.kind == kHull) sdf_planes_h(y, b.planes, b.n_planes, tau, o.f, o.H);
+  else o.f = body_sdf(b, y, tau, inv_tau);
+  return o;
+}
+CM_HD void body_sdf_h_bwd(const Body& b, V3 y, const Sdf1H& s, float tau, float inv_tau, float phibar, V3 gbar,
+                          V3& ybar, V3& dbar) {
+  if (b.kind == kHull) {
+    const float* H = s.H;
+    ybar += s.f.g * phibar + v3(fmaf(H[0], gbar.x, fmaf(H[1], gbar.y, H[2] * gbar.z)),
+                                fmaf(H[1], gbar.x, fmaf(H[3], gbar.y, H[4] * gbar.z)),
+                                fmaf(H[2], gbar.x, fmaf(H[4], gbar.y, H[5] * gbar.z)));
+  } else {
+    body_sdf_bwd(b, y, s.f, tau, inv_tau, phibar, gbar, ybar, dbar);
+  }
+}
+
 // Adds a local-frame adjoint to a pre-selected item's export slot (shared memory).
 CM_HD void export3(float* dst, V3 v) {
   if (dst) {
@@ -470,20 +539,22 @@ CM_HD void vs_bwd(const Frame& F, const Body& A, const Body& B, float4 vL, V3 vB
                   Adj& adj, float* vexp = nullptr) {
   const float tau = F.tau, it = F.inv_tau;
   if (kOfA) {
-    Sdf f = body_sdf(B, vB, tau, it);
+    const Sdf1H fh = body_sdf_h(B, vB, tau, it);
+    const Sdf& f = fh.f;
     float w = sigmoid(-f.phi * it);
     float wb = yb[7] - sb * f.phi;
     float phib = yb[3] - sb * w - wb * sigmoid_grad_from(w) * it;
     V3 gb = normal_bwd(f.g, tau, v3(yb[4], yb[5], yb[6]));
     V3 pb = v3(yb[0], yb[1], yb[2]);
-    body_sdf_bwd(B, vB, f, tau, it, phib, gb, pb, adj.dB);
+    body_sdf_h_bwd(B, vB, fh, tau, it, phib, gb, pb, adj.dB);
     V3 vl = v3(vL.x, vL.y, vL.z);
     V3 vbar = push_point_bwd(F, vl, pb, adj);
     map_vertex_bwd(A.kind, vl, vL.w, A.dims, vbar, adj.dA);
     export3(vexp, vbar);
   } else {
     V3 x = mulT(F.R, vB - F.t);
-    Sdf f = body_sdf(A, x, tau, it);
+    const Sdf1H fh = body_sdf_h(A, x, tau, it);
+    const Sdf& f = fh.f;
     float w = sigmoid(-f.phi * it);
     float wb = yb[7] - sb * f.phi;
     float phib = yb[3] - sb * w - wb * sigmoid_grad_from(w) * it;
@@ -492,7 +563,7 @@ CM_HD void vs_bwd(const Frame& F, const Body& A, const Body& B, float4 vL, V3 vB
     add_outer(adj.R, nub, nuL);
     V3 gb = normal_bwd(f.g, tau, mulT(F.R, nub));
     V3 xb = v3(0.f, 0.f, 0.f);
-    body_sdf_bwd(A, x, f, tau, it, phib, gb, xb, adj.dA);
+    body_sdf_h_bwd(A, x, fh, tau, it, phib, gb, xb, adj.dA);
     V3 pb = v3(yb[0], yb[1], yb[2]) + pull_point_bwd(F, vB, xb, adj);
     map_vertex_bwd(B.kind, vB, vL.w, B.dims, pb, adj.dB);
     export3(vexp, pb);
@@ -577,10 +648,15 @@ struct SdfQuad {
   Sdf B1, B2, A2, A1;
 };
 
-template <class Upstream>
+// kHess: the SDFs come from body_sdf2_h and their reverses need no second pass over
+// a polyhedron's planes (sdf is then unused); otherwise they come from `sdf` when
+// given, else from body_sdf2, with the plane-by-plane reverse.  dqp (optional)
+// receives the QP witnesses' distance.
+template <bool kHess = false, class Upstream>
 CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float rowL,
                   float colL, const QPOut* stored, Upstream&& up, float& t1, float& t2, Adj& adj,
-                  const SdfQuad* sdf = nullptr, float* eAexp = nullptr, float* eBexp = nullptr) {
+                  const SdfQuad* sdf = nullptr, float* eAexp = nullptr, float* eBexp = nullptr,
+                  float* dqp = nullptr) {
   const float tau = F.tau, it = F.inv_tau;
   V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
   V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L);
@@ -592,6 +668,7 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
   // nn indicators rank the QP witnesses' distances; sphere tracing (if on) moves
   // the witnesses everything else uses
   const float dbar_qp = sqrt_(dot(e1 - e2, e1 - e2));
+  if (dqp) *dqp = dbar_qp;
   const int nt = p.trace_iters;
   const V3 e1Lq = e1L, e2q = e2;
   if (nt) {
@@ -605,8 +682,16 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
   float qn = rsq(r2 + tau * tau);
   V3 nbar = D * qn;
   Sdf SB1, SB2, SA2, SA1;
+  Sdf2H hB, hA;
   V3 x2 = mulT(F.R, e2 - F.t);
-  if (sdf) {
+  if (kHess) {
+    hB = body_sdf2_h(B, e1, e2, tau, it);
+    hA = body_sdf2_h(A, x2, e1L, tau, it);
+    SB1 = hB.f1;
+    SB2 = hB.f2;
+    SA2 = hA.f1;
+    SA1 = hA.f2;
+  } else if (sdf) {
     SB1 = sdf->B1;
     SB2 = sdf->B2;
     SA2 = sdf->A2;
@@ -670,11 +755,18 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
   V3 e1b = Db + v3(yb1[0], yb1[1], yb1[2]);
   V3 e2b = -Db + v3(yb2[0], yb2[1], yb2[2]);
   // SDF reverses (one pass per body for its two points)
-  body_sdf2_bwd(B, e1, e2, SB1, SB2, tau, it, phibB1, phibB2, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
+  if (kHess)
+    body_sdf2_h_bwd(B, e1, e2, hB, tau, it, phibB1, phibB2, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
+  else
+    body_sdf2_bwd(B, e1, e2, SB1, SB2, tau, it, phibB1, phibB2, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
   V3 x2b = v3(0.f, 0.f, 0.f), e1Lb = v3(0.f, 0.f, 0.f);
   add_outer(adj.R, nuAb, nuAL);
-  body_sdf2_bwd(A, x2, e1L, SA2, SA1, tau, it, phibA2, phibA1, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b,
-                e1Lb, adj.dA);
+  if (kHess)
+    body_sdf2_h_bwd(A, x2, e1L, hA, tau, it, phibA2, phibA1, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b, e1Lb,
+                    adj.dA);
+  else
+    body_sdf2_bwd(A, x2, e1L, SA2, SA1, tau, it, phibA2, phibA1, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b,
+                  e1Lb, adj.dA);
   e2b += pull_point_bwd(F, e2, x2b, adj);
   if (nt) {  // traced e1 = R_rel e1L + t_rel; back through both traces to the QP witnesses
     e1Lb += push_point_bwd(F, e1L, e1b, adj);
@@ -694,19 +786,30 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
 // the total.
 CM_HD void ee_qp_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float Dbar,
                      const QPOut& o, QPBar qb, Adj& adj, float* eAexp = nullptr, float* eBexp = nullptr) {
+  const V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
+  const V3 z = v3(0.f, 0.f, 0.f);
+  V3 a0b = z, a1b = z, b0b = z, b1b = z;  // endpoint adjoints of both parts, reversed to the parameters once
+  bool any = false;
   if (Dbar != 0.f) {
-    const V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
     const V3 D = fma3(o.a1, a1 - a0, a0) - fma3(o.a2, b1 - b0, b0);
     const float r2 = dot(D, D);
-    if (r2 > 0.f) {
+    if (r2 > 0.f) {  // |e1* - e2*| at fixed alpha, and its alpha part
       const V3 Db = D * (Dbar * rsq(r2));
-      float d1, d2;
-      witness_direct_bwd(F, A, B, g, o, Db, v3(0.f, 0.f, 0.f), -Db, adj, d1, d2, eAexp, eBexp);
-      qb.a1 += d1;
-      qb.a2 += d2;
+      a0b = Db * (1.f - o.a1);
+      a1b = Db * o.a1;
+      b0b = Db * (o.a2 - 1.f);
+      b1b = Db * (-o.a2);
+      qb.a1 += dot(Db, a1 - a0);
+      qb.a2 -= dot(Db, b1 - b0);
+      any = true;
     }
   }
-  if (qb.a1 != 0.f || qb.a2 != 0.f || qb.con != 0.f) witness_qp_bwd(F, A, B, p, g, qb, adj, eAexp, eBexp);
+  if (qb.a1 != 0.f || qb.a2 != 0.f || qb.con != 0.f) {
+    const QPPre q = qp_setup(a0, a1, b0, b1, p.w_reg);
+    qp_bwd(q, p.w_reg, p, qb.a1, qb.a2, qb.con, a0b, a1b, b0b, b1b);
+    any = true;
+  }
+  if (any) endpoints_bwd(F, A, B, g, a0b, a1b, z, z, b0b, b1b, adj, eAexp, eBexp);
 }
 
 // ---------------------------------------------------------------- pose epilogue

@@ -83,20 +83,17 @@ __device__ __forceinline__ EEGeom ee_geom(const FwdArgs& a, const PairShared& ps
   return g;
 }
 
-// Per-thread state of the SoftSort reverse: the direct dL/d s^_k of candidates at or
-// above the K-th score, and for those below it E = sum e and Y = sum e y with
-// e = exp((s - r) / tau) (see ss_bwd).
+// Per-thread state of the SoftSort reverse: for the candidates below the K-th score,
+// E = sum e and Y = sum e y with e = exp((s - r) / tau) (see ss_bwd).  The few at or
+// above it add their dL/d s^_k to the CTA's sums directly.
 template <int KMAX>
 struct SsAcc {
-  float shb[KMAX];
   float E;
   float Y[8];
 };
 
 template <int KMAX>
 __device__ __forceinline__ void ss_acc_zero(SsAcc<KMAX>& a) {
-#pragma unroll
-  for (int k = 0; k < KMAX; ++k) a.shb[k] = 0.f;
   a.E = 0.f;
 #pragma unroll
   for (int c = 0; c < 8; ++c) a.Y[c] = 0.f;
@@ -114,9 +111,9 @@ __device__ __forceinline__ void ss_acc_zero(SsAcc<KMAX>& a) {
 // +1 it gives the tied rows' signs (instead of 0) only reaches w's adjoint and the tied
 // rows' s^_k, both of which meet only the underflowed factor's derivative, which is
 // exactly 0.  The K top entries and ties with w != 0 (a measure-zero set) take the
-// K-row loop.
+// K-row loop, which adds their s^_k terms to bs.shatbar at once.
 template <int KMAX>
-__device__ __forceinline__ void ss_bwd(const BwdShared& bs, int K, float it, float k2, const float (&y)[8], float s,
+__device__ __forceinline__ void ss_bwd(BwdShared& bs, int K, float it, float k2, const float (&y)[8], float s,
                                        float (&yb)[8], float& sb, SsAcc<KMAX>& acc) {
   if (s < bs.r || (s == bs.r && y[7] == 0.f)) {
     const float e = ex2((s - bs.r) * k2);
@@ -153,7 +150,7 @@ __device__ __forceinline__ void ss_bwd(const BwdShared& bs, int K, float it, flo
       const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
       const float term = gam * (a2.x + a2.y) * sg * it;
       sb += term;
-      acc.shb[k] -= term;
+      if (term != 0.f) atomicAdd(&bs.shatbar[k], -term);
     }
   }
 #pragma unroll
@@ -216,7 +213,7 @@ __device__ __forceinline__ void ss_finish(SsAcc<KMAX>& acc, int K, float it, Bwd
       float d = -bs.Gout[k] * acc.E;
 #pragma unroll
       for (int c = 0; c < 8; ++c) d = fmaf(bs.G[k][c], acc.Y[c], d);
-      const float v = warp_sum(acc.shb[k] - bs.c[k] * d * it);
+      const float v = warp_sum(-bs.c[k] * d * it);
       if ((threadIdx.x & 31) == 0) atomicAdd(&bs.shatbar[k], v);
     }
   }
@@ -261,7 +258,7 @@ static __device__ __forceinline__ void fixup_phase(const BwdPair P) {
     const int e = id - P.nvs, i = e >> 1, b = e & 1, kk = i / P.neB, ll = i - kk * P.neB;
     float t1, t2;
     const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
-    const QPBar qb = ee_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, ps, P.sm, kk, ll), P.sm.rowL[kk], P.sm.colL[ll], &qs,
+    const QPBar qb = ee_bwd<true>(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, ps, P.sm, kk, ll), P.sm.rowL[kk], P.sm.colL[ll], &qs,
            [&](const EECand&, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
              for (int c = 0; c < 8; ++c) {
                yb1[c] = 0.f;
@@ -422,13 +419,14 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
   float* colC = sm.colL + a.sm.max_e;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int K = a.p.K;
-  float* Dm = a.scratch + (int64_t)blockIdx.x * a.scratch_stride * 16;
-  float* T1 = Dm + a.scratch_stride;
-  float* T2 = T1 + a.scratch_stride;
-  float* QA1 = T2 + a.scratch_stride;  // alpha1, alpha2, con of every edge pair
-  float* QA2 = QA1 + a.scratch_stride;
-  float* QCN = QA2 + a.scratch_stride;
-  float* SDF = QCN + a.scratch_stride;  // 10 arrays: the element's four SDF evaluations
+  const int64_t ss = a.scratch_stride;
+  float* Dm = a.scratch + (int64_t)blockIdx.x * ss * kBwdScratchArrays;
+  float* T1 = Dm + ss;
+  float* T2 = T1 + ss;
+  float* QA1 = T2 + ss;  // alpha1, alpha2, con of every edge pair
+  float* QA2 = QA1 + ss;
+  float* QCN = QA2 + ss;
+  float* QB = QCN + ss;  // their adjoints (3 arrays)
   int iter = 0;
   for (;;) {
     const int pi = next_pair(a, iter);
@@ -463,72 +461,98 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     const bool no_ee = one_sided || (a.p.flags & 1) != 0;
     const int nvs = one_sided ? ps.nvA : ps.nvA + ps.nvB;
     const int neA = ps.neA, neB = ps.neB, nee = no_ee ? 0 : neA * neB;
+    // the forward's record of this pair (cm_fwd_kernel with a record buffer), if any
+    const float* rec = a.saved ? a.saved + (size_t)pi * a.saved_stride : nullptr;
 
-    // ================= forward recompute
-    WarpTopK st;
-    wtk_init(st, sm.warp + warp * kWarpStateFloats);
-    float y[8], y2[8];
-    for (int base = warp * 32; base < nvs; base += nwarps * 32) {
-      const int c = base + lane;
-      const bool valid = c < nvs;
-      float s = 0.f;
-      if (valid) s = vs_candidate(ps, sm, bb, c, y);
-      wtk_push(st, valid, s, y, K, k2, c);
-    }
-    if (nee) {
-      for (int i = threadIdx.x; i < nee; i += blockDim.x) {
-        const int k = i / neB, l = i - k * neB;
-        const Witness w = ee_witness(edge_pair(sm, k, l), a.p);
-        Dm[i] = w.dbar;
-        QA1[i] = w.qp.a1;
-        QA2[i] = w.qp.a2;
-        QCN[i] = w.qp.con;
-      }
-      __syncthreads();
-      for (int k = warp; k < neA; k += nwarps) {
-        float m = 3.0e38f;
-        for (int l = lane; l < neB; l += 32) m = fminf(m, Dm[k * neB + l]);
-        m = warp_min(m);
-        float S = 0.f;
-        for (int l = lane; l < neB; l += 32) S += ex2((m - Dm[k * neB + l]) * k2);
-        S = warp_sum(S);
-        if (lane == 0) {
-          sm.rowL[k] = m - ps.tau * kLn2 * lg2(S);
+    // ================= the forward's top-K list and nearest-neighbour statistics
+    float y[8], Z = 1.f, ls = -3.0e38f;
+    int lid = -1;
+    if (rec) {
+      if (nee) {
+        for (int k = threadIdx.x; k < neA; k += blockDim.x) {
+          sm.rowL[k] = rec[kRecHead * K + k];
           rowR[k] = 0.f;
         }
-      }
-      for (int l = threadIdx.x; l < neB; l += blockDim.x) {
-        float m = 3.0e38f;
-        for (int k = 0; k < neA; ++k) m = fminf(m, Dm[k * neB + l]);
-        float S = 0.f;
-        for (int k = 0; k < neA; ++k) S += ex2((m - Dm[k * neB + l]) * k2);
-        sm.colL[l] = m - ps.tau * kLn2 * lg2(S);
-        colC[l] = 0.f;
-      }
-      __syncthreads();
-      for (int base = warp * 32; base < nee; base += nwarps * 32) {
-        const int i = base + lane;
-        const bool valid = i < nee;
-        float s1 = 0.f, s2 = 0.f;
-        if (valid) {
-          const int k = i / neB, l = i - k * neB;
-          const EdgePair ep = edge_pair(sm, k, l);
-          const Witness w = ee_witness_from(ep, QPOut{QA1[i], QA2[i], QCN[i]});
-          ee_candidates(ps, sm, bb, ep, w, sm.rowL[k], sm.colL[l], y, y2, s1, s2, SDF, a.scratch_stride, i);
+        for (int l = threadIdx.x; l < neB; l += blockDim.x) {
+          sm.colL[l] = rec[kRecHead * K + a.sm.max_e + l];
+          colC[l] = 0.f;
         }
-        wtk_push(st, valid, s1, y, K, k2, nvs + 2 * i);
-        wtk_push(st, valid, s2, y2, K, k2, nvs + 2 * i + 1);
       }
-    }
-    // merge the warps' states pairwise (log2(nwarps) levels)
-    for (int h = 1; h < nwarps; h <<= 1) {
-      if ((warp & (2 * h - 1)) == h) wtk_store(st, K);
-      __syncthreads();
-      if ((warp & (2 * h - 1)) == 0 && warp + h < nwarps) wtk_merge(st, sm.warp + (warp + h) * kWarpStateFloats, K, k2);
+      if (warp == 0 && lane < K) {
+        ls = rec[lane];
+        lid = __float_as_int(rec[K + lane]);
+        Z = rec[2 * K + lane];
+        for (int c = 0; c < 8; ++c) y[c] = rec[3 * K + 8 * lane + c];
+      }
+    } else {  // recompute the pair's forward
+      WarpTopK st;
+      wtk_init(st, sm.warp + warp * kWarpStateFloats);
+      float y2[8];
+      for (int base = warp * 32; base < nvs; base += nwarps * 32) {
+        const int c = base + lane;
+        const bool valid = c < nvs;
+        float s = 0.f;
+        if (valid) s = vs_candidate(ps, sm, bb, c, y);
+        wtk_push(st, valid, s, y, K, k2, c);
+      }
+      if (nee) {
+        for (int i = threadIdx.x; i < nee; i += blockDim.x) {
+          const int k = i / neB, l = i - k * neB;
+          const Witness w = ee_witness(edge_pair(sm, k, l), a.p);
+          Dm[i] = w.dbar;
+          QA1[i] = w.qp.a1;
+          QA2[i] = w.qp.a2;
+          QCN[i] = w.qp.con;
+        }
+        __syncthreads();
+        for (int k = warp; k < neA; k += nwarps) {
+          float m = 3.0e38f;
+          for (int l = lane; l < neB; l += 32) m = fminf(m, Dm[k * neB + l]);
+          m = warp_min(m);
+          float S = 0.f;
+          for (int l = lane; l < neB; l += 32) S += ex2((m - Dm[k * neB + l]) * k2);
+          S = warp_sum(S);
+          if (lane == 0) {
+            sm.rowL[k] = m - ps.tau * kLn2 * lg2(S);
+            rowR[k] = 0.f;
+          }
+        }
+        for (int l = threadIdx.x; l < neB; l += blockDim.x) {
+          float m = 3.0e38f;
+          for (int k = 0; k < neA; ++k) m = fminf(m, Dm[k * neB + l]);
+          float S = 0.f;
+          for (int k = 0; k < neA; ++k) S += ex2((m - Dm[k * neB + l]) * k2);
+          sm.colL[l] = m - ps.tau * kLn2 * lg2(S);
+          colC[l] = 0.f;
+        }
+        __syncthreads();
+        for (int base = warp * 32; base < nee; base += nwarps * 32) {
+          const int i = base + lane;
+          const bool valid = i < nee;
+          float s1 = 0.f, s2 = 0.f;
+          if (valid) {
+            const int k = i / neB, l = i - k * neB;
+            const EdgePair ep = edge_pair(sm, k, l);
+            const Witness w = ee_witness_from(ep, QPOut{QA1[i], QA2[i], QCN[i]});
+            ee_candidates(ps, sm, bb, ep, w, sm.rowL[k], sm.colL[l], y, y2, s1, s2);
+          }
+          wtk_push(st, valid, s1, y, K, k2, nvs + 2 * i);
+          wtk_push(st, valid, s2, y2, K, k2, nvs + 2 * i + 1);
+        }
+      }
+      // merge the warps' states pairwise (log2(nwarps) levels)
+      for (int h = 1; h < nwarps; h <<= 1) {
+        if ((warp & (2 * h - 1)) == h) wtk_store(st, K);
+        __syncthreads();
+        if ((warp & (2 * h - 1)) == 0 && warp + h < nwarps) wtk_merge(st, sm.warp + (warp + h) * kWarpStateFloats, K, k2);
+      }
+      if (warp == 0) {
+        wtk_finish(st, K, k2, y, &Z);
+        ls = st.ls;
+        lid = st.lid;
+      }
     }
     if (warp == 0) {
-      float Z = 1.f;
-      wtk_finish(st, K, k2, y, &Z);
       // upstream of row k in B's frame and the output-rotation adjoints
       float Rl[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       V3 tl = v3(0.f, 0.f, 0.f);
@@ -544,16 +568,16 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
         }
         bs.Gout[lane] = go;
         bs.invZ[lane] = 1.0f / Z;
-        bs.shat[lane] = st.ls;
-        bs.sid[lane] = st.lid;
+        bs.shat[lane] = ls;
+        bs.sid[lane] = lid;
         bs.shatbar[lane] = 0.f;
         add_outer(Rl, gp, v3(y[0], y[1], y[2]));
         add_outer(Rl, gn, v3(y[4], y[5], y[6]));
         tl = gp;
       }
       // constants of the factorised SoftSort reverse below the K-th score r
-      const float r = __shfl_sync(kFull, st.ls, K - 1);
-      const float ck = lane < K ? ex2((r - st.ls) * k2) * (1.0f / Z) : 0.f;
+      const float r = __shfl_sync(kFull, ls, K - 1);
+      const float ck = lane < K ? ex2((r - ls) * k2) * (1.0f / Z) : 0.f;
       float gcs = 0.f;
       for (int c = 0; c < 8; ++c) {
         const float v = warp_sum(lane < K ? ck * bs.G[lane][c] : 0.f);
@@ -585,8 +609,8 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     P.F = F;
     P.bb = bb;
     P.Dm = Dm; P.T1 = T1; P.T2 = T2; P.QA1 = QA1; P.QA2 = QA2; P.QCN = QCN; P.rowR = rowR; P.colC = colC;
-    P.QB = SDF;
-    P.qbs = a.scratch_stride;
+    P.QB = QB;
+    P.qbs = ss;
     P.nvs = nvs; P.neB = neB; P.nee = nee; P.K = K;
     P.sadj = sadj;
     vs_reverse_phase<KMAX>(P);
@@ -597,32 +621,41 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
       ss_acc_zero(acc);
       for (int i = threadIdx.x; i < nee; i += blockDim.x) {
         const int k = i / neB, l = i - k * neB;
-        const int64_t st = a.scratch_stride;
+        const EEGeom gg = ee_geom(a, ps, sm, k, l);
+        QPOut qs;
+        if (rec) {  // the QP result and the distance matrix for the last pass
+          qs = qp_solve(qp_setup(xyz(gg.a0), xyz(gg.a1), xyz(gg.b0), xyz(gg.b1), a.p.w_reg), a.p.w_reg, a.p);
+          QA1[i] = qs.a1;
+          QA2[i] = qs.a2;
+          QCN[i] = qs.con;
+        } else {
+          qs = QPOut{QA1[i], QA2[i], QCN[i]};
+        }
         float t1, t2;
-        const QPOut qs{QA1[i], QA2[i], QCN[i]};
-        const float* q = SDF + i;
-        SdfQuad sq;
-        sq.B1.phi = q[0];
-        sq.B1.g = v3(0.f, 0.f, 0.f);
-        sq.B2.phi = q[st];
-        sq.B2.g = v3(q[2 * st], q[3 * st], q[4 * st]);
-        sq.A2.phi = q[5 * st];
-        sq.A2.g = v3(0.f, 0.f, 0.f);
-        sq.A1.phi = q[6 * st];
-        sq.A1.g = v3(q[7 * st], q[8 * st], q[9 * st]);
-        const QPBar qb = ee_bwd(F, bb.A, bb.B, a.p, ee_geom(a, ps, sm, k, l), sm.rowL[k], sm.colL[l], &qs,
+        const QPBar qb = ee_bwd<true>(F, bb.A, bb.B, a.p, gg, sm.rowL[k], sm.colL[l], &qs,
                [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
-                 ss_bwd<KMAX>(bs, K, it, k2, cc.y1, cc.s1, yb1, sb1, acc);
-                 ss_bwd<KMAX>(bs, K, it, k2, cc.y2, cc.s2, yb2, sb2, acc);
+                 // both candidates through one copy of the SoftSort reverse
+#pragma unroll 1
+                 for (int j = 0; j < 2; ++j) {
+                   float yc[8], yb[8], sb;
+#pragma unroll
+                   for (int c = 0; c < 8; ++c) yc[c] = j ? cc.y2[c] : cc.y1[c];
+                   ss_bwd<KMAX>(bs, K, it, k2, yc, j ? cc.s2 : cc.s1, yb, sb, acc);
+#pragma unroll
+                   for (int c = 0; c < 8; ++c) {
+                     if (j) yb2[c] = yb[c];
+                     else yb1[c] = yb[c];
+                   }
+                   if (j) sb2 = sb;
+                   else sb1 = sb;
+                 }
                },
-               t1, t2, adj, &sq, eAexp_of(P, k), eBexp_of(P, l));
+               t1, t2, adj, nullptr, eAexp_of(P, k), eBexp_of(P, l), rec ? Dm + i : nullptr);
         T1[i] = t1;
         T2[i] = t2;
-        // the element's SDF values are read above: its first three slots now keep the
-        // QP adjoints for the last pass
-        SDF[i] = qb.a1;
-        SDF[st + i] = qb.a2;
-        SDF[2 * st + i] = qb.con;
+        QB[i] = qb.a1;
+        QB[ss + i] = qb.a2;
+        QB[2 * ss + i] = qb.con;
         atomicAdd(&rowR[k], t1);
         atomicAdd(&colC[l], t2);
       }

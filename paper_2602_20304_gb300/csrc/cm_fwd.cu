@@ -16,6 +16,9 @@
 //      sign, pen, nn, cl and activity -> two candidates per edge pair, streamed
 //      into the warp state;
 //   6. merge the warps' states pairwise and write the K rows, rotated back to world.
+// With a record buffer the pair's selected list, its normalisers and rows and the
+// soft row / column minima are also written for the adjoint (cm_bwd_kernel), which
+// then needs no recompute of the forward's reductions.
 #include "cm_pair.cuh"
 
 namespace cm {
@@ -106,6 +109,11 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
       __syncthreads();
       for (int l = threadIdx.x; l < neB; l += blockDim.x) sm.colL[l] -= ps.tau * kLn2 * lg2(colS[l]);
       __syncthreads();
+      if (a.saved && pi >= a.saved_first) {  // the soft minima go to the pair's record for the adjoint
+        float* rec = a.saved + (size_t)(pi - a.saved_first) * a.saved_stride + kRecHead * K;
+        for (int k = threadIdx.x; k < neA; k += blockDim.x) rec[k] = sm.rowL[k];
+        for (int l = threadIdx.x; l < neB; l += blockDim.x) rec[a.sm.max_e + l] = sm.colL[l];
+      }
       // ---- E-E pass 2: candidates
       for (int base = warp * 32; base < nee; base += nwarps * 32) {
         const int i = base + lane;
@@ -138,7 +146,15 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
       if ((warp & (2 * h - 1)) == 0 && warp + h < nwarps) wtk_merge(st, sm.warp + (warp + h) * kWarpStateFloats, K, k2);
     }
     if (warp == 0) {
-      wtk_finish(st, K, k2, y);
+      float Z = 1.f;
+      wtk_finish(st, K, k2, y, &Z);
+      if (a.saved && pi >= a.saved_first && lane < K) {  // the selected list and its rows (B's frame)
+        float* rec = a.saved + (size_t)(pi - a.saved_first) * a.saved_stride;
+        rec[lane] = st.ls;
+        rec[K + lane] = __int_as_float(st.lid);
+        rec[2 * K + lane] = Z;
+        for (int c = 0; c < 8; ++c) rec[3 * K + 8 * lane + c] = y[c];
+      }
       if (lane < K) {
         V3 p = mul(ps.RB, v3(y[0], y[1], y[2])) + ps.tB;
         V3 n = mul(ps.RB, v3(y[4], y[5], y[6]));

@@ -47,7 +47,21 @@ struct FwdArgs {
   int32_t* work_counter;     // persistent-CTA work queue (may be null: static striding)
   int32_t store_alpha;       // pass 1 keeps (alpha1, alpha2, con) beside dbar: 4 scratch floats per edge pair
   const int32_t* order;      // optional pair order for the work queue (may be null)
+  // Per-pair forward record (may be null): written by the forward, read by the
+  // adjoint, saved_stride floats per pair (see kRecHead).
+  float* saved;
+  int64_t saved_stride;
+  int32_t saved_first;  // the forward writes records of pairs >= saved_first, from record 0
 };
+
+// Forward record of one pair, as the adjoint reads it: the K selected scores s^_k,
+// their candidate ids (int bits), the SoftSort normalisers Z_k and the K output rows
+// in B's frame (8 floats each) -- kRecHead * K floats -- then the soft row minima of
+// the E-E distance matrix (max_e slots) and its soft column minima (max_e slots).
+constexpr int kRecHead = 11;
+// Adjoint scratch per edge pair: the distance, t1, t2, the QP result (3) and its
+// adjoints (3), as arrays of scratch_stride floats in each CTA's slice.
+constexpr int kBwdScratchArrays = 9;
 
 // Launch shape of a manifold kernel: threads per CTA, CTAs per SM (0 = as many
 // as fit) and whether pairs are pulled from the size-ordered work list.
@@ -84,6 +98,6 @@ cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_pose
                        int block, int per_sm, cudaStream_t s);
 int bwd_max_blocks_per_sm(int block, int smem_bytes, int per_sm);
 cudaError_t launch_order(const int32_t* pair_geoms, const GeomHeader* hdr, int n_geoms, int n, int32_t* order,
-                         int32_t* counter, cudaStream_t s);
+                         int32_t* counter, int by_kind, cudaStream_t s);
 
 }  // namespace cm

@@ -293,6 +293,125 @@ CM_HD void sdf_planes2(V3 y1, V3 y2, const float4* P, int nP, float tau, Sdf& o1
   o2.g = G * (t * rcp(S.y));
 }
 
+// The same LSE at two points with what its reverse needs, so that the adjoint
+// makes one pass over the planes instead of two: value and gradient at y1, and
+// value, gradient and Hessian at y2.  With pi_f = softmax_f(s_f / tau) the
+// gradient is g = sum_f pi_f n_f and the Hessian H = (sum_f pi_f n_f n_f^T - g g^T) / tau,
+// so the plane-by-plane reverse sum_f pi_f (phibar + gbar . (n_f - g) / tau) n_f
+// equals phibar g + H gbar.  In the pre-scaled planes (k n, k o), k = log2(e) / tau,
+// with S = sum e_f, G = sum e_f (k n_f), Mq = sum e_f (k n_f)(k n_f)^T:
+// g = (tau ln2) G / S and H = tau ln2^2 (Mq / S - (G / S)(G / S)^T).  H is returned
+// as (xx, xy, xz, yy, yz, zz).  Chunks of 4 planes with an online maximum per point.
+CM_HD void sdf_planes2_h(V3 y1, V3 y2, const float4* P, int nP, float tau, Sdf& o1, Sdf& o2, float (&H)[6]) {
+  const float2 X = make_float2(y1.x, y2.x), Y = make_float2(y1.y, y2.y), Z = make_float2(y1.z, y2.z);
+  float2 m = dup2(-3.0e38f), S = dup2(0.f);
+  float2 Gx = dup2(0.f), Gy = dup2(0.f), Gz = dup2(0.f);  // (point 1, point 2)
+  float2 Mxx_yy = dup2(0.f), Mxy_yz = dup2(0.f), Mxz_zz = dup2(0.f);
+  for (int f0 = 0; f0 < nP; f0 += 4) {
+    float2 z[4];
+    float4 q[4];
+    float2 cm = m;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int f = f0 + j;
+      q[j] = f < nP ? P[f] : make_float4(0.f, 0.f, 0.f, 3.0e38f);
+      z[j] = ffma2(dup2(q[j].x), X, ffma2(dup2(q[j].y), Y, ffma2(dup2(q[j].z), Z, dup2(-q[j].w))));
+      cm.x = fmaxf(cm.x, z[j].x);
+      cm.y = fmaxf(cm.y, z[j].y);
+    }
+    if (cm.x > m.x || cm.y > m.y) {
+      const float2 r = make_float2(ex2(m.x - cm.x), ex2(m.y - cm.y));
+      S = make_float2(S.x * r.x, S.y * r.y);
+      Gx = make_float2(Gx.x * r.x, Gx.y * r.y);
+      Gy = make_float2(Gy.x * r.x, Gy.y * r.y);
+      Gz = make_float2(Gz.x * r.x, Gz.y * r.y);
+      Mxx_yy = make_float2(Mxx_yy.x * r.y, Mxx_yy.y * r.y);
+      Mxy_yz = make_float2(Mxy_yz.x * r.y, Mxy_yz.y * r.y);
+      Mxz_zz = make_float2(Mxz_zz.x * r.y, Mxz_zz.y * r.y);
+      m = cm;
+    }
+    const float2 nm = make_float2(-m.x, -m.y);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 d = fadd2(z[j], nm);
+      const float2 e = make_float2(ex2(d.x), ex2(d.y));
+      S = fadd2(S, e);
+      Gx = ffma2(e, dup2(q[j].x), Gx);
+      Gy = ffma2(e, dup2(q[j].y), Gy);
+      Gz = ffma2(e, dup2(q[j].z), Gz);
+      const float2 txy = make_float2(e.y * q[j].x, e.y * q[j].y);
+      const float tz = e.y * q[j].z;
+      Mxx_yy = ffma2(txy, make_float2(q[j].x, q[j].y), Mxx_yy);
+      Mxy_yz = ffma2(txy, make_float2(q[j].y, q[j].z), Mxy_yz);
+      Mxz_zz = ffma2(make_float2(txy.x, tz), make_float2(q[j].z, q[j].z), Mxz_zz);
+    }
+  }
+  const float t = tau * kLn2;
+  const float i1 = rcp(S.x), i2 = rcp(S.y);
+  o1.phi = t * (m.x + lg2(S.x));
+  o1.g = v3(Gx.x, Gy.x, Gz.x) * (t * i1);
+  o2.phi = t * (m.y + lg2(S.y));
+  const V3 gh = v3(Gx.y * i2, Gy.y * i2, Gz.y * i2);  // G / S at y2, scaled units
+  o2.g = gh * t;
+  const float h = t * kLn2;
+  H[0] = h * fmaf(Mxx_yy.x, i2, -gh.x * gh.x);
+  H[1] = h * fmaf(Mxy_yz.x, i2, -gh.x * gh.y);
+  H[2] = h * fmaf(Mxz_zz.x, i2, -gh.x * gh.z);
+  H[3] = h * fmaf(Mxx_yy.y, i2, -gh.y * gh.y);
+  H[4] = h * fmaf(Mxy_yz.y, i2, -gh.y * gh.z);
+  H[5] = h * fmaf(Mxz_zz.y, i2, -gh.z * gh.z);
+}
+
+// One point of sdf_planes2_h: value, gradient and Hessian (xx, xy, xz, yy, yz, zz).
+CM_HD void sdf_planes_h(V3 y, const float4* P, int nP, float tau, Sdf& o, float (&H)[6]) {
+  float m = -3.0e38f, S = 0.f;
+  V3 G = v3(0.f, 0.f, 0.f);
+  float M[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int f0 = 0; f0 < nP; f0 += 4) {
+    float z[4];
+    float4 q[4];
+    float cm = m;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int f = f0 + j;
+      q[j] = f < nP ? P[f] : make_float4(0.f, 0.f, 0.f, 3.0e38f);
+      z[j] = fmaf(q[j].x, y.x, fmaf(q[j].y, y.y, fmaf(q[j].z, y.z, -q[j].w)));
+      cm = fmaxf(cm, z[j]);
+    }
+    if (cm > m) {
+      const float r = ex2(m - cm);
+      S *= r;
+      G = G * r;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) M[c] *= r;
+      m = cm;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float e = ex2(z[j] - m);
+      S += e;
+      const V3 t = v3(e * q[j].x, e * q[j].y, e * q[j].z);
+      G += t;
+      M[0] = fmaf(t.x, q[j].x, M[0]);
+      M[1] = fmaf(t.x, q[j].y, M[1]);
+      M[2] = fmaf(t.x, q[j].z, M[2]);
+      M[3] = fmaf(t.y, q[j].y, M[3]);
+      M[4] = fmaf(t.y, q[j].z, M[4]);
+      M[5] = fmaf(t.z, q[j].z, M[5]);
+    }
+  }
+  const float t = tau * kLn2, iS = rcp(S), h = t * kLn2;
+  const V3 gh = G * iS;
+  o.phi = t * (m + lg2(S));
+  o.g = gh * t;
+  H[0] = h * fmaf(M[0], iS, -gh.x * gh.x);
+  H[1] = h * fmaf(M[1], iS, -gh.x * gh.y);
+  H[2] = h * fmaf(M[2], iS, -gh.x * gh.z);
+  H[3] = h * fmaf(M[3], iS, -gh.y * gh.y);
+  H[4] = h * fmaf(M[4], iS, -gh.y * gh.z);
+  H[5] = h * fmaf(M[5], iS, -gh.z * gh.z);
+}
+
 // What an edge pair's candidates take from a polyhedron's SDF (Sec. IV-D3):
 // sigma(-phi(y1)/tau) at the other body's witness y1 and the gradient at the
 // body's own witness y2 (for its normal), plus sigma(-phi(y2)/tau) for the

@@ -208,10 +208,14 @@ void shape(const cm_context* c, int bwd, const LaunchCfg& cfg, int n_pairs, Smem
 }
 
 // Forward: dbar, alpha1, alpha2, con per edge pair; adjoint: dbar, t1, t2,
-// alpha1, alpha2, con and the ten floats of the element's four SDF evaluations.
+// alpha1, alpha2, con and the adjoints of the last three.
 size_t scratch_need(const cm_context* c, int bwd, int grid, int64_t stride) {
   if (stride <= 0) stride = std::max<int64_t>(1, (int64_t)c->max_e * c->max_e);
-  return (size_t)grid * stride * (bwd ? 16 : 4);
+  return (size_t)grid * stride * (bwd ? kBwdScratchArrays : 4);
+}
+
+int64_t saved_stride_floats(const cm_context* c, int K) {
+  return ((int64_t)kRecHead * K + 2 * (int64_t)c->max_e + 3) & ~(int64_t)3;
 }
 
 // Queues one manifold step (work ordering + forward or adjoint kernel) on `s`
@@ -219,7 +223,8 @@ size_t scratch_need(const cm_context* c, int bwd, int grid, int64_t stride) {
 cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs, const int32_t* pg,
                        const float* poses, const float* dims, const float* tau, const cm_params* params, float* out,
                        const float* grad_out, float* grad_poses, float* grad_dims, float* scratch,
-                       int32_t* order, int32_t* counter, cudaStream_t s, int64_t stride) {
+                       int32_t* order, int32_t* counter, cudaStream_t s, int64_t stride, float* saved,
+                       int64_t saved_stride, int32_t saved_first) {
   FwdArgs a{};
   int grid = 1;
   shape(c, bwd, cfg, n_pairs, a.sm, grid);
@@ -241,9 +246,12 @@ cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32
   a.work_counter = nullptr;
   a.order = nullptr;
   a.store_alpha = bwd ? 0 : 1;
+  a.saved = saved;
+  a.saved_stride = saved_stride;
+  a.saved_first = saved_first;
   cudaError_t e;
   if (cfg.ordered) {
-    if ((e = launch_order(pg, c->d_hdr, a.n_geoms, n_pairs, order, counter, s)) != cudaSuccess)
+    if ((e = launch_order(pg, c->d_hdr, a.n_geoms, n_pairs, order, counter, bwd, s)) != cudaSuccess)
       return cuda_fail(e, "work-order launch");
     a.order = order;
     a.work_counter = counter;
@@ -257,7 +265,8 @@ cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32
 // Context-owned buffers for one call with the chosen shape, then the step.
 cm_status run_step(cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs, const int32_t* pg,
                    const float* poses, const float* dims, const float* tau, const cm_params* params, float* out,
-                   const float* grad_out, float* grad_poses, float* grad_dims, cudaStream_t s) {
+                   const float* grad_out, float* grad_poses, float* grad_dims, cudaStream_t s,
+                   float* saved = nullptr, int64_t saved_stride = 0) {
   SmemLayout L;
   int grid = 1;
   shape(c, bwd, cfg, n_pairs, L, grid);
@@ -265,7 +274,19 @@ cm_status run_step(cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs
   if (st != CM_OK) return st;
   if ((st = ensure_order(c, (size_t)n_pairs)) != CM_OK) return st;
   return enqueue_step(c, bwd, cfg, n_pairs, pg, poses, dims, tau, params, out, grad_out, grad_poses, grad_dims,
-                      c->d_scratch, c->d_order, c->d_counter, s, 0);
+                      c->d_scratch, c->d_order, c->d_counter, s, 0, saved, saved_stride);
+}
+
+// A caller's record buffer: saved_stride floats per pair, at least what the
+// context's largest geometry needs.
+cm_status check_saved(const cm_context* c, const cm_params* params, const float* saved, int64_t saved_stride) {
+  if (!saved) return fail(CM_ERR_INVALID_ARG, "the record buffer is required");
+  if (saved_stride < saved_stride_floats(c, params->K))
+    return fail(CM_ERR_INVALID_ARG,
+                "saved_stride is below cm_saved_stride for these params and the registered geometry (geometry with "
+                "more edges registered since the record was sized?)");
+  if (reinterpret_cast<uintptr_t>(saved) % 4 != 0) return fail(CM_ERR_INVALID_ARG, "saved must be float-aligned");
+  return CM_OK;
 }
 }  // namespace rt
 }  // namespace cm
@@ -499,9 +520,12 @@ cm_status cm_check_device_error(cm_context* c) {
   return CM_OK;
 }
 
-cm_status cm_contact_manifold_fwd(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
-                                  const float* dims, const float* tau, const cm_params* params, float* out,
-                                  void* stream) {
+}  // extern "C"
+
+namespace {
+cm_status fwd_call(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses, const float* dims,
+                   const float* tau, const cm_params* params, float* out, float* saved, int64_t saved_stride,
+                   bool with_record, void* stream) {
   if (!c) return fail(CM_ERR_INVALID_ARG, "NULL context");
   cm_status st = check_params(params);
   if (st != CM_OK) return st;
@@ -511,18 +535,16 @@ cm_status cm_contact_manifold_fwd(cm_context* c, int32_t n_pairs, const int32_t*
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
+  if (with_record && (st = check_saved(c, params, saved, saved_stride)) != CM_OK) return st;
   cudaSetDevice(c->device);
   if ((st = sync_geometry_locked(c)) != CM_OK) return st;
   return run_step(c, 0, pick_cfg(c, 0, n_pairs, params->flags), n_pairs, pair_geoms, poses, dims, tau, params, out,
-                  nullptr, nullptr, nullptr, (cudaStream_t)stream);
+                  nullptr, nullptr, nullptr, (cudaStream_t)stream, saved, saved_stride);
 }
 
-}  // extern "C"
-
-extern "C" cm_status cm_contact_manifold_bwd(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms,
-                                              const float* poses, const float* dims, const float* tau,
-                                              const cm_params* params, const float* grad_out, float* grad_poses,
-                                              float* grad_dims, void* stream) {
+cm_status bwd_call(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses, const float* dims,
+                   const float* tau, const cm_params* params, const float* saved, int64_t saved_stride,
+                   bool with_record, const float* grad_out, float* grad_poses, float* grad_dims, void* stream) {
   if (!c) return fail(CM_ERR_INVALID_ARG, "NULL context");
   cm_status st = check_params(params);
   if (st != CM_OK) return st;
@@ -533,10 +555,54 @@ extern "C" cm_status cm_contact_manifold_bwd(cm_context* c, int32_t n_pairs, con
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
+  if (with_record && (st = check_saved(c, params, saved, saved_stride)) != CM_OK) return st;
   cudaSetDevice(c->device);
   if ((st = sync_geometry_locked(c)) != CM_OK) return st;
   return run_step(c, 1, pick_cfg(c, 1, n_pairs, params->flags), n_pairs, pair_geoms, poses, dims, tau, params,
-                  nullptr, grad_out, grad_poses, grad_dims, (cudaStream_t)stream);
+                  nullptr, grad_out, grad_poses, grad_dims, (cudaStream_t)stream, const_cast<float*>(saved),
+                  saved_stride);
+}
+}  // namespace
+
+extern "C" {
+
+cm_status cm_contact_manifold_fwd(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
+                                  const float* dims, const float* tau, const cm_params* params, float* out,
+                                  void* stream) {
+  return fwd_call(c, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, 0, false, stream);
+}
+
+cm_status cm_saved_stride(const cm_context* c, const cm_params* params, int64_t* floats_per_pair) {
+  if (!c || !floats_per_pair) return fail(CM_ERR_INVALID_ARG, "NULL argument");
+  cm_status st = check_params(params);
+  if (st != CM_OK) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  *floats_per_pair = saved_stride_floats(c, params->K);
+  return CM_OK;
+}
+
+cm_status cm_contact_manifold_fwd_save(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
+                                       const float* dims, const float* tau, const cm_params* params, float* out,
+                                       float* saved, int64_t saved_stride, void* stream) {
+  return fwd_call(c, n_pairs, pair_geoms, poses, dims, tau, params, out, saved, saved_stride, true, stream);
+}
+
+cm_status cm_contact_manifold_bwd_saved(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
+                                        const float* dims, const float* tau, const cm_params* params,
+                                        const float* saved, int64_t saved_stride, const float* grad_out,
+                                        float* grad_poses, float* grad_dims, void* stream) {
+  return bwd_call(c, n_pairs, pair_geoms, poses, dims, tau, params, saved, saved_stride, true, grad_out, grad_poses,
+                  grad_dims, stream);
+}
+
+}  // extern "C"
+
+extern "C" cm_status cm_contact_manifold_bwd(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms,
+                                              const float* poses, const float* dims, const float* tau,
+                                              const cm_params* params, const float* grad_out, float* grad_poses,
+                                              float* grad_dims, void* stream) {
+  return bwd_call(c, n_pairs, pair_geoms, poses, dims, tau, params, nullptr, 0, false, grad_out, grad_poses,
+                  grad_dims, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -660,6 +726,13 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
   cudaSetDevice(c->device);
   if ((st = sync_geometry_locked(c)) != CM_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  // the adjoint is timed as plans and autograd run it: from the forward's records
+  float* saved = nullptr;
+  const int64_t rs = grad_out ? saved_stride_floats(c, params->K) : 0;
+  if (rs) {
+    cudaError_t e = cudaMalloc(&saved, (size_t)n_pairs * rs * sizeof(float));
+    if (e != cudaSuccess) return fail(CM_ERR_OOM, std::string("autotune records: ") + cudaGetErrorString(e));
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -677,7 +750,7 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
           for (int rep = 0; rep < 3; ++rep) {
             if (rep > 0) cudaEventRecord(e0, s);
             st = run_step(c, bwd, g, n_pairs, pair_geoms, poses, dims, tau, params, out, grad_out, grad_poses,
-                          grad_dims, s);
+                          grad_dims, s, saved, rs);
             if (st != CM_OK) break;
             if (rep > 0) {
               cudaEventRecord(e1, s);
@@ -690,6 +763,8 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
           if (st != CM_OK) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
+            cudaStreamSynchronize(s);
+            cudaFree(saved);
             return st;
           }
           if (ms_sum < best_ms) {
@@ -699,10 +774,23 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
         }
     }
     c->tuned[tune_key(bwd, n_pairs, c->max_e, params->flags)] = best;
+    // the forward's records for the adjoint's shapes, from the chosen forward shape
+    if (!bwd && saved) {
+      st = run_step(c, 0, best, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, nullptr, nullptr, s,
+                    saved, rs);
+      if (st != CM_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamSynchronize(s);
+        cudaFree(saved);
+        return st;
+      }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(saved);
   if (e != cudaSuccess) return cuda_fail(e, "autotune");
   return CM_OK;
 }
@@ -733,6 +821,7 @@ struct cm_plan {
   float* scratch = nullptr;
   int32_t* order = nullptr;
   int32_t* counter = nullptr;
+  float* saved = nullptr;  // forward records for the adjoint (forward + backward plans)
 };
 
 extern "C" void cm_plan_destroy(cm_plan* p) {
@@ -743,6 +832,7 @@ extern "C" void cm_plan_destroy(cm_plan* p) {
   cudaFree(p->scratch);
   cudaFree(p->order);
   cudaFree(p->counter);
+  cudaFree(p->saved);
   delete p;
 }
 
@@ -772,10 +862,12 @@ extern "C" cm_status cm_plan_create(cm_context* c, int32_t n_pairs, const int32_
   shape(c, 1, gb, n_pairs, L, grid_b);
   size_t need = scratch_need(c, 0, grid_f, 0);
   if (grad_out) need = std::max(need, scratch_need(c, 1, grid_b, 0));
+  const int64_t rs = grad_out ? saved_stride_floats(c, params->K) : 0;
   cudaError_t e;
   if ((e = cudaMalloc(&p->scratch, need * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&p->order, (size_t)n_pairs * sizeof(int32_t))) != cudaSuccess ||
-      (e = cudaMalloc(&p->counter, sizeof(int32_t))) != cudaSuccess) {
+      (e = cudaMalloc(&p->counter, sizeof(int32_t))) != cudaSuccess ||
+      (rs && (e = cudaMalloc(&p->saved, (size_t)n_pairs * rs * sizeof(float))) != cudaSuccess)) {
     cm_plan_destroy(p);
     return fail(CM_ERR_OOM, std::string("plan buffers: ") + cudaGetErrorString(e));
   }
@@ -785,19 +877,19 @@ extern "C" cm_status cm_plan_create(cm_context* c, int32_t n_pairs, const int32_
   }
   // first launches outside the capture set the kernels' attributes
   st = enqueue_step(c, 0, gf, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, nullptr, nullptr,
-                    p->scratch, p->order, p->counter, p->cap, 0);
+                    p->scratch, p->order, p->counter, p->cap, 0, p->saved, rs);
   if (st == CM_OK && grad_out)
     st = enqueue_step(c, 1, gb, n_pairs, pair_geoms, poses, dims, tau, params, nullptr, grad_out, grad_poses,
-                      grad_dims, p->scratch, p->order, p->counter, p->cap, 0);
+                      grad_dims, p->scratch, p->order, p->counter, p->cap, 0, p->saved, rs);
   if (st == CM_OK && (e = cudaStreamSynchronize(p->cap)) != cudaSuccess) st = cuda_fail(e, "plan warm-up");
   if (st == CM_OK && (e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     st = cuda_fail(e, "begin capture");
   if (st == CM_OK) {
     cm_status s1 = enqueue_step(c, 0, gf, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, nullptr,
-                                nullptr, p->scratch, p->order, p->counter, p->cap, 0);
+                                nullptr, p->scratch, p->order, p->counter, p->cap, 0, p->saved, rs);
     if (s1 == CM_OK && grad_out)
       s1 = enqueue_step(c, 1, gb, n_pairs, pair_geoms, poses, dims, tau, params, nullptr, grad_out, grad_poses,
-                        grad_dims, p->scratch, p->order, p->counter, p->cap, 0);
+                        grad_dims, p->scratch, p->order, p->counter, p->cap, 0, p->saved, rs);
     e = cudaStreamEndCapture(p->cap, &p->graph);
     if (s1 != CM_OK) st = s1;
     else if (e != cudaSuccess) st = cuda_fail(e, "end capture");

@@ -49,13 +49,16 @@ struct Batch {
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Device bytes of one batch's block, exactly as Server::issue carves it: n pairs
-// of which nb with the adjoint, `grid` scratch slices of max_ee edge pairs (16
-// floats each with an adjoint in the batch, else 4), the work list and its counter.
-size_t batch_layout_bytes(size_t n, size_t nb, int K, size_t grid, int64_t max_ee) {
+// of which nb with the adjoint, `grid` scratch slices of max_ee edge pairs (the
+// adjoint's kBwdScratchArrays floats each with an adjoint in the batch, else 4),
+// the forward's records of the nb adjoint pairs (rec_floats each), the work list
+// and its counter.
+size_t batch_layout_bytes(size_t n, size_t nb, int K, size_t grid, int64_t max_ee, int64_t rec_floats) {
   const size_t nb1 = std::max<size_t>(nb, 1);
   return round256(8 * n) + round256(56 * n) + round256(24 * n) + round256(4 * n) + round256(32 * K * n) +
          round256(32 * K * nb1) + round256(56 * nb1) + round256(24 * nb1) +
-         round256(grid * (size_t)max_ee * (nb ? 16 : 4) * sizeof(float)) + round256(4 * n) + round256(4);
+         round256(grid * (size_t)max_ee * (nb ? kBwdScratchArrays : 4) * sizeof(float)) +
+         round256(nb * (size_t)rec_floats * sizeof(float)) + round256(4 * n) + round256(4);
 }
 }  // namespace
 
@@ -101,7 +104,8 @@ struct Server {
   // largest E_A x E_B is max_ee (a launch never has more CTAs than pairs).
   size_t batch_bytes(int pairs, int bwd_pairs, int64_t max_ee) const {
     const size_t grid = (size_t)std::min(grid_max, std::max(pairs, 1));
-    return batch_layout_bytes((size_t)std::max(pairs, 1), (size_t)bwd_pairs, params.K, grid, max_ee);
+    return batch_layout_bytes((size_t)std::max(pairs, 1), (size_t)bwd_pairs, params.K, grid, max_ee,
+                              saved_stride_floats(ctx, params.K));
   }
 
   // Runs in the scheduler thread with `mu` held on entry and exit.
@@ -222,7 +226,9 @@ struct Server {
     float* gp = (float*)take(56 * std::max<size_t>(nb, 1));
     float* gd = (float*)take(24 * std::max<size_t>(nb, 1));
     const size_t grid = (size_t)std::min(grid_max, (int)std::max<size_t>(n, 1));
-    float* scratch = (float*)take(grid * (size_t)b->max_ee * (nb ? 16 : 4) * sizeof(float));
+    float* scratch = (float*)take(grid * (size_t)b->max_ee * (nb ? kBwdScratchArrays : 4) * sizeof(float));
+    const int64_t rs = saved_stride_floats(ctx, K);
+    float* saved = (float*)take(nb * (size_t)rs * sizeof(float));
     int32_t* order = (int32_t*)take(4 * n);
     int32_t* counter = (int32_t*)take(4);
     if ((size_t)(p - static_cast<char*>(b->mem)) > b->bytes)  // the admission size and the carve disagree
@@ -250,18 +256,20 @@ struct Server {
     {
       std::lock_guard<std::mutex> lk(ctx->mu);
       if ((st = sync_geometry_locked(ctx)) != CM_OK) return st;
+      if (nb && saved_stride_floats(ctx, K) > rs)  // geometry with more edges registered since the block was sized
+        return fail(CM_ERR_INVALID_ARG, "geometry changed while the batch was formed: its records no longer fit");
       const bool has_dims = b->reqs.front()->d.dims != nullptr, has_tau = b->reqs.front()->d.tau != nullptr;
       const float* dptr = has_dims ? dims : nullptr;
       const float* tptr = has_tau ? tau : nullptr;
       LaunchCfg gf = pick_cfg(ctx, 0, (int)n, params.flags);
+      const size_t t0 = n - nb;  // the adjoint requests: a contiguous tail, recorded by the forward
       st = enqueue_step(ctx, 0, gf, (int)n, pg, poses, dptr, tptr, &params, out, nullptr, nullptr, nullptr, scratch,
-                        order, counter, s, b->max_ee);
+                        order, counter, s, b->max_ee, nb ? saved : nullptr, rs, (int32_t)t0);
       if (st == CM_OK && nb) {
-        const size_t t0 = n - nb;
         LaunchCfg gb = pick_cfg(ctx, 1, (int)nb, params.flags);
         st = enqueue_step(ctx, 1, gb, (int)nb, pg + 2 * t0, poses + 14 * t0, has_dims ? dims + 6 * t0 : nullptr,
                           has_tau ? tau + t0 : nullptr, &params, nullptr, gout, gp, gd, scratch, order, counter, s,
-                          b->max_ee);
+                          b->max_ee, saved, rs);
       }
     }
     if (st != CM_OK) return st;

@@ -55,13 +55,29 @@ class Engine:
         api.cm_contact_manifold_fwd(self.ctx, pair_geoms, poses, dims, tau, params, out, stream)
         return out
 
-    def backward(self, pair_geoms, poses, dims, tau, grad_out, params=None, stream=None):
-        """(dL/d poses, dL/d dims or None) for upstream ``grad_out`` (n, K, 8)."""
+    def forward_save(self, pair_geoms, poses, dims=None, tau=None, params=None, stream=None):
+        """(out, saved): the forward manifold and each pair's record for ``backward``."""
+        params = params or self.params()
+        n = int(pair_geoms.shape[0])
+        out = torch.empty((n, params.K, 8), dtype=torch.float32, device=pair_geoms.device)
+        saved = torch.empty((n, api.cm_saved_stride(self.ctx, params)), dtype=torch.float32,
+                            device=pair_geoms.device)
+        api.cm_contact_manifold_fwd_save(self.ctx, pair_geoms, poses, dims, tau, params, out, saved, stream)
+        return out, saved
+
+    def backward(self, pair_geoms, poses, dims, tau, grad_out, params=None, stream=None, saved=None):
+        """(dL/d poses, dL/d dims or None) for upstream ``grad_out`` (n, K, 8); from the
+        forward's records when ``saved`` (see ``forward_save``) is given, else recomputing
+        the forward."""
         params = params or self.params()
         gp = torch.empty_like(poses)
         gd = None if dims is None else torch.empty_like(dims)
-        api.cm_contact_manifold_bwd(self.ctx, pair_geoms, poses, dims, tau, params,
-                                    grad_out.contiguous(), gp, gd, stream)
+        if saved is None:
+            api.cm_contact_manifold_bwd(self.ctx, pair_geoms, poses, dims, tau, params,
+                                        grad_out.contiguous(), gp, gd, stream)
+        else:
+            api.cm_contact_manifold_bwd_saved(self.ctx, pair_geoms, poses, dims, tau, params, saved,
+                                              grad_out.contiguous(), gp, gd, stream)
         return gp, gd
 
     def check(self):
@@ -70,24 +86,25 @@ class Engine:
 
 class ContactManifold(torch.autograd.Function):
     """out = manifold(poses, dims); differentiable in poses and dims through the
-    library's adjoint kernel (the backward recomputes the forward per pair)."""
+    library's adjoint kernel (the forward keeps each pair's per-pair reductions, the
+    backward recomputes every candidate from them)."""
 
     @staticmethod
     def forward(ctx, poses, dims, engine, pair_geoms, tau, params):
-        out = engine.forward(pair_geoms, poses.detach().contiguous(),
-                             None if dims is None else dims.detach().contiguous(), tau, params)
+        out, saved = engine.forward_save(pair_geoms, poses.detach().contiguous(),
+                                         None if dims is None else dims.detach().contiguous(), tau, params)
         ctx.engine, ctx.params = engine, params
         ctx.has_dims = dims is not None
         ctx.save_for_backward(poses.detach(), dims.detach() if dims is not None else poses.new_empty(0),
-                              pair_geoms, tau if tau is not None else poses.new_empty(0))
+                              pair_geoms, tau if tau is not None else poses.new_empty(0), saved)
         ctx.has_tau = tau is not None
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
-        poses, dims, pg, tau = ctx.saved_tensors
+        poses, dims, pg, tau, saved = ctx.saved_tensors
         gp, gd = ctx.engine.backward(pg, poses.contiguous(), dims.contiguous() if ctx.has_dims else None,
-                                     tau if ctx.has_tau else None, grad_out, ctx.params)
+                                     tau if ctx.has_tau else None, grad_out, ctx.params, saved=saved)
         return gp, (gd if ctx.has_dims else None), None, None, None, None
 
 

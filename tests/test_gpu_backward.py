@@ -1,5 +1,7 @@
 """Adjoint kernel against the FP64 oracle's autograd gradient and FP64 central finite
-differences, through the C ABI and through the torch.autograd wrapper."""
+differences, through the C ABI and through the torch.autograd wrapper.  Both ways
+of calling the adjoint are held to the oracle: recomputing the forward inside the
+call ("recompute") and reading the forward's per-pair records ("records")."""
 import numpy as np
 import pytest
 import torch
@@ -20,13 +22,14 @@ def engine():
     e.close()
 
 
-def gpu_grad(engine, w, grad_out, **pkw):
+def gpu_grad(engine, w, grad_out, path="recompute", **pkw):
     from paper_2602_20304_gb300.engine import workload_tensors
     ids = engine.add_geometries(w.geoms)
     pg, poses, dims, tau = workload_tensors(w, id_map=ids)
     params = engine.params(**pkw)
     go = torch.as_tensor(grad_out, dtype=torch.float32, device="cuda").contiguous()
-    gp, gd = engine.backward(pg, poses, dims, tau, go, params)
+    saved = engine.forward_save(pg, poses, dims, tau, params)[1] if path == "records" else None
+    gp, gd = engine.backward(pg, poses, dims, tau, go, params, saved=saved)
     torch.cuda.synchronize()
     engine.check()
     return gp.cpu().numpy().astype(np.float64), gd.cpu().numpy().astype(np.float64), params
@@ -37,8 +40,8 @@ def rel_errors(got, ref):
     return np.abs(got - ref).max(axis=1) / np.maximum(scale, 1e-12)
 
 
-def check_against_oracle(engine, w, grad_out, **pkw):
-    gp, gd, params = gpu_grad(engine, w, grad_out, **pkw)
+def check_against_oracle(engine, w, grad_out, path="recompute", **pkw):
+    gp, gd, params = gpu_grad(engine, w, grad_out, path, **pkw)
     return check_grad(np.concatenate([gp, gd], 1), w, params, grad_out, what="gradients")["max_rel"]
 
 
@@ -54,33 +57,72 @@ def test_box_vs_hull_weighted_distance_loss(engine):
     print("box-vs-hull32 grad rel", check_against_oracle(engine, w, out_grad))
 
 
+PATHS = ["recompute", "records"]
+
+
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("cfg,n", [(1, 48), (2, 48)])
-def test_random_upstream(engine, cfg, n):
+def test_random_upstream(engine, cfg, n, path):
     w = synth.make_config(cfg, n)
     g = np.random.default_rng(cfg).normal(size=(w.n_pairs, 8, 8))
-    print(f"config {cfg} grad rel", check_against_oracle(engine, w, g))
+    print(f"config {cfg} {path} grad rel", check_against_oracle(engine, w, g, path))
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("tau", [1e-3, 1e-2, 1e-1])
-def test_mixed_kinds_and_tau(engine, tau):
+def test_mixed_kinds_and_tau(engine, tau, path):
     w = synth.config_mixed(n=24, seed=5)
     w.tau[:] = tau
     g = np.random.default_rng(7).normal(size=(w.n_pairs, 8, 8))
-    print(f"mixed tau={tau} grad rel", check_against_oracle(engine, w, g))
+    print(f"mixed tau={tau} {path} grad rel", check_against_oracle(engine, w, g, path))
 
 
-def test_hull_vs_hull(engine):
+@pytest.mark.parametrize("path", PATHS)
+def test_hull_vs_hull(engine, path):
     """Both bodies hulls (8..64 points each): the adjoint takes both hulls' plane
     reverses (value at the other witness, Hessian-vector product at its own)."""
     w = synth.config_hull_vs_hull(n=24, tau=1e-2)
     g = np.random.default_rng(11).normal(size=(w.n_pairs, 8, 8))
-    print("hull-vs-hull grad rel", check_against_oracle(engine, w, g))
+    print(f"hull-vs-hull {path} grad rel", check_against_oracle(engine, w, g, path))
 
 
-def test_vertex_contacts_only(engine):
+@pytest.mark.parametrize("path", PATHS)
+def test_vertex_contacts_only(engine, path):
     w = synth.make_config(2, 32)
     g = np.random.default_rng(3).normal(size=(w.n_pairs, 4, 8))
-    check_against_oracle(engine, w, g, flags=1, K=4)
+    check_against_oracle(engine, w, g, path, flags=1, K=4)
+
+
+def test_records_match_recompute(engine):
+    """The two ways of calling the adjoint agree pair by pair (to the rounding of the
+    atomically summed adjoints and of the forward's reductions)."""
+    w = synth.config_mixed(n=64, seed=9)
+    g = np.random.default_rng(5).normal(size=(w.n_pairs, 8, 8))
+    a = np.concatenate(gpu_grad(engine, w, g, "recompute")[:2], 1)
+    b = np.concatenate(gpu_grad(engine, w, g, "records")[:2], 1)
+    rel = rel_errors(b, a)
+    print("records vs recompute, worst relative", rel.max())
+    assert rel.max() <= 1e-3
+
+
+def test_saved_stride_checked(engine):
+    """A record buffer narrower than cm_saved_stride is refused by both calls."""
+    from paper_2602_20304_gb300 import api
+    from paper_2602_20304_gb300.engine import workload_tensors
+    w = synth.make_config(2, 8)
+    ids = engine.add_geometries(w.geoms)
+    pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+    params = engine.params()
+    stride = api.cm_saved_stride(engine.ctx, params)
+    assert stride >= 11 * params.K
+    narrow = torch.empty((w.n_pairs, stride - 4), dtype=torch.float32, device="cuda")
+    out = torch.empty((w.n_pairs, params.K, 8), dtype=torch.float32, device="cuda")
+    with pytest.raises(api.CMError):
+        api.cm_contact_manifold_fwd_save(engine.ctx, pg, poses, dims, tau, params, out, narrow)
+    go = torch.zeros_like(out)
+    gp, gd = torch.empty_like(poses), torch.empty_like(dims)
+    with pytest.raises(api.CMError):
+        api.cm_contact_manifold_bwd_saved(engine.ctx, pg, poses, dims, tau, params, narrow, go, gp, gd)
 
 
 def test_against_fp64_central_differences(engine):

@@ -43,7 +43,9 @@ def test_autotune_then_plan_replay(setup):
     shape_f = api.cm_get_launch_shape(eng.ctx, w.n_pairs, False)
     shape_b = api.cm_get_launch_shape(eng.ctx, w.n_pairs, True)
     assert shape_f[0] in (128, 256, 512) and shape_b[0] in (128, 256)
-    ref_gp, ref_gd = eng.backward(pg, poses, dims, tau, go, params)
+    # the plan's adjoint reads the forward's records, as the autograd path does
+    saved = eng.forward_save(pg, poses, dims, tau, params)[1]
+    ref_gp, ref_gd = eng.backward(pg, poses, dims, tau, go, params, saved=saved)
     # a plan captures ordering + forward + adjoint; replay it twice with new poses in between
     poses_buf = poses.clone()
     plan = api.cm_plan_create(eng.ctx, pg, poses_buf, dims, tau, params, out, go, gp, gd)
@@ -51,7 +53,13 @@ def test_autotune_then_plan_replay(setup):
         api.cm_plan_launch(plan)
         torch.cuda.synchronize()
         assert torch.allclose(out, ref, atol=1e-6, rtol=0)
-        assert torch.allclose(gp, ref_gp, atol=1e-5, rtol=1e-4) and torch.allclose(gd, ref_gd, atol=1e-5, rtol=1e-4)
+        # the adjoint sums with atomics: two launches agree to the rounding of those sums,
+        # held per pair relative to the pair's largest gradient component
+        a = torch.cat([gp, gd], 1).double()
+        b = torch.cat([ref_gp, ref_gd], 1).double()
+        rel = ((a - b).abs().amax(1) / b.abs().amax(1).clamp_min(1e-12)).max().item()
+        print("plan vs direct adjoint, worst per-pair relative difference", rel)
+        assert rel <= 1e-4
         moved = poses.clone()
         moved[:, 4:7] += 0.01
         moved[:, 11:14] += 0.01                     # rigid shift of both bodies
