@@ -21,7 +21,7 @@ but not this use of it) and is "parity unpinned" by the paper's own numbers.
 from .smooth import (sigmoid, relu_s, clip_s, greater_s, smaller_s, within_s,  # noqa: F401
                      argmin_s, lse, sign_s, softplus)
 from .sdf import local_vertices, sdf_local, sdf_world, quat_to_rot  # noqa: F401
-from .edge_edge import solve_box_qp, ee_witness, ee_candidates  # noqa: F401
+from .edge_edge import solve_box_qp, solve_box_qp_hard, ee_witness, ee_candidates  # noqa: F401
 from .vertex_face import vf_witness  # noqa: F401
 from .manifold import (Params, pair_candidates, soft_topk_reduce, pair_manifold,  # noqa: F401
                        batch_manifold, batch_manifold_grad)

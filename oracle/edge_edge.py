@@ -22,8 +22,16 @@ Every objective value is the objective itself evaluated at the candidate, so
 the four costs are mutually consistent (this is what makes the solve
 equivariant under swapping the two edges).
 
+Non-smoothed variant (the paper's Ours-NS, Sec. V): the same steps with the
+hard operators -- the side minimisers clipped to [0, 1], the argmin of the four
+costs (first on ties), con the Iverson bracket of 0 <= alpha_u <= 1 in both
+coordinates (inclusive) and alpha* = alpha_u where con, else the argmin side's
+point.  For the strictly convex regularised QP this is the exact minimiser over
+the box (interior minimiser if feasible, else the best of the four sides, each
+minimised exactly by clipping its 1-D stationary point).
+
 Pins: tests/test_oracle_edge_edge.py -- dense-grid brute force of the
-regularised QP in the near-hard limit, the skew-perpendicular closed form,
+regularised QP in the near-hard limit and of the non-smoothed solve, the skew-perpendicular closed form,
 the parallel-edges closed form, swap equivariance, and continuity of the
 rotating-edge sweep of Fig. 4 (with a jump when smoothing is switched off).
 """
@@ -60,8 +68,30 @@ def solve_box_qp(Q11, Q12, Q22, c1, c2, eps_clip=0.1, eps_min=0.1, eps_comp=0.1)
     return a1, a2, con
 
 
-def ee_witness(a0, a1, b0, b1, w_reg=0.01, eps_clip=0.1, eps_min=0.1, eps_comp=0.1):
-    """Witness points of edge pairs (a0, a1) x (b0, b1) (broadcasting, (..., 3)).
+def solve_box_qp_hard(Q11, Q12, Q22, c1, c2):
+    """Non-smoothed analytic active-set solve (Ours-NS).  Returns (a1, a2, con)."""
+    det = Q11 * Q22 - Q12 * Q12
+    a1_u = (Q12 * c2 - Q22 * c1) / det
+    a2_u = (Q12 * c1 - Q11 * c2) / det
+    one, zero = torch.ones_like(a1_u), torch.zeros_like(a1_u)
+    s1 = torch.clamp(-(Q12 + c2) / Q22, 0.0, 1.0)   # a1 = 1
+    s2 = torch.clamp(-c2 / Q22, 0.0, 1.0)           # a1 = 0
+    s3 = torch.clamp(-(Q12 + c1) / Q11, 0.0, 1.0)   # a2 = 1
+    s4 = torch.clamp(-c1 / Q11, 0.0, 1.0)           # a2 = 0
+    a1_c = torch.stack([one, zero, s3, s4], dim=-1)
+    a2_c = torch.stack([s1, s2, one, zero], dim=-1)
+    costs = _objective(Q11[..., None], Q12[..., None], Q22[..., None],
+                       c1[..., None], c2[..., None], a1_c, a2_c)
+    j = torch.argmin(costs, dim=-1, keepdim=True)
+    a1_cb = torch.gather(a1_c, -1, j)[..., 0]
+    a2_cb = torch.gather(a2_c, -1, j)[..., 0]
+    inside = (a1_u >= 0.0) & (a1_u <= 1.0) & (a2_u >= 0.0) & (a2_u <= 1.0)
+    return torch.where(inside, a1_u, a1_cb), torch.where(inside, a2_u, a2_cb), inside.to(a1_u.dtype)
+
+
+def ee_witness(a0, a1, b0, b1, w_reg=0.01, eps_clip=0.1, eps_min=0.1, eps_comp=0.1, hard=False):
+    """Witness points of edge pairs (a0, a1) x (b0, b1) (broadcasting, (..., 3)); with
+    ``hard`` the non-smoothed solve (Ours-NS).
 
     Returns (e1*, e2*, alpha1, alpha2, con).
     """
@@ -73,7 +103,10 @@ def ee_witness(a0, a1, b0, b1, w_reg=0.01, eps_clip=0.1, eps_min=0.1, eps_comp=0
     Q22 = (t2 * t2).sum(-1) + w_reg
     c1 = (t1 * b).sum(-1) - 0.5 * w_reg
     c2 = (t2 * b).sum(-1) - 0.5 * w_reg
-    al1, al2, con = solve_box_qp(Q11, Q12, Q22, c1, c2, eps_clip, eps_min, eps_comp)
+    if hard:
+        al1, al2, con = solve_box_qp_hard(Q11, Q12, Q22, c1, c2)
+    else:
+        al1, al2, con = solve_box_qp(Q11, Q12, Q22, c1, c2, eps_clip, eps_min, eps_comp)
     e1 = a0 + al1[..., None] * (a1 - a0)
     e2 = b0 + al2[..., None] * (b1 - b0)
     return e1, e2, al1, al2, con
