@@ -110,24 +110,30 @@ def fp32_flops_per_pair(w, flags=0):
 # own recomputation is not counted): the adjoint's algorithmic work is the forward's
 # (it needs every forward value) plus this.
 #   per SDF evaluation (value at one point; value and gradient at the other, whose
-#   normal needs the Hessian-vector product): hull / box per plane 1 exp and 14 flops
-#   (value) or 22 (with the gradient); ellipsoid 2 MUFU and 30 / 50 flops; capsule 6 and
-#   80 / 110; cylinder 5 and 60 / 90;
+#   normal needs the Hessian-vector product): a hull's reverse comes from moments the
+#   forward pass over its planes accumulates -- the gradient at the value point (3 flops
+#   per plane) and sum_f pi_f n_f n_f^T at the other (9 per plane) -- then
+#   phibar g + H gbar (5 / 25 flops, no transcendental); a box's six planes are reversed
+#   one by one (1 exp and 14 / 22 flops each); ellipsoid 2 MUFU and 30 / 50 flops;
+#   capsule 6 and 80 / 110; cylinder 5 and 60 / 90;
 #   per edge pair: SoftSort reverse of two candidates (one exp and 50 flops each),
 #   indicators, soft signs and normals 200 flops, witnesses and the QP's smoothed
 #   active set 420 flops and 24 MUFU (the derivatives of 4 soft clips and 2 soft
 #   comparisons), distance-matrix adjoint 52 flops and 2 exps;
 #   per vertex candidate: SoftSort reverse (1 exp, 50 flops), normal, activity and frame 70.
 def _sdf_bwd_mufu(kind, n_planes):
-    if kind in (synth.KIND_BOX, synth.KIND_HULL):
-        return 6 if kind == synth.KIND_BOX else n_planes
+    if kind == synth.KIND_HULL:
+        return 0
+    if kind == synth.KIND_BOX:
+        return 6
     return {synth.KIND_ELLIPSOID: 2, synth.KIND_CAPSULE: 6, synth.KIND_CYLINDER: 5}[kind]
 
 
 def _sdf_bwd_flops(kind, n_planes, grad):
-    if kind in (synth.KIND_BOX, synth.KIND_HULL):
-        F = 6 if kind == synth.KIND_BOX else n_planes
-        return F * (22 if grad else 14) + 10
+    if kind == synth.KIND_HULL:
+        return n_planes * (9 if grad else 3) + (25 if grad else 5)
+    if kind == synth.KIND_BOX:
+        return 6 * (22 if grad else 14) + 10
     return {synth.KIND_ELLIPSOID: (30, 50), synth.KIND_CAPSULE: (80, 110),
             synth.KIND_CYLINDER: (60, 90)}[kind][1 if grad else 0]
 
@@ -630,14 +636,17 @@ def sq_union_rates(Engine, api, local, steps, flush):
 
 
 def witness_rates(api, n=10_000_000, steps=5):
-    """Queries/s of the batched E-E and V-F witness routines, queries uniform in the unit
-    cube; the rows (48 B in, 32 / 16 B out) exceed L2, so each launch streams from HBM."""
+    """Queries/s of the batched E-E and V-F witness routines, smoothed and non-smoothed
+    (the paper's Ours-NS), queries uniform in the unit cube; the rows (48 B in, 32 / 16 B
+    out) exceed L2, so each launch streams from HBM."""
     import torch
     g = torch.Generator(device="cuda").manual_seed(synth.SEED_BASE + 6)
     q = torch.rand((n, 12), device="cuda", generator=g)
-    p = api.cm_default_params()
     res = {}
-    for name, fn, width in (("ee", api.cm_ee_witness_batch, 8), ("vf", api.cm_vf_witness_batch, 4)):
+    soft, hard = api.cm_default_params(), api.cm_default_params(flags=api.CM_FLAG_HARD)
+    for name, fn, width, p in (("ee", api.cm_ee_witness_batch, 8, soft), ("vf", api.cm_vf_witness_batch, 4, soft),
+                               ("ee_hard", api.cm_ee_witness_batch, 8, hard),
+                               ("vf_hard", api.cm_vf_witness_batch, 4, hard)):
         out = torch.empty((n, width), device="cuda")
         for _ in range(3):
             fn(q, p, out)

@@ -71,10 +71,15 @@ typedef enum {
  * (r, h, -); CYLINDER (r, h, -); ELLIPSOID (a, b, c); HULL and SQ_UNION unused. */
 enum { CM_BOX = 0, CM_CAPSULE = 1, CM_CYLINDER = 2, CM_ELLIPSOID = 3, CM_HULL = 4, CM_SQ_UNION = 5 };
 
-/* Flags of cm_params.flags: the simplifications of Supplement A. */
+/* Flags of cm_params.flags: the simplifications of Supplement A, and the
+ * non-smoothed witness routines of the paper's Sec. V ablation. */
 enum {
-  CM_FLAG_NO_EE = 1,     /* vertex-SDF contacts only ("Ours-NE") */
-  CM_FLAG_ONE_SIDED = 2  /* only A's vertices against B's SDF ("Ours-NE-S"); implies NO_EE */
+  CM_FLAG_NO_EE = 1,      /* vertex-SDF contacts only ("Ours-NE") */
+  CM_FLAG_ONE_SIDED = 2,  /* only A's vertices against B's SDF ("Ours-NE-S"); implies NO_EE */
+  CM_FLAG_HARD = 4        /* witness-point routines without smoothing ("Ours-NS", Sec. V): hard
+                           * clips, argmin and in-box tests; cm_ee_witness_batch and
+                           * cm_vf_witness_batch only -- the manifold calls refuse it
+                           * (CM_ERR_INVALID_ARG), their operators being the smooth ones */
 };
 
 typedef struct cm_context cm_context;
@@ -287,6 +292,34 @@ cm_status cm_contact_manifold_bwd_saved(cm_context* ctx, int32_t n_pairs, const 
                                         const cm_params* params, const float* saved, int64_t saved_stride,
                                         const float* grad_out, float* grad_poses, float* grad_dims, void* stream);
 
+/* Candidate dump: every candidate a pair's manifold is reduced from -- the
+ * vertex-SDF contacts of Sec. IV-C and both witnesses of every edge pair of
+ * Sec. IV-D3 -- as rows (p, d, n, w) in world coordinates, the manifold's own
+ * layout, for checking and debugging a manifold candidate by candidate.
+ * cm_candidate_offsets (host only, touches no device): offsets_host (n_pairs + 1
+ *   int64, caller-owned) receives the first row of each pair (offsets_host[0] = 0,
+ *   offsets_host[n_pairs] = total rows) for these params: per pair the vertex
+ *   candidates (A's, then B's unless CM_FLAG_ONE_SIDED; with top_verts, that many
+ *   selected vertices per body) and, unless CM_FLAG_NO_EE / CM_FLAG_ONE_SIDED,
+ *   2 E_A E_B edge candidates (with top_edges, the selected edges).
+ *   pair_geoms_host: n_pairs x 2 ids in host memory.  CM_ERR_INVALID_ARG for an
+ *   unknown or destroyed id.
+ * cm_contact_manifold_fwd_dump: cm_contact_manifold_fwd that also writes pair i's
+ *   candidate with id c to row candidate_offsets[i] + c of `candidates` (device,
+ *   candidate_rows x 8 floats, caller-owned), ids as the kernels number them: the
+ *   vertex candidates first (A's, then B's), then for edge pair (k, l), i.e.
+ *   j = k E_B + l, the witness on A's edge at 2 j and the one on B's edge at 2 j + 1.
+ *   candidate_offsets: device, n_pairs + 1 int64 from cm_candidate_offsets for the
+ *   same pairs and params.  A pair whose range does not match its candidate count,
+ *   or passes candidate_rows, writes no rows and sets the context's device error
+ *   (cm_check_device_error names it). */
+cm_status cm_candidate_offsets(const cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms_host,
+                               const cm_params* params, int64_t* offsets_host);
+cm_status cm_contact_manifold_fwd_dump(cm_context* ctx, int32_t n_pairs, const int32_t* pair_geoms,
+                                       const float* poses, const float* dims, const float* tau,
+                                       const cm_params* params, float* out, float* candidates,
+                                       int64_t candidate_rows, const int64_t* candidate_offsets, void* stream);
+
 /* Batching layer (not part of the paper's method).
  *
  * cm_autotune times a few launch shapes (threads per CTA, CTAs per SM, with or
@@ -400,7 +433,12 @@ cm_status cm_check_device_error(cm_context* ctx);
 
 /* Witness-point routines on their own, for independent queries (the paper's
  * witness-point throughput setting, Sec. V, Fig. 6).  Device buffers, 16-byte
- * aligned; they run on the current device and need no context.
+ * aligned; they run on the current device and need no context.  With
+ * CM_FLAG_HARD in params->flags both run the same analytic active set without
+ * smoothing (the paper's Ours-NS): the exact box-QP minimiser (con = 1 when the
+ * unconstrained one is inside the box, else 0) and the exact closest point of the
+ * triangle (inside = 1 or 0); ties between sides go to the first in the order
+ * a1 = 1, a1 = 0, a2 = 1, a2 = 0 (E-E) and t0t1, t1t2, t0t2 (V-F).
  * cm_ee_witness_batch: queries n x 12 floats (a0, a1 of edge 1; b0, b1 of edge 2);
  *   the regularised 2x2 box QP with the smoothed analytic active set (Sec. IV-D2)
  *   using params->w_reg and eps_*; out n x 8 floats (e1*, e2*, con, |e1* - e2*|).

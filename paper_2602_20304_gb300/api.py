@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 CM_OK, CM_ERR_INVALID_ARG, CM_ERR_OOM, CM_ERR_CUDA = 0, 1, 2, 3
 CM_ERR_ADMISSION, CM_ERR_TIMEOUT, CM_ERR_NOT_FOUND, CM_ERR_DEVICE = 4, 5, 6, 7
 CM_BOX, CM_CAPSULE, CM_CYLINDER, CM_ELLIPSOID, CM_HULL, CM_SQ_UNION = 0, 1, 2, 3, 4, 5
-CM_FLAG_NO_EE, CM_FLAG_ONE_SIDED = 1, 2
+CM_FLAG_NO_EE, CM_FLAG_ONE_SIDED, CM_FLAG_HARD = 1, 2, 4
 CM_MAX_K = 16
 
 
@@ -78,6 +78,9 @@ _SIGS = {
     "cm_contact_manifold_fwd_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
                                                        ctypes.POINTER(cm_params), _vp, _vp]),
     "cm_saved_stride": (ctypes.c_int, [_vp, ctypes.POINTER(cm_params), ctypes.POINTER(ctypes.c_int64)]),
+    "cm_candidate_offsets": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.POINTER(cm_params), _vp]),
+    "cm_contact_manifold_fwd_dump": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                                    ctypes.POINTER(cm_params), _vp, _vp, ctypes.c_int64, _vp, _vp]),
     "cm_contact_manifold_fwd_save": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
                                                     ctypes.POINTER(cm_params), _vp, _vp, ctypes.c_int64, _vp]),
     "cm_contact_manifold_bwd_saved": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp,
@@ -260,6 +263,33 @@ def cm_contact_manifold_bwd(ctx, pair_geoms, poses, dims, tau, params, grad_out,
     _check(_lib.cm_contact_manifold_bwd(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau),
                                         ctypes.byref(params), _ptr(grad_out), _ptr(grad_poses),
                                         _ptr(grad_dims), _stream_handle(stream)))
+
+
+def cm_candidate_offsets(ctx, pair_geoms, params):
+    """(n + 1,) int64 first candidate row of each pair (host numpy ids (n, 2) in)."""
+    import numpy as np
+    pg = np.ascontiguousarray(pair_geoms, dtype=np.int32)
+    off = np.zeros(pg.shape[0] + 1, dtype=np.int64)
+    _check(_lib.cm_candidate_offsets(ctx, int(pg.shape[0]), pg.ctypes.data, ctypes.byref(params), off.ctypes.data))
+    return off
+
+
+def cm_contact_manifold_fwd_dump(ctx, pair_geoms, poses, dims, tau, params, out, candidates, offsets,
+                                 stream=None) -> None:
+    """Forward manifold that also writes every candidate row (rows, 8) at ``offsets`` (device int64)."""
+    import torch
+    n = int(pair_geoms.shape[0])
+    _check_tensor(pair_geoms, "pair_geoms", torch.int32, n)
+    _check_tensor(poses, "poses", torch.float32, n)
+    _check_tensor(dims, "dims", torch.float32, n)
+    _check_tensor(tau, "tau", torch.float32, n)
+    _check_tensor(out, "out", torch.float32, n)
+    _check_tensor(offsets, "candidate_offsets", torch.int64, n + 1)
+    if not candidates.is_cuda or candidates.dtype != torch.float32 or not candidates.is_contiguous():
+        raise ValueError("candidates must be a contiguous CUDA float32 tensor")
+    _check(_lib.cm_contact_manifold_fwd_dump(ctx, n, _ptr(pair_geoms), _ptr(poses), _ptr(dims), _ptr(tau),
+                                             ctypes.byref(params), _ptr(out), _ptr(candidates),
+                                             int(candidates.numel() // 8), _ptr(offsets), _stream_handle(stream)))
 
 
 def cm_saved_stride(ctx, params) -> int:

@@ -64,8 +64,7 @@ cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32
                        const float* poses, const float* dims, const float* tau, const cm_params* params, float* out,
                        const float* grad_out, float* grad_poses, float* grad_dims, float* scratch,
                        int32_t* order, int32_t* counter, cudaStream_t s, int64_t stride,  // stride <= 0: max_e^2
-                       float* saved = nullptr, int64_t saved_stride = 0,  // per-pair forward records (optional)
-                       int32_t saved_first = 0);  // the forward records pairs >= saved_first
+                       const StepExtras& x = StepExtras{});  // forward records, candidate dump (optional)
 // Floats per pair of the forward's record for the adjoint (see kRecHead).
 int64_t saved_stride_floats(const cm_context* c, int K);
 void server_shutdown(cm_context* c);  // cm_serve.cu

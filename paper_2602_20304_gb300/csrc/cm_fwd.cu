@@ -23,6 +23,15 @@
 
 namespace cm {
 
+// One candidate row (p, d, n, w) of the dump, rotated back to world coordinates.
+__device__ __forceinline__ void dump_row(const FwdArgs& a, const PairShared& ps, int64_t row, const float (&y)[8]) {
+  const V3 p = mul(ps.RB, v3(y[0], y[1], y[2])) + ps.tB;
+  const V3 n = mul(ps.RB, v3(y[4], y[5], y[6]));
+  float* o = a.dump + row * 8;
+  o[0] = p.x; o[1] = p.y; o[2] = p.z; o[3] = y[3];
+  o[4] = n.x; o[5] = n.y; o[6] = n.z; o[7] = y[7];
+}
+
 __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PairShared ps;
@@ -68,11 +77,23 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
     const bool one_sided = (a.p.flags & 2) != 0;
     const bool no_ee = one_sided || (a.p.flags & 1) != 0;
     const int nvs = one_sided ? ps.nvA : ps.nvA + ps.nvB;
+    // candidate dump: this pair's rows start at dump_off[pi], one per candidate id; a
+    // range that does not match the pair's candidate count or the buffer is refused
+    int64_t doff = -1;
+    if (a.dump) {
+      const int64_t o0 = a.dump_off[pi], o1 = a.dump_off[pi + 1];
+      const int64_t total = nvs + (no_ee ? 0 : 2 * (int64_t)ps.neA * ps.neB);
+      if (o0 >= 0 && o1 - o0 == total && o1 <= a.dump_rows) doff = o0;
+      else if (threadIdx.x == 0) atomicCAS(a.err, 0, -(pi + 1));
+    }
     for (int base = (nwarps - 1 - warp) * 32; base < nvs; base += nwarps * 32) {
       const int c = base + lane;
       const bool valid = c < nvs;
       float s = 0.f;
-      if (valid) s = vs_candidate(ps, sm, bb, c, y);
+      if (valid) {
+        s = vs_candidate(ps, sm, bb, c, y);
+        if (doff >= 0) dump_row(a, ps, doff + c, y);
+      }
       wtk_push(st, valid, s, y, K, k2, c);
     }
 
@@ -133,6 +154,10 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
             w = ee_witness(ep, a.p);
           }
           ee_candidates(ps, sm, bb, ep, w, sm.rowL[k], sm.colL[l], y, y2, s1, s2);
+          if (doff >= 0) {
+            dump_row(a, ps, doff + nvs + 2 * (int64_t)i, y);
+            dump_row(a, ps, doff + nvs + 2 * (int64_t)i + 1, y2);
+          }
         }
         wtk_push(st, valid, s1, y, K, k2, nvs + 2 * i);
         wtk_push(st, valid, s2, y2, K, k2, nvs + 2 * i + 1);

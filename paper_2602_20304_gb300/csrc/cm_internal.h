@@ -52,6 +52,21 @@ struct FwdArgs {
   float* saved;
   int64_t saved_stride;
   int32_t saved_first;  // the forward writes records of pairs >= saved_first, from record 0
+  // Candidate dump (may be null): every candidate of pair i as 8 floats (p, d, n, w in
+  // world coordinates) at row dump_off[i] + its id, for rows below dump_rows.
+  float* dump;
+  const int64_t* dump_off;
+  int64_t dump_rows;
+};
+
+// Optional outputs of one step beside the manifold (see FwdArgs).
+struct StepExtras {
+  float* saved = nullptr;
+  int64_t saved_stride = 0;
+  int32_t saved_first = 0;
+  float* dump = nullptr;
+  const int64_t* dump_off = nullptr;
+  int64_t dump_rows = 0;
 };
 
 // Forward record of one pair, as the adjoint reads it: the K selected scores s^_k,

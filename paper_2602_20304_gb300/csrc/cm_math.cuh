@@ -673,6 +673,43 @@ CM_HD QPOut qp_solve(const QPPre& q, float lam, const Params& p) {
   return o;
 }
 
+// The same active set without smoothing (the paper's Ours-NS, Sec. V): the side
+// minimisers clipped to [0, 1], the argmin of the four costs (first on ties) and
+// con the inclusive test 0 <= au <= 1 of both coordinates.
+CM_HD QPOut qp_solve_hard(const QPPre& q, float lam) {
+  V3 X = cross(q.t1, q.t2);
+  float T11 = q.Q11 - lam, T22 = q.Q22 - lam, T12 = q.Q12;
+  float B1 = q.c1 + 0.5f * lam, B2 = q.c2 + 0.5f * lam;
+  float det = dot(X, X) + lam * (T11 + T22) + lam * lam;
+  float n1 = -dot(X, cross(q.b, q.t2)) + lam * (0.5f * (T22 - T12) - B1 + 0.5f * lam);
+  float n2 = -dot(X, cross(q.t1, q.b)) + lam * (0.5f * (T11 - T12) - B2 + 0.5f * lam);
+  float idet = rcp(det);
+  float au1 = n1 * idet, au2 = n2 * idet;
+  QPOut o;
+  if (au1 >= 0.f && au1 <= 1.f && au2 >= 0.f && au2 <= 1.f) {
+    o.a1 = au1;
+    o.a2 = au2;
+    o.con = 1.f;
+    return o;
+  }
+  float iQ11 = rcp(q.Q11), iQ22 = rcp(q.Q22);
+  float s1 = fminf(fmaxf(-(q.Q12 + q.c2) * iQ22, 0.f), 1.f);  // a1 = 1
+  float s2 = fminf(fmaxf(-q.c2 * iQ22, 0.f), 1.f);             // a1 = 0
+  float s3 = fminf(fmaxf(-(q.Q12 + q.c1) * iQ11, 0.f), 1.f);  // a2 = 1
+  float s4 = fminf(fmaxf(-q.c1 * iQ11, 0.f), 1.f);             // a2 = 0
+  float J = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, 1.f, s1);
+  o.a1 = 1.f;
+  o.a2 = s1;
+  const float J2 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, 0.f, s2);
+  if (J2 < J) { J = J2; o.a1 = 0.f; o.a2 = s2; }
+  const float J3 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, s3, 1.f);
+  if (J3 < J) { J = J3; o.a1 = s3; o.a2 = 1.f; }
+  const float J4 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, s4, 0.f);
+  if (J4 < J) { o.a1 = s4; o.a2 = 0.f; }
+  o.con = 0.f;
+  return o;
+}
+
 // ---------------------------------------------------------------- V-F witness (Sec. IV-D1)
 // Smoothed closest point of triangle (t0, t1, t2) to v: plane projection if the
 // soft barycentric test says inside, else the soft-argmin blend of the three
@@ -707,6 +744,40 @@ CM_HD V3 vf_witness(V3 v, V3 t0, V3 t1, V3 t2, const Params& p, float& inside) {
   inside = within01(b0, ic) * within01(b1, ic) * within01(b2, ic);
   const V3 pu = t0 + pr;
   return pc + (pu - pc) * inside;
+}
+
+// The same routine without smoothing (Ours-NS): edge parameters clipped to [0, 1],
+// the nearest of the three edge points (first on ties), and the plane projection
+// where all three barycentric coordinates lie in [0, 1].
+CM_HD V3 vf_witness_hard(V3 v, V3 t0, V3 t1, V3 t2, float& inside) {
+  const V3 d10 = t1 - t0, d20 = t2 - t0;
+  const V3 nb = cross(d10, d20);
+  const float ia = rsq(dot(nb, nb));
+  const V3 n = nb * ia;
+  const V3 rel = v - t0;
+  const V3 pr = rel - n * dot(rel, n);
+  const float b2 = dot(cross(d10, pr), n) * ia, b1 = dot(cross(pr, d20), n) * ia, b0 = 1.f - b1 - b2;
+  if (b0 >= 0.f && b0 <= 1.f && b1 >= 0.f && b1 <= 1.f && b2 >= 0.f && b2 <= 1.f) {
+    inside = 1.f;
+    return t0 + pr;
+  }
+  inside = 0.f;
+  const V3 A[3] = {t0, t1, t0}, B[3] = {t1, t2, t2};
+  V3 best = t0;
+  float bc = 3.0e38f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const V3 e = B[j] - A[j];
+    const float s = fminf(fmaxf(dot(v - A[j], e) * rcp(dot(e, e)), 0.f), 1.f);
+    const V3 q = fma3(s, e, A[j]);
+    const V3 d = v - q;
+    const float c = dot(d, d);
+    if (c < bc) {
+      bc = c;
+      best = q;
+    }
+  }
+  return best;
 }
 
 }  // namespace cm

@@ -94,7 +94,7 @@ cm_status check_params(const cm_params* p) {
   if (!(std::isfinite(p->w_reg) && p->w_reg > 0.f))
     return fail(CM_ERR_INVALID_ARG, "w_reg must be finite and > 0 (the E-E QP needs it to be strictly convex)");
   if (p->K < 1 || p->K > CM_MAX_K) return fail(CM_ERR_INVALID_ARG, "K must be in 1..16");
-  if (p->flags & ~3) return fail(CM_ERR_INVALID_ARG, "unknown flag bits");
+  if (p->flags & ~7) return fail(CM_ERR_INVALID_ARG, "unknown flag bits");
   if (p->top_verts < 0 || p->top_verts > CM_MAX_SELECT || p->top_edges < 0 || p->top_edges > CM_MAX_SELECT)
     return fail(CM_ERR_INVALID_ARG, "top_verts and top_edges must be in 0..32");
   if (p->trace_iters < 0 || p->trace_iters > CM_MAX_TRACE)
@@ -156,6 +156,8 @@ cm_status ensure_order(cm_context* c, size_t n) {
 }
 
 cm_status check_k(const cm_context* c, const cm_params* params) {
+  if (params->flags & CM_FLAG_HARD)
+    return fail(CM_ERR_INVALID_ARG, "CM_FLAG_HARD applies to the witness-point routines only");
   if (params->flags & (CM_FLAG_NO_EE | CM_FLAG_ONE_SIDED)) {
     const int nv = params->top_verts ? std::min(params->top_verts, c->min_v) : c->min_v;
     const int min_cands = (params->flags & CM_FLAG_ONE_SIDED) ? nv : 2 * nv;
@@ -223,8 +225,7 @@ int64_t saved_stride_floats(const cm_context* c, int K) {
 cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs, const int32_t* pg,
                        const float* poses, const float* dims, const float* tau, const cm_params* params, float* out,
                        const float* grad_out, float* grad_poses, float* grad_dims, float* scratch,
-                       int32_t* order, int32_t* counter, cudaStream_t s, int64_t stride, float* saved,
-                       int64_t saved_stride, int32_t saved_first) {
+                       int32_t* order, int32_t* counter, cudaStream_t s, int64_t stride, const StepExtras& x) {
   FwdArgs a{};
   int grid = 1;
   shape(c, bwd, cfg, n_pairs, a.sm, grid);
@@ -246,9 +247,12 @@ cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32
   a.work_counter = nullptr;
   a.order = nullptr;
   a.store_alpha = bwd ? 0 : 1;
-  a.saved = saved;
-  a.saved_stride = saved_stride;
-  a.saved_first = saved_first;
+  a.saved = x.saved;
+  a.saved_stride = x.saved_stride;
+  a.saved_first = x.saved_first;
+  a.dump = bwd ? nullptr : x.dump;
+  a.dump_off = x.dump_off;
+  a.dump_rows = x.dump_rows;
   cudaError_t e;
   if (cfg.ordered) {
     if ((e = launch_order(pg, c->d_hdr, a.n_geoms, n_pairs, order, counter, bwd, s)) != cudaSuccess)
@@ -266,7 +270,7 @@ cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32
 cm_status run_step(cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs, const int32_t* pg,
                    const float* poses, const float* dims, const float* tau, const cm_params* params, float* out,
                    const float* grad_out, float* grad_poses, float* grad_dims, cudaStream_t s,
-                   float* saved = nullptr, int64_t saved_stride = 0) {
+                   const StepExtras& x = StepExtras{}) {
   SmemLayout L;
   int grid = 1;
   shape(c, bwd, cfg, n_pairs, L, grid);
@@ -274,7 +278,7 @@ cm_status run_step(cm_context* c, int bwd, const LaunchCfg& cfg, int32_t n_pairs
   if (st != CM_OK) return st;
   if ((st = ensure_order(c, (size_t)n_pairs)) != CM_OK) return st;
   return enqueue_step(c, bwd, cfg, n_pairs, pg, poses, dims, tau, params, out, grad_out, grad_poses, grad_dims,
-                      c->d_scratch, c->d_order, c->d_counter, s, 0, saved, saved_stride);
+                      c->d_scratch, c->d_order, c->d_counter, s, 0, x);
 }
 
 // A caller's record buffer: saved_stride floats per pair, at least what the
@@ -513,8 +517,11 @@ cm_status cm_check_device_error(cm_context* c) {
     return cuda_fail(e, "read device error flag");
   if (v != 0) {
     cudaMemset(c->d_err, 0, sizeof(int));
-    char buf[128];
-    std::snprintf(buf, sizeof buf, "pair %d names an unknown or destroyed geometry id", v - 1);
+    char buf[160];
+    if (v > 0) std::snprintf(buf, sizeof buf, "pair %d names an unknown or destroyed geometry id", v - 1);
+    else
+      std::snprintf(buf, sizeof buf,
+                    "pair %d: the candidate offsets do not match its candidate count or pass the dump's rows", -v - 1);
     return fail(CM_ERR_DEVICE, buf);
   }
   return CM_OK;
@@ -524,8 +531,8 @@ cm_status cm_check_device_error(cm_context* c) {
 
 namespace {
 cm_status fwd_call(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses, const float* dims,
-                   const float* tau, const cm_params* params, float* out, float* saved, int64_t saved_stride,
-                   bool with_record, void* stream) {
+                   const float* tau, const cm_params* params, float* out, const StepExtras& x, bool with_record,
+                   void* stream) {
   if (!c) return fail(CM_ERR_INVALID_ARG, "NULL context");
   cm_status st = check_params(params);
   if (st != CM_OK) return st;
@@ -535,11 +542,13 @@ cm_status fwd_call(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, co
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->hdr.empty()) return fail(CM_ERR_INVALID_ARG, "no geometry registered");
   if ((st = check_k(c, params)) != CM_OK) return st;
-  if (with_record && (st = check_saved(c, params, saved, saved_stride)) != CM_OK) return st;
+  if (with_record && (st = check_saved(c, params, x.saved, x.saved_stride)) != CM_OK) return st;
+  if (x.dump && (!x.dump_off || x.dump_rows < 0 || (reinterpret_cast<uintptr_t>(x.dump) & 3)))
+    return fail(CM_ERR_INVALID_ARG, "the candidate dump needs a float-aligned buffer, its row count and the offsets");
   cudaSetDevice(c->device);
   if ((st = sync_geometry_locked(c)) != CM_OK) return st;
   return run_step(c, 0, pick_cfg(c, 0, n_pairs, params->flags), n_pairs, pair_geoms, poses, dims, tau, params, out,
-                  nullptr, nullptr, nullptr, (cudaStream_t)stream, saved, saved_stride);
+                  nullptr, nullptr, nullptr, (cudaStream_t)stream, x);
 }
 
 cm_status bwd_call(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses, const float* dims,
@@ -558,9 +567,11 @@ cm_status bwd_call(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, co
   if (with_record && (st = check_saved(c, params, saved, saved_stride)) != CM_OK) return st;
   cudaSetDevice(c->device);
   if ((st = sync_geometry_locked(c)) != CM_OK) return st;
+  StepExtras x;
+  x.saved = const_cast<float*>(saved);
+  x.saved_stride = saved_stride;
   return run_step(c, 1, pick_cfg(c, 1, n_pairs, params->flags), n_pairs, pair_geoms, poses, dims, tau, params,
-                  nullptr, grad_out, grad_poses, grad_dims, (cudaStream_t)stream, const_cast<float*>(saved),
-                  saved_stride);
+                  nullptr, grad_out, grad_poses, grad_dims, (cudaStream_t)stream, x);
 }
 }  // namespace
 
@@ -569,7 +580,7 @@ extern "C" {
 cm_status cm_contact_manifold_fwd(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
                                   const float* dims, const float* tau, const cm_params* params, float* out,
                                   void* stream) {
-  return fwd_call(c, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, 0, false, stream);
+  return fwd_call(c, n_pairs, pair_geoms, poses, dims, tau, params, out, StepExtras{}, false, stream);
 }
 
 cm_status cm_saved_stride(const cm_context* c, const cm_params* params, int64_t* floats_per_pair) {
@@ -584,7 +595,47 @@ cm_status cm_saved_stride(const cm_context* c, const cm_params* params, int64_t*
 cm_status cm_contact_manifold_fwd_save(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
                                        const float* dims, const float* tau, const cm_params* params, float* out,
                                        float* saved, int64_t saved_stride, void* stream) {
-  return fwd_call(c, n_pairs, pair_geoms, poses, dims, tau, params, out, saved, saved_stride, true, stream);
+  StepExtras x;
+  x.saved = saved;
+  x.saved_stride = saved_stride;
+  return fwd_call(c, n_pairs, pair_geoms, poses, dims, tau, params, out, x, true, stream);
+}
+
+cm_status cm_candidate_offsets(const cm_context* c, int32_t n_pairs, const int32_t* pair_geoms_host,
+                               const cm_params* params, int64_t* offsets_host) {
+  if (!c || !offsets_host || (n_pairs > 0 && !pair_geoms_host)) return fail(CM_ERR_INVALID_ARG, "NULL argument");
+  if (n_pairs < 0) return fail(CM_ERR_INVALID_ARG, "n_pairs < 0");
+  cm_status st = check_params(params);
+  if (st != CM_OK) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  const bool one_sided = params->flags & CM_FLAG_ONE_SIDED, no_ee = one_sided || (params->flags & CM_FLAG_NO_EE);
+  const auto sel = [](int limit, int n) { return limit ? std::min(limit, n) : n; };
+  int64_t acc = 0;
+  offsets_host[0] = 0;
+  for (int32_t i = 0; i < n_pairs; ++i) {
+    const int32_t ga = pair_geoms_host[2 * i], gb = pair_geoms_host[2 * i + 1];
+    if (ga < 0 || gb < 0 || ga >= (int32_t)c->hdr.size() || gb >= (int32_t)c->hdr.size() ||
+        c->hdr[ga].n_verts <= 0 || c->hdr[gb].n_verts <= 0)
+      return fail(CM_ERR_INVALID_ARG, "pair names an unknown or destroyed geometry id");
+    const GeomHeader &A = c->hdr[ga], &B = c->hdr[gb];
+    const int64_t nva = sel(params->top_verts, A.n_verts), nvb = sel(params->top_verts, B.n_verts);
+    const int64_t nea = sel(params->top_edges, A.n_edges), neb = sel(params->top_edges, B.n_edges);
+    acc += (one_sided ? nva : nva + nvb) + (no_ee ? 0 : 2 * nea * neb);
+    offsets_host[i + 1] = acc;
+  }
+  return CM_OK;
+}
+
+cm_status cm_contact_manifold_fwd_dump(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
+                                       const float* dims, const float* tau, const cm_params* params, float* out,
+                                       float* candidates, int64_t candidate_rows, const int64_t* candidate_offsets,
+                                       void* stream) {
+  StepExtras x;
+  x.dump = candidates;
+  x.dump_off = candidate_offsets;
+  x.dump_rows = candidate_rows;
+  if (!candidates || !candidate_offsets) return fail(CM_ERR_INVALID_ARG, "candidates and candidate_offsets are required");
+  return fwd_call(c, n_pairs, pair_geoms, poses, dims, tau, params, out, x, false, stream);
 }
 
 cm_status cm_contact_manifold_bwd_saved(cm_context* c, int32_t n_pairs, const int32_t* pair_geoms, const float* poses,
@@ -729,9 +780,12 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
   // the adjoint is timed as plans and autograd run it: from the forward's records
   float* saved = nullptr;
   const int64_t rs = grad_out ? saved_stride_floats(c, params->K) : 0;
+  StepExtras rec;
+  rec.saved_stride = rs;
   if (rs) {
     cudaError_t e = cudaMalloc(&saved, (size_t)n_pairs * rs * sizeof(float));
     if (e != cudaSuccess) return fail(CM_ERR_OOM, std::string("autotune records: ") + cudaGetErrorString(e));
+    rec.saved = saved;
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -750,7 +804,7 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
           for (int rep = 0; rep < 3; ++rep) {
             if (rep > 0) cudaEventRecord(e0, s);
             st = run_step(c, bwd, g, n_pairs, pair_geoms, poses, dims, tau, params, out, grad_out, grad_poses,
-                          grad_dims, s, saved, rs);
+                          grad_dims, s, rec);
             if (st != CM_OK) break;
             if (rep > 0) {
               cudaEventRecord(e1, s);
@@ -777,7 +831,7 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
     // the forward's records for the adjoint's shapes, from the chosen forward shape
     if (!bwd && saved) {
       st = run_step(c, 0, best, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, nullptr, nullptr, s,
-                    saved, rs);
+                    rec);
       if (st != CM_OK) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -863,6 +917,7 @@ extern "C" cm_status cm_plan_create(cm_context* c, int32_t n_pairs, const int32_
   size_t need = scratch_need(c, 0, grid_f, 0);
   if (grad_out) need = std::max(need, scratch_need(c, 1, grid_b, 0));
   const int64_t rs = grad_out ? saved_stride_floats(c, params->K) : 0;
+  StepExtras rec;
   cudaError_t e;
   if ((e = cudaMalloc(&p->scratch, need * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&p->order, (size_t)n_pairs * sizeof(int32_t))) != cudaSuccess ||
@@ -871,25 +926,27 @@ extern "C" cm_status cm_plan_create(cm_context* c, int32_t n_pairs, const int32_
     cm_plan_destroy(p);
     return fail(CM_ERR_OOM, std::string("plan buffers: ") + cudaGetErrorString(e));
   }
+  rec.saved = p->saved;
+  rec.saved_stride = rs;
   if ((e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess) {
     cm_plan_destroy(p);
     return cuda_fail(e, "plan stream");
   }
   // first launches outside the capture set the kernels' attributes
   st = enqueue_step(c, 0, gf, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, nullptr, nullptr,
-                    p->scratch, p->order, p->counter, p->cap, 0, p->saved, rs);
+                    p->scratch, p->order, p->counter, p->cap, 0, rec);
   if (st == CM_OK && grad_out)
     st = enqueue_step(c, 1, gb, n_pairs, pair_geoms, poses, dims, tau, params, nullptr, grad_out, grad_poses,
-                      grad_dims, p->scratch, p->order, p->counter, p->cap, 0, p->saved, rs);
+                      grad_dims, p->scratch, p->order, p->counter, p->cap, 0, rec);
   if (st == CM_OK && (e = cudaStreamSynchronize(p->cap)) != cudaSuccess) st = cuda_fail(e, "plan warm-up");
   if (st == CM_OK && (e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     st = cuda_fail(e, "begin capture");
   if (st == CM_OK) {
     cm_status s1 = enqueue_step(c, 0, gf, n_pairs, pair_geoms, poses, dims, tau, params, out, nullptr, nullptr,
-                                nullptr, p->scratch, p->order, p->counter, p->cap, 0, p->saved, rs);
+                                nullptr, p->scratch, p->order, p->counter, p->cap, 0, rec);
     if (s1 == CM_OK && grad_out)
       s1 = enqueue_step(c, 1, gb, n_pairs, pair_geoms, poses, dims, tau, params, nullptr, grad_out, grad_poses,
-                        grad_dims, p->scratch, p->order, p->counter, p->cap, 0, p->saved, rs);
+                        grad_dims, p->scratch, p->order, p->counter, p->cap, 0, rec);
     e = cudaStreamEndCapture(p->cap, &p->graph);
     if (s1 != CM_OK) st = s1;
     else if (e != cudaSuccess) st = cuda_fail(e, "end capture");

@@ -263,13 +263,19 @@ struct Server {
       const float* tptr = has_tau ? tau : nullptr;
       LaunchCfg gf = pick_cfg(ctx, 0, (int)n, params.flags);
       const size_t t0 = n - nb;  // the adjoint requests: a contiguous tail, recorded by the forward
+      StepExtras fwd_rec, bwd_rec;
+      fwd_rec.saved = nb ? saved : nullptr;
+      fwd_rec.saved_stride = rs;
+      fwd_rec.saved_first = (int32_t)t0;
+      bwd_rec.saved = saved;
+      bwd_rec.saved_stride = rs;
       st = enqueue_step(ctx, 0, gf, (int)n, pg, poses, dptr, tptr, &params, out, nullptr, nullptr, nullptr, scratch,
-                        order, counter, s, b->max_ee, nb ? saved : nullptr, rs, (int32_t)t0);
+                        order, counter, s, b->max_ee, fwd_rec);
       if (st == CM_OK && nb) {
         LaunchCfg gb = pick_cfg(ctx, 1, (int)nb, params.flags);
         st = enqueue_step(ctx, 1, gb, (int)nb, pg + 2 * t0, poses + 14 * t0, has_dims ? dims + 6 * t0 : nullptr,
                           has_tau ? tau + t0 : nullptr, &params, nullptr, gout, gp, gd, scratch, order, counter, s,
-                          b->max_ee, saved, rs);
+                          b->max_ee, bwd_rec);
       }
     }
     if (st != CM_OK) return st;

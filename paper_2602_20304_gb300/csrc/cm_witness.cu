@@ -9,6 +9,8 @@
 namespace cm {
 namespace {
 
+// kHard: the non-smoothed active set (the paper's Ours-NS, Sec. V)
+template <bool kHard>
 __global__ void __launch_bounds__(256) ee_witness_kernel(int n, const float4* __restrict__ q, Params p,
                                                          float4* __restrict__ out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -16,7 +18,7 @@ __global__ void __launch_bounds__(256) ee_witness_kernel(int n, const float4* __
     const V3 a0 = v3(r0.x, r0.y, r0.z), a1 = v3(r0.w, r1.x, r1.y), b0 = v3(r1.z, r1.w, r2.x),
              b1 = v3(r2.y, r2.z, r2.w);
     const QPPre pre = qp_setup(a0, a1, b0, b1, p.w_reg);
-    const QPOut o = qp_solve(pre, p.w_reg, p);
+    const QPOut o = kHard ? qp_solve_hard(pre, p.w_reg) : qp_solve(pre, p.w_reg, p);
     const V3 e1 = fma3(o.a1, a1 - a0, a0), e2 = fma3(o.a2, b1 - b0, b0);
     const V3 d = e1 - e2;
     out[2 * i] = make_float4(e1.x, e1.y, e1.z, e2.x);
@@ -24,13 +26,15 @@ __global__ void __launch_bounds__(256) ee_witness_kernel(int n, const float4* __
   }
 }
 
+template <bool kHard>
 __global__ void __launch_bounds__(256) vf_witness_kernel(int n, const float4* __restrict__ q, Params p,
                                                          float4* __restrict__ out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float4 r0 = q[3 * i], r1 = q[3 * i + 1], r2 = q[3 * i + 2];
     float inside;
-    const V3 w = vf_witness(v3(r0.x, r0.y, r0.z), v3(r0.w, r1.x, r1.y), v3(r1.z, r1.w, r2.x), v3(r2.y, r2.z, r2.w),
-                            p, inside);
+    const V3 v = v3(r0.x, r0.y, r0.z), t0 = v3(r0.w, r1.x, r1.y), t1 = v3(r1.z, r1.w, r2.x),
+             t2 = v3(r2.y, r2.z, r2.w);
+    const V3 w = kHard ? vf_witness_hard(v, t0, t1, t2, inside) : vf_witness(v, t0, t1, t2, p, inside);
     out[i] = make_float4(w.x, w.y, w.z, inside);
   }
 }
@@ -63,8 +67,10 @@ extern "C" cm_status cm_ee_witness_batch(int32_t n, const float* queries, const 
   if (st != CM_OK || n == 0) return st;
   const Params p{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K,
                  params->flags, 0, 0};
-  ee_witness_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, reinterpret_cast<const float4*>(queries), p,
-                                                                   reinterpret_cast<float4*>(out));
+  const float4* q4 = reinterpret_cast<const float4*>(queries);
+  float4* o4 = reinterpret_cast<float4*>(out);
+  if (params->flags & CM_FLAG_HARD) ee_witness_kernel<true><<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, q4, p, o4);
+  else ee_witness_kernel<false><<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, q4, p, o4);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CM_OK : rt::cuda_fail(e, "E-E witness launch");
 }
@@ -75,8 +81,10 @@ extern "C" cm_status cm_vf_witness_batch(int32_t n, const float* queries, const 
   if (st != CM_OK || n == 0) return st;
   const Params p{params->tau, params->w_reg, params->eps_clip, params->eps_min, params->eps_comp, params->K,
                  params->flags, 0, 0};
-  vf_witness_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, reinterpret_cast<const float4*>(queries), p,
-                                                                   reinterpret_cast<float4*>(out));
+  const float4* q4 = reinterpret_cast<const float4*>(queries);
+  float4* o4 = reinterpret_cast<float4*>(out);
+  if (params->flags & CM_FLAG_HARD) vf_witness_kernel<true><<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, q4, p, o4);
+  else vf_witness_kernel<false><<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(n, q4, p, o4);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CM_OK : rt::cuda_fail(e, "V-F witness launch");
 }

@@ -55,6 +55,18 @@ class Engine:
         api.cm_contact_manifold_fwd(self.ctx, pair_geoms, poses, dims, tau, params, out, stream)
         return out
 
+    def forward_dump(self, pair_geoms, poses, dims=None, tau=None, params=None, stream=None):
+        """(out, candidates, offsets): the forward manifold, every candidate row (rows, 8) in
+        world coordinates and the host offsets (n + 1) of each pair's first row."""
+        params = params or self.params()
+        n = int(pair_geoms.shape[0])
+        off = api.cm_candidate_offsets(self.ctx, pair_geoms.cpu().numpy(), params)
+        out = torch.empty((n, params.K, 8), dtype=torch.float32, device=pair_geoms.device)
+        cand = torch.empty((max(int(off[-1]), 1), 8), dtype=torch.float32, device=pair_geoms.device)
+        d_off = torch.as_tensor(off, device=pair_geoms.device)
+        api.cm_contact_manifold_fwd_dump(self.ctx, pair_geoms, poses, dims, tau, params, out, cand, d_off, stream)
+        return out, cand, off
+
     def forward_save(self, pair_geoms, poses, dims=None, tau=None, params=None, stream=None):
         """(out, saved): the forward manifold and each pair's record for ``backward``."""
         params = params or self.params()

@@ -92,3 +92,140 @@ def test_empty_and_misaligned():
     buf = torch.empty(12 * 4 + 1, device="cuda")
     with pytest.raises(api.CMError):
         api.cm_ee_witness_batch(buf[1:].view(4, 12), p, torch.empty((4, 8), device="cuda"))
+
+
+def _hard_params():
+    from paper_2602_20304_gb300 import api
+    return api.cm_default_params(flags=api.CM_FLAG_HARD)
+
+
+def test_edge_edge_witness_batch_hard():
+    """Non-smoothed E-E routine (Ours-NS) on 2e5 unit-cube queries.  Its result is the
+    minimiser of the strictly convex regularised box QP.  Where the objective is flat (near
+    parallel edges, two sides' costs within FP32 resolution of each other) points far apart
+    are optimal to FP32 precision, so the minimiser is not unique at that precision: what is
+    unique is the optimal value.  The witnesses and their distance are held to 1e-5 for at
+    least 99.9 % of the queries; every other query must give a feasible point whose FP64
+    objective is within 1e-6 of the optimum.  con is 0 or 1 and must equal the oracle's
+    wherever the unconstrained minimiser lies more than 1e-4 from the box's boundary."""
+    from paper_2602_20304_gb300 import api
+    rng = np.random.default_rng(11)
+    n = 200_000
+    q = rng.uniform(0, 1, size=(n, 12)).astype(np.float32)
+    out = torch.empty((n, 8), device="cuda")
+    api.cm_ee_witness_batch(torch.from_numpy(q).cuda(), _hard_params(), out)
+    got = out.cpu().numpy().astype(np.float64)
+    t = torch.from_numpy(q.astype(np.float64))
+    a0, a1, b0, b1 = t[:, 0:3], t[:, 3:6], t[:, 6:9], t[:, 9:12]
+    e1, e2, _, _, con = oracle.ee_witness(a0, a1, b0, b1, hard=True)
+    err = np.maximum(np.abs(got[:, 0:3] - e1.numpy()).max(1), np.abs(got[:, 3:6] - e2.numpy()).max(1))
+    err = np.maximum(err, np.abs(got[:, 7] - torch.linalg.vector_norm(e1 - e2, dim=1).numpy()))
+    over = err > 1e-5
+    print("hard E-E witnesses within 1e-5:", 1 - over.mean(), "interior share", float(con.mean()))
+    assert over.mean() <= 1e-3
+    assert set(np.unique(got[:, 6])) <= {0.0, 1.0}
+    lam = 0.01
+
+    def objective(e1x, e2x, al1, al2):
+        return ((e1x - e2x) ** 2).sum(1) + lam * ((al1 - 0.5) ** 2 + (al2 - 0.5) ** 2)
+    A0, A1, B0, B1 = (x.numpy()[over] for x in (a0, a1, b0, b1))
+    g1, g2 = got[over, 0:3], got[over, 3:6]
+    al1 = ((g1 - A0) * (A1 - A0)).sum(1) / ((A1 - A0) ** 2).sum(1)
+    al2 = ((g2 - B0) * (B1 - B0)).sum(1) / ((B1 - B0) ** 2).sum(1)
+    assert (al1 > -1e-6).all() and (al1 < 1 + 1e-6).all() and (al2 > -1e-6).all() and (al2 < 1 + 1e-6).all()
+    assert np.abs(g1 - (A0 + al1[:, None] * (A1 - A0))).max() < 1e-5     # on the edges
+    assert np.abs(g2 - (B0 + al2[:, None] * (B1 - B0))).max() < 1e-5
+    r1 = ((e1.numpy()[over] - A0) * (A1 - A0)).sum(1) / ((A1 - A0) ** 2).sum(1)
+    r2 = ((e2.numpy()[over] - B0) * (B1 - B0)).sum(1) / ((B1 - B0) ** 2).sum(1)
+    gap = objective(g1, g2, al1, al2) - objective(e1.numpy()[over], e2.numpy()[over], r1, r2)
+    print("off-point queries:", int(over.sum()), "largest objective excess", float(gap.max()) if over.any() else 0.0)
+    assert (gap <= 1e-6).all()
+    # margin of the unconstrained minimiser from the box boundary, in FP64
+    t1, t2, bb = a1 - a0, b0 - b1, a0 - b0
+    Q11 = (t1 * t1).sum(1) + lam
+    Q12 = (t1 * t2).sum(1)
+    Q22 = (t2 * t2).sum(1) + lam
+    c1 = (t1 * bb).sum(1) - 0.5 * lam
+    c2 = (t2 * bb).sum(1) - 0.5 * lam
+    det = Q11 * Q22 - Q12 * Q12
+    au = torch.stack([(Q12 * c2 - Q22 * c1) / det, (Q12 * c1 - Q11 * c2) / det], 1).numpy()
+    margin = np.minimum(np.abs(au), np.abs(au - 1.0)).min(1)
+    clear = margin > 1e-4
+    assert (got[clear, 6] == con.numpy()[clear]).all()
+    assert 0.05 < con.numpy().mean() < 0.95          # both branches are exercised
+
+
+def test_vertex_face_witness_batch_hard():
+    """Non-smoothed V-F routine (Ours-NS): the exact closest point of the triangle, held to
+    1e-5 for at least 99.9 % of the queries; every other query (the FP32 inside decision or
+    edge choice taken the other way, mostly on thin triangles) must give a point on the
+    triangle whose distance to the vertex is within 1e-6 of the optimal distance, the
+    value that is unique.  The inside flag must equal the oracle's wherever the plane
+    projection's smallest barycentric coordinate is more than 1e-4 from 0 and the oracle's
+    own flag survives one-ulp moves of the query."""
+    from _parity import ULP_DRAWS, _ulp
+    from paper_2602_20304_gb300 import api
+    rng = np.random.default_rng(12)
+    n = 200_000
+    q = rng.uniform(0, 1, size=(n, 12)).astype(np.float32)
+    out = torch.empty((n, 4), device="cuda")
+    api.cm_vf_witness_batch(torch.from_numpy(q).cuda(), _hard_params(), out)
+    got = out.cpu().numpy().astype(np.float64)
+
+    def ref_of(qq):
+        t = torch.from_numpy(qq.astype(np.float64))
+        w, inside = oracle.vf_witness(t[:, 0:3], t[:, 3:6], t[:, 6:9], t[:, 9:12], hard=True)
+        return w.numpy(), inside.numpy()
+    w_ref, in_ref = ref_of(q)
+    err = np.abs(got[:, 0:3] - w_ref).max(1)
+    over = np.nonzero(err > 1e-5)[0]
+    print("hard V-F queries within 1e-5:", 1 - len(over) / n, "inside share", float(in_ref.mean()))
+    assert len(over) / n <= 1e-3
+    flips = np.zeros(n, bool)
+    draw = np.random.default_rng(13)
+    for _ in range(ULP_DRAWS):
+        flips |= ref_of(_ulp(q, draw))[1] != in_ref
+    assert set(np.unique(got[:, 3])) <= {0.0, 1.0}
+    qd = q[over].astype(np.float64)
+    vv, T0, T1, T2 = qd[:, 0:3], qd[:, 3:6], qd[:, 6:9], qd[:, 9:12]
+    pg = got[over, 0:3]
+    nb_o = np.cross(T1 - T0, T2 - T0)
+    a2_o = np.linalg.norm(nb_o, axis=1)
+    n_o = nb_o / a2_o[:, None]
+    assert (np.abs(((pg - T0) * n_o).sum(1)) < 1e-5).all()               # in the triangle's plane
+    c2 = (np.cross(T1 - T0, pg - T0) * n_o).sum(1) / a2_o
+    c1 = (np.cross(pg - T0, T2 - T0) * n_o).sum(1) / a2_o
+    tol_b = 1e-5 / np.minimum(a2_o, 1.0)
+    assert (np.minimum(np.minimum(1 - c1 - c2, c1), c2) > -tol_b).all()   # inside it
+    excess = np.linalg.norm(vv - pg, axis=1) - np.linalg.norm(vv - w_ref[over], axis=1)
+    print("off-point queries:", len(over), "largest distance excess", float(excess.max()) if len(over) else 0.0)
+    assert (excess <= 1e-6).all()
+    # smallest barycentric coordinate of the plane projection, FP64
+    t = torch.from_numpy(q.astype(np.float64))
+    v, t0, t1, t2 = t[:, 0:3], t[:, 3:6], t[:, 6:9], t[:, 9:12]
+    nb = torch.cross(t1 - t0, t2 - t0, dim=1)
+    area2 = torch.linalg.vector_norm(nb, dim=1)
+    nrm = nb / area2[:, None]
+    rel = v - t0
+    p = rel - (rel * nrm).sum(1, keepdim=True) * nrm
+    b2 = (torch.cross(t1 - t0, p, dim=1) * nrm).sum(1) / area2
+    b1 = (torch.cross(p, t2 - t0, dim=1) * nrm).sum(1) / area2
+    bmin = torch.minimum(torch.minimum(1.0 - b1 - b2, b1), b2).numpy()
+    clear = (np.abs(bmin) > 1e-4) & ~flips
+    assert (got[clear, 3] == in_ref[clear]).all()
+    assert 0.05 < in_ref.mean() < 0.95
+
+
+def test_hard_flag_refused_by_the_manifold():
+    from paper_2602_20304_gb300 import api
+    from paper_2602_20304_gb300.engine import Engine, workload_tensors
+    import synth
+    w = synth.make_config(1, 4)
+    eng = Engine(0)
+    try:
+        ids = eng.add_geometries(w.geoms)
+        pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+        with pytest.raises(api.CMError):
+            eng.forward(pg, poses, dims, tau, _hard_params())
+    finally:
+        eng.close()

@@ -196,7 +196,11 @@ def test_bench_alu_roofline_object():
     assert bench.alu_roofline(w, 1e-5, (1, 1))["algorithmic_bytes"] == 348 * 16
     fl_b, mu_b = bench.bwd_work_per_pair(w)
     fl_f, mu_f = bench.fp32_flops_per_pair(w), bench.mufu_ops_per_pair(w)
-    assert (fl_b > 2 * fl_f).all() and (mu_b > 1.5 * mu_f).all()
+    # the reverse adds work on both pipes; a hull's reverse needs no transcendental per
+    # plane (its moments come from the forward pass), so the adjoint's MUFU work grows
+    # less than its FP32 work
+    assert (fl_b > 1.5 * fl_f).all() and (mu_b > 1.1 * mu_f).all()
+    assert ((mu_b / mu_f) < (fl_b / fl_f)).all()
 
 
 def test_bench_cpu_baseline_leg():
