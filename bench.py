@@ -665,11 +665,11 @@ def witness_rates(api, n=10_000_000, steps=5):
 
 # ----------------------------------------------------------------- our arm
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pair of one forward and
-# one adjoint launch on the headline workload, from one ncu capture each of a 2048-pair
-# replica of it (the full batch is too large to capture), scaled by the pairs a launch
-# processes; None until a capture of the current kernels exists.
-FWD_TRAFFIC_PER_PAIR = None
-BWD_TRAFFIC_PER_PAIR = None
+# one adjoint launch of the current kernels on the full 65536-pair headline batch, from one
+# single-pass ncu capture of each (default launch shape; profiles/headline_dram_65536.md):
+# forward 0.617 + 3.010 GB, adjoint 8.526 + 14.819 GB per launch.
+FWD_TRAFFIC_PER_PAIR = (0.616987e9 + 3.009642e9) / 65536
+BWD_TRAFFIC_PER_PAIR = (8.526086e9 + 14.818653e9) / 65536
 
 
 def main():
