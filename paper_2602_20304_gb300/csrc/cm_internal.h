@@ -84,6 +84,7 @@ struct LaunchCfg {
   int block;
   int per_sm;
   int ordered;
+  int warp = 0;  // forward only: one warp per pair (cm_fwd_warp_kernel)
 };
 
 constexpr int kMaxK = 16;
@@ -109,6 +110,12 @@ cudaError_t ensure_smem_attr(const void* kernel, int bytes);
 
 cudaError_t launch_fwd(const FwdArgs& a, int grid, int block, cudaStream_t s);
 int fwd_max_blocks_per_sm(int block, int smem_bytes);
+// One warp per pair (cm_fwd_warp.cu): a.sm is the single-warp layout without the
+// pre-selection area; each warp's slice adds 4 max_e^2 floats of edge-pair data.
+cudaError_t launch_fwd_warp(const FwdArgs& a, int grid, int block, cudaStream_t s);
+int fwd_warp_bytes(const SmemLayout& L);
+int fwd_warp_max_blocks_per_sm(int block, int smem_bytes);
+bool fwd_warp_fits(const SmemLayout& L, int block);
 cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,
                        int block, int per_sm, cudaStream_t s);
 int bwd_max_blocks_per_sm(int block, int smem_bytes, int per_sm);

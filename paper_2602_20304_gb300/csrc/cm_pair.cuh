@@ -115,24 +115,26 @@ __device__ inline void pair_setup(const FwdArgs& a, int pi, PairShared& ps) {
 }
 
 // Cooperative: copy pair `pi`'s geometry into shared memory (A's vertices moved
-// into B's frame).  Caller syncs before and after.
-__device__ inline void pair_stage(const FwdArgs& a, int pi, const PairShared& ps, const PairSmem& sm) {
+// into B's frame), thread t0 of a group of ts threads (the CTA, or one warp).
+// Caller syncs the group before and after.
+__device__ inline void pair_stage_by(const FwdArgs& a, int pi, const PairShared& ps, const PairSmem& sm, int t0,
+                                     int ts) {
   const int ga = a.pair_geoms[2 * pi], gb = a.pair_geoms[2 * pi + 1];
   const GeomHeader& A = a.hdr[ga];
   const GeomHeader& B = a.hdr[gb];
-  for (int i = threadIdx.x; i < ps.nvA; i += blockDim.x) {
+  for (int i = t0; i < ps.nvA; i += ts) {
     float4 u = a.verts[A.v_off + i];
     V3 v = map_vertex(ps.kindA, u.x, u.y, u.z, u.w, ps.dA);
     V3 y = mul(ps.Rrel, v) + ps.trel;
     sm.vA[i] = make_float4(y.x, y.y, y.z, 0.f);
     sm.vAl[i] = make_float4(v.x, v.y, v.z, u.w);  // w: template cap sign (capsules)
   }
-  for (int i = threadIdx.x; i < ps.nvB; i += blockDim.x) {
+  for (int i = t0; i < ps.nvB; i += ts) {
     float4 u = a.verts[B.v_off + i];
     V3 v = map_vertex(ps.kindB, u.x, u.y, u.z, u.w, ps.dB);
     sm.vB[i] = make_float4(v.x, v.y, v.z, u.w);
   }
-  for (int i = threadIdx.x; i < ps.neA; i += blockDim.x) {
+  for (int i = t0; i < ps.neA; i += ts) {
     const uint32_t e = a.edges[A.e_off + i];
     sm.eA[i] = e;
     const float4 u0 = a.verts[A.v_off + (e & 0xffffu)], u1 = a.verts[A.v_off + (e >> 16)];
@@ -145,7 +147,7 @@ __device__ inline void pair_stage(const FwdArgs& a, int pi, const PairShared& ps
     sm.eAl6[i] = l0.x; sm.eAl6[es + i] = l0.y; sm.eAl6[2 * es + i] = l0.z;
     sm.eAl6[3 * es + i] = l1.x; sm.eAl6[4 * es + i] = l1.y; sm.eAl6[5 * es + i] = l1.z;
   }
-  for (int i = threadIdx.x; i < ps.neB; i += blockDim.x) {
+  for (int i = t0; i < ps.neB; i += ts) {
     const uint32_t e = a.edges[B.e_off + i];
     sm.eB[i] = e;
     const float4 u0 = a.verts[B.v_off + (e & 0xffffu)], u1 = a.verts[B.v_off + (e >> 16)];
@@ -158,14 +160,18 @@ __device__ inline void pair_stage(const FwdArgs& a, int pi, const PairShared& ps
   // hull planes pre-scaled by k = log2(e) / tau (see sdf_planes); superquadric
   // rows as packed
   const float kA = ps.kindA == kHull ? ps.k2 : 1.f, kB = ps.kindB == kHull ? ps.k2 : 1.f;
-  for (int i = threadIdx.x; i < ps.npA; i += blockDim.x) {
+  for (int i = t0; i < ps.npA; i += ts) {
     const float4 q = a.planes[A.p_off + i];
     sm.pA[i] = make_float4(q.x * kA, q.y * kA, q.z * kA, q.w * kA);
   }
-  for (int i = threadIdx.x; i < ps.npB; i += blockDim.x) {
+  for (int i = t0; i < ps.npB; i += ts) {
     const float4 q = a.planes[B.p_off + i];
     sm.pB[i] = make_float4(q.x * kB, q.y * kB, q.z * kB, q.w * kB);
   }
+}
+
+__device__ __forceinline__ void pair_stage(const FwdArgs& a, int pi, const PairShared& ps, const PairSmem& sm) {
+  pair_stage_by(a, pi, ps, sm, threadIdx.x, blockDim.x);
 }
 
 // Next pair of this CTA: from the size-ordered work queue when one is given

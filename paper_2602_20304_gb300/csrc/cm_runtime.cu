@@ -102,7 +102,7 @@ cm_status check_params(const cm_params* p) {
   return CM_OK;
 }
 
-SmemLayout make_layout(const cm_context* c, int nwarps, int bwd) {
+SmemLayout make_layout(const cm_context* c, int nwarps, int bwd, bool with_sel = true) {
   SmemLayout L;
   int o = 0;
   L.max_v = c->max_v;
@@ -121,7 +121,8 @@ SmemLayout make_layout(const cm_context* c, int nwarps, int bwd) {
   L.eA6 = o; o = align16(o + 24 * c->max_e);
   L.eAl6 = o; o = align16(o + 24 * c->max_e);
   L.eB6 = o; o = align16(o + 24 * c->max_e);
-  L.sel = o; o = align16(o + 4 * (2 * c->max_v + kSelFloats));
+  L.sel = o;
+  if (with_sel) o = align16(o + 4 * (2 * c->max_v + kSelFloats));
   L.sadj = o;
   if (bwd) o = align16(o + 4 * (kSelAdjFloats + 2 * c->max_v));  // pre-selection adjoint slots
   L.total = o;
@@ -182,12 +183,21 @@ uint64_t tune_key(int bwd, int n_pairs, int max_e, int flags) {
   return ((uint64_t)bwd << 40) | ((uint64_t)nb << 32) | ((uint64_t)(max_e / 32) << 8) | (uint64_t)(flags & 3);
 }
 
+// The one-warp-per-pair forward can run this context's pairs: no pre-selection and
+// 8 warps' slices fit the shared memory.
+bool warp_path_ok(const cm_context* c, int flags_unused, int top_verts, int top_edges) {
+  (void)flags_unused;
+  if (top_verts || top_edges) return false;
+  return fwd_warp_fits(make_layout(c, 1, 0, false), 256);
+}
+
 LaunchCfg default_cfg(const cm_context* c, int bwd, int n_pairs) {
   LaunchCfg g;
   g.block = 256;
   g.per_sm = 0;
   g.ordered = n_pairs >= 2 * c->num_sms ? 1 : 0;
-  (void)bwd;
+  // small bodies (box-sized: up to 48 edges) go one warp per pair by default
+  g.warp = (!bwd && c->max_e <= 48 && warp_path_ok(c, 0, 0, 0)) ? 1 : 0;
   return g;
 }
 
@@ -203,6 +213,14 @@ Params to_params(const cm_params* p) {
 
 // Grid and shared-memory layout of one launch shape.
 void shape(const cm_context* c, int bwd, const LaunchCfg& cfg, int n_pairs, SmemLayout& L, int& grid) {
+  if (!bwd && cfg.warp) {
+    L = make_layout(c, 1, 0, false);
+    const int nw = cfg.block / 32;
+    int per_sm = std::max(1, fwd_warp_max_blocks_per_sm(cfg.block, fwd_warp_bytes(L) * nw));
+    if (cfg.per_sm > 0) per_sm = std::min(per_sm, cfg.per_sm);
+    grid = std::max(1, std::min<int>((n_pairs + nw - 1) / nw, c->num_sms * per_sm));
+    return;
+  }
   L = make_layout(c, cfg.block / 32, bwd);
   int per_sm = bwd ? bwd_max_blocks_per_sm(cfg.block, L.total, cfg.per_sm) : fwd_max_blocks_per_sm(cfg.block, L.total);
   if (cfg.per_sm > 0) per_sm = std::min(per_sm, cfg.per_sm);
@@ -260,8 +278,12 @@ cm_status enqueue_step(const cm_context* c, int bwd, const LaunchCfg& cfg, int32
     a.order = order;
     a.work_counter = counter;
   }
+  const bool warp = !bwd && cfg.warp && !params->top_verts && !params->top_edges;
+  if (!bwd && cfg.warp && !warp) {  // a tuned warp shape met pre-selection: the CTA kernel's layout
+    shape(c, 0, LaunchCfg{cfg.block, cfg.per_sm, cfg.ordered, 0}, n_pairs, a.sm, grid);
+  }
   e = bwd ? launch_bwd(a, grad_out, grad_poses, grad_dims, grid, cfg.block, cfg.per_sm, s)
-          : launch_fwd(a, grid, cfg.block, s);
+      : warp ? launch_fwd_warp(a, grid, cfg.block, s) : launch_fwd(a, grid, cfg.block, s);
   if (e != cudaSuccess) return cuda_fail(e, bwd ? "backward launch" : "forward launch");
   return CM_OK;
 }
@@ -798,8 +820,12 @@ extern "C" cm_status cm_autotune(cm_context* c, int32_t n_pairs, const int32_t* 
     for (int bi = 0; bi < 4; ++bi) {
       if (bwd && (blocks[bi] > 256 || blocks[bi] < 128)) continue;  // the adjoint kernel: 128..256 threads
       for (int pi = 0; pi < 3; ++pi)
-        for (int ord = 0; ord < 2; ++ord) {
-          LaunchCfg g{blocks[bi], per_sms[pi], ord};
+        for (int v = 0; v < 4; ++v) {  // work order on / off, CTA or warp per pair (forward)
+          const int ord = v & 1, wp = v >> 1;
+          if (wp && (bwd || blocks[bi] > 256 || !warp_path_ok(c, params->flags, params->top_verts, params->top_edges) ||
+                     !fwd_warp_fits(make_layout(c, 1, 0, false), blocks[bi])))
+            continue;
+          LaunchCfg g{blocks[bi], per_sms[pi], ord, wp};
           float ms_sum = 0.f;
           for (int rep = 0; rep < 3; ++rep) {
             if (rep > 0) cudaEventRecord(e0, s);
