@@ -31,13 +31,23 @@ CM_HD void add_outer(float* R, V3 u, V3 v) {
 
 // ---------------------------------------------------------------- smooth operators
 CM_HD float sigmoid_grad_from(float s) { return s * (1.f - s); }            // d sigmoid / dx
-CM_HD float clip_s_grad(float x, float lo, float hi, float inv_eps) {       // d clip_s / dx
-  return sigmoid((x - lo) * inv_eps) - sigmoid((x - hi) * inv_eps);
+// clip_s(x, 0, 1) and its derivative from shared exponentials: with e0 = exp(-|x| / eps)
+// and e1 = exp(-|x - 1| / eps) the value is max(x, 0) - max(x - 1, 0) + eps ln((1 + e0) / (1 + e1))
+// and the derivative sigma(x / eps) - sigma((x - 1) / eps), sigma(u / eps) = (u >= 0 ? 1 : e) / (1 + e).
+CM_HD float clip01_s_vg(float x, float inv_eps, float eps, float& grad) {
+  const float k = inv_eps * kLog2e;
+  const float e0 = ex2(-fabsf(x) * k), e1 = ex2(-fabsf(x - 1.f) * k);
+  const float r0 = rcp(1.f + e0), r1 = rcp(1.f + e1);
+  grad = (x >= 0.f ? r0 : e0 * r0) - (x >= 1.f ? r1 : e1 * r1);
+  return fmaxf(x, 0.f) - fmaxf(x - 1.f, 0.f) + (eps * kLn2) * lg2((1.f + e0) * r1);
 }
-// d within01 / dx = within * (sigma((1-x)/eps) - sigma(x/eps)) / eps
-CM_HD float within01_grad(float x, float inv_eps) {
-  float a = sigmoid(x * inv_eps), b = sigmoid((1.f - x) * inv_eps);
-  return a * b * (b - a) * inv_eps;
+// within01(x) = sigma(x / eps) sigma((1 - x) / eps) and its derivative
+// within01 (sigma((1 - x) / eps) - sigma(x / eps)) / eps from the same two sigmoids.
+CM_HD float within01_vg(float x, float inv_eps, float& grad) {
+  const float a = sigmoid(x * inv_eps), b = sigmoid((1.f - x) * inv_eps);
+  const float w = a * b;
+  grad = w * (b - a) * inv_eps;
+  return w;
 }
 
 // ---------------------------------------------------------------- normal
@@ -119,9 +129,12 @@ CM_HD void sdf_ellipsoid_bwd(V3 y, V3 d, float phibar, V3 gbar, V3& ybar, V3& db
 // g = (u_x, u_y, u_z (1 - c')) with u = w / rho, c' = sig+ - sig-.
 CM_HD void sdf_capsule_bwd(V3 y, float rad, float h, float tau, float inv_tau, float phibar, V3 gbar, V3& ybar,
                            V3& dbar) {
+  // the soft clip's softplus terms and sigmoids from shared exponentials (as in sdf_capsule)
   float up = (y.z + h) * inv_tau, dn = (y.z - h) * inv_tau;
-  float c = -h + tau * (softplus(up) - softplus(dn));
-  float sp = sigmoid(up), sn = sigmoid(dn);
+  const float Eu = exp_(-fabsf(up)), Ed = exp_(-fabsf(dn));
+  const float iu = rcp(1.f + Eu), id = rcp(1.f + Ed);
+  float c = -h + tau * ((fmaxf(up, 0.f) - fmaxf(dn, 0.f)) + kLn2 * lg2((1.f + Eu) * id));
+  float sp = up >= 0.f ? iu : Eu * iu, sn = dn >= 0.f ? id : Ed * id;
   float cp = sp - sn;
   V3 w = v3(y.x, y.y, y.z - c);
   float r2 = dot(w, w);
@@ -429,8 +442,10 @@ CM_HD void qp_bwd(const QPPre& q, float lam, const Params& p, float ab1, float a
   float ie = rcp(p.eps_clip);
   float iQ11 = rcp(q.Q11), iQ22 = rcp(q.Q22);
   float z1 = -(q.Q12 + q.c2) * iQ22, z2 = -q.c2 * iQ22, z3 = -(q.Q12 + q.c1) * iQ11, z4 = -q.c1 * iQ11;
-  float s1 = clip_s(z1, 0.f, 1.f, ie, p.eps_clip), s2 = clip_s(z2, 0.f, 1.f, ie, p.eps_clip);
-  float s3 = clip_s(z3, 0.f, 1.f, ie, p.eps_clip), s4 = clip_s(z4, 0.f, 1.f, ie, p.eps_clip);
+  // the soft clips with their derivatives (sharing each side's exponentials)
+  float cg1, cg2, cg3, cg4;
+  float s1 = clip01_s_vg(z1, ie, p.eps_clip, cg1), s2 = clip01_s_vg(z2, ie, p.eps_clip, cg2);
+  float s3 = clip01_s_vg(z3, ie, p.eps_clip, cg3), s4 = clip01_s_vg(z4, ie, p.eps_clip, cg4);
   float J1 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, 1.f, s1);
   float J2 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, 0.f, s2);
   float J3 = qp_cost(q.Q11, q.Q12, q.Q22, q.c1, q.c2, s3, 1.f);
@@ -444,15 +459,16 @@ CM_HD void qp_bwd(const QPPre& q, float lam, const Params& p, float ab1, float a
   float ac1 = pr1 + pr3 * s3 + pr4 * s4;
   float ac2 = pr1 * s1 + pr2 * s2 + pr3;
   float ic = rcp(p.eps_comp);
-  float wi1 = within01(au1, ic), wi2 = within01(au2, ic);
+  float wg1, wg2;
+  float wi1 = within01_vg(au1, ic, wg1), wi2 = within01_vg(au2, ic, wg2);
   float con = wi1 * wi2;
 
   // ---- reverse of alpha = con au + (1 - con) ac
   float aub1 = con * ab1, aub2 = con * ab2;
   float acb1 = (1.f - con) * ab1, acb2 = (1.f - con) * ab2;
   float cb = conb + ab1 * (au1 - ac1) + ab2 * (au2 - ac2);
-  aub1 += cb * wi2 * within01_grad(au1, ic);
-  aub2 += cb * wi1 * within01_grad(au2, ic);
+  aub1 += cb * wi2 * wg1;
+  aub2 += cb * wi1 * wg2;
 
   // ---- soft argmin: ac = sum_j pr_j a_j, candidates (1, s1), (0, s2), (s3, 1), (s4, 0)
   float pb1 = acb1 + acb2 * s1, pb2 = acb2 * s2, pb3 = acb1 * s3 + acb2, pb4 = acb1 * s4;
@@ -479,8 +495,8 @@ CM_HD void qp_bwd(const QPPre& q, float lam, const Params& p, float ab1, float a
   cost_bwd(Jb4, s4, 0.f, sbar4, dummy);
 
   // ---- side minimisers z_j through the soft clip
-  float zb1 = sbar1 * clip_s_grad(z1, 0.f, 1.f, ie), zb2 = sbar2 * clip_s_grad(z2, 0.f, 1.f, ie);
-  float zb3 = sbar3 * clip_s_grad(z3, 0.f, 1.f, ie), zb4 = sbar4 * clip_s_grad(z4, 0.f, 1.f, ie);
+  float zb1 = sbar1 * cg1, zb2 = sbar2 * cg2;
+  float zb3 = sbar3 * cg3, zb4 = sbar4 * cg4;
   // z1 = -(Q12 + c2)/Q22, z2 = -c2/Q22, z3 = -(Q12 + c1)/Q11, z4 = -c1/Q11
   Qb12 += -zb1 * iQ22 - zb3 * iQ11;
   cb2 += -(zb1 + zb2) * iQ22;
