@@ -56,13 +56,14 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
       continue;
     }
     pair_stage(a, pi, ps, sm);
-    // column statistics of the E-E distance matrix: running minimum (as the bits of
-    // a non-negative float) and the soft-minimum sum
+    // row and column statistics of the E-E distance matrix: running minima (as the
+    // bits of non-negative floats) and the column soft-minimum sums
     float* colS = sm.colL + a.sm.max_e;
     for (int l = threadIdx.x; l < ps.neB; l += blockDim.x) {
       sm.colL[l] = 3.0e38f;
       colS[l] = 0.f;
     }
+    for (int k = threadIdx.x; k < ps.neA; k += blockDim.x) sm.rowL[k] = 3.0e38f;
     __syncthreads();
     const PairBodies bb = pair_bodies(ps, sm);
     if (ps.preselect) preselect_pair(a, ps, sm, bb);
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
         Witness w = ee_witness(edge_pair(sm, k, l), a.p);
         D[i] = w.dbar;
         atomicMin(reinterpret_cast<int*>(sm.colL) + l, __float_as_int(w.dbar));
+        atomicMin(reinterpret_cast<int*>(sm.rowL) + k, __float_as_int(w.dbar));
         if (a.store_alpha) {
           A1[i] = w.qp.a1;
           A2[i] = w.qp.a2;
@@ -113,11 +115,9 @@ __global__ void __launch_bounds__(512) cm_fwd_kernel(const FwdArgs a) {
       }
       __syncthreads();
       // ---- soft row minima (warp per row, coalesced over the row) and, in the same
-      // sweep, the column sums against the column minima found in pass 1
+      // sweep, the column sums, both against the minima found in pass 1
       for (int k = warp; k < neA; k += nwarps) {
-        float m = 3.0e38f;
-        for (int l = lane; l < neB; l += 32) m = fminf(m, D[k * neB + l]);
-        m = warp_min(m);
+        const float m = sm.rowL[k];
         float S = 0.f;
         for (int l = lane; l < neB; l += 32) {
           const float d = D[k * neB + l];
