@@ -340,6 +340,70 @@ CM_HD void body_sdf2_h_bwd(const Body& b, V3 y1, V3 y2, const Sdf2H& s, float ta
   }
 }
 
+// Pair classes of the edge-pair reverse: 0 any kinds; 1 A a polyhedron (hull) and B
+// a box, capsule, cylinder or ellipsoid -- the common case, compiled without the
+// kind dispatch and the branches the other kinds need.
+CM_HD Sdf prim_sdf(const Body& b, V3 y, float tau, float inv_tau) {
+  switch (b.kind) {
+    case kBox: return sdf_box(y, b.dims, tau, inv_tau);
+    case kEllipsoid: return sdf_ellipsoid(y, b.dims);
+    case kCapsule: return sdf_capsule(y, b.dims.x, b.dims.y, tau, inv_tau);
+    default: return sdf_cylinder(y, b.dims.x, b.dims.y, tau, inv_tau);
+  }
+}
+CM_HD void prim_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_tau, float phibar, V3 gbar,
+                        V3& ybar, V3& dbar) {
+  switch (b.kind) {
+    case kBox: sdf_box_bwd(y, b.dims, f, inv_tau, phibar, gbar, ybar, dbar); break;
+    case kEllipsoid: sdf_ellipsoid_bwd(y, b.dims, phibar, gbar, ybar, dbar); break;
+    case kCapsule: sdf_capsule_bwd(y, b.dims.x, b.dims.y, tau, inv_tau, phibar, gbar, ybar, dbar); break;
+    default: sdf_cylinder_bwd(y, b.dims.x, b.dims.y, f, inv_tau, phibar, gbar, ybar, dbar); break;
+  }
+}
+// body_sdf2_h of body A (kRole 0) or B (kRole 1) in pair class kCls.
+template <int kRole, int kCls>
+CM_HD Sdf2H sdf2h_of(const Body& b, V3 y1, V3 y2, float tau, float inv_tau) {
+  if (kCls == 1) {
+    Sdf2H o;
+    if (kRole == 0) {
+      sdf_planes2_h(y1, y2, b.planes, b.n_planes, tau, o.f1, o.f2, o.H);
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < 2; ++j) {
+        const Sdf f = prim_sdf(b, j ? y2 : y1, tau, inv_tau);
+        if (j) o.f2 = f;
+        else o.f1 = f;
+      }
+    }
+    return o;
+  }
+  return body_sdf2_h(b, y1, y2, tau, inv_tau);
+}
+template <int kRole, int kCls>
+CM_HD void sdf2h_bwd_of(const Body& b, V3 y1, V3 y2, const Sdf2H& s, float tau, float inv_tau, float phibar1,
+                        float phibar2, V3 gbar2, V3& ybar1, V3& ybar2, V3& dbar) {
+  if (kCls == 1) {
+    if (kRole == 0) {
+      const float* H = s.H;
+      ybar1 += s.f1.g * phibar1;
+      ybar2 += s.f2.g * phibar2 + v3(fmaf(H[0], gbar2.x, fmaf(H[1], gbar2.y, H[2] * gbar2.z)),
+                                     fmaf(H[1], gbar2.x, fmaf(H[3], gbar2.y, H[4] * gbar2.z)),
+                                     fmaf(H[2], gbar2.x, fmaf(H[4], gbar2.y, H[5] * gbar2.z)));
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < 2; ++j) {
+        V3 yb = v3(0.f, 0.f, 0.f);
+        prim_sdf_bwd(b, j ? y2 : y1, j ? s.f2 : s.f1, tau, inv_tau, j ? phibar2 : phibar1,
+                     j ? gbar2 : v3(0.f, 0.f, 0.f), yb, dbar);
+        if (j) ybar2 += yb;
+        else ybar1 += yb;
+      }
+    }
+    return;
+  }
+  body_sdf2_h_bwd(b, y1, y2, s, tau, inv_tau, phibar1, phibar2, gbar2, ybar1, ybar2, dbar);
+}
+
 // One point of body_sdf2_h / body_sdf2_h_bwd.
 struct Sdf1H {
   Sdf f;
@@ -597,13 +661,16 @@ CM_HD V3 xyz(float4 f) { return v3(f.x, f.y, f.z); }
 // Endpoint adjoints -> relative pose, dims of both bodies and the pre-selected edges'
 // exports: a0b, a1b for A's endpoints in B's frame, l0x, l1x added to them in A's
 // own frame, b0b, b1b for B's.
+template <int kCls = 0>
 CM_HD void endpoints_bwd(const Frame& F, const Body& A, const Body& B, const EEGeom& g, V3 a0b, V3 a1b, V3 l0x,
                          V3 l1x, V3 b0b, V3 b1b, Adj& adj, float* eAexp, float* eBexp) {
   const V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L), b0 = xyz(g.b0), b1 = xyz(g.b1);
   const V3 l0 = push_point_bwd(F, a0L, a0b, adj) + l0x;
   const V3 l1 = push_point_bwd(F, a1L, a1b, adj) + l1x;
-  map_vertex_bwd(A.kind, a0L, g.a0L.w, A.dims, l0, adj.dA);
-  map_vertex_bwd(A.kind, a1L, g.a1L.w, A.dims, l1, adj.dA);
+  if (kCls != 1) {  // a hull's vertices are fixed: no dims to map
+    map_vertex_bwd(A.kind, a0L, g.a0L.w, A.dims, l0, adj.dA);
+    map_vertex_bwd(A.kind, a1L, g.a1L.w, A.dims, l1, adj.dA);
+  }
   map_vertex_bwd(B.kind, b0, g.b0.w, B.dims, b0b, adj.dB);
   map_vertex_bwd(B.kind, b1, g.b1.w, B.dims, b1b, adj.dB);
   // pre-selected edges: their endpoints' local adjoints feed the selection's reverse
@@ -620,12 +687,13 @@ CM_HD void endpoints_bwd(const Frame& F, const Body& A, const Body& B, const EEG
 // Witness reverse at a fixed QP result: e1 = a0 + al1 (a1 - a0) in B's frame (e1L
 // likewise in A's frame), e2 = b0 + al2 (b1 - b0).  The endpoints' adjoints at fixed
 // alpha go to the parameters; the alpha adjoints are returned for the QP's reverse.
+template <int kCls = 0>
 CM_HD void witness_direct_bwd(const Frame& F, const Body& A, const Body& B, const EEGeom& g, const QPOut& o, V3 e1b,
                               V3 e1Lb, V3 e2b, Adj& adj, float& ab1, float& ab2, float* eAexp, float* eBexp) {
   const V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
   ab1 = dot(e1b, a1 - a0) + dot(e1Lb, xyz(g.a1L) - xyz(g.a0L));
   ab2 = dot(e2b, b1 - b0);
-  endpoints_bwd(F, A, B, g, e1b * (1.f - o.a1), e1b * o.a1, e1Lb * (1.f - o.a1), e1Lb * o.a1, e2b * (1.f - o.a2),
+  endpoints_bwd<kCls>(F, A, B, g, e1b * (1.f - o.a1), e1b * o.a1, e1Lb * (1.f - o.a1), e1Lb * o.a1, e2b * (1.f - o.a2),
                 e2b * o.a2, adj, eAexp, eBexp);
 }
 
@@ -668,7 +736,7 @@ struct SdfQuad {
 // a polyhedron's planes (sdf is then unused); otherwise they come from `sdf` when
 // given, else from body_sdf2, with the plane-by-plane reverse.  dqp (optional)
 // receives the QP witnesses' distance.
-template <bool kHess = false, class Upstream>
+template <bool kHess = false, int kCls = 0, class Upstream>
 CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float rowL,
                   float colL, const QPOut* stored, Upstream&& up, float& t1, float& t2, Adj& adj,
                   const SdfQuad* sdf = nullptr, float* eAexp = nullptr, float* eBexp = nullptr,
@@ -701,8 +769,8 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
   Sdf2H hB, hA;
   V3 x2 = mulT(F.R, e2 - F.t);
   if (kHess) {
-    hB = body_sdf2_h(B, e1, e2, tau, it);
-    hA = body_sdf2_h(A, x2, e1L, tau, it);
+    hB = sdf2h_of<1, kCls>(B, e1, e2, tau, it);
+    hA = sdf2h_of<0, kCls>(A, x2, e1L, tau, it);
     SB1 = hB.f1;
     SB2 = hB.f2;
     SA2 = hA.f1;
@@ -772,14 +840,14 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
   V3 e2b = -Db + v3(yb2[0], yb2[1], yb2[2]);
   // SDF reverses (one pass per body for its two points)
   if (kHess)
-    body_sdf2_h_bwd(B, e1, e2, hB, tau, it, phibB1, phibB2, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
+    sdf2h_bwd_of<1, kCls>(B, e1, e2, hB, tau, it, phibB1, phibB2, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
   else
     body_sdf2_bwd(B, e1, e2, SB1, SB2, tau, it, phibB1, phibB2, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
   V3 x2b = v3(0.f, 0.f, 0.f), e1Lb = v3(0.f, 0.f, 0.f);
   add_outer(adj.R, nuAb, nuAL);
   if (kHess)
-    body_sdf2_h_bwd(A, x2, e1L, hA, tau, it, phibA2, phibA1, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b, e1Lb,
-                    adj.dA);
+    sdf2h_bwd_of<0, kCls>(A, x2, e1L, hA, tau, it, phibA2, phibA1, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b,
+                          e1Lb, adj.dA);
   else
     body_sdf2_bwd(A, x2, e1L, SA2, SA1, tau, it, phibA2, phibA1, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b,
                   e1Lb, adj.dA);
@@ -791,7 +859,7 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
     e1b = v3(0.f, 0.f, 0.f);
   }
   QPBar qb;
-  witness_direct_bwd(F, A, B, g, o, e1b, e1Lb, e2b, adj, qb.a1, qb.a2, eAexp, eBexp);
+  witness_direct_bwd<kCls>(F, A, B, g, o, e1b, e1Lb, e2b, adj, qb.a1, qb.a2, eAexp, eBexp);
   qb.con = conb;
   return qb;
 }

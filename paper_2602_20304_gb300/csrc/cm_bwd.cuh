@@ -408,6 +408,67 @@ static __device__ __forceinline__ void depth_adjoint_phase(const BwdPair P) {
   adj_reduce(adj, P.bs->adj);
 }
 
+// The reverse sweep's pass over the edge pairs (step 2 of the header) for pair class
+// kCls (0: any kinds; 1: A a hull and B a primitive, see sdf2h_of): the QP (solved here
+// when the forward's record is read), both candidates, their SoftSort reverse and the
+// rest of the element's reverse, keeping t1, t2 and the QP adjoints per edge pair.
+template <int KMAX, int kCls>
+__device__ __forceinline__ void ee_reverse_pass(const BwdPair& P, BwdShared& bs, const float* rec, int64_t ss) {
+  const FwdArgs& a = *P.a;
+  const PairShared& ps = *P.ps;
+  const PairSmem& sm = P.sm;
+  const int K = P.K, neB = P.neB, nee = P.nee;
+  const float it = P.F.inv_tau, k2 = P.F.k2;
+  float *Dm = P.Dm, *T1 = P.T1, *T2 = P.T2, *QA1 = P.QA1, *QA2 = P.QA2, *QCN = P.QCN, *QB = P.QB;
+  float *rowR = P.rowR, *colC = P.colC;
+  Adj adj;
+  adj_zero(adj);
+  SsAcc<KMAX> acc;
+  ss_acc_zero(acc);
+  for (int i = threadIdx.x; i < nee; i += blockDim.x) {
+    const int k = i / neB, l = i - k * neB;
+    const EEGeom gg = ee_geom(a, ps, sm, k, l);
+    QPOut qs;
+    if (rec) {  // the QP result and the distance matrix for the last pass
+      qs = qp_solve(qp_setup(xyz(gg.a0), xyz(gg.a1), xyz(gg.b0), xyz(gg.b1), a.p.w_reg), a.p.w_reg, a.p);
+      QA1[i] = qs.a1;
+      QA2[i] = qs.a2;
+      QCN[i] = qs.con;
+    } else {
+      qs = QPOut{QA1[i], QA2[i], QCN[i]};
+    }
+    float t1, t2;
+    const QPBar qb = ee_bwd<true, kCls>(P.F, P.bb.A, P.bb.B, a.p, gg, sm.rowL[k], sm.colL[l], &qs,
+           [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
+             // both candidates through one copy of the SoftSort reverse
+#pragma unroll 1
+             for (int j = 0; j < 2; ++j) {
+               float yc[8], yb[8], sb;
+#pragma unroll
+               for (int c = 0; c < 8; ++c) yc[c] = j ? cc.y2[c] : cc.y1[c];
+               ss_bwd<KMAX>(bs, K, it, k2, yc, j ? cc.s2 : cc.s1, yb, sb, acc);
+#pragma unroll
+               for (int c = 0; c < 8; ++c) {
+                 if (j) yb2[c] = yb[c];
+                 else yb1[c] = yb[c];
+               }
+               if (j) sb2 = sb;
+               else sb1 = sb;
+             }
+           },
+           t1, t2, adj, nullptr, eAexp_of(P, k), eBexp_of(P, l), rec ? Dm + i : nullptr);
+    T1[i] = t1;
+    T2[i] = t2;
+    QB[i] = qb.a1;
+    QB[ss + i] = qb.a2;
+    QB[2 * ss + i] = qb.con;
+    atomicAdd(&rowR[k], t1);
+    atomicAdd(&colC[l], t2);
+  }
+  ss_finish<KMAX>(acc, K, it, bs);
+  adj_reduce(adj, bs.adj);
+}
+
 template <int kMinBlocks, int KMAX>
 __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a, const float* grad_out,
                                                                  float* grad_poses, float* grad_dims) {
@@ -614,54 +675,8 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     P.nvs = nvs; P.neB = neB; P.nee = nee; P.K = K;
     P.sadj = sadj;
     vs_reverse_phase<KMAX>(P);
-    {
-      Adj adj;
-      adj_zero(adj);
-      SsAcc<KMAX> acc;
-      ss_acc_zero(acc);
-      for (int i = threadIdx.x; i < nee; i += blockDim.x) {
-        const int k = i / neB, l = i - k * neB;
-        const EEGeom gg = ee_geom(a, ps, sm, k, l);
-        QPOut qs;
-        if (rec) {  // the QP result and the distance matrix for the last pass
-          qs = qp_solve(qp_setup(xyz(gg.a0), xyz(gg.a1), xyz(gg.b0), xyz(gg.b1), a.p.w_reg), a.p.w_reg, a.p);
-          QA1[i] = qs.a1;
-          QA2[i] = qs.a2;
-          QCN[i] = qs.con;
-        } else {
-          qs = QPOut{QA1[i], QA2[i], QCN[i]};
-        }
-        float t1, t2;
-        const QPBar qb = ee_bwd<true>(F, bb.A, bb.B, a.p, gg, sm.rowL[k], sm.colL[l], &qs,
-               [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
-                 // both candidates through one copy of the SoftSort reverse
-#pragma unroll 1
-                 for (int j = 0; j < 2; ++j) {
-                   float yc[8], yb[8], sb;
-#pragma unroll
-                   for (int c = 0; c < 8; ++c) yc[c] = j ? cc.y2[c] : cc.y1[c];
-                   ss_bwd<KMAX>(bs, K, it, k2, yc, j ? cc.s2 : cc.s1, yb, sb, acc);
-#pragma unroll
-                   for (int c = 0; c < 8; ++c) {
-                     if (j) yb2[c] = yb[c];
-                     else yb1[c] = yb[c];
-                   }
-                   if (j) sb2 = sb;
-                   else sb1 = sb;
-                 }
-               },
-               t1, t2, adj, nullptr, eAexp_of(P, k), eBexp_of(P, l), rec ? Dm + i : nullptr);
-        T1[i] = t1;
-        T2[i] = t2;
-        QB[i] = qb.a1;
-        QB[ss + i] = qb.a2;
-        QB[2 * ss + i] = qb.con;
-        atomicAdd(&rowR[k], t1);
-        atomicAdd(&colC[l], t2);
-      }
-      ss_finish<KMAX>(acc, K, it, bs);
-      adj_reduce(adj, bs.adj);
-    }
+    if (ps.kindA == kHull && ps.kindB <= kEllipsoid) ee_reverse_pass<KMAX, 1>(P, bs, rec, ss);
+    else ee_reverse_pass<KMAX, 0>(P, bs, rec, ss);
     __syncthreads();
     if (threadIdx.x < K) fixup_phase(P);
     __syncthreads();
