@@ -427,6 +427,34 @@ CM_HD void body_sdf_h_bwd(const Body& b, V3 y, const Sdf1H& s, float tau, float 
   }
 }
 
+// body_sdf_h / body_sdf_h_bwd of body A (kRole 0) or B (kRole 1) in pair class kCls.
+template <int kRole, int kCls>
+CM_HD Sdf1H sdf1h_of(const Body& b, V3 y, float tau, float inv_tau) {
+  if (kCls == 1) {
+    Sdf1H o;
+    if (kRole == 0) sdf_planes_h(y, b.planes, b.n_planes, tau, o.f, o.H);
+    else o.f = prim_sdf(b, y, tau, inv_tau);
+    return o;
+  }
+  return body_sdf_h(b, y, tau, inv_tau);
+}
+template <int kRole, int kCls>
+CM_HD void sdf1h_bwd_of(const Body& b, V3 y, const Sdf1H& s, float tau, float inv_tau, float phibar, V3 gbar,
+                        V3& ybar, V3& dbar) {
+  if (kCls == 1) {
+    if (kRole == 0) {
+      const float* H = s.H;
+      ybar += s.f.g * phibar + v3(fmaf(H[0], gbar.x, fmaf(H[1], gbar.y, H[2] * gbar.z)),
+                                  fmaf(H[1], gbar.x, fmaf(H[3], gbar.y, H[4] * gbar.z)),
+                                  fmaf(H[2], gbar.x, fmaf(H[4], gbar.y, H[5] * gbar.z)));
+    } else {
+      prim_sdf_bwd(b, y, s.f, tau, inv_tau, phibar, gbar, ybar, dbar);
+    }
+    return;
+  }
+  body_sdf_h_bwd(b, y, s, tau, inv_tau, phibar, gbar, ybar, dbar);
+}
+
 // Adds a local-frame adjoint to a pre-selected item's export slot (shared memory).
 CM_HD void export3(float* dst, V3 v) {
   if (dst) {
@@ -614,26 +642,26 @@ CM_HD V3 push_point_bwd(const Frame& F, V3 v, V3 ybar, Adj& adj) {
 // Candidate of A's vertex (vL local, vB in B's frame) against B, or of B's
 // vertex (vB) against A.  Upstream: yb[8] for (p, d, n, w) in B's frame, sb for
 // the score s = -w d.
-template <bool kOfA>
+template <bool kOfA, int kCls = 0>
 CM_HD void vs_bwd(const Frame& F, const Body& A, const Body& B, float4 vL, V3 vB, const float (&yb)[8], float sb,
                   Adj& adj, float* vexp = nullptr) {
   const float tau = F.tau, it = F.inv_tau;
   if (kOfA) {
-    const Sdf1H fh = body_sdf_h(B, vB, tau, it);
+    const Sdf1H fh = sdf1h_of<1, kCls>(B, vB, tau, it);
     const Sdf& f = fh.f;
     float w = sigmoid(-f.phi * it);
     float wb = yb[7] - sb * f.phi;
     float phib = yb[3] - sb * w - wb * sigmoid_grad_from(w) * it;
     V3 gb = normal_bwd(f.g, tau, v3(yb[4], yb[5], yb[6]));
     V3 pb = v3(yb[0], yb[1], yb[2]);
-    body_sdf_h_bwd(B, vB, fh, tau, it, phib, gb, pb, adj.dB);
+    sdf1h_bwd_of<1, kCls>(B, vB, fh, tau, it, phib, gb, pb, adj.dB);
     V3 vl = v3(vL.x, vL.y, vL.z);
     V3 vbar = push_point_bwd(F, vl, pb, adj);
-    map_vertex_bwd(A.kind, vl, vL.w, A.dims, vbar, adj.dA);
+    if (kCls != 1) map_vertex_bwd(A.kind, vl, vL.w, A.dims, vbar, adj.dA);
     export3(vexp, vbar);
   } else {
     V3 x = mulT(F.R, vB - F.t);
-    const Sdf1H fh = body_sdf_h(A, x, tau, it);
+    const Sdf1H fh = sdf1h_of<0, kCls>(A, x, tau, it);
     const Sdf& f = fh.f;
     float w = sigmoid(-f.phi * it);
     float wb = yb[7] - sb * f.phi;
@@ -643,7 +671,7 @@ CM_HD void vs_bwd(const Frame& F, const Body& A, const Body& B, float4 vL, V3 vB
     add_outer(adj.R, nub, nuL);
     V3 gb = normal_bwd(f.g, tau, mulT(F.R, nub));
     V3 xb = v3(0.f, 0.f, 0.f);
-    body_sdf_h_bwd(A, x, fh, tau, it, phib, gb, xb, adj.dA);
+    sdf1h_bwd_of<0, kCls>(A, x, fh, tau, it, phib, gb, xb, adj.dA);
     V3 pb = v3(yb[0], yb[1], yb[2]) + pull_point_bwd(F, vB, xb, adj);
     map_vertex_bwd(B.kind, vB, vL.w, B.dims, pb, adj.dB);
     export3(vexp, pb);
@@ -868,6 +896,7 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
 // dbar = |e1* - e2*| of the QP witnesses (its direct part to the endpoints, its alpha
 // part added to the candidates' alpha adjoints), then the QP's reverse runs once on
 // the total.
+template <int kCls = 0>
 CM_HD void ee_qp_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float Dbar,
                      const QPOut& o, QPBar qb, Adj& adj, float* eAexp = nullptr, float* eBexp = nullptr) {
   const V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
@@ -893,7 +922,7 @@ CM_HD void ee_qp_bwd(const Frame& F, const Body& A, const Body& B, const Params&
     qp_bwd(q, p.w_reg, p, qb.a1, qb.a2, qb.con, a0b, a1b, b0b, b1b);
     any = true;
   }
-  if (any) endpoints_bwd(F, A, B, g, a0b, a1b, z, z, b0b, b1b, adj, eAexp, eBexp);
+  if (any) endpoints_bwd<kCls>(F, A, B, g, a0b, a1b, z, z, b0b, b1b, adj, eAexp, eBexp);
 }
 
 // ---------------------------------------------------------------- pose epilogue

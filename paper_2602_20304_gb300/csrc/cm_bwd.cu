@@ -1,5 +1,5 @@
 // cm_bwd.cu -- dispatch of the adjoint kernel builds (instantiated in
-// cm_bwd_k8.cu and cm_bwd_k16.cu, see cm_bwd.cuh).
+// cm_bwd_k8.cu, cm_bwd_k8b.cu, cm_bwd_k16.cu and cm_bwd_k16b.cu, see cm_bwd.cuh).
 #include "cm_bwd.cuh"
 
 namespace cm {
@@ -8,7 +8,8 @@ extern template cudaError_t launch_bwd_t<1, 8>(const FwdArgs&, const float*, flo
 extern template cudaError_t launch_bwd_t<2, 8>(const FwdArgs&, const float*, float*, float*, int, int, cudaStream_t);
 extern template cudaError_t launch_bwd_t<1, 16>(const FwdArgs&, const float*, float*, float*, int, int, cudaStream_t);
 extern template cudaError_t launch_bwd_t<2, 16>(const FwdArgs&, const float*, float*, float*, int, int, cudaStream_t);
-int bwd_occupancy(int mb, int block, int smem_bytes);
+int bwd_occupancy_1(int block, int smem_bytes);
+int bwd_occupancy_2(int block, int smem_bytes);
 
 cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_poses, float* grad_dims, int grid,
                        int block, int per_sm, cudaStream_t s) {
@@ -21,7 +22,8 @@ cudaError_t launch_bwd(const FwdArgs& a, const float* grad_out, float* grad_pose
 }
 
 int bwd_max_blocks_per_sm(int block, int smem_bytes, int per_sm) {
-  return bwd_occupancy((per_sm == 1 || smem_bytes > kBwdSmem2) ? 1 : 2, block, smem_bytes);
+  return (per_sm == 1 || smem_bytes > kBwdSmem2) ? bwd_occupancy_1(block, smem_bytes)
+                                                 : bwd_occupancy_2(block, smem_bytes);
 }
 
 }  // namespace cm

@@ -24,8 +24,9 @@
 #include "cm_adjoint.cuh"
 #include "cm_pair.cuh"
 
-// The kernel builds are instantiated in cm_bwd_k8.cu (K <= 8) and
-// cm_bwd_k16.cu (K <= 16), compiled in parallel; cm_bwd.cu dispatches.
+// The kernel builds are instantiated one per translation unit in cm_bwd_k8.cu,
+// cm_bwd_k8b.cu (K <= 8), cm_bwd_k16.cu, cm_bwd_k16b.cu (K <= 16), compiled in
+// parallel; cm_bwd.cu dispatches.
 
 namespace cm {
 
@@ -220,7 +221,7 @@ __device__ __forceinline__ void ss_finish(SsAcc<KMAX>& acc, int K, float it, Bwd
 }
 
 // Vertex-SDF reverse of this thread's candidates.
-template <int KMAX>
+template <int KMAX, int kCls>
 __device__ __forceinline__ void vs_reverse_phase(const BwdPair P) {
   const PairShared& ps = *P.ps;
   Adj adj;
@@ -232,16 +233,19 @@ __device__ __forceinline__ void vs_reverse_phase(const BwdPair P) {
     const float s = vs_candidate(ps, P.sm, P.bb, c, y);
     float yb[8], sb;
     ss_bwd<KMAX>(*P.bs, P.K, P.F.inv_tau, P.F.k2, y, s, yb, sb, acc);
-    if (c < ps.nvA) vs_bwd<true>(P.F, P.bb.A, P.bb.B, P.sm.vAl[c], ld3(P.sm.vA[c]), yb, sb, adj, vexp_of(P, c));
+    if (c < ps.nvA)
+      vs_bwd<true, kCls>(P.F, P.bb.A, P.bb.B, P.sm.vAl[c], ld3(P.sm.vA[c]), yb, sb, adj, vexp_of(P, c));
     else
-      vs_bwd<false>(P.F, P.bb.A, P.bb.B, P.sm.vB[c - ps.nvA], ld3(P.sm.vB[c - ps.nvA]), yb, sb, adj, vexp_of(P, c));
+      vs_bwd<false, kCls>(P.F, P.bb.A, P.bb.B, P.sm.vB[c - ps.nvA], ld3(P.sm.vB[c - ps.nvA]), yb, sb, adj,
+                          vexp_of(P, c));
   }
   ss_finish<KMAX>(acc, P.K, P.F.inv_tau, *P.bs);
   adj_reduce(adj, P.bs->adj);
 }
 
 // The K selected scores pass dL/d s^_k to their own candidates (threads < K).
-static __device__ __forceinline__ void fixup_phase(const BwdPair P) {
+template <int kCls>
+__device__ __forceinline__ void fixup_phase(const BwdPair P) {
   const PairShared& ps = *P.ps;
   const int k = threadIdx.x;
   const int id = P.bs->sid[k];
@@ -250,15 +254,16 @@ static __device__ __forceinline__ void fixup_phase(const BwdPair P) {
   Adj adj;
   adj_zero(adj);
   if (id >= 0 && id < P.nvs) {
-    if (id < ps.nvA) vs_bwd<true>(P.F, P.bb.A, P.bb.B, P.sm.vAl[id], ld3(P.sm.vA[id]), zero, sx, adj, vexp_of(P, id));
+    if (id < ps.nvA) vs_bwd<true, kCls>(P.F, P.bb.A, P.bb.B, P.sm.vAl[id], ld3(P.sm.vA[id]), zero, sx, adj, vexp_of(P, id));
     else
-      vs_bwd<false>(P.F, P.bb.A, P.bb.B, P.sm.vB[id - ps.nvA], ld3(P.sm.vB[id - ps.nvA]), zero, sx, adj,
+      vs_bwd<false, kCls>(P.F, P.bb.A, P.bb.B, P.sm.vB[id - ps.nvA], ld3(P.sm.vB[id - ps.nvA]), zero, sx, adj,
                     vexp_of(P, id));
   } else if (id >= P.nvs) {
     const int e = id - P.nvs, i = e >> 1, b = e & 1, kk = i / P.neB, ll = i - kk * P.neB;
     float t1, t2;
     const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
-    const QPBar qb = ee_bwd<true>(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, ps, P.sm, kk, ll), P.sm.rowL[kk], P.sm.colL[ll], &qs,
+    const QPBar qb = ee_bwd<true, kCls>(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, ps, P.sm, kk, ll), P.sm.rowL[kk],
+                                        P.sm.colL[ll], &qs,
            [&](const EECand&, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
              for (int c = 0; c < 8; ++c) {
                yb1[c] = 0.f;
@@ -286,6 +291,7 @@ static __device__ __forceinline__ void fixup_phase(const BwdPair P) {
 // Last pass over the edge pairs: the distance-matrix adjoint through the
 // nearest-neighbour softmaxes, then each edge pair's QP reverse once, on the sum of
 // its candidates' and its distance's (alpha, con) adjoints.
+template <int kCls>
 __device__ __forceinline__ void qp_phase(const BwdPair P) {
   Adj adj;
   adj_zero(adj);
@@ -297,8 +303,8 @@ __device__ __forceinline__ void qp_phase(const BwdPair P) {
     const float Db = (nn1 * P.rowR[k] - P.T1[i] + nn2 * P.colC[l] - P.T2[i]) * it;
     const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
     const QPBar qb{P.QB[i], P.QB[P.qbs + i], P.QB[2 * P.qbs + i]};
-    ee_qp_bwd(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, *P.ps, P.sm, k, l), Db, qs, qb, adj, eAexp_of(P, k),
-              eBexp_of(P, l));
+    ee_qp_bwd<kCls>(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, *P.ps, P.sm, k, l), Db, qs, qb, adj, eAexp_of(P, k),
+                    eBexp_of(P, l));
   }
   adj_reduce(adj, P.bs->adj);
 }
@@ -674,13 +680,23 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     P.qbs = ss;
     P.nvs = nvs; P.neB = neB; P.nee = nee; P.K = K;
     P.sadj = sadj;
-    vs_reverse_phase<KMAX>(P);
-    if (ps.kindA == kHull && ps.kindB <= kEllipsoid) ee_reverse_pass<KMAX, 1>(P, bs, rec, ss);
-    else ee_reverse_pass<KMAX, 0>(P, bs, rec, ss);
+    // the common pair class (A a hull, B a primitive) runs code specialised for it
+    const bool cls1 = ps.kindA == kHull && ps.kindB <= kEllipsoid;
+    if (cls1) {
+      vs_reverse_phase<KMAX, 1>(P);
+      ee_reverse_pass<KMAX, 1>(P, bs, rec, ss);
+    } else {
+      vs_reverse_phase<KMAX, 0>(P);
+      ee_reverse_pass<KMAX, 0>(P, bs, rec, ss);
+    }
     __syncthreads();
-    if (threadIdx.x < K) fixup_phase(P);
+    if (threadIdx.x < K) {
+      if (cls1) fixup_phase<1>(P);
+      else fixup_phase<0>(P);
+    }
     __syncthreads();
-    qp_phase(P);
+    if (cls1) qp_phase<1>(P);
+    else qp_phase<0>(P);
     __syncthreads();
     if (sadj) {  // pre-selection: stage the original geometry again, then its reverse
       if (threadIdx.x == 0) {
