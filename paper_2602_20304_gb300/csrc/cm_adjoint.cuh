@@ -343,14 +343,6 @@ CM_HD void body_sdf2_h_bwd(const Body& b, V3 y1, V3 y2, const Sdf2H& s, float ta
 // Pair classes of the edge-pair reverse: 0 any kinds; 1 A a polyhedron (hull) and B
 // a box, capsule, cylinder or ellipsoid -- the common case, compiled without the
 // kind dispatch and the branches the other kinds need.
-CM_HD Sdf prim_sdf(const Body& b, V3 y, float tau, float inv_tau) {
-  switch (b.kind) {
-    case kBox: return sdf_box(y, b.dims, tau, inv_tau);
-    case kEllipsoid: return sdf_ellipsoid(y, b.dims);
-    case kCapsule: return sdf_capsule(y, b.dims.x, b.dims.y, tau, inv_tau);
-    default: return sdf_cylinder(y, b.dims.x, b.dims.y, tau, inv_tau);
-  }
-}
 CM_HD void prim_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_tau, float phibar, V3 gbar,
                         V3& ybar, V3& dbar) {
   switch (b.kind) {

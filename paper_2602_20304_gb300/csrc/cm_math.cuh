@@ -574,6 +574,16 @@ CM_HD Sdf body_sdf(const Body& b, V3 y, float tau, float inv_tau) {
   }
 }
 
+// A box, capsule, cylinder or ellipsoid: body_sdf without the polyhedron and
+// superquadric branches (for code compiled for a known pair class).
+CM_HD Sdf prim_sdf(const Body& b, V3 y, float tau, float inv_tau) {
+  switch (b.kind) {
+    case kBox: return sdf_box(y, b.dims, tau, inv_tau);
+    case kEllipsoid: return sdf_ellipsoid(y, b.dims);
+    case kCapsule: return sdf_capsule(y, b.dims.x, b.dims.y, tau, inv_tau);
+    default: return sdf_cylinder(y, b.dims.x, b.dims.y, tau, inv_tau);
+  }
+}
 // A body's SDF at two points: o1 for its value at y1, o2 for its gradient at y2.
 CM_HD void body_sdf2(const Body& b, V3 y1, V3 y2, float tau, float inv_tau, Sdf& o1, Sdf& o2) {
   if (b.kind == kHull) {

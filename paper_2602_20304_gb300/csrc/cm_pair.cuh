@@ -281,14 +281,13 @@ __device__ __forceinline__ Witness ee_witness(const EdgePair& e, const Params& p
 // A's normal at its own witness is evaluated from A's local vertices: the SDF
 // normal near a mesh corner turns at a rate ~1/tau, and a frame round trip of
 // e1* would add FP32 position error that the soft sign then amplifies.
-// sdf_out (optional): the four SDF evaluations of the element, kept for the
-// adjoint as 10 arrays of stride sdf_stride at index idx: phi_B(e1*), phi_B(e2*),
-// grad_B(e2*) (3), phi_A(e2*), phi_A(e1*), grad_A(e1*) in A's frame (3).
+// kCls 1: A is a hull and B a box, capsule, cylinder or ellipsoid (compiled without
+// the other kinds' branches); 0: any kinds.
+template <int kCls = 0>
 __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSmem& sm,
                                               const PairBodies& bb, const EdgePair& ep,
                                               const Witness& w, float rowL, float colL,
-                                              float (&y1)[8], float (&y2)[8], float& s1, float& s2,
-                                              float* sdf_out = nullptr, int64_t sdf_stride = 0, int idx = 0) {
+                                              float (&y1)[8], float (&y2)[8], float& s1, float& s2) {
   const float tau = ps.tau, it = ps.inv_tau;
   const int es = sm.es, k = ep.k;
   const V3 la0 = v3(sm.eAl6[k], sm.eAl6[es + k], sm.eAl6[2 * es + k]);
@@ -305,16 +304,18 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
   }
   V3 nbar = delta * rsq(dot(delta, delta) + tau * tau);
   Sdf B_e1, B_e2, A_e2, A_e1;
-  body_sdf2(bb.B, e1, e2, tau, it, B_e1, B_e2);         // phi_B(e1*), nu_B(e2*)
+  if (kCls == 1) {                                     // phi_B(e1*), nu_B(e2*)
+    B_e1 = prim_sdf(bb.B, e1, tau, it);
+    B_e2 = prim_sdf(bb.B, e2, tau, it);
+  } else {
+    body_sdf2(bb.B, e1, e2, tau, it, B_e1, B_e2);
+  }
   const V3 x2 = mulT(ps.Rrel, e2 - ps.trel);
   // A hull's sums without a shift (sdf_planes_ee) while e1* is within a scaled
-  // distance of 60 of A's edge; the values kept for the adjoint are then tau ln S (a
-  // sum that underflows, a point deeper than 126 tau ln 2 inside every plane, keeps
-  // the value at that depth: sigma(-phi / tau) is exactly 1 either way and the
-  // adjoint's plane pass stays finite).
+  // distance of 60 of A's edge (see sdf_planes_ee).
   float pen2 = -1.f, safe1 = 1.f;
   bool fast = false;
-  if (!ps.trace && bb.A.kind == kHull) {
+  if (!ps.trace && (kCls == 1 || bb.A.kind == kHull)) {
     const V3 t1 = la1 - la0;
     const float ex = fmaxf(fmaxf(-w.qp.a1, w.qp.a1 - 1.f), 0.f) * ps.k2;
     fast = ex * ex * dot(t1, t1) <= 3600.f;
@@ -324,20 +325,11 @@ __device__ __forceinline__ void ee_candidates(const PairShared& ps, const PairSm
     sdf_planes_ee(x2, e1l, bb.A.planes, bb.A.n_planes, tau, S1, S2, A_e1.g);
     pen2 = rcp(1.f + S1);
     safe1 = rcp(1.f + S2);
-    if (sdf_out) {
-      A_e2.phi = tau * kLn2 * lg2(fmaxf(S1, 1.17549435e-38f));
-      A_e1.phi = tau * kLn2 * lg2(fmaxf(S2, 1.17549435e-38f));
-    }
   } else {
-    body_sdf2(bb.A, x2, e1l, tau, it, A_e2, A_e1);      // phi_A(e2*), nu_A(e1*) in A's frame
+    if (kCls == 1) sdf_planes2(x2, e1l, bb.A.planes, bb.A.n_planes, tau, A_e2, A_e1);
+    else body_sdf2(bb.A, x2, e1l, tau, it, A_e2, A_e1);  // phi_A(e2*), nu_A(e1*) in A's frame
     pen2 = sigmoid(-A_e2.phi * it);
     safe1 = sigmoid(-A_e1.phi * it);
-  }
-  if (sdf_out) {
-    float* o = sdf_out + idx;
-    const int64_t st = sdf_stride;
-    o[0] = B_e1.phi; o[st] = B_e2.phi; o[2 * st] = B_e2.g.x; o[3 * st] = B_e2.g.y; o[4 * st] = B_e2.g.z;
-    o[5 * st] = A_e2.phi; o[6 * st] = A_e1.phi; o[7 * st] = A_e1.g.x; o[8 * st] = A_e1.g.y; o[9 * st] = A_e1.g.z;
   }
   A_e1.g = mul(ps.Rrel, A_e1.g);
   V3 nuB = normal_of(B_e2.g, tau);
