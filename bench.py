@@ -667,9 +667,9 @@ def witness_rates(api, n=10_000_000, steps=5):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pair of one forward and
 # one adjoint launch of the current kernels on the full 65536-pair headline batch, from one
 # single-pass ncu capture of each (default launch shape; profiles/headline_dram_65536.md):
-# forward 0.617 + 3.010 GB, adjoint 8.526 + 14.819 GB per launch.
-FWD_TRAFFIC_PER_PAIR = (0.616987e9 + 3.009642e9) / 65536
-BWD_TRAFFIC_PER_PAIR = (8.526086e9 + 14.818653e9) / 65536
+# forward 0.622 + 3.013 GB, adjoint 7.854 + 13.486 GB per launch.
+FWD_TRAFFIC_PER_PAIR = (0.622416e9 + 3.013445e9) / 65536
+BWD_TRAFFIC_PER_PAIR = (7.854090e9 + 13.485996e9) / 65536
 
 
 def main():
