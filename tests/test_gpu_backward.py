@@ -163,3 +163,23 @@ def test_autograd_wrapper(engine):
     rp, rd = engine.backward(pg, poses.detach(), dims.detach(), tau, go)
     # the adjoint sums with atomics, so two launches agree to rounding, not bitwise
     assert torch.allclose(gp, rp, rtol=1e-4, atol=1e-6) and torch.allclose(gd, rd, rtol=1e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("pkw", [dict(top_verts=6, top_edges=5), dict(trace_iters=3), dict(K=16),
+                                 dict(flags=1, K=4), dict(flags=2, K=4)],
+                         ids=["preselect", "trace", "K16", "vertex-only", "one-sided"])
+def test_records_on_every_path(engine, pkw):
+    """The record-driven adjoint on pre-selection, sphere tracing, the K <= 16 builds and the
+    simplified modes: the same gradients as the adjoint that recomputes the forward, and the
+    oracle's on a sample of the pairs."""
+    w = synth.make_config(2, 24)
+    K = pkw.get("K", 8)
+    g = np.random.default_rng(17).normal(size=(w.n_pairs, K, 8))
+    a = np.concatenate(gpu_grad(engine, w, g, "recompute", **pkw)[:2], 1)
+    got, gd, params = gpu_grad(engine, w, g, "records", **pkw)
+    b = np.concatenate([got, gd], 1)
+    rel = rel_errors(b, a)
+    print(pkw, "records vs recompute, worst relative", rel.max())
+    assert rel.max() <= 1e-3
+    idx = np.arange(0, w.n_pairs, 3)
+    check_grad(b[idx], w, params, g[idx], idx, what=f"records {pkw}")
