@@ -259,41 +259,6 @@ CM_HD void body_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_
   }
 }
 
-// Reverse of sdf_planes2: the value at y1 (adjoint phibar1) and the value and
-// gradient at y2 (adjoints phibar2, gbar2) in one pass over the (pre-scaled) planes.
-CM_HD void sdf_planes2_bwd(V3 y1, V3 y2, const float4* P, int nP, const Sdf& f1, const Sdf& f2, float inv_tau,
-                           float phibar1, float phibar2, V3 gbar2, V3& ybar1, V3& ybar2) {
-  const float k = inv_tau * kLog2e, ik = rcp(k);
-  const float2 X = make_float2(y1.x, y2.x), Y = make_float2(y1.y, y2.y), Z = make_float2(y1.z, y2.z);
-  const float2 mk = make_float2(-f1.phi * k, -f2.phi * k);
-  const float base2 = phibar2 - dot(gbar2, f2.g) * inv_tau;
-  const float gk = inv_tau * ik;
-  float2 ax = dup2(0.f), ay = dup2(0.f), az = dup2(0.f);
-  for (int i = 0; i < nP; ++i) {
-    const float4 q = P[i];
-    const float2 z = ffma2(dup2(q.x), X, ffma2(dup2(q.y), Y, ffma2(dup2(q.z), Z, dup2(-q.w))));
-    const float2 d = fadd2(z, mk);
-    const float p1 = ex2(d.x), p2 = ex2(d.y);
-    const float2 sb = make_float2(p1 * phibar1, p2 * (base2 + (gbar2.x * q.x + gbar2.y * q.y + gbar2.z * q.z) * gk));
-    ax = ffma2(sb, dup2(q.x), ax);
-    ay = ffma2(sb, dup2(q.y), ay);
-    az = ffma2(sb, dup2(q.z), az);
-  }
-  ybar1 += v3(ax.x, ay.x, az.x) * ik;
-  ybar2 += v3(ax.y, ay.y, az.y) * ik;
-}
-
-// Reverse of body_sdf2 (value at y1; value and gradient at y2).
-CM_HD void body_sdf2_bwd(const Body& b, V3 y1, V3 y2, const Sdf& f1, const Sdf& f2, float tau, float inv_tau,
-                         float phibar1, float phibar2, V3 gbar2, V3& ybar1, V3& ybar2, V3& dbar) {
-  if (b.kind == kHull) {
-    sdf_planes2_bwd(y1, y2, b.planes, b.n_planes, f1, f2, inv_tau, phibar1, phibar2, gbar2, ybar1, ybar2);
-  } else {
-    body_sdf_bwd(b, y1, f1, tau, inv_tau, phibar1, v3(0.f, 0.f, 0.f), ybar1, dbar);
-    body_sdf_bwd(b, y2, f2, tau, inv_tau, phibar2, gbar2, ybar2, dbar);
-  }
-}
-
 // A body's SDF at the two points an edge pair uses, with what the reverse needs
 // (see sdf_planes2_h): value and gradient at y1 and at y2, and for a polyhedron
 // the Hessian at y2.
@@ -746,21 +711,13 @@ struct EECand {
   float s1, s2;
 };
 
-// The four SDF evaluations of an edge pair (values at e1*, e2* of B and at
-// e2*, e1* of A; gradients at e2* of B and at e1* of A, the latter in A's frame).
-struct SdfQuad {
-  Sdf B1, B2, A2, A1;
-};
-
-// kHess: the SDFs come from body_sdf2_h and their reverses need no second pass over
-// a polyhedron's planes (sdf is then unused); otherwise they come from `sdf` when
-// given, else from body_sdf2, with the plane-by-plane reverse.  dqp (optional)
-// receives the QP witnesses' distance.
-template <bool kHess = false, int kCls = 0, class Upstream>
+// The SDFs come from sdf2h_of (a polyhedron's value, gradient and Hessian in one pass
+// over its planes), so their reverses need no second pass; kCls is the pair class (see
+// sdf2h_of).  dqp (optional) receives the QP witnesses' distance.
+template <int kCls = 0, class Upstream>
 CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g, float rowL,
                   float colL, const QPOut* stored, Upstream&& up, float& t1, float& t2, Adj& adj,
-                  const SdfQuad* sdf = nullptr, float* eAexp = nullptr, float* eBexp = nullptr,
-                  float* dqp = nullptr) {
+                  float* eAexp = nullptr, float* eBexp = nullptr, float* dqp = nullptr) {
   const float tau = F.tau, it = F.inv_tau;
   V3 a0 = xyz(g.a0), a1 = xyz(g.a1), b0 = xyz(g.b0), b1 = xyz(g.b1);
   V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L);
@@ -785,25 +742,10 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
   float dbar = sqrt_(r2);
   float qn = rsq(r2 + tau * tau);
   V3 nbar = D * qn;
-  Sdf SB1, SB2, SA2, SA1;
-  Sdf2H hB, hA;
   V3 x2 = mulT(F.R, e2 - F.t);
-  if (kHess) {
-    hB = sdf2h_of<1, kCls>(B, e1, e2, tau, it);
-    hA = sdf2h_of<0, kCls>(A, x2, e1L, tau, it);
-    SB1 = hB.f1;
-    SB2 = hB.f2;
-    SA2 = hA.f1;
-    SA1 = hA.f2;
-  } else if (sdf) {
-    SB1 = sdf->B1;
-    SB2 = sdf->B2;
-    SA2 = sdf->A2;
-    SA1 = sdf->A1;
-  } else {
-    body_sdf2(B, e1, e2, tau, it, SB1, SB2);
-    body_sdf2(A, x2, e1L, tau, it, SA2, SA1);
-  }
+  const Sdf2H hB = sdf2h_of<1, kCls>(B, e1, e2, tau, it);   // phi_B(e1*), nu_B(e2*)
+  const Sdf2H hA = sdf2h_of<0, kCls>(A, x2, e1L, tau, it);  // phi_A(e2*), nu_A(e1*) in A's frame
+  const Sdf &SB1 = hB.f1, &SB2 = hB.f2, &SA2 = hA.f1, &SA1 = hA.f2;
   V3 nuB = normal_of(SB2.g, tau);
   V3 nuAL = normal_of(SA1.g, tau);
   V3 nuA = mul(F.R, nuAL);
@@ -859,18 +801,11 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
   V3 e1b = Db + v3(yb1[0], yb1[1], yb1[2]);
   V3 e2b = -Db + v3(yb2[0], yb2[1], yb2[2]);
   // SDF reverses (one pass per body for its two points)
-  if (kHess)
-    sdf2h_bwd_of<1, kCls>(B, e1, e2, hB, tau, it, phibB1, phibB2, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
-  else
-    body_sdf2_bwd(B, e1, e2, SB1, SB2, tau, it, phibB1, phibB2, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
+  sdf2h_bwd_of<1, kCls>(B, e1, e2, hB, tau, it, phibB1, phibB2, normal_bwd(SB2.g, tau, nuBb), e1b, e2b, adj.dB);
   V3 x2b = v3(0.f, 0.f, 0.f), e1Lb = v3(0.f, 0.f, 0.f);
   add_outer(adj.R, nuAb, nuAL);
-  if (kHess)
-    sdf2h_bwd_of<0, kCls>(A, x2, e1L, hA, tau, it, phibA2, phibA1, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b,
-                          e1Lb, adj.dA);
-  else
-    body_sdf2_bwd(A, x2, e1L, SA2, SA1, tau, it, phibA2, phibA1, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b,
-                  e1Lb, adj.dA);
+  sdf2h_bwd_of<0, kCls>(A, x2, e1L, hA, tau, it, phibA2, phibA1, normal_bwd(SA1.g, tau, mulT(F.R, nuAb)), x2b, e1Lb,
+                        adj.dA);
   e2b += pull_point_bwd(F, e2, x2b, adj);
   if (nt) {  // traced e1 = R_rel e1L + t_rel; back through both traces to the QP witnesses
     e1Lb += push_point_bwd(F, e1L, e1b, adj);

@@ -262,7 +262,7 @@ __device__ __forceinline__ void fixup_phase(const BwdPair P) {
     const int e = id - P.nvs, i = e >> 1, b = e & 1, kk = i / P.neB, ll = i - kk * P.neB;
     float t1, t2;
     const QPOut qs{P.QA1[i], P.QA2[i], P.QCN[i]};
-    const QPBar qb = ee_bwd<true, kCls>(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, ps, P.sm, kk, ll), P.sm.rowL[kk],
+    const QPBar qb = ee_bwd<kCls>(P.F, P.bb.A, P.bb.B, P.a->p, ee_geom(*P.a, ps, P.sm, kk, ll), P.sm.rowL[kk],
                                         P.sm.colL[ll], &qs,
            [&](const EECand&, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
              for (int c = 0; c < 8; ++c) {
@@ -272,7 +272,7 @@ __device__ __forceinline__ void fixup_phase(const BwdPair P) {
              sb1 = b == 0 ? sx : 0.f;
              sb2 = b == 1 ? sx : 0.f;
            },
-           t1, t2, adj, nullptr, eAexp_of(P, kk), eBexp_of(P, ll));
+           t1, t2, adj, eAexp_of(P, kk), eBexp_of(P, ll));
     atomicAdd(&P.T1[i], t1);
     atomicAdd(&P.T2[i], t2);
     atomicAdd(&P.rowR[kk], t1);
@@ -444,7 +444,7 @@ __device__ __forceinline__ void ee_reverse_pass(const BwdPair& P, BwdShared& bs,
       qs = QPOut{QA1[i], QA2[i], QCN[i]};
     }
     float t1, t2;
-    const QPBar qb = ee_bwd<true, kCls>(P.F, P.bb.A, P.bb.B, a.p, gg, sm.rowL[k], sm.colL[l], &qs,
+    const QPBar qb = ee_bwd<kCls>(P.F, P.bb.A, P.bb.B, a.p, gg, sm.rowL[k], sm.colL[l], &qs,
            [&](const EECand& cc, float (&yb1)[8], float& sb1, float (&yb2)[8], float& sb2) {
              // both candidates through one copy of the SoftSort reverse
 #pragma unroll 1
@@ -462,7 +462,7 @@ __device__ __forceinline__ void ee_reverse_pass(const BwdPair& P, BwdShared& bs,
                else sb1 = sb;
              }
            },
-           t1, t2, adj, nullptr, eAexp_of(P, k), eBexp_of(P, l), rec ? Dm + i : nullptr);
+           t1, t2, adj, eAexp_of(P, k), eBexp_of(P, l), rec ? Dm + i : nullptr);
     T1[i] = t1;
     T2[i] = t2;
     QB[i] = qb.a1;
