@@ -305,9 +305,10 @@ CM_HD void body_sdf2_h_bwd(const Body& b, V3 y1, V3 y2, const Sdf2H& s, float ta
   }
 }
 
-// Pair classes of the edge-pair reverse: 0 any kinds; 1 A a polyhedron (hull) and B
-// a box, capsule, cylinder or ellipsoid -- the common case, compiled without the
-// kind dispatch and the branches the other kinds need.
+// Pair classes of the reverse: 0 any kinds; 1 A a polyhedron (hull) and B a box,
+// capsule, cylinder or ellipsoid; 2 the other way round -- compiled without the kind
+// dispatch and the branches the other kinds need.  kRole 0 is body A, 1 body B.
+CM_HD constexpr bool is_hull_role(int kRole, int kCls) { return (kCls == 1 && kRole == 0) || (kCls == 2 && kRole == 1); }
 CM_HD void prim_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_tau, float phibar, V3 gbar,
                         V3& ybar, V3& dbar) {
   switch (b.kind) {
@@ -320,9 +321,9 @@ CM_HD void prim_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_
 // body_sdf2_h of body A (kRole 0) or B (kRole 1) in pair class kCls.
 template <int kRole, int kCls>
 CM_HD Sdf2H sdf2h_of(const Body& b, V3 y1, V3 y2, float tau, float inv_tau) {
-  if (kCls == 1) {
+  if (kCls != 0) {
     Sdf2H o;
-    if (kRole == 0) {
+    if (is_hull_role(kRole, kCls)) {
       sdf_planes2_h(y1, y2, b.planes, b.n_planes, tau, o.f1, o.f2, o.H);
     } else {
 #pragma unroll 1
@@ -339,8 +340,8 @@ CM_HD Sdf2H sdf2h_of(const Body& b, V3 y1, V3 y2, float tau, float inv_tau) {
 template <int kRole, int kCls>
 CM_HD void sdf2h_bwd_of(const Body& b, V3 y1, V3 y2, const Sdf2H& s, float tau, float inv_tau, float phibar1,
                         float phibar2, V3 gbar2, V3& ybar1, V3& ybar2, V3& dbar) {
-  if (kCls == 1) {
-    if (kRole == 0) {
+  if (kCls != 0) {
+    if (is_hull_role(kRole, kCls)) {
       const float* H = s.H;
       ybar1 += s.f1.g * phibar1;
       ybar2 += s.f2.g * phibar2 + v3(fmaf(H[0], gbar2.x, fmaf(H[1], gbar2.y, H[2] * gbar2.z)),
@@ -387,9 +388,9 @@ CM_HD void body_sdf_h_bwd(const Body& b, V3 y, const Sdf1H& s, float tau, float 
 // body_sdf_h / body_sdf_h_bwd of body A (kRole 0) or B (kRole 1) in pair class kCls.
 template <int kRole, int kCls>
 CM_HD Sdf1H sdf1h_of(const Body& b, V3 y, float tau, float inv_tau) {
-  if (kCls == 1) {
+  if (kCls != 0) {
     Sdf1H o;
-    if (kRole == 0) sdf_planes_h(y, b.planes, b.n_planes, tau, o.f, o.H);
+    if (is_hull_role(kRole, kCls)) sdf_planes_h(y, b.planes, b.n_planes, tau, o.f, o.H);
     else o.f = prim_sdf(b, y, tau, inv_tau);
     return o;
   }
@@ -398,8 +399,8 @@ CM_HD Sdf1H sdf1h_of(const Body& b, V3 y, float tau, float inv_tau) {
 template <int kRole, int kCls>
 CM_HD void sdf1h_bwd_of(const Body& b, V3 y, const Sdf1H& s, float tau, float inv_tau, float phibar, V3 gbar,
                         V3& ybar, V3& dbar) {
-  if (kCls == 1) {
-    if (kRole == 0) {
+  if (kCls != 0) {
+    if (is_hull_role(kRole, kCls)) {
       const float* H = s.H;
       ybar += s.f.g * phibar + v3(fmaf(H[0], gbar.x, fmaf(H[1], gbar.y, H[2] * gbar.z)),
                                   fmaf(H[1], gbar.x, fmaf(H[3], gbar.y, H[4] * gbar.z)),
@@ -614,7 +615,7 @@ CM_HD void vs_bwd(const Frame& F, const Body& A, const Body& B, float4 vL, V3 vB
     sdf1h_bwd_of<1, kCls>(B, vB, fh, tau, it, phib, gb, pb, adj.dB);
     V3 vl = v3(vL.x, vL.y, vL.z);
     V3 vbar = push_point_bwd(F, vl, pb, adj);
-    if (kCls != 1) map_vertex_bwd(A.kind, vl, vL.w, A.dims, vbar, adj.dA);
+    if (!is_hull_role(0, kCls)) map_vertex_bwd(A.kind, vl, vL.w, A.dims, vbar, adj.dA);
     export3(vexp, vbar);
   } else {
     V3 x = mulT(F.R, vB - F.t);
@@ -652,12 +653,14 @@ CM_HD void endpoints_bwd(const Frame& F, const Body& A, const Body& B, const EEG
   const V3 a0L = xyz(g.a0L), a1L = xyz(g.a1L), b0 = xyz(g.b0), b1 = xyz(g.b1);
   const V3 l0 = push_point_bwd(F, a0L, a0b, adj) + l0x;
   const V3 l1 = push_point_bwd(F, a1L, a1b, adj) + l1x;
-  if (kCls != 1) {  // a hull's vertices are fixed: no dims to map
+  if (!is_hull_role(0, kCls)) {  // a hull's vertices are fixed: no dims to map
     map_vertex_bwd(A.kind, a0L, g.a0L.w, A.dims, l0, adj.dA);
     map_vertex_bwd(A.kind, a1L, g.a1L.w, A.dims, l1, adj.dA);
   }
-  map_vertex_bwd(B.kind, b0, g.b0.w, B.dims, b0b, adj.dB);
-  map_vertex_bwd(B.kind, b1, g.b1.w, B.dims, b1b, adj.dB);
+  if (!is_hull_role(1, kCls)) {
+    map_vertex_bwd(B.kind, b0, g.b0.w, B.dims, b0b, adj.dB);
+    map_vertex_bwd(B.kind, b1, g.b1.w, B.dims, b1b, adj.dB);
+  }
   // pre-selected edges: their endpoints' local adjoints feed the selection's reverse
   if (eAexp) {
     export3(eAexp, l0);

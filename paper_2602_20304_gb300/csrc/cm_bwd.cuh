@@ -680,22 +680,28 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
     P.qbs = ss;
     P.nvs = nvs; P.neB = neB; P.nee = nee; P.K = K;
     P.sadj = sadj;
-    // the common pair class (A a hull, B a primitive) runs code specialised for it
-    const bool cls1 = ps.kindA == kHull && ps.kindB <= kEllipsoid;
-    if (cls1) {
+    // a hull against a primitive (either way round) runs code specialised for it
+    const int cls = (ps.kindA == kHull && ps.kindB <= kEllipsoid) ? 1
+                    : (ps.kindA <= kEllipsoid && ps.kindB == kHull) ? 2 : 0;
+    if (cls == 1) {
       vs_reverse_phase<KMAX, 1>(P);
       ee_reverse_pass<KMAX, 1>(P, bs, rec, ss);
+    } else if (cls == 2) {
+      vs_reverse_phase<KMAX, 2>(P);
+      ee_reverse_pass<KMAX, 2>(P, bs, rec, ss);
     } else {
       vs_reverse_phase<KMAX, 0>(P);
       ee_reverse_pass<KMAX, 0>(P, bs, rec, ss);
     }
     __syncthreads();
     if (threadIdx.x < K) {
-      if (cls1) fixup_phase<1>(P);
+      if (cls == 1) fixup_phase<1>(P);
+      else if (cls == 2) fixup_phase<2>(P);
       else fixup_phase<0>(P);
     }
     __syncthreads();
-    if (cls1) qp_phase<1>(P);
+    if (cls == 1) qp_phase<1>(P);
+    else if (cls == 2) qp_phase<2>(P);
     else qp_phase<0>(P);
     __syncthreads();
     if (sadj) {  // pre-selection: stage the original geometry again, then its reverse
