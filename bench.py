@@ -667,9 +667,9 @@ def witness_rates(api, n=10_000_000, steps=5):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pair of one forward and
 # one adjoint launch of the current kernels on the full 65536-pair headline batch, from one
 # single-pass ncu capture of each (default launch shape; profiles/headline_dram_65536.md):
-# forward 0.622 + 3.013 GB, adjoint 7.854 + 13.486 GB per launch.
-FWD_TRAFFIC_PER_PAIR = (0.622416e9 + 3.013445e9) / 65536
-BWD_TRAFFIC_PER_PAIR = (7.854090e9 + 13.485996e9) / 65536
+# forward 0.625 + 3.014 GB, adjoint 7.752 + 13.421 GB per launch.
+FWD_TRAFFIC_PER_PAIR = (0.624633e9 + 3.014153e9) / 65536
+BWD_TRAFFIC_PER_PAIR = (7.751737e9 + 13.421239e9) / 65536
 
 
 def main():
