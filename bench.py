@@ -665,11 +665,44 @@ def witness_rates(api, n=10_000_000, steps=5):
 
 # ----------------------------------------------------------------- our arm
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pair of one forward and
-# one adjoint launch of the current kernels on the full 65536-pair headline batch, from one
-# single-pass ncu capture of each (default launch shape; profiles/headline_dram_65536.md):
-# forward 0.625 + 3.014 GB, adjoint 7.752 + 13.421 GB per launch.
-FWD_TRAFFIC_PER_PAIR = (0.624633e9 + 3.014153e9) / 65536
-BWD_TRAFFIC_PER_PAIR = (7.751737e9 + 13.421239e9) / 65536
+# one adjoint launch of the current kernels on the 65536-pair headline batch, from one
+# single-pass ncu capture of each (`--profile-case headline`, default launch shape):
+# forward 0.520 + 3.016 GB, adjoint 7.520 + 13.416 GB per launch.
+FWD_TRAFFIC_PER_PAIR = (0.519528e9 + 3.016125e9) / 65536
+BWD_TRAFFIC_PER_PAIR = (7.519558e9 + 13.416463e9) / 65536
+
+
+# Workloads of the ncu captures: the 4096-pair hull-vs-primitive setting (``--set full``
+# fits its launches) and the 65536-pair headline batch (single-pass DRAM counters).
+PROFILE_CASES = {"hull4096": lambda: synth.make_config(2), "headline": lambda: headline_workload(0)}
+
+
+def profile_case(name, device, iters):
+    """Forward with records, then the record-driven adjoint, ``iters`` times on the
+    default launch shape (no autotuning, no graph) with a seeded upstream gradient: per
+    iteration one cm_fwd_kernel and one cm_bwd_kernel launch (each after its work-order
+    launch when the shape orders the batch)."""
+    import torch
+    from paper_2602_20304_gb300.engine import Engine, workload_tensors
+    w = PROFILE_CASES[name]()
+    eng = Engine(device)
+    try:
+        ids = eng.add_geometries(w.geoms)
+        pg, poses, dims, tau = workload_tensors(w, id_map=ids)
+        params = eng.params()
+        g = torch.Generator(device="cuda").manual_seed(0)
+        grad_out = torch.randn((w.n_pairs, params.K, 8), device="cuda", generator=g)
+        for _ in range(iters):
+            out, saved = eng.forward_save(pg, poses, dims, tau, params)
+            gp, gd = eng.backward(pg, poses, dims, tau, grad_out, params, saved=saved)
+        torch.cuda.synchronize()
+        eng.check()
+        ok = bool(torch.isfinite(out).all() and torch.isfinite(gp).all() and torch.isfinite(gd).all())
+        print(json.dumps({"profile_case": name, "pairs": w.n_pairs, "iters": iters, "finite": ok}), flush=True)
+        if not ok:
+            raise SystemExit(1)
+    finally:
+        eng.close()
 
 
 def main():
@@ -687,6 +720,9 @@ def main():
                     help="length of the Poisson serving trace at 2000 req/s (0 skips the serving comparison)")
     ap.add_argument("--serve-below-seconds", type=float, default=5.0,
                     help="length of the serving trace offered below capacity (400 req/s)")
+    ap.add_argument("--profile-case", choices=list(PROFILE_CASES),
+                    help="only run forward (with records) then adjoint, warmup + steps times, untimed: "
+                         "the launches the ncu summaries capture")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -702,6 +738,9 @@ def main():
     from paper_2602_20304_gb300.engine import Engine, workload_tensors
 
     torch.cuda.set_device(local)
+    if args.profile_case:
+        profile_case(args.profile_case, local, args.warmup + args.steps)
+        return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 

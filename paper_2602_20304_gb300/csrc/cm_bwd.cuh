@@ -1,13 +1,18 @@
 // cm_bwd.cuh -- adjoint kernel of the contact manifold (sm_103a).
 //
 // Given dL/d out (K x 8 per pair) it returns dL/d poses (14 per pair) and
-// dL/d dims (6 per pair).  Nothing of the forward is stored between the calls:
-// each CTA recomputes its pair's forward (candidates, distance matrix,
-// nearest-neighbour statistics, the SoftSort top-K list and normalisers) and
-// then runs the reverse sweep:
-//   1. SoftSort reverse per candidate (K exponentials) -> dL/d(p, d, n, w) and
-//      dL/d score, while accumulating dL/d s^_k of the K largest scores;
-//      vertex-SDF candidates are backpropagated to the parameters right away;
+// dL/d dims (6 per pair).  No candidate of the forward is stored between the
+// calls.  With the forward's per-pair record (cm_fwd_kernel given a record
+// buffer: the K selected scores, their ids and normalisers, the K rows and the
+// soft row / column minima of the E-E distance matrix) a CTA starts from those
+// reductions; without it the CTA first recomputes them (candidates, distance
+// matrix, nearest-neighbour statistics, the SoftSort top-K list and
+// normalisers).  Either way every candidate is then recomputed in the reverse
+// sweep:
+//   1. SoftSort reverse per candidate (below the K-th score one exponential per
+//      candidate, see ss_bwd) -> dL/d(p, d, n, w) and dL/d score, while
+//      accumulating dL/d s^_k of the K largest scores; vertex-SDF candidates are
+//      backpropagated to the parameters right away;
 //   2. each edge pair's reverse (indicators, sign, SDF normals through their
 //      Hessian-vector products, witnesses at the fixed QP result) except the
 //      nearest-neighbour softmax's coupling across its row and column, kept as
@@ -734,12 +739,10 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
   }
 }
 
-// Two builds of the adjoint kernel: one CTA per SM with up to 255 registers,
-// or two CTAs per SM within 128 registers (spilling to L1); the launch shape's
-// CTAs-per-SM picks one (1 -> the first, otherwise the second).
 // Builds of the adjoint kernel: one CTA per SM with up to 255 registers, or two
-// CTAs per SM within 128 registers (the launch shape's CTAs per SM picks: 1 ->
-// the first); each for K <= 8 and K <= 16 (the SoftSort reverse unrolls to it).
+// CTAs per SM within 128 registers (spilling to L1; the launch shape's CTAs per
+// SM picks: 1 -> the first); each for K <= 8 and K <= 16 (the SoftSort reverse
+// unrolls to it).
 // Dynamic shared memory the two builds are configured for: the two-CTA build
 // takes layouts up to kBwdSmem2, larger ones run the one-CTA build.
 constexpr int kBwdSmem1 = 180 * 1024, kBwdSmem2 = 110 * 1024;
