@@ -318,13 +318,16 @@ CM_HD void prim_sdf_bwd(const Body& b, V3 y, const Sdf& f, float tau, float inv_
     default: sdf_cylinder_bwd(y, b.dims.x, b.dims.y, f, inv_tau, phibar, gbar, ybar, dbar); break;
   }
 }
-// body_sdf2_h of body A (kRole 0) or B (kRole 1) in pair class kCls.
+// body_sdf2_h of body A (kRole 0) or B (kRole 1) in pair class kCls.  `plain`: the
+// polyhedron's sums are taken without a shift (sdf_planes2_h_ee; y2 is the body's own
+// witness within a scaled distance of 60 of its edge).
 template <int kRole, int kCls>
-CM_HD Sdf2H sdf2h_of(const Body& b, V3 y1, V3 y2, float tau, float inv_tau) {
+CM_HD Sdf2H sdf2h_of(const Body& b, V3 y1, V3 y2, float tau, float inv_tau, bool plain = false) {
   if (kCls != 0) {
     Sdf2H o;
     if (is_hull_role(kRole, kCls)) {
-      sdf_planes2_h(y1, y2, b.planes, b.n_planes, tau, o.f1, o.f2, o.H);
+      if (plain) sdf_planes2_h_ee(y1, y2, b.planes, b.n_planes, tau, o.f1, o.f2, o.H);
+      else sdf_planes2_h(y1, y2, b.planes, b.n_planes, tau, o.f1, o.f2, o.H);
     } else {
 #pragma unroll 1
       for (int j = 0; j < 2; ++j) {
@@ -746,8 +749,19 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
   float qn = rsq(r2 + tau * tau);
   V3 nbar = D * qn;
   V3 x2 = mulT(F.R, e2 - F.t);
-  const Sdf2H hB = sdf2h_of<1, kCls>(B, e1, e2, tau, it);   // phi_B(e1*), nu_B(e2*)
-  const Sdf2H hA = sdf2h_of<0, kCls>(A, x2, e1L, tau, it);  // phi_A(e2*), nu_A(e1*) in A's frame
+  // the polyhedron of the pair class sums its planes without a shift while its own
+  // witness (at alpha on its edge's line, no sphere tracing, no soft pre-selection) is
+  // within a scaled distance of 60 of the edge, as the forward does
+  const bool guard = p.top_verts > 0 || p.top_edges > 0;
+  bool plain = false;
+  if (kCls != 0 && !nt && !guard) {
+    const float al = kCls == 1 ? o.a1 : o.a2;
+    const V3 te = kCls == 1 ? a1L - a0L : b1 - b0;
+    const float ex = fmaxf(fmaxf(-al, al - 1.f), 0.f) * F.k2;
+    plain = ex * ex * dot(te, te) <= 3600.f;
+  }
+  const Sdf2H hB = sdf2h_of<1, kCls>(B, e1, e2, tau, it, plain);   // phi_B(e1*), nu_B(e2*)
+  const Sdf2H hA = sdf2h_of<0, kCls>(A, x2, e1L, tau, it, plain);  // phi_A(e2*), nu_A(e1*) in A's frame
   const Sdf &SB1 = hB.f1, &SB2 = hB.f2, &SA2 = hA.f1, &SA1 = hA.f2;
   V3 nuB = normal_of(SB2.g, tau);
   V3 nuAL = normal_of(SA1.g, tau);
@@ -758,7 +772,6 @@ CM_HD QPBar ee_bwd(const Frame& F, const Body& A, const Body& B, const Params& p
   float nn1 = ex2((rowL - dbar_qp) * F.k2), nn2 = ex2((colL - dbar_qp) * F.k2);
   float con = o.con;
   // pre-selection's safeguard (Supplement B): each witness inside its own body
-  const bool guard = p.top_verts > 0 || p.top_edges > 0;
   const float sg1 = guard ? sigmoid(-SA1.phi * it) : 1.f, sg2 = guard ? sigmoid(-SB2.phi * it) : 1.f;
   const float pr1 = pen1, pr2 = pen2;  // the penetration indicators without the safeguard
   pen1 *= sg1;

@@ -248,11 +248,10 @@ __device__ __forceinline__ void vs_reverse_phase(const BwdPair P) {
   adj_reduce(adj, P.bs->adj);
 }
 
-// The K selected scores pass dL/d s^_k to their own candidates (threads < K).
+// The k-th selected score passes dL/d s^_k to its own candidate.
 template <int kCls>
-__device__ __forceinline__ void fixup_phase(const BwdPair P) {
+__device__ __forceinline__ void fixup_phase(const BwdPair P, const int k) {
   const PairShared& ps = *P.ps;
-  const int k = threadIdx.x;
   const int id = P.bs->sid[k];
   const float sx = P.bs->shatbar[k];
   const float zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -699,10 +698,14 @@ __global__ void __launch_bounds__(256, kMinBlocks) cm_bwd_kernel(const FwdArgs a
       ee_reverse_pass<KMAX, 0>(P, bs, rec, ss);
     }
     __syncthreads();
-    if (threadIdx.x < K) {
-      if (cls == 1) fixup_phase<1>(P);
-      else if (cls == 2) fixup_phase<2>(P);
-      else fixup_phase<0>(P);
+    {  // selected candidate k on lane k / nwarps of warp k % nwarps: each warp runs its
+       // own candidates' reverse, so vertex and edge candidates do not serialise in one warp
+      const int k = lane * nwarps + warp;
+      if (k < K) {
+        if (cls == 1) fixup_phase<1>(P, k);
+        else if (cls == 2) fixup_phase<2>(P, k);
+        else fixup_phase<0>(P, k);
+      }
     }
     __syncthreads();
     if (cls == 1) qp_phase<1>(P);

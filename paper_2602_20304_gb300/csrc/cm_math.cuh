@@ -362,6 +362,51 @@ CM_HD void sdf_planes2_h(V3 y1, V3 y2, const float4* P, int nP, float tau, Sdf& 
   H[5] = h * fmaf(Mxz_zz.y, i2, -gh.z * gh.z);
 }
 
+// sdf_planes2_h without a shift, for an edge pair whose y2 is the body's own witness
+// within a scaled distance of 60 of its own edge (the condition of sdf_planes_ee):
+// the sums at y2 then stay within 2^-60 .. nP 2^60, and every plane term is added
+// as it is read, with no running maximum.  At y1 (the other body's witness) the
+// plain sum S1 may overflow to +inf or underflow to 0; phi(y1) = tau ln S1 is then
+// +inf or -inf, so sigma(-phi(y1)/tau) is exactly 0 or 1 with derivative 0, and
+// the gradient at y1, which only multiplies that derivative, is returned as 0
+// whenever S1 lies outside 2^-100 .. 2^100 (there sigma' < 2^-100 / tau).
+CM_HD void sdf_planes2_h_ee(V3 y1, V3 y2, const float4* P, int nP, float tau, Sdf& o1, Sdf& o2,
+                            float (&H)[6]) {
+  const float2 X = make_float2(y1.x, y2.x), Y = make_float2(y1.y, y2.y), Z = make_float2(y1.z, y2.z);
+  float2 S = dup2(0.f), Gx = dup2(0.f), Gy = dup2(0.f), Gz = dup2(0.f);
+  float2 Mxx_yy = dup2(0.f), Mxy_yz = dup2(0.f), Mxz_zz = dup2(0.f);
+#pragma unroll 4
+  for (int f = 0; f < nP; ++f) {
+    const float4 q = P[f];
+    const float2 z = ffma2(dup2(q.x), X, ffma2(dup2(q.y), Y, ffma2(dup2(q.z), Z, dup2(-q.w))));
+    const float2 e = make_float2(ex2(z.x), ex2(z.y));
+    S = fadd2(S, e);
+    Gx = ffma2(e, dup2(q.x), Gx);
+    Gy = ffma2(e, dup2(q.y), Gy);
+    Gz = ffma2(e, dup2(q.z), Gz);
+    const float2 txy = make_float2(e.y * q.x, e.y * q.y);
+    const float tz = e.y * q.z;
+    Mxx_yy = ffma2(txy, make_float2(q.x, q.y), Mxx_yy);
+    Mxy_yz = ffma2(txy, make_float2(q.y, q.z), Mxy_yz);
+    Mxz_zz = ffma2(make_float2(txy.x, tz), make_float2(q.z, q.z), Mxz_zz);
+  }
+  const float t = tau * kLn2;
+  o1.phi = t * lg2(S.x);
+  const bool in1 = S.x >= 0x1p-100f && S.x <= 0x1p100f;
+  o1.g = in1 ? v3(Gx.x, Gy.x, Gz.x) * (t * rcp(S.x)) : v3(0.f, 0.f, 0.f);
+  const float i2 = rcp(S.y);
+  o2.phi = t * lg2(S.y);
+  const V3 gh = v3(Gx.y * i2, Gy.y * i2, Gz.y * i2);  // G / S at y2, scaled units
+  o2.g = gh * t;
+  const float h = t * kLn2;
+  H[0] = h * fmaf(Mxx_yy.x, i2, -gh.x * gh.x);
+  H[1] = h * fmaf(Mxy_yz.x, i2, -gh.x * gh.y);
+  H[2] = h * fmaf(Mxz_zz.x, i2, -gh.x * gh.z);
+  H[3] = h * fmaf(Mxx_yy.y, i2, -gh.y * gh.y);
+  H[4] = h * fmaf(Mxy_yz.y, i2, -gh.y * gh.z);
+  H[5] = h * fmaf(Mxz_zz.y, i2, -gh.z * gh.z);
+}
+
 // One point of sdf_planes2_h: value, gradient and Hessian (xx, xy, xz, yy, yz, zz).
 CM_HD void sdf_planes_h(V3 y, const float4* P, int nP, float tau, Sdf& o, float (&H)[6]) {
   float m = -3.0e38f, S = 0.f;
