@@ -667,9 +667,9 @@ def witness_rates(api, n=10_000_000, steps=5):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pair of one forward and
 # one adjoint launch of the current kernels on the 65536-pair headline batch, from one
 # single-pass ncu capture of each (`--profile-case headline`, default launch shape):
-# forward 0.520 + 3.016 GB, adjoint 7.520 + 13.416 GB per launch.
-FWD_TRAFFIC_PER_PAIR = (0.519528e9 + 3.016125e9) / 65536
-BWD_TRAFFIC_PER_PAIR = (7.519558e9 + 13.416463e9) / 65536
+# forward 0.523 + 3.018 GB, adjoint 8.119 + 13.788 GB per launch.
+FWD_TRAFFIC_PER_PAIR = (0.522727e9 + 3.017795e9) / 65536
+BWD_TRAFFIC_PER_PAIR = (8.119439e9 + 13.788441e9) / 65536
 
 
 # Workloads of the ncu captures: the 4096-pair hull-vs-primitive setting (``--set full``
