@@ -693,17 +693,6 @@ struct QPBar {
   float a1, a2, con;
 };
 
-// The QP's reverse: (abar1, abar2, conbar) through the smoothed active set, Q and c to
-// the four endpoints, and from there to the parameters.
-CM_HD void witness_qp_bwd(const Frame& F, const Body& A, const Body& B, const Params& p, const EEGeom& g,
-                          const QPBar& qb, Adj& adj, float* eAexp, float* eBexp) {
-  const QPPre q = qp_setup(xyz(g.a0), xyz(g.a1), xyz(g.b0), xyz(g.b1), p.w_reg);
-  const V3 z = v3(0.f, 0.f, 0.f);
-  V3 a0b = z, a1b = z, b0b = z, b1b = z;
-  qp_bwd(q, p.w_reg, p, qb.a1, qb.a2, qb.con, a0b, a1b, b0b, b1b);
-  endpoints_bwd(F, A, B, g, a0b, a1b, z, z, b0b, b1b, adj, eAexp, eBexp);
-}
-
 // ---------------------------------------------------------------- E-E element
 // Recomputes both candidates of an edge pair, asks `up` for their upstream
 // adjoints, and backpropagates them to the witness points and from there, at the
