@@ -1,16 +1,17 @@
 // Host build of the adjoint's E-E element (ee_bwd: both candidates of an edge
 // pair recomputed and reversed; ee_qp_bwd: the QP's reverse; pose_epilogue: the
-// chain to the quaternion and translation) for tests/test_host_ee_element.py, on a
-// pair whose A is a convex polyhedron and B a box (the kernels' hull-vs-primitive
-// pair class) with one edge each, so that both nearest-neighbour indicators are 1.
-// Input: "tau F", F plane rows (n_x n_y n_z c, A's frame, unnormalised by tau), then
-// per line: qA(4) tA(3) a0(3) a1(3) (A's edge, A's frame) u0(3) u1(3) (B's edge as box
-// template rows) hB(3) (B's half-extents) yb1(8) sb1 yb2(8) sb2 (upstream adjoints of
-// both candidates' rows (p, d, n, w) and scores s = -w d); B sits at the origin
-// unrotated.  Output per line: y1(8) s1 y2(8) s2, the gradient of
-// yb1 . y1 + sb1 s1 + yb2 . y2 + sb2 s2 with respect to qA(4), tA(3) and hB(3), and 1
-// if the polyhedron's plain sums were taken (its witness within a scaled distance of
-// 60 of its edge), else 0.
+// chain to the quaternion and translation) for tests/test_host_ee_element.py, on the
+// kernels' two specialised pair classes -- class 1: A a convex polyhedron, B a box;
+// class 2: A a box, B a convex polyhedron -- with one edge each, so that both
+// nearest-neighbour indicators are 1.  Input: "tau F cls", F plane rows (n_x n_y n_z c
+// in the polyhedron's frame, unnormalised by tau), then per line: qA(4) tA(3) a0(3)
+// a1(3) b0(3) b1(3) h(3) yb1(8) sb1 yb2(8) sb2, where the edges are in their own
+// body's frame (a box edge as template rows, scaled by the box's half-extents h) and
+// yb, sb are the upstream adjoints of both candidates' rows (p, d, n, w) and scores
+// s = -w d; B sits at the origin unrotated.  Output per line: y1(8) s1 y2(8) s2, the
+// gradient of yb1 . y1 + sb1 s1 + yb2 . y2 + sb2 s2 with respect to qA(4), tA(3) and
+// h(3), and 1 if the polyhedron's plain sums were taken (its witness within a scaled
+// distance of 60 of its edge), else 0.
 #include <cstdio>
 #include <vector>
 
@@ -35,8 +36,8 @@ struct Upstream {
 
 int main() {
   float tau;
-  int F;
-  if (std::scanf("%f %d", &tau, &F) != 2 || F <= 0) return 2;
+  int F, cls;
+  if (std::scanf("%f %d %d", &tau, &F, &cls) != 3 || F <= 0 || (cls != 1 && cls != 2)) return 2;
   const float k2 = kLog2e / tau;
   std::vector<float4> P(F);
   for (int f = 0; f < F; ++f) {
@@ -61,11 +62,14 @@ int main() {
     Fr.tau = tau;
     Fr.inv_tau = 1.f / tau;
     Fr.k2 = k2;
-    const Body A{kHull, v3(1.f, 1.f, 1.f), P.data(), F};
-    const V3 hB = v3(v[19], v[20], v[21]);
-    const Body B{kBox, hB, nullptr, 0};
-    const V3 a0L = v3(v[7], v[8], v[9]), a1L = v3(v[10], v[11], v[12]);
-    const V3 b0 = v3(v[13] * hB.x, v[14] * hB.y, v[15] * hB.z), b1 = v3(v[16] * hB.x, v[17] * hB.y, v[18] * hB.z);
+    const V3 h = v3(v[19], v[20], v[21]);
+    const Body hull{kHull, v3(1.f, 1.f, 1.f), P.data(), F};
+    const Body box{kBox, h, nullptr, 0};
+    const Body& A = cls == 1 ? hull : box;
+    const Body& B = cls == 1 ? box : hull;
+    const V3 sa = cls == 1 ? v3(1.f, 1.f, 1.f) : h, sb = cls == 1 ? h : v3(1.f, 1.f, 1.f);
+    const V3 a0L = v3(v[7] * sa.x, v[8] * sa.y, v[9] * sa.z), a1L = v3(v[10] * sa.x, v[11] * sa.y, v[12] * sa.z);
+    const V3 b0 = v3(v[13] * sb.x, v[14] * sb.y, v[15] * sb.z), b1 = v3(v[16] * sb.x, v[17] * sb.y, v[18] * sb.z);
     const V3 a0 = mul(Fr.R, a0L) + Fr.t, a1 = mul(Fr.R, a1L) + Fr.t;
     EEGeom g;
     g.a0 = make_float4(a0.x, a0.y, a0.z, 0.f);
@@ -82,24 +86,34 @@ int main() {
     adj_zero(adj);
     EECand cand;
     Upstream up{v, &cand};
-    ee_bwd<1>(Fr, A, B, p, g, 0.f, 0.f, &o, up, t1, t2, adj, nullptr, nullptr, &dqp);
-    adj_zero(adj);
-    const QPBar qb = ee_bwd<1>(Fr, A, B, p, g, dqp, dqp, &o, up, t1, t2, adj);
-    // distance-matrix adjoint of a 1 x 1 matrix: (nn1 R - t1 + nn2 C - t2) / tau = 0
-    ee_qp_bwd<1>(Fr, A, B, p, g, ((t1 - t1) + (t2 - t2)) * Fr.inv_tau, o, qb, adj);
+    QPBar qb;
+    if (cls == 1) {
+      ee_bwd<1>(Fr, A, B, p, g, 0.f, 0.f, &o, up, t1, t2, adj, nullptr, nullptr, &dqp);
+      adj_zero(adj);
+      qb = ee_bwd<1>(Fr, A, B, p, g, dqp, dqp, &o, up, t1, t2, adj);
+      // distance-matrix adjoint of a 1 x 1 matrix: (nn1 R - t1 + nn2 C - t2) / tau = 0
+      ee_qp_bwd<1>(Fr, A, B, p, g, ((t1 - t1) + (t2 - t2)) * Fr.inv_tau, o, qb, adj);
+    } else {
+      ee_bwd<2>(Fr, A, B, p, g, 0.f, 0.f, &o, up, t1, t2, adj, nullptr, nullptr, &dqp);
+      adj_zero(adj);
+      qb = ee_bwd<2>(Fr, A, B, p, g, dqp, dqp, &o, up, t1, t2, adj);
+      ee_qp_bwd<2>(Fr, A, B, p, g, ((t1 - t1) + (t2 - t2)) * Fr.inv_tau, o, qb, adj);
+    }
     const M3 RB = quat_rot(1.f, 0.f, 0.f, 0.f);
     const float Rout[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float gp[14];
     pose_epilogue(pose, Fr.R, RB, adj, Rout, v3(0.f, 0.f, 0.f), gp);
-    const V3 te = a1L - a0L;
-    const float ex = fmaxf(fmaxf(-o.a1, o.a1 - 1.f), 0.f) * k2;
+    const V3 te = cls == 1 ? a1L - a0L : b1 - b0;
+    const float al = cls == 1 ? o.a1 : o.a2;
+    const float ex = fmaxf(fmaxf(-al, al - 1.f), 0.f) * k2;
     const int plain = ex * ex * dot(te, te) <= 3600.f;
     for (int i = 0; i < 8; ++i) std::printf("%.9g ", cand.y1[i]);
     std::printf("%.9g ", cand.s1);
     for (int i = 0; i < 8; ++i) std::printf("%.9g ", cand.y2[i]);
     std::printf("%.9g ", cand.s2);
     for (int i = 0; i < 7; ++i) std::printf("%.9g ", gp[i]);
-    std::printf("%.9g %.9g %.9g %d\n", adj.dB.x, adj.dB.y, adj.dB.z, plain);
+    const V3 dh = cls == 1 ? adj.dB : adj.dA;
+    std::printf("%.9g %.9g %.9g %d\n", dh.x, dh.y, dh.z, plain);
   }
   return 0;
 }

@@ -1,7 +1,7 @@
 """The adjoint's E-E element, built for the host, against the FP64 oracle.
 
 For one edge of a convex polyhedron A and one edge of a box B (the kernels'
-hull-vs-primitive pair class) the element recomputes both witnesses' candidates
+hull-vs-primitive pair class; also the other way round) the element recomputes both witnesses' candidates
 (Sec. IV-D3: QP witnesses, signed distances and normals through the soft sign, the
 penetration and clashing indicators, the weights) and reverses them, the QP and the
 pose chain by hand (``ee_bwd``, ``ee_qp_bwd``, ``pose_epilogue``).  With one edge per
@@ -66,6 +66,13 @@ def f32(x):
     return np.asarray(x, dtype=np.float32).astype(np.float64)
 
 
+def relative_to_b(p):
+    """A's pose (q, t) in B's frame from a pair's world poses (14,)."""
+    qB = p[7:11] / np.linalg.norm(p[7:11])
+    qA = quat_mul(qB * np.array([1, -1, -1, -1]), p[0:4] / np.linalg.norm(p[0:4]))
+    return f32(qA), f32(rot(qB).T @ (p[4:7] - p[11:14]))
+
+
 def box_pairs(tau, n_pairs, seed):
     """Placed hull-vs-box pairs, re-expressed with B at the origin: (hull, box geometry,
     qA, tA, hB) with every number FP32-representable."""
@@ -75,19 +82,16 @@ def box_pairs(tau, n_pairs, seed):
         ga, gb = w.geoms[w.pair_geoms[i, 0]], w.geoms[w.pair_geoms[i, 1]]
         if gb.kind != synth.KIND_BOX:
             continue
-        p = w.poses[i].astype(np.float64)
-        qB = p[7:11] / np.linalg.norm(p[7:11])
-        qA = quat_mul(qB * np.array([1, -1, -1, -1]), p[0:4] / np.linalg.norm(p[0:4]))
-        tA = rot(qB).T @ (p[4:7] - p[11:14])
-        out.append((ga, gb, f32(qA), f32(tA), f32(w.dims[i, 3:])))
+        qA, tA = relative_to_b(w.poses[i].astype(np.float64))
+        out.append((ga, gb, qA, tA, f32(w.dims[i, 3:])))
         if len(out) == n_pairs:
             break
     return out
 
 
-def run_hull(exe, ga, tau, rows):
-    pl = f32(ga.planes)
-    lines = [f"{tau!r} {len(pl)}"] + [" ".join(f"{v:.9g}" for v in r) for r in pl]
+def run_hull(exe, hull, tau, rows, cls=1):
+    pl = f32(hull.planes)
+    lines = [f"{tau!r} {len(pl)} {cls}"] + [" ".join(f"{v:.9g}" for v in r) for r in pl]
     lines += [" ".join(f"{v:.9g}" for v in f32(r)) for r in rows]
     res = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
     out = np.array([[float(v) for v in ln.split()] for ln in res.stdout.strip().splitlines()])
@@ -110,10 +114,13 @@ def within_bar(e):
     return e["p"] <= 1e-5 and e["d"] <= 1e-5 and e["n"] <= 1e-4 and e["w"] <= 1e-4 and e["grad"] <= 1e-3
 
 
-def oracle_element(ga, gb, ea, eb, qA, tA, hB, tau, ybar):
-    x = torch.tensor(np.r_[qA, tA, hB], dtype=F64, requires_grad=True)
-    A = _Body(ga, x[:7], torch.ones(3, dtype=F64), tau)
-    B = _Body(gb, torch.tensor([1.0, 0, 0, 0, 0, 0, 0], dtype=F64), x[7:], tau)
+def oracle_element(ga, gb, ea, eb, qA, tA, h, tau, ybar, cls=1):
+    """Rows and gradient (qA, tA, h) of the oracle's element; h are the half-extents of
+    the box, B in class 1 and A in class 2."""
+    x = torch.tensor(np.r_[qA, tA, h], dtype=F64, requires_grad=True)
+    one = torch.ones(3, dtype=F64)
+    A = _Body(ga, x[:7], one if cls == 1 else x[7:], tau)
+    B = _Body(gb, torch.tensor([1.0, 0, 0, 0, 0, 0, 0], dtype=F64), x[7:] if cls == 1 else one, tau)
     a0, a1 = A.verts[A.edges[ea, 0]][None], A.verts[A.edges[ea, 1]][None]
     b0, b1 = B.verts[B.edges[eb, 0]][None], B.verts[B.edges[eb, 1]][None]
     c = ee_candidates(a0, a1, b0, b1, A.sdf, B.sdf, tau)
@@ -190,3 +197,37 @@ def test_long_edge_takes_both_sums(exe):
         want_vals, want_grad = oracle_element(ga, gb, ea, eb, qA, tA, hB, tau, ybar)
         e = element_errors(row[:18], want_vals, row[18:28], want_grad)
         assert within_bar(e), e
+
+
+@pytest.mark.parametrize("tau", [1e-2, 1e-1])
+def test_box_against_hull_element_matches_the_oracle(exe, tau):
+    """The other specialised pair class: A a box, B the hull of 32 points on the unit
+    sphere (the box-vs-hull differentiation setting), with B's polyhedron taking the
+    plain sums; the dims gradient is the box's (A's)."""
+    rng = np.random.default_rng(int(round(-np.log10(tau))) + 80)
+    w = synth.config_box_vs_sphere_hull(n=4, seed=synth.SEED_BASE + 33, tau=tau)
+    plain_seen, n_el = 0, 0
+    for i in range(w.n_pairs):
+        ga, gb = w.geoms[w.pair_geoms[i, 0]], w.geoms[w.pair_geoms[i, 1]]
+        qA, tA = relative_to_b(w.poses[i].astype(np.float64))
+        hA = f32(w.dims[i, :3])
+        va = ga.verts[:, :3].astype(np.float64) * hA @ rot(qA).T + tA
+        vb = gb.verts[:, :3].astype(np.float64)
+        d = np.array([[np.linalg.norm(0.5 * (va[a0] + va[a1]) - 0.5 * (vb[b0] + vb[b1]))
+                       for b0, b1 in gb.edges] for a0, a1 in ga.edges])
+        picks = list(np.argsort(d, axis=None)[:4]) + list(rng.choice(d.size, 4, replace=False))
+        rows, meta = [], []
+        for flat in picks:
+            ea, eb = np.unravel_index(flat, d.shape)
+            ybar = rng.normal(size=18)
+            rows.append(np.r_[qA, tA, ga.verts[ga.edges[ea, 0], :3], ga.verts[ga.edges[ea, 1], :3],
+                              gb.verts[gb.edges[eb, 0], :3], gb.verts[gb.edges[eb, 1], :3], hA, ybar])
+            meta.append((ea, eb, ybar))
+        out = run_hull(exe, gb, tau, rows, cls=2)
+        for row, (ea, eb, ybar) in zip(out, meta):
+            plain_seen += int(row[28])
+            n_el += 1
+            want_vals, want_grad = oracle_element(ga, gb, ea, eb, qA, tA, hA, tau, ybar, cls=2)
+            e = element_errors(row[:18], want_vals, row[18:28], want_grad)
+            assert within_bar(e), e
+    assert plain_seen == n_el
